@@ -1,0 +1,254 @@
+"""Plain FP64 CPU oracle of the geometric-multigrid pieces (test infrastructure only).
+
+Nothing on the product path imports this module. It states, as plainly as possible, what each
+step of the V-cycle preconditioner computes, so that the GPU kernels can be compared with it one
+step at a time:
+
+  * coarse grids by re-discretisation with each material field transferred on its own
+    (Sec. "Geometric vs Algebraic Multigrid");
+  * restriction = normalised bilinear-weighted accumulation (Sec. "Restriction and Prolongation
+    Operators", the normalised-sum equation), built here by brute force from the staggered
+    positions; prolongation = bilinear interpolation from the four surrounding coarse points;
+  * damped red-black Gauss-Seidel (Sec. "Smoothers", eq. sor_update) on the velocity block;
+  * the V-cycle of eq. multigrid_levels with a direct coarsest solve;
+  * one Uzawa sweep as the preconditioner M^-1 (Sec. "Uzawa Iteration as a Fixed Point Method").
+
+Readings (the paper is silent or inconsistent; each is listed with the design notes):
+  * only fine locations that are unknowns (velocity) or real nodes / cells (viscosity) enter a
+    restriction sum, and the normalisation compensates for the truncated support at walls;
+  * coarse ghost values used by the prolongation follow the homogeneous boundary rule;
+  * viscosity is coarsened with the same normalised bilinear weights, arithmetically or on
+    log(eta) (geometric mean);
+  * RBGS colour order: vx-red, vx-black, vy-red, vy-black with colour (i + j) mod 2;
+  * pressure sign of M^-1: the paper's splitting puts -(alpha eta)^-1 in the pressure block, but
+    with L negative definite (as the paper states) D L^-1 G is negative semi-definite and that
+    sign makes the stationary Uzawa iteration diverge. We take z_p = alpha eta_c (r_p - D z_v),
+    i.e. the surrogate carries the sign of the operator it stands for; the test suite pins this by
+    showing the stationary iteration converges with it and diverges with the literal sign.
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .stokes import Grid, assemble
+
+ETA_ARITH, ETA_GEOM = 0, 1
+
+
+def coarsen_grid(g):
+    if g.nx % 2 or g.ny % 2:
+        raise ValueError("factor-2 coarsening needs even cell counts")
+    return Grid(g.nx // 2, g.ny // 2, g.Lx, g.Ly, g.bc)
+
+
+def n_levels(nx, ny, coarsest_min):
+    """Levels of a factor-2 hierarchy: halve while both counts are even and the short side stays
+    >= coarsest_min after halving."""
+    L = 1
+    while nx % 2 == 0 and ny % 2 == 0 and min(nx, ny) // 2 >= coarsest_min:
+        nx //= 2; ny //= 2; L += 1
+    return L
+
+
+# ---- staggered positions --------------------------------------------------------------------
+def positions(g, fld):
+    if fld == "vx":
+        return g.vx_j * g.dx, (g.vx_i - 0.5) * g.dy
+    if fld == "vy":
+        return (g.vy_j - 0.5) * g.dx, g.vy_i * g.dy
+    raise ValueError(fld)
+
+
+def _unknown_lookup(g, fld):
+    return g.idx_vx if fld == "vx" else g.idx_vy
+
+
+def restriction_matrix(fine, coarse, fld):
+    """R with (R r)_K = sum_k w_Kk r_k / sum_k w_Kk, w = (1-|dx|/Hx)(1-|dy|/Hy) over fine unknowns."""
+    Xc, Yc = positions(coarse, fld)
+    Xf, Yf = positions(fine, fld)
+    idx = _unknown_lookup(fine, fld)
+    base = 0 if fld == "vx" else fine.n_vx
+    # candidate fine indices: every fine unknown whose position is within one coarse spacing
+    ci = coarse.vx_i if fld == "vx" else coarse.vy_i
+    cj = coarse.vx_j if fld == "vx" else coarse.vy_j
+    rows, cols, vals = [], [], []
+    for di in range(-3, 4):
+        for dj in range(-3, 4):
+            fi = 2 * ci + di
+            fj = 2 * cj + dj
+            ok = (fi >= 0) & (fi < fine.ny + 2) & (fj >= 0) & (fj < fine.nx + 2)
+            fi_ = np.where(ok, fi, 0); fj_ = np.where(ok, fj, 0)
+            col = idx[fi_, fj_]
+            ok &= col >= 0
+            col = col - base
+            xf = np.where(ok, Xf[np.maximum(col, 0)], 0.0)
+            yf = np.where(ok, Yf[np.maximum(col, 0)], 0.0)
+            wx = 1 - np.abs(xf - Xc) / coarse.dx
+            wy = 1 - np.abs(yf - Yc) / coarse.dy
+            ok &= (wx > 1e-9) & (wy > 1e-9)          # inside the bilinear support
+            w = wx * wy
+            k = np.nonzero(ok)[0]
+            rows.append(k); cols.append(col[k]); vals.append(w[k])
+    nC = len(Xc); nF = len(Xf)
+    R = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(nC, nF))
+    R.sum_duplicates()
+    s = np.asarray(R.sum(axis=1)).ravel()
+    return sp.diags(1.0 / s) @ R
+
+
+def prolongation_matrix(fine, coarse, fld):
+    """P: bilinear interpolation of a coarse correction at every fine unknown from the four
+    surrounding coarse points of the same staggered family (ghosts by the homogeneous rule)."""
+    Xf, Yf = positions(fine, fld)
+    H, K = coarse.dx, coarse.dy
+    if fld == "vx":
+        fx, fy = Xf / H, Yf / K + 0.5          # coarse vx at X = J*H, Y = (I - 1/2)*K
+    else:
+        fx, fy = Xf / H + 0.5, Yf / K          # coarse vy at X = (J - 1/2)*H, Y = I*K
+    J0 = np.floor(fx + 1e-12).astype(np.int64); I0 = np.floor(fy + 1e-12).astype(np.int64)
+    tx = fx - J0; ty = fy - I0
+    rows, cols, vals = [], [], []
+    nF = len(Xf)
+    for di, wy in ((0, 1 - ty), (1, ty)):
+        for dj, wx in ((0, 1 - tx), (1, tx)):
+            w = wy * wx
+            I = I0 + di; J = J0 + dj
+            m = w > 1e-14
+            if fld == "vx":
+                col, c, _, keep = coarse._resolve_vx(I[m], J[m], w[m])
+            else:
+                col, c, _, keep = coarse._resolve_vy(I[m], J[m], w[m])
+                col = col - coarse.n_vx
+            r = np.nonzero(m)[0]
+            rows.append(r[keep]); cols.append(col[keep]); vals.append(c[keep])
+    nC = coarse.n_vx if fld == "vx" else coarse.n_vy
+    P = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(nF, nC))
+    P.sum_duplicates()
+    return P
+
+
+def _material_restrict(fine, coarse, a, centred):
+    """Normalised bilinear restriction of a material field (cells if centred, else nodes)."""
+    nx, ny = coarse.nx, coarse.ny
+    out = np.zeros((ny + 2, nx + 2))
+    if centred:
+        I, J = np.meshgrid(np.arange(1, ny + 1), np.arange(1, nx + 1), indexing="ij")
+        Xc, Yc = (J - 0.5) * coarse.dx, (I - 0.5) * coarse.dy
+        lo_i, hi_i, lo_j, hi_j = 1, fine.ny, 1, fine.nx
+        posf = lambda i, j: ((j - 0.5) * fine.dx, (i - 0.5) * fine.dy)
+    else:
+        I, J = np.meshgrid(np.arange(0, ny + 1), np.arange(0, nx + 1), indexing="ij")
+        Xc, Yc = J * coarse.dx, I * coarse.dy
+        lo_i, hi_i, lo_j, hi_j = 0, fine.ny, 0, fine.nx
+        posf = lambda i, j: (j * fine.dx, i * fine.dy)
+    acc = np.zeros(I.shape); wsum = np.zeros(I.shape)
+    for di in range(-3, 4):
+        for dj in range(-3, 4):
+            fi = 2 * I + di; fj = 2 * J + dj
+            ok = (fi >= lo_i) & (fi <= hi_i) & (fj >= lo_j) & (fj <= hi_j)
+            xf, yf = posf(fi, fj)
+            wx = 1 - np.abs(xf - Xc) / coarse.dx
+            wy = 1 - np.abs(yf - Yc) / coarse.dy
+            ok &= (wx > 1e-9) & (wy > 1e-9)          # inside the bilinear support
+            w = wx * wy
+            vals = a[np.where(ok, fi, lo_i), np.where(ok, fj, lo_j)]
+            acc += np.where(ok, w * vals, 0.0); wsum += np.where(ok, w, 0.0)
+    out[I, J] = acc / wsum
+    return out
+
+
+def coarsen_eta(fine, coarse, eta_n, eta_c, mode=ETA_ARITH):
+    if mode == ETA_GEOM:
+        en = np.exp(_material_restrict(fine, coarse, np.log(np.where(eta_n > 0, eta_n, 1.0)), False))
+        ec = np.exp(_material_restrict(fine, coarse, np.log(np.where(eta_c > 0, eta_c, 1.0)), True))
+        en[coarse.ny + 1, :] = 0; en[:, coarse.nx + 1] = 0
+        ec[0, :] = 0; ec[:, 0] = 0; ec[coarse.ny + 1, :] = 0; ec[:, coarse.nx + 1] = 0
+        return en, ec
+    return (_material_restrict(fine, coarse, eta_n, False),
+            _material_restrict(fine, coarse, eta_c, True))
+
+
+# ---- smoother --------------------------------------------------------------------------------
+def colour_sets(g):
+    """Row index sets of the four half-sweeps in order vx-red, vx-black, vy-red, vy-black."""
+    vx_red = np.nonzero((g.vx_i + g.vx_j) % 2 == 0)[0]
+    vx_blk = np.nonzero((g.vx_i + g.vx_j) % 2 == 1)[0]
+    vy_red = g.n_vx + np.nonzero((g.vy_i + g.vy_j) % 2 == 0)[0]
+    vy_blk = g.n_vx + np.nonzero((g.vy_i + g.vy_j) % 2 == 1)[0]
+    return [vx_red, vx_blk, vy_red, vy_blk]
+
+
+def rbgs_sweep(L, f, x, sets, omega):
+    """One damped red-black Gauss-Seidel sweep: for each colour set S in order,
+    x_S += omega * (f_S - (L x)_S) / diag(L)_S (points of one set do not couple)."""
+    x = x.copy()
+    d = L.diagonal()
+    for S in sets:
+        r = f[S] - L[S] @ x
+        x[S] += omega * r / d[S]
+    return x
+
+
+# ---- hierarchy and V-cycle ---------------------------------------------------------------------
+class Hierarchy:
+    def __init__(self, grid, eta_n, eta_c, coarsest_min=4, eta_mode=ETA_ARITH, n_lev=None):
+        L = n_levels(grid.nx, grid.ny, coarsest_min) if n_lev is None else n_lev
+        self.grids = [grid]; self.eta = [(eta_n, eta_c)]
+        for _ in range(L - 1):
+            c = coarsen_grid(self.grids[-1])
+            en, ec = coarsen_eta(self.grids[-1], c, *self.eta[-1], mode=eta_mode)
+            self.grids.append(c); self.eta.append((en, ec))
+        self.L = [assemble(g, en, ec, velocity_only=True).A.tocsr() for g, (en, ec) in zip(self.grids, self.eta)]
+        self.sets = [colour_sets(g) for g in self.grids]
+        self.R = []; self.P = []
+        for f, c in zip(self.grids[:-1], self.grids[1:]):
+            self.R.append(sp.block_diag([restriction_matrix(f, c, "vx"), restriction_matrix(f, c, "vy")]).tocsr())
+            self.P.append(sp.block_diag([prolongation_matrix(f, c, "vx"), prolongation_matrix(f, c, "vy")]).tocsr())
+        self.coarse_lu = spla.splu(self.L[-1].tocsc())
+
+    @property
+    def nlev(self):
+        return len(self.grids)
+
+
+def vcycle(h, f, nu1=2, nu2=2, omega=1.0, level=0):
+    """One V-cycle for L x = f at `level` from x = 0 (eq. multigrid_levels, steps (1)-(6))."""
+    if level == h.nlev - 1:
+        return h.coarse_lu.solve(f)
+    L = h.L[level]
+    x = np.zeros_like(f)
+    for _ in range(nu1):
+        x = rbgs_sweep(L, f, x, h.sets[level], omega)             # (1) pre-smoothing
+    r = f - L @ x                                                 # (2) residual
+    fc = h.R[level] @ r                                           # (3) restriction
+    dc = vcycle(h, fc, nu1, nu2, omega, level + 1)                # (4) coarse solve / recursion
+    x = x + h.P[level] @ dc                                       # (5) prolongation + correction
+    for _ in range(nu2):
+        x = rbgs_sweep(L, f, x, h.sets[level], omega)             # (6) post-smoothing
+    return x
+
+
+def divergence(grid, zv):
+    """D z_v at every pressure unknown (continuity rows of the assembled system, velocity part)."""
+    from .stokes import vector_to_fields
+    vx, vy, _ = vector_to_fields(grid, np.concatenate([zv, np.zeros(grid.n_p)]), fill_ghosts=True)
+    i, j = grid.p_i, grid.p_j
+    jm = j - 1
+    if grid.periodic:
+        jm = np.where(jm == 0, grid.nx, jm)
+        vx = vx.copy(); vx[:, grid.nx] = vx[:, 0]
+    return (vx[i, j] - vx[i, jm]) / grid.dx + (vy[i, j] - vy[i - 1, j]) / grid.dy
+
+
+def uzawa_precond(h, r, eta_c, alpha=0.6, nu1=2, nu2=2, omega=1.0, literal_sign=False):
+    """z = M^-1 r for one Uzawa sweep: z_v = V-cycle(L, r_v), z_p = alpha eta_c (r_p - D z_v),
+    then the mean of z_p is removed (Eq. pressure_normalization). `literal_sign` flips to the
+    paper's printed sign alpha eta_c (D z_v - r_p) (used only to demonstrate the reading)."""
+    g = h.grids[0]
+    zv = vcycle(h, r[:g.n_v], nu1, nu2, omega)
+    e = g.eta_c_at(eta_c, g.p_i, g.p_j)
+    dz = divergence(g, zv)
+    zp = alpha * e * ((dz - r[g.n_v:]) if literal_sign else (r[g.n_v:] - dz))
+    zp -= zp.mean()
+    return np.concatenate([zv, zp])

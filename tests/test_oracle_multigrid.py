@@ -1,0 +1,169 @@
+"""Pins of the oracle's multigrid pieces (CPU only)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import stokes as S
+from oracle import multigrid as M
+from synth import sinker
+
+
+def rand_eta(nx, ny, seed, lo=-1, hi=1):
+    rng = np.random.default_rng(seed)
+    return 10.0 ** rng.uniform(lo, hi, (ny + 2, nx + 2)), 10.0 ** rng.uniform(lo, hi, (ny + 2, nx + 2))
+
+
+@pytest.mark.parametrize("fld", ["vx", "vy"])
+def test_restriction_preserves_constants_and_is_scaled_transpose(fld):
+    fine, coarse = S.Grid(16, 12), S.Grid(8, 6)
+    R = M.restriction_matrix(fine, coarse, fld)
+    P = M.prolongation_matrix(fine, coarse, fld)
+    assert np.allclose(R @ np.ones(R.shape[1]), 1.0, atol=1e-15)
+    # interior: weights [1,2,1]/4 (node direction) x [1,3,3,1]/8 (cell direction) = P^T / 4
+    Xc, Yc = M.positions(coarse, fld)
+    inner = np.nonzero((Xc > 2 * coarse.dx) & (Xc < coarse.Lx - 2 * coarse.dx) &
+                       (Yc > 2 * coarse.dy) & (Yc < coarse.Ly - 2 * coarse.dy))[0]
+    assert len(inner) > 4
+    Rd, Pd = R.toarray(), P.toarray()
+    assert np.allclose(Rd[inner], Pd.T[inner] / 4.0, atol=1e-15)
+    row = Rd[inner[0]]
+    assert sorted(np.round(row[row > 0] * 32).astype(int).tolist()) == sorted([1, 3, 3, 1, 2, 6, 6, 2, 1, 3, 3, 1])
+
+
+@pytest.mark.parametrize("fld", ["vx", "vy"])
+def test_prolongation_exact_on_bilinear(fld):
+    fine, coarse = S.Grid(16, 12, 2.0, 1.5), S.Grid(8, 6, 2.0, 1.5)
+    P = M.prolongation_matrix(fine, coarse, fld)
+    Xc, Yc = M.positions(coarse, fld)
+    Xf, Yf = M.positions(fine, fld)
+    fn = lambda x, y: 0.3 + 1.7 * x - 0.9 * y + 0.4 * x * y
+    pf = P @ fn(Xc, Yc)
+    # points whose four coarse neighbours are all unknowns
+    ok = (Xf > coarse.dx) & (Xf < coarse.Lx - coarse.dx) & (Yf > coarse.dy) & (Yf < coarse.Ly - coarse.dy)
+    assert ok.sum() > 10
+    assert np.allclose(pf[ok], fn(Xf, Yf)[ok], atol=1e-13)
+    # each row's weights sum to one away from walls (constants are reproduced)
+    assert np.allclose((P @ np.ones(P.shape[1]))[ok], 1.0)
+
+
+def test_prolongation_boundary_rule():
+    """At the first fine row under a free-slip (no-slip) wall the mirrored coarse ghost gives
+    weight 3/4 + 1/4 (3/4 - 1/4) on the first coarse row."""
+    for kind, expect in ((S.FREE_SLIP, 1.0), (S.NO_SLIP, 0.5)):
+        bc = S.BC(kind=(kind,) * 4)
+        fine, coarse = S.Grid(8, 8, bc=bc), S.Grid(4, 4, bc=bc)
+        P = M.prolongation_matrix(fine, coarse, "vx").toarray()
+        r = fine.idx_vx[1, 2]
+        c = coarse.idx_vx[1, 1]
+        assert P[r, c] == pytest.approx(expect)
+
+
+def test_eta_coarsening():
+    fine, coarse = S.Grid(16, 8, 2.0, 1.0), S.Grid(8, 4, 2.0, 1.0)
+    c = np.full((10, 18), 3.5)
+    en, ec = M.coarsen_eta(fine, coarse, c, c)
+    assert np.allclose(en[:5, :9], 3.5) and np.allclose(ec[1:5, 1:9], 3.5)
+    en_g, ec_g = M.coarsen_eta(fine, coarse, c, c, M.ETA_GEOM)
+    assert np.allclose(en_g[:5, :9], 3.5) and np.allclose(ec_g[1:5, 1:9], 3.5)
+    # geometric = exp(arithmetic of log)
+    a, b = rand_eta(16, 8, 7)
+    ga = M.coarsen_eta(fine, coarse, a, b, M.ETA_GEOM)
+    la = M.coarsen_eta(fine, coarse, np.log(a), np.log(b))
+    assert np.allclose(ga[0][:5, :9], np.exp(la[0][:5, :9]))
+    assert np.allclose(ga[1][1:5, 1:9], np.exp(la[1][1:5, 1:9]))
+    # interior node: [1,2,1]/4 x [1,2,1]/4 weights
+    I, J = 2, 3
+    w = np.array([1, 2, 1]) / 4
+    ex = sum(w[di] * w[dj] * a[2 * I - 1 + di, 2 * J - 1 + dj] for di in range(3) for dj in range(3))
+    assert la[0] is not None and M.coarsen_eta(fine, coarse, a, b)[0][I, J] == pytest.approx(ex)
+
+
+@pytest.mark.parametrize("omega", [1.0, 0.7])
+def test_rbgs_is_textbook_sor_in_colour_order(omega):
+    """One red-black sweep = one SOR sweep (D + w L_low) x' = w f - (w U + (w - 1) D) x in the
+    permuted order vx-red, vx-black, vy-red, vy-black."""
+    g = S.Grid(10, 8, bc=S.BC(kind=(S.NO_SLIP, S.FREE_SLIP, S.FREE_SLIP, S.NO_SLIP)))
+    en, ec = rand_eta(10, 8, 9)
+    L = S.assemble(g, en, ec, velocity_only=True).A.tocsr()
+    rng = np.random.default_rng(3)
+    f, x0 = rng.standard_normal(g.n_v), rng.standard_normal(g.n_v)
+    sets = M.colour_sets(g)
+    x1 = M.rbgs_sweep(L, f, x0, sets, omega)
+    perm = np.concatenate(sets)
+    Lp = L[perm][:, perm]
+    D = sp.diags(Lp.diagonal())
+    Llow, U = sp.tril(Lp, -1), sp.triu(Lp, 1)
+    rhs = omega * f[perm] - (omega * U + (omega - 1) * D) @ x0[perm]
+    xp = spla.spsolve_triangular((D + omega * Llow).tocsr(), rhs, lower=True)
+    x_text = np.empty_like(xp); x_text[perm] = xp
+    assert np.allclose(x1, x_text, rtol=1e-12, atol=1e-12)
+
+
+def test_colours_decouple():
+    g = S.Grid(12, 10)
+    en, ec = rand_eta(12, 10, 2)
+    L = S.assemble(g, en, ec, velocity_only=True).A.tocsr()
+    for s in M.colour_sets(g):
+        sub = L[s][:, s]
+        assert (sub - sp.diags(sub.diagonal())).count_nonzero() == 0
+
+
+def test_single_level_vcycle_is_exact():
+    g = S.Grid(8, 8)
+    en, ec = rand_eta(8, 8, 1)
+    h = M.Hierarchy(g, en, ec, n_lev=1)
+    f = np.random.default_rng(0).standard_normal(g.n_v)
+    x = M.vcycle(h, f)
+    assert np.allclose(h.L[0] @ x, f, atol=1e-10)
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_vcycle_textbook_convergence(n):
+    """Constant viscosity: the V(2,2) cycle as a stationary iteration contracts the error by a
+    grid-independent factor well below 1 (multigrid's defining property)."""
+    g = S.Grid(n, n)
+    one = np.ones((n + 2, n + 2))
+    h = M.Hierarchy(g, one, one, coarsest_min=2)
+    assert h.nlev >= 4
+    rng = np.random.default_rng(1)
+    f = rng.standard_normal(g.n_v)
+    L = h.L[0]
+    x = np.zeros_like(f)
+    res = [np.linalg.norm(f)]
+    for _ in range(6):
+        x = x + M.vcycle(h, f - L @ x)
+        res.append(np.linalg.norm(f - L @ x))
+    rate = (res[-1] / res[1]) ** (1 / 5)
+    assert rate < 0.2
+
+
+def test_uzawa_sign_reading():
+    """Exact velocity solve: the stationary iteration x += M^-1 (b - A x) converges with the sign
+    reading and diverges with the literal printed sign (the reason for the reading)."""
+    f = sinker(16, 16, eta_inc=10.0)
+    g = S.Grid(16, 16)
+    sysm = S.assemble(g, f.eta_n, f.eta_c, f.rho, (0.0, 1.0))
+    h = M.Hierarchy(g, f.eta_n, f.eta_c, n_lev=1)
+    for literal, expect_conv in ((False, True), (True, False)):
+        x = np.zeros(g.n)
+        e0 = S.energy_residual(sysm, f.eta_c, x)[0]
+        for _ in range(60):
+            x = x + M.uzawa_precond(h, sysm.b - sysm.A @ x, f.eta_c, alpha=0.6, literal_sign=literal)
+        e1 = S.energy_residual(sysm, f.eta_c, x)[0]
+        if expect_conv:
+            assert e1 < 1e-3 * e0
+        else:
+            assert e1 > e0
+
+
+def test_preconditioner_pressure_mean_zero_and_linear():
+    f = sinker(16, 16)
+    g = S.Grid(16, 16)
+    h = M.Hierarchy(g, f.eta_n, f.eta_c, coarsest_min=4)
+    rng = np.random.default_rng(5)
+    r1, r2 = rng.standard_normal(g.n), rng.standard_normal(g.n)
+    z1, z2 = M.uzawa_precond(h, r1, f.eta_c), M.uzawa_precond(h, r2, f.eta_c)
+    z12 = M.uzawa_precond(h, 2 * r1 - 3 * r2, f.eta_c)
+    assert abs(z1[g.n_v:].mean()) < 1e-14
+    assert np.allclose(z12, 2 * z1 - 3 * z2, atol=1e-10)
