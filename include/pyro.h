@@ -1,0 +1,189 @@
+/*
+ * pyro.h — C ABI of libpyro: matrix-free staggered-grid 2D variable-viscosity Stokes solver for
+ * one NVIDIA B300 (sm_103a).
+ *
+ * The operator is the stress-conservative finite-difference discretisation of the incompressible
+ * Stokes equations on a fully staggered grid (paper: Sec. "Conservation of Mass and Momentum",
+ * eqs. xmom/ymom/mass; Sec. "Staggered Grid Layout"; Sec. "Stress-Conservative Finite
+ * Differences"). The solve is flexible GMRES (Sec. "Comparison with FGMRES") preconditioned by one
+ * Uzawa sweep (Sec. "Uzawa Iteration as a Fixed Point Method", eq. uzawa_split_system) whose
+ * velocity block is one geometric-multigrid V-cycle (Sec. "Multigrid Cycles", eq.
+ * multigrid_levels) with damped red-black Gauss-Seidel smoothing (Sec. "Smoothers", eq.
+ * sor_update). Convergence is measured by the relative energy residual of Sec. "Global Relative
+ * Energy Residual".
+ *
+ * ---------------------------------------------------------------------------------------------
+ * GRID AND ARRAY LAYOUT (every field argument)
+ *   nx, ny are CELL counts; hx = Lx/nx, hy = Ly/ny. Every field is a row-major array of
+ *   (ny+2) x (nx+2) doubles (the paper's (n_y+1) x (n_x+1) in node counts); element (i, j) is at
+ *   offset i*(nx+2) + j. Row 0 is the top (y = 0); y and the row index grow downward. Each
+ *   staggered quantity carries the index of the basic node at its lower-right (paper's rule):
+ *     vx(i,j) at (j*hx, (i-1/2)*hy)      meaningful i in [1,ny], j in [0,nx]; unknowns j in [1,nx-1]
+ *     vy(i,j) at ((j-1/2)*hx, i*hy)      meaningful i in [0,ny], j in [1,nx]; unknowns i in [1,ny-1]
+ *     p(i,j), eta_c(i,j) at cell centres meaningful i in [1,ny], j in [1,nx]
+ *     eta_n(i,j), rho(i,j) at basic nodes meaningful i in [0,ny], j in [0,nx]
+ *   Entries outside the meaningful ranges are ignored on input. On output, velocity ghosts and
+ *   walls are written with the boundary values; other non-meaningful entries are written as 0.
+ *
+ * POINTERS
+ *   Field pointers may be device pointers or host pointers (pageable or pinned); the library
+ *   detects which with cudaPointerGetAttributes. Host buffers are staged through the handle's own
+ *   device workspace with copies ordered on `cuda_stream`. The caller owns every buffer.
+ *   `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ *
+ * STATUS CODES: 0 = success; > 0 warning with a valid best-effort result; < 0 error (outputs
+ *   undefined). No C++ exception crosses this interface. A handle is not thread-safe; distinct
+ *   handles are independent and may be used from different host threads and streams.
+ *
+ * SYNCHRONISATION: pyro_stokes_solve and pyro_stokes_adjoint drive the Krylov loop from the host
+ *   and return when the result is complete on `cuda_stream` (they synchronise that stream).
+ *   pyro_stokes_apply and pyro_stokes_precond also return after completion (they read an error flag).
+ * ---------------------------------------------------------------------------------------------
+ */
+#ifndef PYRO_H
+#define PYRO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PYRO_OK 0
+#define PYRO_W_NOT_CONVERGED 1   /* max_iter reached; best iterate returned */
+#define PYRO_E_INVALID (-1)      /* bad argument, unsupported size or boundary combination */
+#define PYRO_E_NOMEM (-2)        /* device allocation failed (or the handle's memory budget) */
+#define PYRO_E_CUDA (-3)         /* a CUDA runtime call failed */
+#define PYRO_E_NONFINITE (-4)    /* an input field holds NaN/Inf, or the iteration produced one */
+#define PYRO_E_TIMEOUT (-5)      /* wall-clock limit of the solve exceeded */
+#define PYRO_E_BREAKDOWN (-6)    /* Krylov breakdown that a restart could not cure */
+
+/* Boundary kinds per side (paper Sec. "Boundary Conditions", eqs. free_slip_bc, no_slip_bc).
+ * The normal velocity is zero on every wall. The tangential ghost is eliminated with
+ * ghost = s * interior + c: free slip s=+1, c=0; no slip s=-1, c=0 (the paper's mirror rule);
+ * prescribed tangential velocity U: s=-1, c=2U. PYRO_BC_PERIODIC is accepted by the oracle only;
+ * the library rejects it with PYRO_E_INVALID. */
+typedef enum { PYRO_BC_FREE_SLIP = 0, PYRO_BC_NO_SLIP = 1, PYRO_BC_PERIODIC = 2, PYRO_BC_VELOCITY = 3 } pyro_bc_kind;
+
+/* Sides are ordered W, E, N (top, row 0), S (bottom). vt = tangential velocity for VELOCITY. */
+typedef struct {
+  int kind[4];
+  double vt[4];
+} pyro_bc;
+
+typedef enum { PYRO_PREC_FP64 = 0, PYRO_PREC_MIXED = 1 } pyro_precision;
+typedef enum { PYRO_ETA_ARITH = 0, PYRO_ETA_GEOM = 1 } pyro_eta_coarsening;
+
+/* Solver options. pyro_default_opts() fills the defaults given in brackets. */
+typedef struct {
+  int nu1, nu2;          /* pre/post RBGS sweeps per level [2, 2] */
+  double omega_v;        /* RBGS damping (eq. sor_update) [1.0] */
+  double alpha_p;        /* Uzawa pressure relaxation alpha (eq. uzawa_iteration) [1.0] */
+  int restart_m;         /* FGMRES restart length, 1..64 [30] */
+  int max_iter;          /* total FGMRES iterations before PYRO_W_NOT_CONVERGED [500] */
+  int prec;              /* pyro_precision [PYRO_PREC_MIXED] */
+  int coarsest_min;      /* halve while the short side stays >= this many cells [2] */
+  int eta_coarsen;       /* pyro_eta_coarsening [PYRO_ETA_ARITH] */
+  int warm_start;        /* 1: vx, vy, p passed to solve hold the initial guess [0] */
+  int use_graphs;        /* 1: capture the FGMRES iteration into a CUDA graph [1] */
+  double timeout_s;      /* wall-clock limit of one solve, <= 0 for none [0] */
+} pyro_opts;
+
+typedef struct {
+  int iters;             /* FGMRES iterations (= preconditioner applications) */
+  int restarts;          /* completed restart cycles */
+  int vcycles;           /* V-cycles applied */
+  int status;            /* return status of the call */
+  double rel_energy_res; /* true relative energy residual of the returned iterate */
+  double rel_l2_res;     /* true ||b - A x||_2 / ||b||_2 of the returned iterate */
+  double t_setup_ms;     /* hierarchy set-up time (device) */
+  double t_solve_ms;     /* Krylov loop time (device) */
+  double alg_bytes;      /* algorithmic HBM bytes of the call (model, see the design notes) */
+  int levels;            /* multigrid levels */
+  int coarse_n;          /* unknowns of the coarsest direct solve */
+  long long kernel_launches; /* CUDA kernels this call launched (graph kernel nodes included) */
+} pyro_stats;
+
+typedef struct pyro_stokes_s* pyro_stokes;
+
+/* Default options (see pyro_opts). */
+void pyro_default_opts(pyro_opts* opts);
+
+/* Create a solver for an nx x ny cell grid on an Lx x Ly box with boundary `bc` (NULL = free slip
+ * on all sides) and options `opts` (NULL = defaults). Allocates the whole multigrid hierarchy, the
+ * Krylov bases and all workspaces on the current CUDA device; they stay resident until destroy,
+ * so repeated solves of one shape reuse them. nx, ny >= 2 and even; the coarsest level must hold
+ * at most 1024 velocity unknowns (sizes with few factors of 2 are rejected: PYRO_E_INVALID).
+ * Returns PYRO_OK and *out, or an error (then *out = NULL). */
+int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc,
+                       const pyro_opts* opts, pyro_stokes* out);
+
+/* Bytes of device memory pyro_stokes_create(nx, ny, ..., opts) allocates (used for admission
+ * control by callers that share the GPU). 0 if the size is invalid. */
+size_t pyro_stokes_footprint(int nx, int ny, const pyro_opts* opts);
+
+/* y = A x for the saddle-point operator [[L, G], [D, 0]] (eq. stokes_saddle) with homogeneous
+ * boundary rules (no boundary constants; those belong to the right-hand side). Inputs eta_n,
+ * eta_c, vx, vy, p; outputs Ax (x-momentum rows), Ay (y-momentum rows), Ap (continuity rows),
+ * each written at its unknown locations and 0 elsewhere. Computed in FP64. */
+int pyro_stokes_apply(pyro_stokes h, const double* eta_n, const double* eta_c,
+                      const double* vx, const double* vy, const double* p,
+                      double* Ax, double* Ay, double* Ap, void* cuda_stream);
+
+/* Solve A [v; p] = [f; 0] with f = -rho g (gravity g = (gx, gy) in the grid frame, y down; the
+ * paper's Sec. "Viscosity Rescaling and Initial Guess" lithostatic convention) plus the boundary
+ * constants, to relative energy residual <= tol. Output pressure has zero mean (eq.
+ * pressure_normalization). vx, vy, p: initial guess on input if opts.warm_start, solution on
+ * output. stats (host pointer) may be NULL. Returns PYRO_OK, PYRO_W_NOT_CONVERGED, or an error. */
+int pyro_stokes_solve(pyro_stokes h, const double* eta_n, const double* eta_c, const double* rho,
+                      double gx, double gy, double tol, double* vx, double* vy, double* p,
+                      pyro_stats* stats, void* cuda_stream);
+
+/* Adjoint of the last successful solve on h: solves A lambda = [dJ_dvx; dJ_dvy; dJ_dp] (A is
+ * symmetric) to tol and forms
+ *   dJ_deta_c(cell) = 2 (exx(v) exx(lambda) + eyy(v) eyy(lambda)),
+ *   dJ_deta_n(node) = w_n gamma(v) gamma(lambda)   (w_n = 1 inside, 1/2 on walls, 0 at corners),
+ *   dJ_drho(node)   = lambda . d f / d rho          (may be NULL),
+ * with exx = d vx/dx, eyy = d vy/dy at cells and gamma = d vx/dy + d vy/dx at nodes (boundary
+ * ghosts filled homogeneously for lambda). Not in the paper: this is the discrete adjoint of its
+ * operator. Rejects prescribed-velocity boundaries (PYRO_E_INVALID). */
+int pyro_stokes_adjoint(pyro_stokes h, const double* dJ_dvx, const double* dJ_dvy,
+                        const double* dJ_dp, double tol, double* dJ_deta_n, double* dJ_deta_c,
+                        double* dJ_drho, pyro_stats* stats, void* cuda_stream);
+
+/* One application of the preconditioner z = M^-1 r (diagnostic / test entry point): sets up the
+ * hierarchy from eta_n, eta_c exactly as pyro_stokes_solve does, then applies one Uzawa sweep
+ * (paper Sec. "Uzawa Iteration as a Fixed Point Method"): z_v = one multigrid V-cycle on L z_v = r_v
+ * from zero (eq. multigrid_levels), z_p = alpha_p eta_c (r_p - D z_v) with its mean removed. In
+ * PYRO_PREC_MIXED the V-cycle runs in FP32 and z is rounded to FP32 before it is returned.
+ * Inputs r_vx, r_vy, r_p are read at their unknown locations; outputs are written there and 0
+ * elsewhere. Returns after completion on cuda_stream. */
+int pyro_stokes_precond(pyro_stokes h, const double* eta_n, const double* eta_c, const double* r_vx,
+                        const double* r_vy, const double* r_p, double* z_vx, double* z_vy, double* z_p,
+                        void* cuda_stream);
+
+/* Device-time breakdown of the FGMRES iterations (diagnostic). When enabled (takes effect at the
+ * next solve, accumulators reset), CUDA events are recorded around the phases of every iteration
+ * and read back at the iteration's existing host synchronisation. ms[6] receives accumulated
+ * milliseconds of: [0] preconditioner input cast, [1] finest-level pre-smoothing sweeps,
+ * [2] all coarser-level work (residual, restriction, coarse levels, prolongation), [3] finest-level
+ * post-smoothing sweeps, [4] pressure block + FP64 operator A z, [5] orthogonalisation;
+ * counts[2] receives [0] timed iterations, [1] finest-level smoothing sweeps (each sweep =
+ * vx-red, vx-black, vy-red, vy-black launches). Returns PYRO_E_INVALID on a NULL handle. */
+int pyro_stokes_set_timing(pyro_stokes h, int enable);
+int pyro_stokes_get_timing(pyro_stokes h, double* ms, long long* counts);
+
+/* Release every device allocation of h (NULL is a no-op). */
+void pyro_stokes_destroy(pyro_stokes h);
+
+/* Static description of a status code. */
+const char* pyro_strerror(int status);
+
+/* Library version string. */
+const char* pyro_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PYRO_H */

@@ -1,0 +1,12 @@
+"""B300-native (sm_103a) matrix-free staggered-grid Stokes solver: multigrid-preconditioned FGMRES.
+
+The compute path is libpyro.so (CUDA kernels + C ABI, include/pyro.h); this package is its thin
+Python binding plus the autograd wrapper and the continuous-batching solve server.
+"""
+from .pyro import (Stokes, PyroError, PyroOpts, PyroBC, PyroStats, default_opts, make_bc, footprint, lib,
+                   load_library, EXPORTED, FREE_SLIP, NO_SLIP, PERIODIC, VELOCITY, PREC_FP64, PREC_MIXED,
+                   ETA_ARITH, ETA_GEOM, PYRO_OK, PYRO_W_NOT_CONVERGED)
+
+__all__ = ["Stokes", "PyroError", "PyroOpts", "PyroBC", "PyroStats", "default_opts", "make_bc", "footprint", "lib",
+           "load_library", "EXPORTED", "FREE_SLIP", "NO_SLIP", "PERIODIC", "VELOCITY", "PREC_FP64", "PREC_MIXED",
+           "ETA_ARITH", "ETA_GEOM", "PYRO_OK", "PYRO_W_NOT_CONVERGED"]

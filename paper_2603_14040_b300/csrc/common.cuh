@@ -1,0 +1,119 @@
+// Shared device-side definitions of libpyro: grid geometry, staggered-field accessors and the
+// point operators of the stress-conservative staggered discretisation.
+//
+// Layout: every field is a row-major (ny+2) x (nx+2) array with row stride ld = nx+2 (the
+// paper's uniform padded staggered arrays, Sec. "Staggered Grid Layout"). Unknowns:
+//   vx: i in [1,ny], j in [1,nx-1];  vy: i in [1,ny-1], j in [1,nx];  p: i in [1,ny], j in [1,nx].
+// Walls (vx columns 0 and nx, vy rows 0 and ny) hold zero normal velocity. Tangential ghosts
+// (vx rows 0 and ny+1, vy columns 0 and nx+1) are never read: the point operators substitute
+// s * (adjacent interior value), which eliminates them exactly (free slip s=+1, no slip and
+// prescribed velocity s=-1; the constant part of a prescribed velocity lives in the RHS).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace pyro {
+
+struct Geom {
+  int nx, ny;      // cell counts
+  int ld;          // row stride (nx + 2)
+  double dx, dy;   // cell sizes
+  double sN, sS, sW, sE;  // tangential ghost factors
+};
+
+template <typename T>
+struct GeomT {
+  int nx, ny, ld;
+  T idx2, idy2, idxdy;  // 1/dx^2, 1/dy^2, 1/(dx dy)
+  T idx, idy;           // 1/dx, 1/dy
+  T sN, sS, sW, sE;
+};
+
+template <typename T>
+__host__ __device__ inline GeomT<T> geomT(const Geom& g) {
+  GeomT<T> t;
+  t.nx = g.nx; t.ny = g.ny; t.ld = g.ld;
+  t.idx2 = (T)(1.0 / (g.dx * g.dx));
+  t.idy2 = (T)(1.0 / (g.dy * g.dy));
+  t.idxdy = (T)(1.0 / (g.dx * g.dy));
+  t.idx = (T)(1.0 / g.dx);
+  t.idy = (T)(1.0 / g.dy);
+  t.sN = (T)g.sN; t.sS = (T)g.sS; t.sW = (T)g.sW; t.sE = (T)g.sE;
+  return t;
+}
+
+__host__ __device__ inline bool is_vx(int nx, int ny, int i, int j) { return i >= 1 && i <= ny && j >= 1 && j <= nx - 1; }
+__host__ __device__ inline bool is_vy(int nx, int ny, int i, int j) { return i >= 1 && i <= ny - 1 && j >= 1 && j <= nx; }
+__host__ __device__ inline bool is_p(int nx, int ny, int i, int j) { return i >= 1 && i <= ny && j >= 1 && j <= nx; }
+
+// vx value with walls masked (used where a reference may land on a wall column)
+template <typename T, typename S>
+__device__ inline T ldvx(const S* vx, int ld, int nx, int i, int j) {
+  return (j <= 0 || j >= nx) ? T(0) : (T)vx[(size_t)i * ld + j];
+}
+template <typename T, typename S>
+__device__ inline T ldvy(const S* vy, int ld, int ny, int i, int j) {
+  return (i <= 0 || i >= ny) ? T(0) : (T)vy[(size_t)i * ld + j];
+}
+
+// x-momentum velocity part at the vx unknown (i, j):
+//   (sxx(i,j+1) - sxx(i,j))/dx + (sxy(i,j) - sxy(i-1,j))/dy
+// with sxx = 2 eta_c d vx/dx at cells and sxy = eta_n (d vx/dy + d vy/dx) at basic nodes.
+// Returns the value and the diagonal coefficient (boundary elimination included).
+template <typename T, typename SV, typename SE>
+__device__ inline T lx_point(const GeomT<T>& g, int i, int j, const SV* vx, const SV* vy,
+                             const SE* en, const SE* ec, T& diag) {
+  const int ld = g.ld;
+  const size_t c = (size_t)i * ld + j;
+  const T eA = (T)ec[c], eB = (T)ec[c + 1];       // cells west / east of vx(i,j)
+  const T e1 = (T)en[c - ld], e2 = (T)en[c];       // nodes above / below
+  const T vc = (T)vx[c];
+  const T vw = ldvx<T>(vx, ld, g.nx, i, j - 1);
+  const T ve = ldvx<T>(vx, ld, g.nx, i, j + 1);
+  const T vn = (i == 1) ? g.sN * vc : (T)vx[c - ld];
+  const T vs = (i == g.ny) ? g.sS * vc : (T)vx[c + ld];
+  const T yA = ldvy<T>(vy, ld, g.ny, i - 1, j), yB = ldvy<T>(vy, ld, g.ny, i - 1, j + 1);
+  const T yC = ldvy<T>(vy, ld, g.ny, i, j), yD = ldvy<T>(vy, ld, g.ny, i, j + 1);
+  const T sxxE = T(2) * eB * (ve - vc);
+  const T sxxW = T(2) * eA * (vc - vw);
+  const T sxyS = e2 * ((vs - vc) * g.idy2 + (yD - yC) * g.idxdy);
+  const T sxyN = e1 * ((vc - vn) * g.idy2 + (yB - yA) * g.idxdy);
+  diag = -T(2) * (eA + eB) * g.idx2 - (e1 + e2) * g.idy2;
+  if (i == 1) diag += g.sN * e1 * g.idy2;
+  if (i == g.ny) diag += g.sS * e2 * g.idy2;
+  return (sxxE - sxxW) * g.idx2 + sxyS - sxyN;
+}
+
+// y-momentum velocity part at the vy unknown (i, j):
+//   (syy(i+1,j) - syy(i,j))/dy + (sxy(i,j) - sxy(i,j-1))/dx
+template <typename T, typename SV, typename SE>
+__device__ inline T ly_point(const GeomT<T>& g, int i, int j, const SV* vx, const SV* vy,
+                             const SE* en, const SE* ec, T& diag) {
+  const int ld = g.ld;
+  const size_t c = (size_t)i * ld + j;
+  const T eA = (T)ec[c], eB = (T)ec[c + ld];      // cells above / below vy(i,j)
+  const T e1 = (T)en[c - 1], e2 = (T)en[c];        // nodes west / east
+  const T vc = (T)vy[c];
+  const T vn = ldvy<T>(vy, ld, g.ny, i - 1, j);
+  const T vs = ldvy<T>(vy, ld, g.ny, i + 1, j);
+  const T vw = (j == 1) ? g.sW * vc : (T)vy[c - 1];
+  const T ve = (j == g.nx) ? g.sE * vc : (T)vy[c + 1];
+  const T xA = ldvx<T>(vx, ld, g.nx, i, j - 1), xB = ldvx<T>(vx, ld, g.nx, i + 1, j - 1);
+  const T xC = ldvx<T>(vx, ld, g.nx, i, j), xD = ldvx<T>(vx, ld, g.nx, i + 1, j);
+  const T syyS = T(2) * eB * (vs - vc);
+  const T syyN = T(2) * eA * (vc - vn);
+  const T sxyE = e2 * ((ve - vc) * g.idx2 + (xD - xC) * g.idxdy);
+  const T sxyW = e1 * ((vc - vw) * g.idx2 + (xB - xA) * g.idxdy);
+  diag = -T(2) * (eA + eB) * g.idy2 - (e1 + e2) * g.idx2;
+  if (j == 1) diag += g.sW * e1 * g.idx2;
+  if (j == g.nx) diag += g.sE * e2 * g.idx2;
+  return (syyS - syyN) * g.idy2 + sxyE - sxyW;
+}
+
+// Error flags written by kernels (host reads them after a sync).
+enum : int { FLAG_NONFINITE = 1, FLAG_BREAKDOWN = 2 };
+
+constexpr int kReduceBlocks = 296;  // 2 x 148 SMs: fixed so reductions are deterministic
+constexpr int kThreads = 256;
+
+}  // namespace pyro

@@ -1,0 +1,314 @@
+// Multigrid kernels of the velocity block L (Sec. "The Multigrid Method"), templated on the
+// arithmetic type T (float for the mixed-precision V-cycle, double for the plain FP64 one).
+//
+//  * k_rbgs: one colour of one field of damped red-black Gauss-Seidel (eq. sor_update); the
+//    sweep order is vx-red, vx-black, vy-red, vy-black with colour (i + j) mod 2.
+//  * k_vresidual: r = f - L x on one level (eq. mg_residual).
+//  * k_restrict: normalised bilinear-weighted restriction (Sec. "Restriction"): for factor-2
+//    coarsening the bilinear weights are [1,2,1]/4 across node-centred directions and
+//    [1,3,3,1]/8 across cell-centred ones; locations that are not unknowns drop out and the
+//    normalisation divides by the weights that remain. Each coarse point gathers its own fine
+//    support, so no colouring and no atomics are needed.
+//  * k_prolong_add: x_fine += P x_coarse, bilinear from the four surrounding coarse points
+//    (Sec. "Prolongation"); coarse ghosts follow the homogeneous boundary rule.
+//  * k_coarsen_eta: eta_n / eta_c of the next level with the same normalised bilinear weights,
+//    arithmetic or on log(eta) (each field transferred on its own, Sec. "Geometric vs Algebraic").
+//  * k_coarse_assemble / k_coarse_invert / k_coarse_solve: FP64 direct solve on the coarsest
+//    level (Sec. "Multigrid Cycles", coarsest level solved directly): dense -L is assembled,
+//    inverted once per set-up by Gauss-Jordan (it is SPD, no pivoting) and applied as a matvec.
+#pragma once
+#include "common.cuh"
+
+namespace pyro {
+
+template <typename T>
+__global__ void k_rbgs(GeomT<T> g, T* __restrict__ vx, T* __restrict__ vy, const T* __restrict__ fx,
+                       const T* __restrict__ fy, const T* __restrict__ en, const T* __restrict__ ec,
+                       int field, int colour, T omega) {
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  const int jh = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = 2 * jh + ((i + colour) & 1);
+  if (i > g.ny + 1 || j > g.nx + 1) return;
+  const size_t c = (size_t)i * g.ld + j;
+  T diag;
+  if (field == 0) {
+    if (!is_vx(g.nx, g.ny, i, j)) return;
+    const T Lv = lx_point<T>(g, i, j, vx, vy, en, ec, diag);
+    vx[c] += omega * (fx[c] - Lv) / diag;
+  } else {
+    if (!is_vy(g.nx, g.ny, i, j)) return;
+    const T Lv = ly_point<T>(g, i, j, vx, vy, en, ec, diag);
+    vy[c] += omega * (fy[c] - Lv) / diag;
+  }
+}
+
+template <typename T>
+__global__ void k_vresidual(GeomT<T> g, const T* __restrict__ vx, const T* __restrict__ vy,
+                            const T* __restrict__ fx, const T* __restrict__ fy, const T* __restrict__ en,
+                            const T* __restrict__ ec, T* __restrict__ rx, T* __restrict__ ry) {
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > g.ny + 1 || j > g.nx + 1) return;
+  const size_t c = (size_t)i * g.ld + j;
+  T d, ox = T(0), oy = T(0);
+  if (is_vx(g.nx, g.ny, i, j)) ox = fx[c] - lx_point<T>(g, i, j, vx, vy, en, ec, d);
+  if (is_vy(g.nx, g.ny, i, j)) oy = fy[c] - ly_point<T>(g, i, j, vx, vy, en, ec, d);
+  rx[c] = ox;
+  ry[c] = oy;
+}
+
+template <typename T>
+__global__ void k_restrict(GeomT<T> gf, GeomT<T> gc, const T* __restrict__ rx, const T* __restrict__ ry,
+                           T* __restrict__ fxc, T* __restrict__ fyc) {
+  const int I = blockIdx.y * blockDim.y + threadIdx.y;
+  const int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I > gc.ny + 1 || J > gc.nx + 1) return;
+  const size_t C = (size_t)I * gc.ld + J;
+  const T w4[4] = {T(1), T(3), T(3), T(1)};
+  const T w3[3] = {T(1), T(2), T(1)};
+  T ox = T(0), oy = T(0);
+  if (is_vx(gc.nx, gc.ny, I, J)) {
+    // rows 2I-2 .. 2I+1 (cell-centred direction), columns 2J-1 .. 2J+1 (node direction)
+    T s = T(0), ws = T(0);
+    for (int a = 0; a < 4; ++a) {
+      const int i = 2 * I - 2 + a;
+      if (i < 1 || i > gf.ny) continue;
+      for (int b = 0; b < 3; ++b) {
+        const int j = 2 * J - 1 + b;
+        const T w = w4[a] * w3[b];
+        s += w * rx[(size_t)i * gf.ld + j];
+        ws += w;
+      }
+    }
+    ox = s / ws;
+  }
+  if (is_vy(gc.nx, gc.ny, I, J)) {
+    T s = T(0), ws = T(0);
+    for (int a = 0; a < 3; ++a) {
+      const int i = 2 * I - 1 + a;
+      for (int b = 0; b < 4; ++b) {
+        const int j = 2 * J - 2 + b;
+        if (j < 1 || j > gf.nx) continue;
+        const T w = w3[a] * w4[b];
+        s += w * ry[(size_t)i * gf.ld + j];
+        ws += w;
+      }
+    }
+    oy = s / ws;
+  }
+  fxc[C] = ox;
+  fyc[C] = oy;
+}
+
+template <typename T>
+__device__ inline T coarse_vx(const GeomT<T>& gc, const T* vxc, int I, int J) {
+  if (J <= 0 || J >= gc.nx) return T(0);
+  if (I == 0) return gc.sN * vxc[(size_t)1 * gc.ld + J];
+  if (I == gc.ny + 1) return gc.sS * vxc[(size_t)gc.ny * gc.ld + J];
+  return vxc[(size_t)I * gc.ld + J];
+}
+template <typename T>
+__device__ inline T coarse_vy(const GeomT<T>& gc, const T* vyc, int I, int J) {
+  if (I <= 0 || I >= gc.ny) return T(0);
+  if (J == 0) return gc.sW * vyc[(size_t)I * gc.ld + 1];
+  if (J == gc.nx + 1) return gc.sE * vyc[(size_t)I * gc.ld + gc.nx];
+  return vyc[(size_t)I * gc.ld + J];
+}
+
+template <typename T>
+__global__ void k_prolong_add(GeomT<T> gf, GeomT<T> gc, T* __restrict__ vxf, T* __restrict__ vyf,
+                              const T* __restrict__ vxc, const T* __restrict__ vyc) {
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > gf.ny + 1 || j > gf.nx + 1) return;
+  const size_t c = (size_t)i * gf.ld + j;
+  if (is_vx(gf.nx, gf.ny, i, j)) {
+    // rows: cell-centred (weights 3/4, 1/4); columns: node-centred (1 or 1/2, 1/2)
+    const int I0 = (i & 1) ? (i - 1) / 2 : i / 2;
+    const T wy0 = (i & 1) ? T(0.25) : T(0.75);
+    const T wy1 = T(1) - wy0;
+    T v;
+    if (j & 1) {
+      const int J0 = (j - 1) / 2;
+      v = T(0.5) * (wy0 * coarse_vx(gc, vxc, I0, J0) + wy1 * coarse_vx(gc, vxc, I0 + 1, J0) +
+                    wy0 * coarse_vx(gc, vxc, I0, J0 + 1) + wy1 * coarse_vx(gc, vxc, I0 + 1, J0 + 1));
+    } else {
+      const int J = j / 2;
+      v = wy0 * coarse_vx(gc, vxc, I0, J) + wy1 * coarse_vx(gc, vxc, I0 + 1, J);
+    }
+    vxf[c] += v;
+  }
+  if (is_vy(gf.nx, gf.ny, i, j)) {
+    const int J0 = (j & 1) ? (j - 1) / 2 : j / 2;
+    const T wx0 = (j & 1) ? T(0.25) : T(0.75);
+    const T wx1 = T(1) - wx0;
+    T v;
+    if (i & 1) {
+      const int I0 = (i - 1) / 2;
+      v = T(0.5) * (wx0 * coarse_vy(gc, vyc, I0, J0) + wx1 * coarse_vy(gc, vyc, I0, J0 + 1) +
+                    wx0 * coarse_vy(gc, vyc, I0 + 1, J0) + wx1 * coarse_vy(gc, vyc, I0 + 1, J0 + 1));
+    } else {
+      const int I = i / 2;
+      v = wx0 * coarse_vy(gc, vyc, I, J0) + wx1 * coarse_vy(gc, vyc, I, J0 + 1);
+    }
+    vyf[c] += v;
+  }
+}
+
+template <typename T>
+__global__ void k_coarsen_eta(GeomT<T> gf, GeomT<T> gc, const T* __restrict__ enf, const T* __restrict__ ecf,
+                              T* __restrict__ enc, T* __restrict__ ecc, int geometric) {
+  const int I = blockIdx.y * blockDim.y + threadIdx.y;
+  const int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I > gc.ny + 1 || J > gc.nx + 1) return;
+  const size_t C = (size_t)I * gc.ld + J;
+  const T w4[4] = {T(1), T(3), T(3), T(1)};
+  const T w3[3] = {T(1), T(2), T(1)};
+  T on = T(0), oc = T(0);
+  if (I <= gc.ny && J <= gc.nx) {
+    T s = T(0), ws = T(0);
+    for (int a = 0; a < 3; ++a) {
+      const int i = 2 * I - 1 + a;
+      if (i < 0 || i > gf.ny) continue;
+      for (int b = 0; b < 3; ++b) {
+        const int j = 2 * J - 1 + b;
+        if (j < 0 || j > gf.nx) continue;
+        const T w = w3[a] * w3[b];
+        const T e = enf[(size_t)i * gf.ld + j];
+        s += w * (geometric ? log(e) : e);
+        ws += w;
+      }
+    }
+    on = geometric ? exp(s / ws) : s / ws;
+  }
+  if (I >= 1 && I <= gc.ny && J >= 1 && J <= gc.nx) {
+    T s = T(0), ws = T(0);
+    for (int a = 0; a < 4; ++a) {
+      const int i = 2 * I - 2 + a;
+      if (i < 1 || i > gf.ny) continue;
+      for (int b = 0; b < 4; ++b) {
+        const int j = 2 * J - 2 + b;
+        if (j < 1 || j > gf.nx) continue;
+        const T w = w4[a] * w4[b];
+        const T e = ecf[(size_t)i * gf.ld + j];
+        s += w * (geometric ? log(e) : e);
+        ws += w;
+      }
+    }
+    oc = geometric ? exp(s / ws) : s / ws;
+  }
+  enc[C] = on;
+  ecc[C] = oc;
+}
+
+// ---- coarsest level: unknown numbering vx (row-major over i in [1,ny], j in [1,nx-1]) then vy
+__host__ __device__ inline int coarse_n(int nx, int ny) { return ny * (nx - 1) + (ny - 1) * nx; }
+
+template <typename T>
+__global__ void k_coarse_assemble(Geom g, const T* __restrict__ en, const T* __restrict__ ec,
+                                  double* __restrict__ A, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int nx = g.nx, ny = g.ny, ld = g.ld;
+  const int nvx = ny * (nx - 1);
+  const double idx2 = 1.0 / (g.dx * g.dx), idy2 = 1.0 / (g.dy * g.dy), ixy = 1.0 / (g.dx * g.dy);
+  auto VX = [&](int i, int j) { return (i - 1) * (nx - 1) + (j - 1); };
+  auto VY = [&](int i, int j) { return nvx + (i - 1) * nx + (j - 1); };
+  double* row = A + (size_t)k * n;
+  // row entries are those of -L
+  if (k < nvx) {
+    const int i = k / (nx - 1) + 1, j = k % (nx - 1) + 1;
+    const size_t c = (size_t)i * ld + j;
+    const double eA = ec[c], eB = ec[c + 1], e1 = en[c - ld], e2 = en[c];
+    double d = -2.0 * (eA + eB) * idx2 - (e1 + e2) * idy2;
+    if (i == 1) d += g.sN * e1 * idy2;
+    if (i == ny) d += g.sS * e2 * idy2;
+    row[k] = -d;
+    if (j - 1 >= 1) row[VX(i, j - 1)] = -2.0 * eA * idx2;
+    if (j + 1 <= nx - 1) row[VX(i, j + 1)] = -2.0 * eB * idx2;
+    if (i >= 2) row[VX(i - 1, j)] = -e1 * idy2;
+    if (i <= ny - 1) row[VX(i + 1, j)] = -e2 * idy2;
+    if (i - 1 >= 1) { row[VY(i - 1, j)] = -e1 * ixy; row[VY(i - 1, j + 1)] = e1 * ixy; }
+    if (i <= ny - 1) { row[VY(i, j)] = e2 * ixy; row[VY(i, j + 1)] = -e2 * ixy; }
+  } else {
+    const int kk = k - nvx;
+    const int i = kk / nx + 1, j = kk % nx + 1;
+    const size_t c = (size_t)i * ld + j;
+    const double eA = ec[c], eB = ec[c + ld], e1 = en[c - 1], e2 = en[c];
+    double d = -2.0 * (eA + eB) * idy2 - (e1 + e2) * idx2;
+    if (j == 1) d += g.sW * e1 * idx2;
+    if (j == nx) d += g.sE * e2 * idx2;
+    row[k] = -d;
+    if (i - 1 >= 1) row[VY(i - 1, j)] = -2.0 * eA * idy2;
+    if (i + 1 <= ny - 1) row[VY(i + 1, j)] = -2.0 * eB * idy2;
+    if (j >= 2) row[VY(i, j - 1)] = -e1 * idx2;
+    if (j <= nx - 1) row[VY(i, j + 1)] = -e2 * idx2;
+    if (j <= nx - 1) { row[VX(i + 1, j)] = -e2 * ixy; row[VX(i, j)] = e2 * ixy; }
+    if (j - 1 >= 1) { row[VX(i + 1, j - 1)] = e1 * ixy; row[VX(i, j - 1)] = -e1 * ixy; }
+  }
+}
+
+// In-place Gauss-Jordan inversion of the SPD matrix A (n x n) by one thread block.
+__global__ void k_coarse_invert(double* __restrict__ A, int n, int* __restrict__ flag) {
+  extern __shared__ double col[];
+  for (int k = 0; k < n; ++k) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = A[(size_t)i * n + k];
+    __syncthreads();
+    const double piv = col[k];
+    if (!(piv > 0.0)) {  // not SPD or non-finite: report and leave
+      if (threadIdx.x == 0) atomicOr(flag, FLAG_BREAKDOWN);
+      return;
+    }
+    const double ip = 1.0 / piv;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      double* a = A + (size_t)k * n + j;
+      *a = (j == k) ? ip : (*a) * ip;
+    }
+    __syncthreads();
+    const size_t total = (size_t)n * n;
+    for (size_t e = threadIdx.x; e < total; e += blockDim.x) {
+      const int i = (int)(e / n), j = (int)(e % n);
+      if (i == k) continue;
+      const double f = col[i];
+      if (j == k) A[e] = -f * ip;
+      else A[e] -= f * A[(size_t)k * n + j];
+    }
+    __syncthreads();
+  }
+}
+
+// x = L^-1 f = -(-L)^-1 f on the coarsest level (FP64 whatever T is).
+template <typename T>
+__global__ void k_coarse_solve(Geom g, const double* __restrict__ Ainv, int n, const T* __restrict__ fx,
+                               const T* __restrict__ fy, T* __restrict__ vx, T* __restrict__ vy) {
+  extern __shared__ double fv[];
+  const int nx = g.nx, ny = g.ny, ld = g.ld, nvx = ny * (nx - 1);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    if (k < nvx) { const int i = k / (nx - 1) + 1, j = k % (nx - 1) + 1; fv[k] = (double)fx[(size_t)i * ld + j]; }
+    else { const int kk = k - nvx; const int i = kk / nx + 1, j = kk % nx + 1; fv[k] = (double)fy[(size_t)i * ld + j]; }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double s = 0.0;
+    const double* a = Ainv + (size_t)k * n;
+    for (int l = 0; l < n; ++l) s += a[l] * fv[l];
+    if (k < nvx) { const int i = k / (nx - 1) + 1, j = k % (nx - 1) + 1; vx[(size_t)i * ld + j] = (T)(-s); }
+    else { const int kk = k - nvx; const int i = kk / nx + 1, j = kk % nx + 1; vy[(size_t)i * ld + j] = (T)(-s); }
+  }
+}
+
+// ---- explicit instantiations ---------------------------------------------------------------
+#define PYRO_INST(T)                                                                                         \
+  template __global__ void k_rbgs<T>(GeomT<T>, T*, T*, const T*, const T*, const T*, const T*, int, int, T); \
+  template __global__ void k_vresidual<T>(GeomT<T>, const T*, const T*, const T*, const T*, const T*,      \
+                                          const T*, T*, T*);                                                \
+  template __global__ void k_restrict<T>(GeomT<T>, GeomT<T>, const T*, const T*, T*, T*);                  \
+  template __global__ void k_prolong_add<T>(GeomT<T>, GeomT<T>, T*, T*, const T*, const T*);               \
+  template __global__ void k_coarsen_eta<T>(GeomT<T>, GeomT<T>, const T*, const T*, T*, T*, int);          \
+  template __global__ void k_coarse_assemble<T>(Geom, const T*, const T*, double*, int);                   \
+  template __global__ void k_coarse_solve<T>(Geom, const double*, int, const T*, const T*, T*, T*);
+PYRO_INST(float)
+PYRO_INST(double)
+#undef PYRO_INST
+
+}  // namespace pyro

@@ -1,0 +1,907 @@
+// Host side of libpyro (single translation unit: the kernel headers are included here): solver handle, multigrid hierarchy, V-cycle driver, flexible GMRES with
+// the Uzawa/multigrid preconditioner, adjoint, and the extern "C" entry points of pyro.h.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/pyro.h"
+#include "common.cuh"
+
+#include "kernels_mg.cuh"
+#include "kernels_krylov.cuh"
+
+using namespace pyro;
+
+namespace {
+
+constexpr int kMaxRestart = 64;
+constexpr int kMaxCoarse = 1024;
+constexpr int kHcolStride = 66;
+
+struct CudaError {
+  cudaError_t e;
+};
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t _e = (call);                       \
+    if (_e != cudaSuccess) throw CudaError{_e};    \
+  } while (0)
+
+inline dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + 2 + b.x - 1) / b.x, (ny + 2 + b.y - 1) / b.y); }
+inline dim3 grid_rb(int nx, int ny, dim3 b) { return dim3(((nx + 2) / 2 + 1 + b.x - 1) / b.x, (ny + 2 + b.y - 1) / b.y); }
+const dim3 kBlk2(32, 8);
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct DevAlloc {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  template <typename T>
+  T* get(size_t n) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      throw std::bad_alloc();
+    }
+    ptrs.push_back(p);
+    bytes += n * sizeof(T);
+    return (T*)p;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+Geom make_geom(int nx, int ny, double Lx, double Ly, const pyro_bc& bc) {
+  Geom g;
+  g.nx = nx; g.ny = ny; g.ld = nx + 2;
+  g.dx = Lx / nx; g.dy = Ly / ny;
+  auto s = [&](int side) { return bc.kind[side] == PYRO_BC_FREE_SLIP ? 1.0 : -1.0; };
+  g.sW = s(0); g.sE = s(1); g.sN = s(2); g.sS = s(3);
+  return g;
+}
+
+int count_levels(int nx, int ny, int cmin) {
+  int L = 1;
+  while (nx % 2 == 0 && ny % 2 == 0 && std::min(nx, ny) / 2 >= cmin) { nx /= 2; ny /= 2; ++L; }
+  return L;
+}
+
+// ---- multigrid hierarchy on one arithmetic type --------------------------------------------
+template <typename T>
+struct Level {
+  Geom g;
+  GeomT<T> gt;
+  size_t P;
+  T *vx, *vy, *fx, *fy, *rx, *ry, *en, *ec;
+};
+
+template <typename T>
+struct MG {
+  std::vector<Level<T>> lv;
+  double* Ainv = nullptr;  // coarsest (-L)^-1, dense FP64
+  int nc = 0;              // coarse unknowns
+  int nu1 = 2, nu2 = 2, eta_mode = 0;
+  T omega = T(1);
+  const cudaEvent_t* hooks = nullptr;  // level-0 phase events (timing mode), else null
+  long long* nlaunch = nullptr;        // kernel-launch counter of the owning handle
+  void count(long long k) const { if (nlaunch) *nlaunch += k; }
+
+  static size_t bytes(int nx, int ny, int nlev) {
+    size_t b = 0;
+    for (int l = 0; l < nlev; ++l) {
+      b += (size_t)8 * (size_t)(ny + 2) * (nx + 2) * sizeof(T);
+      if (l + 1 < nlev) { nx /= 2; ny /= 2; }
+    }
+    const size_t nc = (size_t)(ny * (nx - 1) + (ny - 1) * nx);
+    return b + nc * nc * sizeof(double);
+  }
+
+  void alloc(DevAlloc& A, const Geom& g0, int nlev, bool alias_eta0) {
+    Geom g = g0;
+    for (int l = 0; l < nlev; ++l) {
+      Level<T> L;
+      L.g = g;
+      L.gt = geomT<T>(g);
+      L.P = (size_t)(g.ny + 2) * g.ld;
+      L.vx = A.get<T>(L.P); L.vy = A.get<T>(L.P); L.fx = A.get<T>(L.P); L.fy = A.get<T>(L.P);
+      L.rx = A.get<T>(L.P); L.ry = A.get<T>(L.P);
+      if (l == 0 && alias_eta0) { L.en = nullptr; L.ec = nullptr; }
+      else { L.en = A.get<T>(L.P); L.ec = A.get<T>(L.P); }
+      lv.push_back(L);
+      if (l + 1 < nlev) {
+        g.nx /= 2; g.ny /= 2; g.ld = g.nx + 2; g.dx *= 2; g.dy *= 2;
+      }
+    }
+    const Geom& gc = lv.back().g;
+    nc = gc.ny * (gc.nx - 1) + (gc.ny - 1) * gc.nx;
+    Ainv = A.get<double>((size_t)nc * nc);
+  }
+
+  // viscosity on every level + coarse inverse (eta of level 0 must already be in place)
+  void setup(cudaStream_t s, int* flag) {
+    for (size_t l = 1; l < lv.size(); ++l) {
+      const Level<T>& F = lv[l - 1];
+      Level<T>& C = lv[l];
+      k_coarsen_eta<T><<<grid2(C.g.nx, C.g.ny, kBlk2), kBlk2, 0, s>>>(F.gt, C.gt, F.en, F.ec, C.en, C.ec, eta_mode);
+    }
+    const Level<T>& C = lv.back();
+    CK(cudaMemsetAsync(Ainv, 0, (size_t)nc * nc * sizeof(double), s));
+    k_coarse_assemble<T><<<(nc + 127) / 128, 128, 0, s>>>(C.g, C.en, C.ec, Ainv, nc);
+    k_coarse_invert<<<1, 1024, nc * sizeof(double), s>>>(Ainv, nc, flag);
+    count((long long)lv.size() - 1 + 2);
+  }
+
+  void sweep(int l, cudaStream_t s) {
+    Level<T>& L = lv[l];
+    const dim3 g = grid_rb(L.g.nx, L.g.ny, kBlk2);
+    for (int f = 0; f < 2; ++f)
+      for (int c = 0; c < 2; ++c)
+        k_rbgs<T><<<g, kBlk2, 0, s>>>(L.gt, L.vx, L.vy, L.fx, L.fy, L.en, L.ec, f, c, omega);
+    count(4);
+  }
+
+  // one V-cycle at level l for L x = f from x = 0 (x_l must be zero on entry)
+  void cycle(int l, cudaStream_t s) {
+    Level<T>& L = lv[l];
+    if (l == (int)lv.size() - 1) {
+      k_coarse_solve<T><<<1, 256, nc * sizeof(double), s>>>(L.g, Ainv, nc, L.fx, L.fy, L.vx, L.vy);
+      count(1);
+      return;
+    }
+    Level<T>& C = lv[l + 1];
+    for (int k = 0; k < nu1; ++k) sweep(l, s);
+    if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[2], s, cudaEventRecordExternal));
+    k_vresidual<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, L.vx, L.vy, L.fx, L.fy, L.en, L.ec, L.rx, L.ry);
+    k_restrict<T><<<grid2(C.g.nx, C.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C.gt, L.rx, L.ry, C.fx, C.fy);
+    count(2);
+    CK(cudaMemsetAsync(C.vx, 0, C.P * sizeof(T), s));
+    CK(cudaMemsetAsync(C.vy, 0, C.P * sizeof(T), s));
+    cycle(l + 1, s);
+    k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C.gt, L.vx, L.vy, C.vx, C.vy);
+    count(1);
+    if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[3], s, cudaEventRecordExternal));
+    for (int k = 0; k < nu2; ++k) sweep(l, s);
+    if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[4], s, cudaEventRecordExternal));
+  }
+};
+
+}  // namespace
+
+// ---- the handle -----------------------------------------------------------------------------
+struct pyro_stokes_s {
+  int dev = 0;
+  int nx = 0, ny = 0;
+  double Lx = 1, Ly = 1;
+  pyro_bc bc{};
+  pyro_opts o{};
+  Geom g{};
+  GeomT<double> g64{};
+  size_t P = 0, n3 = 0;
+  int nlev = 1;
+  bool mixed = true;
+  DevAlloc mem;
+  // FP64 state
+  double *en = nullptr, *ec = nullptr, *rho = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *w = nullptr,
+         *W = nullptr, *stage = nullptr, *xf = nullptr, *V = nullptr;
+  void* Z = nullptr;
+  double *h1 = nullptr, *h2 = nullptr, *partial = nullptr, *part2 = nullptr, *hcol = nullptr, *inv = nullptr,
+         *ydev = nullptr;
+  int *d_j = nullptr, *flag = nullptr;
+  // pinned host scratch
+  double* hbuf = nullptr;
+  int* hflag = nullptr;
+  MG<float> mgf;
+  MG<double> mgd;
+  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t ev[4]{};
+  bool have_solution = false;
+  double last_gx = 0, last_gy = 0;
+  int m = 30;
+  size_t dot_grid_y = 1;
+  // timing mode
+  bool timing = false, graph_timing = false;
+  cudaEvent_t tev[7]{};
+  double tacc[6]{};
+  long long tcount[2]{};
+  long long launches = 0;       // kernels launched by the current call
+  long long graph_kernels = 0;  // kernel nodes of the captured iteration graph
+};
+
+namespace {
+
+inline void mark(pyro_stokes_s* h, int k, cudaStream_t s) {
+  if (h->timing) CK(cudaEventRecordWithFlags(h->tev[k], s, cudaEventRecordExternal));
+}
+
+template <typename T, typename TZ>
+void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s) {
+  Level<T>& L0 = mg.lv[0];
+  mark(h, 0, s);
+  k_precond_in<T><<<kReduceBlocks, kThreads, 0, s>>>(h->P, h->V, h->n3, h->d_j, L0.fx, L0.fy, L0.vx, L0.vy);
+  mark(h, 1, s);
+  mg.hooks = h->timing ? h->tev : nullptr;
+  mg.nlaunch = &h->launches;
+  mg.cycle(0, s);
+  mg.hooks = nullptr;
+  h->launches += 4;
+  k_precond_out<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.vx, L0.vy, h->V, (TZ*)h->Z, h->n3, h->d_j,
+                                                           h->ec, h->o.alpha_p, h->part2);
+  k_sub_mean<TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, (TZ*)h->Z + 2 * h->P, h->n3, h->d_j, h->part2, kReduceBlocks);
+  k_apply<TZ><<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->ec, (const TZ*)h->Z, h->n3, h->d_j, h->w);
+  mark(h, 5, s);
+}
+
+// one Arnoldi step j (j read on the device): z_j = M^-1 v_j, w = A z_j, CGS2 against v_0..v_j,
+// v_{j+1} = w / ||w||_W, Hessenberg column j into hcol, j += 1.
+void iteration_body(pyro_stokes_s* h, cudaStream_t s) {
+  if (h->mixed) precond_body<float, float>(h, h->mgf, s);
+  else precond_body<double, double>(h, h->mgd, s);
+  const dim3 gd(kReduceBlocks, (unsigned)h->dot_grid_y);
+  k_multidot<<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial);
+  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, h->h1);
+  k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h1, h->n3, nullptr, nullptr);
+  k_multidot<<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial);
+  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, h->h2);
+  k_multiaxpy<<<kReduceBlocks, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h2, h->n3, h->W, h->part2);
+  k_arnoldi_finish<<<1, kThreads, 0, s>>>(h->d_j, h->h1, h->h2, h->part2, kReduceBlocks, h->hcol, h->inv, h->flag);
+  k_scale_next<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, h->n3, h->d_j, h->w, h->inv, h->n3);
+  k_inc<<<1, 1, 0, s>>>(h->d_j);
+  h->launches += 9;
+  mark(h, 6, s);
+}
+
+// after the iteration's sync: accumulate the phase times
+void collect_timing(pyro_stokes_s* h) {
+  if (!h->timing) return;
+  float t[6];
+  const int pairs[6][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {5, 6}};
+  for (int k = 0; k < 6; ++k) {
+    t[k] = 0.f;
+    if (cudaEventElapsedTime(&t[k], h->tev[pairs[k][0]], h->tev[pairs[k][1]]) != cudaSuccess) {
+      cudaGetLastError();
+      t[k] = 0.f;
+    }
+    h->tacc[k] += t[k];
+  }
+  h->tcount[0] += 1;
+  h->tcount[1] += h->o.nu1 + h->o.nu2;
+}
+
+void launch_iteration(pyro_stokes_s* h, cudaStream_t s) {
+  if (h->o.use_graphs) {
+    if (h->graph && h->graph_timing != h->timing) {
+      cudaGraphExecDestroy(h->graph);
+      h->graph = nullptr;
+    }
+    if (!h->graph) {
+      const long long saved = h->launches;  // capture records kernels, it does not launch them
+      h->graph_timing = h->timing;
+      cudaStream_t cs;
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaGraph_t gr;
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      iteration_body(h, cs);
+      cudaError_t e = cudaStreamEndCapture(cs, &gr);
+      cudaStreamDestroy(cs);
+      CK(e);
+      size_t nn = 0;
+      h->graph_kernels = 0;
+      if (cudaGraphGetNodes(gr, nullptr, &nn) == cudaSuccess && nn > 0) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(gr, nodes.data(), &nn);
+        for (auto nd : nodes) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++h->graph_kernels;
+        }
+      }
+      e = cudaGraphInstantiate(&h->graph, gr, 0);
+      cudaGraphDestroy(gr);
+      h->launches = saved;
+      CK(e);
+    }
+    CK(cudaGraphLaunch(h->graph, s));
+    h->launches += h->graph_kernels;
+  } else {
+    iteration_body(h, s);
+  }
+}
+
+// host-side sum of the per-block partials (fixed order)
+std::pair<double, double> residual_norms(pyro_stokes_s* h, const double* b, const double* x, double* r, cudaStream_t s) {
+  k_residual<<<kReduceBlocks, kThreads, 0, s>>>(h->g64, h->en, h->ec, b, x, r, h->W, h->partial);
+  h->launches += 1;
+  CK(cudaMemcpyAsync(h->hbuf, h->partial, 2 * kReduceBlocks * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double a = 0, c = 0;
+  for (int k = 0; k < kReduceBlocks; ++k) { a += h->hbuf[2 * k]; c += h->hbuf[2 * k + 1]; }
+  return {a, c};
+}
+
+double weighted_norm2(pyro_stokes_s* h, const double* v, cudaStream_t s) {
+  k_multidot<<<dim3(kReduceBlocks, 1), kThreads, 0, s>>>(v, 0, nullptr, 1, v, h->W, h->n3, h->partial);
+  h->launches += 1;
+  CK(cudaMemcpyAsync(h->hbuf, h->partial, kReduceBlocks * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double a = 0;
+  for (int k = 0; k < kReduceBlocks; ++k) a += h->hbuf[k];
+  return a;
+}
+
+double l2_norm2(pyro_stokes_s* h, const double* v, cudaStream_t s) {
+  k_sumsq<<<kReduceBlocks, kThreads, 0, s>>>(v, h->n3, h->partial);
+  h->launches += 1;
+  CK(cudaMemcpyAsync(h->hbuf, h->partial, kReduceBlocks * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double c = 0;
+  for (int k = 0; k < kReduceBlocks; ++k) c += h->hbuf[k];
+  return c;
+}
+
+void ingest(pyro_stokes_s* h, const double* src, double* dst, int kind, cudaStream_t s) {
+  const double* from = src;
+  if (!is_device_ptr(src)) {
+    CK(cudaMemcpyAsync(h->stage, src, h->P * sizeof(double), cudaMemcpyHostToDevice, s));
+    from = h->stage;
+  }
+  k_ingest<<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->nx, h->ny, h->g.ld, from, dst, kind, h->flag);
+  h->launches += 1;
+}
+
+// write x (3 planes) to caller arrays (host or device), ghosts by the boundary rule
+void emit(pyro_stokes_s* h, const double* x, double* vx, double* vy, double* p, bool with_bc_consts, cudaStream_t s) {
+  const double cN = with_bc_consts && h->bc.kind[2] == PYRO_BC_VELOCITY ? 2 * h->bc.vt[2] : 0.0;
+  const double cS = with_bc_consts && h->bc.kind[3] == PYRO_BC_VELOCITY ? 2 * h->bc.vt[3] : 0.0;
+  const double cW = with_bc_consts && h->bc.kind[0] == PYRO_BC_VELOCITY ? 2 * h->bc.vt[0] : 0.0;
+  const double cE = with_bc_consts && h->bc.kind[1] == PYRO_BC_VELOCITY ? 2 * h->bc.vt[1] : 0.0;
+  double* outs[3] = {vx, vy, p};
+  bool dev[3];
+  for (int k = 0; k < 3; ++k) dev[k] = outs[k] && is_device_ptr(outs[k]);
+  double* d[3];
+  for (int k = 0; k < 3; ++k) d[k] = outs[k] ? (dev[k] ? outs[k] : h->stage + k * h->P) : nullptr;
+  k_output<<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, x, d[0], d[1], d[2], cN, cS, cW, cE);
+  h->launches += 1;
+  for (int k = 0; k < 3; ++k)
+    if (outs[k] && !dev[k]) CK(cudaMemcpyAsync(outs[k], d[k], h->P * sizeof(double), cudaMemcpyDeviceToHost, s));
+}
+
+void setup_eta(pyro_stokes_s* h, cudaStream_t s) {
+  // level-0 viscosity of the V-cycle: FP32 copies (mixed) or the FP64 arrays themselves
+  if (h->mixed) {
+    Level<float>& L0 = h->mgf.lv[0];
+    k_to_float<<<kReduceBlocks, kThreads, 0, s>>>(h->en, L0.en, h->P);
+    k_to_float<<<kReduceBlocks, kThreads, 0, s>>>(h->ec, L0.ec, h->P);
+    h->launches += 2;
+    h->mgf.nlaunch = &h->launches;
+    h->mgf.setup(s, h->flag);
+  } else {
+    h->mgd.nlaunch = &h->launches;
+    h->mgd.setup(s, h->flag);
+  }
+  k_weights<<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->ec, h->W);
+  h->launches += 1;
+}
+
+// Givens-rotation least squares of FGMRES on the host
+struct Givens {
+  std::vector<double> H, cs, sn, gv;
+  int m;
+  explicit Givens(int m_) : H((size_t)(m_ + 1) * m_), cs(m_), sn(m_), gv(m_ + 1), m(m_) {}
+  double& at(int i, int j) { return H[(size_t)j * (m + 1) + i]; }
+  void start(double beta) { std::fill(gv.begin(), gv.end(), 0.0); gv[0] = beta; }
+  // returns |residual estimate|
+  double add_column(int j, const double* col) {
+    for (int i = 0; i <= j + 1; ++i) at(i, j) = col[i];
+    for (int k = 0; k < j; ++k) {
+      const double t = cs[k] * at(k, j) + sn[k] * at(k + 1, j);
+      at(k + 1, j) = -sn[k] * at(k, j) + cs[k] * at(k + 1, j);
+      at(k, j) = t;
+    }
+    const double a = at(j, j), bb = at(j + 1, j);
+    const double d = std::hypot(a, bb);
+    cs[j] = d > 0 ? a / d : 1.0;
+    sn[j] = d > 0 ? bb / d : 0.0;
+    at(j, j) = d;
+    at(j + 1, j) = 0.0;
+    gv[j + 1] = -sn[j] * gv[j];
+    gv[j] = cs[j] * gv[j];
+    return std::fabs(gv[j + 1]);
+  }
+  void solve(int k, double* y) {
+    for (int i = k - 1; i >= 0; --i) {
+      double t = gv[i];
+      for (int l = i + 1; l < k; ++l) t -= at(i, l) * y[l];
+      y[i] = at(i, i) != 0.0 ? t / at(i, i) : 0.0;
+    }
+  }
+};
+
+// FGMRES(m) on A x = b (h->b, h->x), preconditioned by one Uzawa/multigrid sweep, minimising the
+// W-weighted (energy) residual; restarts recompute the true FP64 residual (refinement step).
+int fgmres(pyro_stokes_s* h, double tol, pyro_stats* st, cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  CK(cudaEventRecord(h->ev[2], s));
+  const double nb2 = weighted_norm2(h, h->b, s);
+  const double nb = std::sqrt(nb2);
+  Givens gv(h->m);
+  std::vector<double> y(h->m);
+  int total = 0, restarts = 0, status = PYRO_OK;
+  double rel_e = 1.0;
+  if (nb == 0.0) {
+    CK(cudaMemsetAsync(h->x, 0, h->n3 * sizeof(double), s));
+    rel_e = 0.0;
+  }
+  while (nb > 0.0) {
+    auto rn = residual_norms(h, h->b, h->x, h->r, s);
+    const double beta = std::sqrt(rn.first);
+    rel_e = beta / nb;
+    if (!std::isfinite(beta)) { status = PYRO_E_NONFINITE; break; }
+    if (rel_e <= tol) break;
+    if (total >= h->o.max_iter) { status = PYRO_W_NOT_CONVERGED; break; }
+    if (h->o.timeout_s > 0) {
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > h->o.timeout_s) { status = PYRO_E_TIMEOUT; break; }
+    }
+    k_scale<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, h->r, 1.0 / beta, h->n3);
+    h->launches += 1;
+    CK(cudaMemsetAsync(h->d_j, 0, sizeof(int), s));
+    gv.start(beta);
+    int k = 0;
+    bool stop_inner = false;
+    for (int j = 0; j < h->m; ++j) {
+      launch_iteration(h, s);
+      CK(cudaMemcpyAsync(h->hbuf, h->hcol + (size_t)j * kHcolStride, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(h->hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      collect_timing(h);
+      ++total;
+      k = j + 1;
+      if (*h->hflag & FLAG_NONFINITE) { status = PYRO_E_NONFINITE; stop_inner = true; break; }
+      const double est = gv.add_column(j, h->hbuf);
+      const double hnext = h->hbuf[j + 1];
+      if (!std::isfinite(est)) { status = PYRO_E_NONFINITE; stop_inner = true; break; }
+      // stop the cycle a little below tol so the true residual check at restart passes
+      if (est <= 0.5 * tol * nb || hnext <= 1e-300) break;
+      if (total >= h->o.max_iter) break;
+      if (h->o.timeout_s > 0) {
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > h->o.timeout_s) break;
+      }
+    }
+    if (stop_inner && status != PYRO_OK) break;
+    gv.solve(k, y.data());
+    std::memcpy(h->hbuf, y.data(), k * sizeof(double));
+    CK(cudaMemcpyAsync(h->ydev, h->hbuf, k * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (h->mixed)
+      k_update_x<float><<<kReduceBlocks * 2, kThreads, 0, s>>>(h->x, (const float*)h->Z, h->n3, k, h->ydev, h->n3);
+    else
+      k_update_x<double><<<kReduceBlocks * 2, kThreads, 0, s>>>(h->x, (const double*)h->Z, h->n3, k, h->ydev, h->n3);
+    h->launches += 1;
+    ++restarts;
+  }
+  // zero-mean pressure (eq. pressure_normalization), then the final true residuals
+  k_psum<<<kReduceBlocks, kThreads, 0, s>>>(h->g64, h->x + 2 * h->P, h->part2);
+  k_sub_mean<double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, h->x + 2 * h->P, 0, nullptr, h->part2, kReduceBlocks);
+  h->launches += 2;
+  auto rn = residual_norms(h, h->b, h->x, h->r, s);
+  CK(cudaEventRecord(h->ev[3], s));
+  CK(cudaStreamSynchronize(s));
+  if (st) {
+    st->iters += total;
+    st->restarts += restarts;
+    st->vcycles += total;
+    st->rel_energy_res = nb > 0 ? std::sqrt(rn.first) / nb : 0.0;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
+    st->t_solve_ms += ms;
+    // algorithmic bytes: per iteration one V-cycle, the FP64 operator, and CGS2 over j+1 vectors
+    const double cells = (double)h->nx * h->ny;
+    const double tb = h->mixed ? 4.0 : 8.0;
+    const double vcycle = (h->o.nu1 + h->o.nu2) * 8.0 * tb * 4.0 / 3.0 + 10.0 * tb;
+    const double per_it = vcycle + 64.0 + 2 * 24.0 + 24.0 * 4.0 * (h->m / 4.0 + 1);
+    st->alg_bytes += cells * per_it * total;
+  }
+  if (status == PYRO_OK && !(rel_e <= tol) && nb > 0) {
+    const double fin = std::sqrt(rn.first) / nb;
+    if (!(fin <= tol)) status = PYRO_W_NOT_CONVERGED;
+  }
+  if (st) {
+    const double l2b = l2_norm2(h, h->b, s);
+    st->rel_l2_res = l2b > 0 ? std::sqrt(rn.second / l2b) : 0.0;
+  }
+  return status;
+}
+
+void validate_opts(pyro_opts& o) {
+  if (o.nu1 < 0) o.nu1 = 0;
+  if (o.nu2 < 0) o.nu2 = 0;
+  if (o.nu1 + o.nu2 == 0) o.nu2 = 1;
+  if (o.restart_m < 1) o.restart_m = 1;
+  if (o.restart_m > kMaxRestart) o.restart_m = kMaxRestart;
+  if (o.max_iter < 1) o.max_iter = 1;
+  if (o.coarsest_min < 1) o.coarsest_min = 1;
+}
+
+int check_size(int nx, int ny, const pyro_opts& o) {
+  if (nx < 2 || ny < 2 || (nx & 1) || (ny & 1)) return PYRO_E_INVALID;
+  int L = count_levels(nx, ny, o.coarsest_min);
+  int cx = nx, cy = ny;
+  for (int l = 1; l < L; ++l) { cx /= 2; cy /= 2; }
+  const int nc = cy * (cx - 1) + (cy - 1) * cx;
+  if (nc > kMaxCoarse || nc < 1) return PYRO_E_INVALID;
+  return L;
+}
+
+size_t footprint_bytes(int nx, int ny, const pyro_opts& o, int L) {
+  const size_t P = (size_t)(ny + 2) * (nx + 2);
+  const size_t n3 = 3 * P;
+  const bool mixed = o.prec == PYRO_PREC_MIXED;
+  const size_t m = (size_t)o.restart_m;
+  size_t b = 0;
+  b += 3 * P * 8;                  // en, ec, rho
+  b += 6 * n3 * 8;                 // b, x, r, w, W, xf
+  b += n3 * 8;                     // stage
+  b += (m + 1) * n3 * 8;           // V
+  b += m * n3 * (mixed ? 4 : 8);   // Z
+  b += mixed ? MG<float>::bytes(nx, ny, L) : MG<double>::bytes(nx, ny, L) - 2 * P * 8;
+  b += 2 * (kMaxRestart + 2) * 8 + 2 * (size_t)kReduceBlocks * (kMaxRestart + 1) * 8 + 4 * kReduceBlocks * 8 +
+       (size_t)kMaxRestart * kHcolStride * 8 + 64;
+  return b;
+}
+
+}  // namespace
+
+// ---- C ABI --------------------------------------------------------------------------------------
+extern "C" {
+
+void pyro_default_opts(pyro_opts* o) {
+  if (!o) return;
+  o->nu1 = 2; o->nu2 = 2;
+  o->omega_v = 1.0;
+  o->alpha_p = 1.0;
+  o->restart_m = 30;
+  o->max_iter = 500;
+  o->prec = PYRO_PREC_MIXED;
+  o->coarsest_min = 2;
+  o->eta_coarsen = PYRO_ETA_ARITH;
+  o->warm_start = 0;
+  o->use_graphs = 1;
+  o->timeout_s = 0.0;
+}
+
+const char* pyro_version(void) { return "pyro-b300 0.1 (sm_103a)"; }
+
+const char* pyro_strerror(int s) {
+  switch (s) {
+    case PYRO_OK: return "ok";
+    case PYRO_W_NOT_CONVERGED: return "not converged within max_iter (best iterate returned)";
+    case PYRO_E_INVALID: return "invalid argument or unsupported grid / boundary";
+    case PYRO_E_NOMEM: return "device allocation failed";
+    case PYRO_E_CUDA: return "CUDA runtime error";
+    case PYRO_E_NONFINITE: return "non-finite input or iterate";
+    case PYRO_E_TIMEOUT: return "wall-clock limit exceeded";
+    case PYRO_E_BREAKDOWN: return "Krylov or coarse-solve breakdown";
+    default: return "unknown status";
+  }
+}
+
+size_t pyro_stokes_footprint(int nx, int ny, const pyro_opts* opts) {
+  pyro_opts o;
+  pyro_default_opts(&o);
+  if (opts) o = *opts;
+  validate_opts(o);
+  const int L = check_size(nx, ny, o);
+  if (L < 1) return 0;
+  return footprint_bytes(nx, ny, o, L);
+}
+
+int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, const pyro_opts* opts,
+                       pyro_stokes* out) {
+  if (!out) return PYRO_E_INVALID;
+  *out = nullptr;
+  if (!(Lx > 0) || !(Ly > 0)) return PYRO_E_INVALID;
+  pyro_opts o;
+  pyro_default_opts(&o);
+  if (opts) o = *opts;
+  validate_opts(o);
+  pyro_bc b{};
+  for (int k = 0; k < 4; ++k) { b.kind[k] = PYRO_BC_FREE_SLIP; b.vt[k] = 0.0; }
+  if (bc) b = *bc;
+  for (int k = 0; k < 4; ++k) {
+    if (b.kind[k] != PYRO_BC_FREE_SLIP && b.kind[k] != PYRO_BC_NO_SLIP && b.kind[k] != PYRO_BC_VELOCITY)
+      return PYRO_E_INVALID;  // periodic: oracle only
+    if (!std::isfinite(b.vt[k])) return PYRO_E_INVALID;
+  }
+  const int L = check_size(nx, ny, o);
+  if (L < 1) return PYRO_E_INVALID;
+  pyro_stokes_s* h = new (std::nothrow) pyro_stokes_s();
+  if (!h) return PYRO_E_NOMEM;
+  try {
+    CK(cudaGetDevice(&h->dev));
+    h->nx = nx; h->ny = ny; h->Lx = Lx; h->Ly = Ly; h->bc = b; h->o = o;
+    h->g = make_geom(nx, ny, Lx, Ly, b);
+    h->g64 = geomT<double>(h->g);
+    h->P = (size_t)(ny + 2) * (nx + 2);
+    h->n3 = 3 * h->P;
+    h->nlev = L;
+    h->mixed = o.prec == PYRO_PREC_MIXED;
+    h->m = o.restart_m;
+    h->dot_grid_y = (h->m + 1 + 7) / 8;
+    DevAlloc& A = h->mem;
+    h->en = A.get<double>(h->P); h->ec = A.get<double>(h->P); h->rho = A.get<double>(h->P);
+    h->b = A.get<double>(h->n3); h->x = A.get<double>(h->n3); h->r = A.get<double>(h->n3);
+    h->w = A.get<double>(h->n3); h->W = A.get<double>(h->n3); h->xf = A.get<double>(h->n3);
+    h->stage = A.get<double>(h->n3);
+    h->V = A.get<double>((size_t)(h->m + 1) * h->n3);
+    if (h->mixed) h->Z = A.get<float>((size_t)h->m * h->n3);
+    else h->Z = A.get<double>((size_t)h->m * h->n3);
+    h->h1 = A.get<double>(kMaxRestart + 2); h->h2 = A.get<double>(kMaxRestart + 2);
+    h->partial = A.get<double>((size_t)kReduceBlocks * (kMaxRestart + 1) * 2);
+    h->part2 = A.get<double>(4 * kReduceBlocks);
+    h->hcol = A.get<double>((size_t)kMaxRestart * kHcolStride);
+    h->inv = A.get<double>(1);
+    h->ydev = A.get<double>(kMaxRestart + 2);
+    h->d_j = A.get<int>(1);
+    h->flag = A.get<int>(1);
+    if (h->mixed) {
+      h->mgf.nu1 = o.nu1; h->mgf.nu2 = o.nu2; h->mgf.omega = (float)o.omega_v; h->mgf.eta_mode = o.eta_coarsen;
+      h->mgf.alloc(A, h->g, L, false);
+    } else {
+      h->mgd.nu1 = o.nu1; h->mgd.nu2 = o.nu2; h->mgd.omega = o.omega_v; h->mgd.eta_mode = o.eta_coarsen;
+      h->mgd.alloc(A, h->g, L, true);
+      h->mgd.lv[0].en = h->en;
+      h->mgd.lv[0].ec = h->ec;
+    }
+    CK(cudaMallocHost(&h->hbuf, 4 * kReduceBlocks * sizeof(double) + 1024));
+    CK(cudaMallocHost(&h->hflag, sizeof(int)));
+    for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&h->ev[k]));
+    for (int k = 0; k < 7; ++k) CK(cudaEventCreate(&h->tev[k]));
+    CK(cudaMemset(h->x, 0, h->n3 * sizeof(double)));
+    CK(cudaMemset(h->xf, 0, h->n3 * sizeof(double)));
+    CK(cudaMemset(h->flag, 0, sizeof(int)));
+    CK(cudaDeviceSynchronize());
+  } catch (const std::bad_alloc&) {
+    pyro_stokes_destroy(h);
+    return PYRO_E_NOMEM;
+  } catch (const CudaError&) {
+    pyro_stokes_destroy(h);
+    return PYRO_E_CUDA;
+  }
+  *out = h;
+  return PYRO_OK;
+}
+
+int pyro_stokes_precond(pyro_stokes h, const double* eta_n, const double* eta_c, const double* r_vx,
+                        const double* r_vy, const double* r_p, double* z_vx, double* z_vy, double* z_p,
+                        void* cuda_stream) {
+  if (!h || !eta_n || !eta_c || !r_vx || !r_vy || !r_p || !z_vx || !z_vy || !z_p) return PYRO_E_INVALID;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  try {
+    CK(cudaSetDevice(h->dev));
+    h->have_solution = false;
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    ingest(h, eta_n, h->en, 3, s);
+    ingest(h, eta_c, h->ec, 2, s);
+    ingest(h, r_vx, h->V, 4, s);
+    ingest(h, r_vy, h->V + h->P, 5, s);
+    ingest(h, r_p, h->V + 2 * h->P, 2, s);
+    setup_eta(h, s);
+    CK(cudaMemsetAsync(h->d_j, 0, sizeof(int), s));
+    if (h->mixed) {
+      Level<float>& L0 = h->mgf.lv[0];
+      k_precond_in<float><<<kReduceBlocks, kThreads, 0, s>>>(h->P, h->V, h->n3, h->d_j, L0.fx, L0.fy, L0.vx, L0.vy);
+      h->mgf.cycle(0, s);
+      k_precond_out<float, float><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.vx, L0.vy, h->V, (float*)h->Z, h->n3,
+                                                                      h->d_j, h->ec, h->o.alpha_p, h->part2);
+      k_sub_mean<float><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, (float*)h->Z + 2 * h->P, h->n3, h->d_j, h->part2,
+                                                          kReduceBlocks);
+      k_to_double<<<kReduceBlocks, kThreads, 0, s>>>((const float*)h->Z, h->w, h->n3);
+    } else {
+      Level<double>& L0 = h->mgd.lv[0];
+      k_precond_in<double><<<kReduceBlocks, kThreads, 0, s>>>(h->P, h->V, h->n3, h->d_j, L0.fx, L0.fy, L0.vx, L0.vy);
+      h->mgd.cycle(0, s);
+      k_precond_out<double, double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.vx, L0.vy, h->V, (double*)h->Z,
+                                                                        h->n3, h->d_j, h->ec, h->o.alpha_p, h->part2);
+      k_sub_mean<double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, (double*)h->Z + 2 * h->P, h->n3, h->d_j, h->part2,
+                                                           kReduceBlocks);
+      CK(cudaMemcpyAsync(h->w, h->Z, h->n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    double* outs[3] = {z_vx, z_vy, z_p};
+    for (int k = 0; k < 3; ++k)
+      CK(cudaMemcpyAsync(outs[k], h->w + k * h->P, h->P * sizeof(double),
+                         is_device_ptr(outs[k]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*h->hflag & FLAG_NONFINITE) return PYRO_E_NONFINITE;
+    if (*h->hflag & FLAG_BREAKDOWN) return PYRO_E_BREAKDOWN;
+  } catch (const CudaError&) {
+    return PYRO_E_CUDA;
+  }
+  return PYRO_OK;
+}
+
+int pyro_stokes_set_timing(pyro_stokes h, int enable) {
+  if (!h) return PYRO_E_INVALID;
+  h->timing = enable != 0;
+  for (int k = 0; k < 6; ++k) h->tacc[k] = 0.0;
+  h->tcount[0] = h->tcount[1] = 0;
+  return PYRO_OK;
+}
+
+int pyro_stokes_get_timing(pyro_stokes h, double* ms, long long* counts) {
+  if (!h) return PYRO_E_INVALID;
+  if (ms)
+    for (int k = 0; k < 6; ++k) ms[k] = h->tacc[k];
+  if (counts) { counts[0] = h->tcount[0]; counts[1] = h->tcount[1]; }
+  return PYRO_OK;
+}
+
+void pyro_stokes_destroy(pyro_stokes h) {
+  if (!h) return;
+  cudaSetDevice(h->dev);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (int k = 0; k < 4; ++k)
+    if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+  for (int k = 0; k < 7; ++k)
+    if (h->tev[k]) cudaEventDestroy(h->tev[k]);
+  if (h->hbuf) cudaFreeHost(h->hbuf);
+  if (h->hflag) cudaFreeHost(h->hflag);
+  h->mem.release();
+  delete h;
+}
+
+int pyro_stokes_apply(pyro_stokes h, const double* eta_n, const double* eta_c, const double* vx, const double* vy,
+                      const double* p, double* Ax, double* Ay, double* Ap, void* cuda_stream) {
+  if (!h || !eta_n || !eta_c || !vx || !vy || !p || !Ax || !Ay || !Ap) return PYRO_E_INVALID;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  try {
+    CK(cudaSetDevice(h->dev));
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    ingest(h, eta_n, h->en, 3, s);
+    ingest(h, eta_c, h->ec, 2, s);
+    ingest(h, vx, h->r, 4, s);
+    ingest(h, vy, h->r + h->P, 5, s);
+    ingest(h, p, h->r + 2 * h->P, 2, s);
+    k_apply<double><<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->ec, h->r, 0, nullptr, h->w);
+    double* outs[3] = {Ax, Ay, Ap};
+    for (int k = 0; k < 3; ++k) {
+      if (is_device_ptr(outs[k])) CK(cudaMemcpyAsync(outs[k], h->w + k * h->P, h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      else CK(cudaMemcpyAsync(outs[k], h->w + k * h->P, h->P * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaMemcpyAsync(h->hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*h->hflag & FLAG_NONFINITE) return PYRO_E_NONFINITE;
+  } catch (const CudaError&) {
+    return PYRO_E_CUDA;
+  }
+  return PYRO_OK;
+}
+
+int pyro_stokes_solve(pyro_stokes h, const double* eta_n, const double* eta_c, const double* rho, double gx, double gy,
+                      double tol, double* vx, double* vy, double* p, pyro_stats* stats, void* cuda_stream) {
+  if (!h || !eta_n || !eta_c || !rho || !vx || !vy || !p) return PYRO_E_INVALID;
+  if (!(tol > 0) || !std::isfinite(gx) || !std::isfinite(gy)) return PYRO_E_INVALID;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  pyro_stats st{};
+  st.levels = h->nlev;
+  st.coarse_n = h->mixed ? h->mgf.nc : h->mgd.nc;
+  int status = PYRO_OK;
+  h->launches = 0;
+  try {
+    CK(cudaSetDevice(h->dev));
+    h->have_solution = false;
+    CK(cudaEventRecord(h->ev[0], s));
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    ingest(h, eta_n, h->en, 3, s);
+    ingest(h, eta_c, h->ec, 2, s);
+    ingest(h, rho, h->rho, 3, s);
+    if (h->o.warm_start) {
+      ingest(h, vx, h->x, 4, s);
+      ingest(h, vy, h->x + h->P, 5, s);
+      ingest(h, p, h->x + 2 * h->P, 2, s);
+    } else {
+      CK(cudaMemsetAsync(h->x, 0, h->n3 * sizeof(double), s));
+    }
+    CK(cudaMemcpyAsync(h->hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*h->hflag & FLAG_NONFINITE) { status = PYRO_E_NONFINITE; }
+    else {
+      const pyro_bc& b = h->bc;
+      auto cst = [&](int side) { return b.kind[side] == PYRO_BC_VELOCITY ? 2.0 * b.vt[side] : 0.0; };
+      k_rhs<<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->rho, gx, gy, cst(2), cst(3), cst(0), cst(1), h->b);
+      h->launches += 1;
+      setup_eta(h, s);
+      CK(cudaMemcpyAsync(h->hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaEventRecord(h->ev[1], s));
+      CK(cudaStreamSynchronize(s));
+      float ms = 0;
+      cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+      st.t_setup_ms = ms;
+      if (*h->hflag & FLAG_BREAKDOWN) status = PYRO_E_BREAKDOWN;
+      else status = fgmres(h, tol, &st, s);
+    }
+    if (status >= 0) {
+      CK(cudaMemcpyAsync(h->xf, h->x, h->n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      emit(h, h->x, vx, vy, p, true, s);
+      CK(cudaStreamSynchronize(s));
+      h->have_solution = true;
+      h->last_gx = gx; h->last_gy = gy;
+    }
+  } catch (const CudaError&) {
+    status = PYRO_E_CUDA;
+  }
+  st.status = status;
+  st.kernel_launches = h->launches;
+  if (stats) *stats = st;
+  return status;
+}
+
+int pyro_stokes_adjoint(pyro_stokes h, const double* dJ_dvx, const double* dJ_dvy, const double* dJ_dp, double tol,
+                        double* dJ_deta_n, double* dJ_deta_c, double* dJ_drho, pyro_stats* stats, void* cuda_stream) {
+  if (!h || !dJ_dvx || !dJ_dvy || !dJ_dp || !dJ_deta_n || !dJ_deta_c || !(tol > 0)) return PYRO_E_INVALID;
+  if (!h->have_solution) return PYRO_E_INVALID;
+  for (int k = 0; k < 4; ++k)
+    if (h->bc.kind[k] == PYRO_BC_VELOCITY) return PYRO_E_INVALID;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  pyro_stats st{};
+  st.levels = h->nlev;
+  st.coarse_n = h->mixed ? h->mgf.nc : h->mgd.nc;
+  int status = PYRO_OK;
+  h->launches = 0;
+  try {
+    CK(cudaSetDevice(h->dev));
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+    ingest(h, dJ_dvx, h->b, 4, s);
+    ingest(h, dJ_dvy, h->b + h->P, 5, s);
+    ingest(h, dJ_dp, h->b + 2 * h->P, 2, s);
+    // the constant-pressure null space: only the zero-mean part of dJ/dp is solvable
+    k_psum<<<kReduceBlocks, kThreads, 0, s>>>(h->g64, h->b + 2 * h->P, h->part2);
+    k_sub_mean<double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, h->b + 2 * h->P, 0, nullptr, h->part2, kReduceBlocks);
+    CK(cudaMemsetAsync(h->x, 0, h->n3 * sizeof(double), s));
+    CK(cudaMemcpyAsync(h->hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*h->hflag & FLAG_NONFINITE) status = PYRO_E_NONFINITE;
+    else status = fgmres(h, tol, &st, s);   // eta and the hierarchy of the last solve are still in place
+    if (status >= 0) {
+      // lambda is in h->x, the forward solution in h->xf
+      double* on = dJ_deta_n; double* oc = dJ_deta_c; double* orh = dJ_drho;
+      const bool dn = is_device_ptr(on), dc = is_device_ptr(oc), dr = orh && is_device_ptr(orh);
+      double* tn = dn ? on : h->stage;
+      double* tc = dc ? oc : h->stage + h->P;
+      double* tr = orh ? (dr ? orh : h->stage + 2 * h->P) : nullptr;
+      k_strain_product<<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->xf, h->x, tn, tc);
+      if (tr) k_rho_grad<<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->x, h->last_gx, h->last_gy, tr);
+      h->launches += tr ? 2 : 1;
+      if (!dn) CK(cudaMemcpyAsync(on, tn, h->P * sizeof(double), cudaMemcpyDeviceToHost, s));
+      if (!dc) CK(cudaMemcpyAsync(oc, tc, h->P * sizeof(double), cudaMemcpyDeviceToHost, s));
+      if (tr && !dr) CK(cudaMemcpyAsync(orh, tr, h->P * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    // restore the forward solution as the handle's current iterate
+    CK(cudaMemcpyAsync(h->x, h->xf, h->n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  } catch (const CudaError&) {
+    status = PYRO_E_CUDA;
+  }
+  st.status = status;
+  st.kernel_launches = h->launches;
+  if (stats) *stats = st;
+  return status;
+}
+
+}  // extern "C"

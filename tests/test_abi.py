@@ -1,0 +1,52 @@
+"""The C ABI library builds for sm_103a, loads, and exports every symbol declared in include/pyro.h
+(no compute call: this runs without a GPU)."""
+import os
+import re
+import ctypes
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    hdr = open(os.path.join(ROOT, "include", "pyro.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(pyro_[a-z_]+)\s*\(", hdr)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2603_14040_b300 import _build
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    syms = declared_symbols()
+    assert len(syms) >= 10
+    for s in syms:
+        assert hasattr(lib, s), s
+    import paper_2603_14040_b300 as P
+    assert sorted(P.EXPORTED) == syms
+
+
+def test_host_logic_without_gpu():
+    import paper_2603_14040_b300 as P
+    assert P.lib().pyro_version().startswith(b"pyro-b300")
+    assert P.lib().pyro_strerror(-4) == b"non-finite input or iterate"
+    o = P.default_opts()
+    assert (o.nu1, o.nu2, o.restart_m, o.prec, o.coarsest_min) == (2, 2, 30, P.PREC_MIXED, 2)
+    # footprint: odd / too coarse-unfriendly sizes are rejected, valid ones scale with the grid
+    assert P.footprint(100, 100) == 0 and P.footprint(3, 8) == 0
+    f1, f2 = P.footprint(512, 512), P.footprint(1024, 1024)
+    assert 3.5 < f2 / f1 < 4.5
+    o64 = P.default_opts(prec=P.PREC_FP64)
+    assert P.footprint(1024, 1024, o64) > f2
+    o10 = P.default_opts(restart_m=10)
+    assert P.footprint(1024, 1024, o10) < f2
+
+
+def test_product_path_has_no_oracle_dependency():
+    pkg = os.path.join(ROOT, "paper_2603_14040_b300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
