@@ -173,6 +173,28 @@ int pyro_stokes_precond(pyro_stokes h, const double* eta_n, const double* eta_c,
 int pyro_stokes_set_timing(pyro_stokes h, int enable);
 int pyro_stokes_get_timing(pyro_stokes h, double* ms, long long* counts);
 
+/* Allocation-free residual (no counterpart in the paper: an interface addition of this library).
+ * For callers that cannot call cudaMalloc — e.g. an application whose own pool allocator owns all
+ * device memory, or a latency-critical loop where an allocation's implicit synchronisation is
+ * not acceptable. Needs no handle and allocates nothing: computes r = b - A x with
+ * b = -rho g plus the boundary constants (exactly the residual of pyro_stokes_solve) for the
+ * fields vx, vy, p, writes r_vx, r_vy, r_p (residual at unknowns, 0 elsewhere) and
+ * rel_res[0] = relative energy residual, rel_res[1] = relative l2 residual (rel_res may be a
+ * host or device pointer; every field pointer must be a device pointer). Its only scratch is a
+ * fixed 128 KiB array in device global memory (16384 doubles: one 4-value partial per block of 4
+ * grid rows), held by every GPU that loads the library until the process exits; hence ny + 2 must
+ * not exceed 16380 rows (else PYRO_E_INVALID, as for host pointers or a periodic boundary). The
+ * first call on a device looks up the array's device address (once per device, with that device
+ * current); make that first call before any stream capture. All calls share the array and it keeps
+ * the last call's contents (every slot read is written first in the same call, so nothing needs to
+ * start at zero); calls that overlap on the GPU, on any streams, race on it. Returns after
+ * completion on cuda_stream. */
+int pyro_stokes_residual_noalloc(int nx, int ny, double Lx, double Ly, const pyro_bc* bc,
+                                 const double* eta_n, const double* eta_c, const double* rho,
+                                 double gx, double gy, const double* vx, const double* vy,
+                                 const double* p, double* r_vx, double* r_vy, double* r_p,
+                                 double* rel_res, void* cuda_stream);
+
 /* Release every device allocation of h (NULL is a no-op). */
 void pyro_stokes_destroy(pyro_stokes h);
 

@@ -23,11 +23,12 @@ def up_to_date():
 
 
 def build(force=False, verbose=False):
-    """Compile csrc/solver.cu (which includes the kernel headers) into libpyro.so."""
+    """Compile the translation units of csrc/ (solver.cu includes the kernel headers) into libpyro.so."""
     if not force and up_to_date():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc] + NVCC_FLAGS + ["-o", LIB + ".tmp", os.path.join(CSRC, "solver.cu")]
+    units = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cu")]
+    cmd = [nvcc] + NVCC_FLAGS + ["-o", LIB + ".tmp"] + units
     if verbose:
         print(" ".join(cmd))
     subprocess.run(cmd, check=True, cwd=CSRC)

@@ -42,7 +42,8 @@ class PyroStats(ctypes.Structure):
 
 
 EXPORTED = ["pyro_default_opts", "pyro_stokes_create", "pyro_stokes_footprint", "pyro_stokes_apply",
-            "pyro_stokes_solve", "pyro_stokes_precond", "pyro_stokes_set_timing", "pyro_stokes_get_timing", "pyro_stokes_adjoint", "pyro_stokes_destroy", "pyro_strerror", "pyro_version"]
+            "pyro_stokes_solve", "pyro_stokes_precond", "pyro_stokes_set_timing", "pyro_stokes_get_timing",
+            "pyro_stokes_residual_noalloc", "pyro_stokes_adjoint", "pyro_stokes_destroy", "pyro_strerror", "pyro_version"]
 
 
 def load_library(path=_LIB_PATH):
@@ -64,6 +65,9 @@ def load_library(path=_LIB_PATH):
     lib.pyro_stokes_set_timing.restype = I
     lib.pyro_stokes_get_timing.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
     lib.pyro_stokes_get_timing.restype = I
+    lib.pyro_stokes_residual_noalloc.argtypes = [I, I, D, D, ctypes.POINTER(PyroBC), P, P, P, D, D, P, P, P, P, P, P,
+                                                 P, P]
+    lib.pyro_stokes_residual_noalloc.restype = I
     lib.pyro_stokes_precond.argtypes = [P] * 9 + [P]
     lib.pyro_stokes_precond.restype = I
     lib.pyro_stokes_adjoint.argtypes = [P, P, P, P, D, P, P, P, ctypes.POINTER(PyroStats), P]
@@ -147,6 +151,18 @@ def _stream_handle(stream):
 
 def footprint(nx, ny, opts=None):
     return int(lib().pyro_stokes_footprint(nx, ny, ctypes.byref(opts) if opts is not None else None))
+
+
+def residual_noalloc(nx, ny, Lx, Ly, bc, eta_n, eta_c, rho, g, vx, vy, p, r_vx, r_vy, r_p, rel_res, stream=None):
+    """pyro_stokes_residual_noalloc: residual and relative energy / l2 residuals without any device
+    allocation (for callers that cannot allocate; see include/pyro.h). All fields must be CUDA
+    tensors; rel_res is a float64 array of 2 (host or device). Returns the status code."""
+    s = (ny + 2, nx + 2)
+    return lib().pyro_stokes_residual_noalloc(int(nx), int(ny), float(Lx), float(Ly),
+                                              ctypes.byref(bc if bc is not None else make_bc()),
+                                              _ptr(eta_n, s), _ptr(eta_c, s), _ptr(rho, s), float(g[0]),
+                                              float(g[1]), _ptr(vx, s), _ptr(vy, s), _ptr(p, s), _ptr(r_vx, s),
+                                              _ptr(r_vy, s), _ptr(r_p, s), _ptr(rel_res), _stream_handle(stream))
 
 
 class Stokes:
