@@ -87,6 +87,16 @@ typedef struct {
   int warm_start;        /* 1: vx, vy, p passed to solve hold the initial guess [0] */
   int use_graphs;        /* 1: capture the FGMRES iteration into a CUDA graph [1] */
   double timeout_s;      /* wall-clock limit of one solve, <= 0 for none [0] */
+  int kcycle;            /* K-cycle depth: on levels l < kcycle the coarse correction is two
+                            flexible-CG steps preconditioned by the next level's cycle (recursive
+                            Krylov cycle, not in the paper; 0 = the paper's plain V-cycle) [0] */
+  int cluster_cells;     /* levels with at most this many cells run their whole cycle inside one
+                            thread-block-cluster launch (8 CTAs, cluster barriers between steps);
+                            <= 0 = never, every step is its own kernel [0] */
+  int tile_fusion;       /* 1: smoothing sweeps (with the prolongation) and residual+restriction run
+                            as shared-memory tile kernels, one launch each per level visit (all FP32
+                            levels; FP64 levels up to 65536 cells); 0: one kernel per colour and
+                            step [1] */
 } pyro_opts;
 
 typedef struct {
@@ -155,7 +165,7 @@ int pyro_stokes_adjoint(pyro_stokes h, const double* dJ_dvx, const double* dJ_dv
  * hierarchy from eta_n, eta_c exactly as pyro_stokes_solve does, then applies one Uzawa sweep
  * (paper Sec. "Uzawa Iteration as a Fixed Point Method"): z_v = one multigrid V-cycle on L z_v = r_v
  * from zero (eq. multigrid_levels), z_p = alpha_p eta_c (r_p - D z_v) with its mean removed. In
- * PYRO_PREC_MIXED the V-cycle runs in FP32 and z is rounded to FP32 before it is returned.
+ * PYRO_PREC_MIXED the V-cycle runs in FP32 (z_v holds its FP32 values) and z_p is FP64.
  * Inputs r_vx, r_vy, r_p are read at their unknown locations; outputs are written there and 0
  * elsewhere. Returns after completion on cuda_stream. */
 int pyro_stokes_precond(pyro_stokes h, const double* eta_n, const double* eta_c, const double* r_vx,

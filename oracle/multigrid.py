@@ -212,8 +212,13 @@ class Hierarchy:
         return len(self.grids)
 
 
-def vcycle(h, f, nu1=2, nu2=2, omega=1.0, level=0):
-    """One V-cycle for L x = f at `level` from x = 0 (eq. multigrid_levels, steps (1)-(6))."""
+def vcycle(h, f, nu1=2, nu2=2, omega=1.0, level=0, kcycle=0):
+    """One V-cycle for L x = f at `level` from x = 0 (eq. multigrid_levels, steps (1)-(6)).
+
+    With kcycle > 0, on levels l < kcycle whose next level is not the coarsest, step (4) is
+    replaced by the recursive Krylov cycle of Notay & Vassilevski (Numer. Linear Algebra Appl.
+    15, 2008): two flexible conjugate-gradient steps on the next level's correction equation,
+    each preconditioned by one cycle of that level (not part of the paper)."""
     if level == h.nlev - 1:
         return h.coarse_lu.solve(f)
     L = h.L[level]
@@ -222,11 +227,33 @@ def vcycle(h, f, nu1=2, nu2=2, omega=1.0, level=0):
         x = rbgs_sweep(L, f, x, h.sets[level], omega)             # (1) pre-smoothing
     r = f - L @ x                                                 # (2) residual
     fc = h.R[level] @ r                                           # (3) restriction
-    dc = vcycle(h, fc, nu1, nu2, omega, level + 1)                # (4) coarse solve / recursion
+    if level < kcycle and level + 1 < h.nlev - 1:                 # (4) by two flexible-CG steps
+        dc = kcycle_correction(h, fc, nu1, nu2, omega, level + 1, kcycle)
+    else:                                                         # (4) coarse solve / recursion
+        dc = vcycle(h, fc, nu1, nu2, omega, level + 1, kcycle)
     x = x + h.P[level] @ dc                                       # (5) prolongation + correction
     for _ in range(nu2):
         x = rbgs_sweep(L, f, x, h.sets[level], omega)             # (6) post-smoothing
     return x
+
+
+def kcycle_correction(h, f, nu1, nu2, omega, level, kcycle):
+    """Two flexible-CG steps for L e = f on `level` from e = 0, preconditioner = one cycle.
+    L is negative definite; the step lengths are the usual CG ones written for L itself."""
+    L = h.L[level]
+    rc = f.copy()
+    z1 = vcycle(h, rc, nu1, nu2, omega, level, kcycle)
+    d1 = z1
+    q1 = L @ d1
+    a1 = (rc @ d1) / (d1 @ q1) if (d1 @ q1) != 0 else 0.0
+    e = a1 * d1
+    rc = rc - a1 * q1
+    z2 = vcycle(h, rc, nu1, nu2, omega, level, kcycle)
+    beta = (z2 @ q1) / (d1 @ q1) if (d1 @ q1) != 0 else 0.0
+    d2 = z2 - beta * d1                      # L-conjugate to d1 (flexible CG)
+    q2 = L @ d2
+    a2 = (rc @ d2) / (d2 @ q2) if (d2 @ q2) != 0 else 0.0
+    return e + a2 * d2
 
 
 def divergence(grid, zv):
@@ -241,12 +268,12 @@ def divergence(grid, zv):
     return (vx[i, j] - vx[i, jm]) / grid.dx + (vy[i, j] - vy[i - 1, j]) / grid.dy
 
 
-def uzawa_precond(h, r, eta_c, alpha=0.6, nu1=2, nu2=2, omega=1.0, literal_sign=False):
+def uzawa_precond(h, r, eta_c, alpha=0.6, nu1=2, nu2=2, omega=1.0, literal_sign=False, kcycle=0):
     """z = M^-1 r for one Uzawa sweep: z_v = V-cycle(L, r_v), z_p = alpha eta_c (r_p - D z_v),
     then the mean of z_p is removed (Eq. pressure_normalization). `literal_sign` flips to the
     paper's printed sign alpha eta_c (D z_v - r_p) (used only to demonstrate the reading)."""
     g = h.grids[0]
-    zv = vcycle(h, r[:g.n_v], nu1, nu2, omega)
+    zv = vcycle(h, r[:g.n_v], nu1, nu2, omega, kcycle=kcycle)
     e = g.eta_c_at(eta_c, g.p_i, g.p_j)
     dz = divergence(g, zv)
     zp = alpha * e * ((dz - r[g.n_v:]) if literal_sign else (r[g.n_v:] - dz))

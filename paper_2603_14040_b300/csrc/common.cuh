@@ -113,7 +113,7 @@ __device__ inline T ly_point(const GeomT<T>& g, int i, int j, const SV* vx, cons
 // Error flags written by kernels (host reads them after a sync).
 enum : int { FLAG_NONFINITE = 1, FLAG_BREAKDOWN = 2 };
 
-constexpr int kReduceBlocks = 296;  // 2 x 148 SMs: fixed so reductions are deterministic
+constexpr int kReduceBlocks = 592;  // 4 x 148 SMs: fixed so reductions are deterministic
 constexpr int kThreads = 256;
 
 }  // namespace pyro

@@ -181,15 +181,20 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
 // nvec = *d_j + 1 (or nfix when d_j is null). blockIdx.y selects the group of 8 vectors.
 __global__ void k_multidot(const double* __restrict__ V, size_t stride, const int* __restrict__ d_j, int nfix,
                            const double* __restrict__ w, const double* __restrict__ W, size_t n,
-                           double* __restrict__ partial) {
+                           double* __restrict__ partial, const int* __restrict__ d_run, double* __restrict__ part_ww) {
   __shared__ double sh[32];
+  if (d_run && *d_run == 0) return;  // optional device-side switch
   const int nvec = d_j ? (*d_j + 1) : nfix;
   const int k0 = blockIdx.y * 8;
   if (k0 >= nvec) return;
   const int kn = min(8, nvec - k0);
+  const bool ww = part_ww && blockIdx.y == 0;
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double aww = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const double t = W[e] * w[e];
+    const double we = w[e];
+    const double t = W[e] * we;
+    if (ww) aww += t * we;
 #pragma unroll
     for (int q = 0; q < 8; ++q)
       if (q < kn) acc[q] += t * V[(size_t)(k0 + q) * stride + e];
@@ -198,12 +203,17 @@ __global__ void k_multidot(const double* __restrict__ V, size_t stride, const in
     const double s = block_sum(acc[q], sh);
     if (threadIdx.x == 0) partial[(size_t)(k0 + q) * gridDim.x + blockIdx.x] = s;
   }
+  if (ww) {
+    const double s = block_sum(aww, sh);
+    if (threadIdx.x == 0) part_ww[blockIdx.x] = s;
+  }
 }
 
 // out[k] = sum_b partial[k * nblk + b] for k < nvec (one block per k, fixed order)
 __global__ void k_reduce(const double* __restrict__ partial, int nblk, const int* __restrict__ d_j, int nfix,
-                         double* __restrict__ out) {
+                         double* __restrict__ out, const int* __restrict__ d_run) {
   __shared__ double sh[32];
+  if (d_run && *d_run == 0) return;
   const int nvec = d_j ? (*d_j + 1) : nfix;
   const int k = blockIdx.x;
   if (k >= nvec) return;
@@ -216,9 +226,10 @@ __global__ void k_reduce(const double* __restrict__ partial, int nblk, const int
 // w -= sum_{k<nvec} h[k] V_k; if part != null also per-block sum(W w^2) into part[blockIdx.x]
 __global__ void k_multiaxpy(double* __restrict__ w, const double* __restrict__ V, size_t stride,
                             const int* __restrict__ d_j, const double* __restrict__ h, size_t n,
-                            const double* __restrict__ W, double* __restrict__ part) {
+                            const double* __restrict__ W, double* __restrict__ part, const int* __restrict__ d_run) {
   __shared__ double sh[32];
   __shared__ double hs[128];
+  if (d_run && *d_run == 0) return;
   const int nvec = *d_j + 1;
   for (int k = threadIdx.x; k < nvec; k += blockDim.x) hs[k] = h[k];
   __syncthreads();
@@ -239,15 +250,19 @@ __global__ void k_multiaxpy(double* __restrict__ w, const double* __restrict__ V
 // hcol[k] = h1[k] + h2[k] (k <= j), hcol[j+1] = ||w||_W; inv = 1/||w||_W.
 __global__ void k_arnoldi_finish(const int* __restrict__ d_j, const double* __restrict__ h1,
                                  const double* __restrict__ h2, const double* __restrict__ part, int nblk,
-                                 double* __restrict__ hcol, double* __restrict__ inv, int* __restrict__ flag) {
+                                 double* __restrict__ hcol, double* __restrict__ inv, int* __restrict__ flag,
+                                 const int* __restrict__ d_run, const double* __restrict__ nrm2_after1) {
   __shared__ double sh[32];
+  const bool second = d_run == nullptr || *d_run != 0;
   double s = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[b];
+  if (second)
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[b];
   s = block_sum(s, sh);
   if (threadIdx.x != 0) return;
+  if (!second) s = *nrm2_after1;
   const int j = *d_j;
   double* col = hcol + (size_t)j * 66;
-  for (int k = 0; k <= j; ++k) col[k] = h1[k] + h2[k];
+  for (int k = 0; k <= j; ++k) col[k] = h1[k] + (second ? h2[k] : 0.0);
   const double nrm = sqrt(s);
   col[j + 1] = nrm;
   if (!isfinite(nrm)) atomicOr(flag, FLAG_NONFINITE);
@@ -464,8 +479,8 @@ template __global__ void k_update_x<float>(double*, const float*, size_t, int, c
 template __global__ void k_precond_in<float>(size_t, const double*, size_t, const int*, float*, float*, float*, float*);
 template __global__ void k_precond_in<double>(size_t, const double*, size_t, const int*, double*, double*, double*,
                                               double*);
-template __global__ void k_precond_out<float, float>(GeomT<double>, const float*, const float*, const double*, float*,
-                                                     size_t, const int*, const double*, double, double*);
+template __global__ void k_precond_out<float, double>(GeomT<double>, const float*, const float*, const double*,
+                                                      double*, size_t, const int*, const double*, double, double*);
 template __global__ void k_precond_out<double, double>(GeomT<double>, const double*, const double*, const double*,
                                                        double*, size_t, const int*, const double*, double, double*);
 template __global__ void k_sub_mean<float>(GeomT<double>, float*, size_t, const int*, const double*, int);

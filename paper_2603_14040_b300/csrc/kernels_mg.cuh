@@ -21,34 +21,64 @@
 
 namespace pyro {
 
+// idg (optional): precomputed 1/diag per field (used on FP64 levels, where a division costs far
+// more than a load); without it the diagonal is divided inline.
 template <typename T>
-__global__ void k_rbgs(GeomT<T> g, T* __restrict__ vx, T* __restrict__ vy, const T* __restrict__ fx,
-                       const T* __restrict__ fy, const T* __restrict__ en, const T* __restrict__ ec,
-                       int field, int colour, T omega) {
-  const int i = blockIdx.y * blockDim.y + threadIdx.y;
-  const int jh = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = 2 * jh + ((i + colour) & 1);
-  if (i > g.ny + 1 || j > g.nx + 1) return;
+__device__ inline void rbgs_point(const GeomT<T>& g, int i, int j, int field, T omega, T* vx, T* vy, const T* fx,
+                                  const T* fy, const T* en, const T* ec, const T* idgx, const T* idgy) {
   const size_t c = (size_t)i * g.ld + j;
   T diag;
   if (field == 0) {
     if (!is_vx(g.nx, g.ny, i, j)) return;
     const T Lv = lx_point<T>(g, i, j, vx, vy, en, ec, diag);
-    vx[c] += omega * (fx[c] - Lv) / diag;
+    if (idgx) vx[c] += omega * (fx[c] - Lv) * idgx[c];
+    else vx[c] += omega * (fx[c] - Lv) / diag;
   } else {
     if (!is_vy(g.nx, g.ny, i, j)) return;
     const T Lv = ly_point<T>(g, i, j, vx, vy, en, ec, diag);
-    vy[c] += omega * (fy[c] - Lv) / diag;
+    if (idgy) vy[c] += omega * (fy[c] - Lv) * idgy[c];
+    else vy[c] += omega * (fy[c] - Lv) / diag;
   }
 }
 
 template <typename T>
-__global__ void k_vresidual(GeomT<T> g, const T* __restrict__ vx, const T* __restrict__ vy,
-                            const T* __restrict__ fx, const T* __restrict__ fy, const T* __restrict__ en,
-                            const T* __restrict__ ec, T* __restrict__ rx, T* __restrict__ ry) {
+__global__ void k_invdiag(GeomT<T> g, const T* __restrict__ en, const T* __restrict__ ec, T* __restrict__ idgx,
+                          T* __restrict__ idgy) {
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (i > g.ny + 1 || j > g.nx + 1) return;
+  const size_t c = (size_t)i * g.ld + j;
+  T ox = T(0), oy = T(0);
+  if (is_vx(g.nx, g.ny, i, j)) {
+    T d = -T(2) * (ec[c] + ec[c + 1]) * g.idx2 - (en[c - g.ld] + en[c]) * g.idy2;
+    if (i == 1) d += g.sN * en[c - g.ld] * g.idy2;
+    if (i == g.ny) d += g.sS * en[c] * g.idy2;
+    ox = T(1) / d;
+  }
+  if (is_vy(g.nx, g.ny, i, j)) {
+    T d = -T(2) * (ec[c] + ec[c + g.ld]) * g.idy2 - (en[c - 1] + en[c]) * g.idx2;
+    if (j == 1) d += g.sW * en[c - 1] * g.idx2;
+    if (j == g.nx) d += g.sE * en[c] * g.idx2;
+    oy = T(1) / d;
+  }
+  idgx[c] = ox;
+  idgy[c] = oy;
+}
+
+template <typename T>
+__global__ void k_rbgs(GeomT<T> g, T* __restrict__ vx, T* __restrict__ vy, const T* __restrict__ fx,
+                       const T* __restrict__ fy, const T* __restrict__ en, const T* __restrict__ ec,
+                       int field, int colour, T omega, const T* __restrict__ idgx, const T* __restrict__ idgy) {
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  const int jh = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = 2 * jh + ((i + colour) & 1);
+  if (i > g.ny + 1 || j > g.nx + 1) return;
+  rbgs_point<T>(g, i, j, field, omega, vx, vy, fx, fy, en, ec, idgx, idgy);
+}
+
+template <typename T>
+__device__ inline void vresid_point(const GeomT<T>& g, int i, int j, const T* vx, const T* vy, const T* fx,
+                                    const T* fy, const T* en, const T* ec, T* rx, T* ry) {
   const size_t c = (size_t)i * g.ld + j;
   T d, ox = T(0), oy = T(0);
   if (is_vx(g.nx, g.ny, i, j)) ox = fx[c] - lx_point<T>(g, i, j, vx, vy, en, ec, d);
@@ -58,11 +88,18 @@ __global__ void k_vresidual(GeomT<T> g, const T* __restrict__ vx, const T* __res
 }
 
 template <typename T>
-__global__ void k_restrict(GeomT<T> gf, GeomT<T> gc, const T* __restrict__ rx, const T* __restrict__ ry,
-                           T* __restrict__ fxc, T* __restrict__ fyc) {
-  const int I = blockIdx.y * blockDim.y + threadIdx.y;
-  const int J = blockIdx.x * blockDim.x + threadIdx.x;
-  if (I > gc.ny + 1 || J > gc.nx + 1) return;
+__global__ void k_vresidual(GeomT<T> g, const T* __restrict__ vx, const T* __restrict__ vy,
+                            const T* __restrict__ fx, const T* __restrict__ fy, const T* __restrict__ en,
+                            const T* __restrict__ ec, T* __restrict__ rx, T* __restrict__ ry) {
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > g.ny + 1 || j > g.nx + 1) return;
+  vresid_point<T>(g, i, j, vx, vy, fx, fy, en, ec, rx, ry);
+}
+
+template <typename T>
+__device__ inline void restrict_point(const GeomT<T>& gf, const GeomT<T>& gc, int I, int J, const T* rx,
+                                      const T* ry, T* fxc, T* fyc) {
   const size_t C = (size_t)I * gc.ld + J;
   const T w4[4] = {T(1), T(3), T(3), T(1)};
   const T w3[3] = {T(1), T(2), T(1)};
@@ -100,6 +137,16 @@ __global__ void k_restrict(GeomT<T> gf, GeomT<T> gc, const T* __restrict__ rx, c
   fyc[C] = oy;
 }
 
+
+template <typename T>
+__global__ void k_restrict(GeomT<T> gf, GeomT<T> gc, const T* __restrict__ rx, const T* __restrict__ ry,
+                           T* __restrict__ fxc, T* __restrict__ fyc) {
+  const int I = blockIdx.y * blockDim.y + threadIdx.y;
+  const int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I > gc.ny + 1 || J > gc.nx + 1) return;
+  restrict_point<T>(gf, gc, I, J, rx, ry, fxc, fyc);
+}
+
 template <typename T>
 __device__ inline T coarse_vx(const GeomT<T>& gc, const T* vxc, int I, int J) {
   if (J <= 0 || J >= gc.nx) return T(0);
@@ -115,44 +162,51 @@ __device__ inline T coarse_vy(const GeomT<T>& gc, const T* vyc, int I, int J) {
   return vyc[(size_t)I * gc.ld + J];
 }
 
+// bilinear coarse-to-fine increments at a fine vx / vy unknown (rows and columns follow the
+// node-centred or cell-centred direction of each component)
+template <typename T>
+__device__ inline T prolong_vx_inc(const GeomT<T>& gc, int i, int j, const T* vxc) {
+  const int I0 = (i & 1) ? (i - 1) / 2 : i / 2;
+  const T wy0 = (i & 1) ? T(0.25) : T(0.75);
+  const T wy1 = T(1) - wy0;
+  if (j & 1) {
+    const int J0 = (j - 1) / 2;
+    return T(0.5) * (wy0 * coarse_vx(gc, vxc, I0, J0) + wy1 * coarse_vx(gc, vxc, I0 + 1, J0) +
+                     wy0 * coarse_vx(gc, vxc, I0, J0 + 1) + wy1 * coarse_vx(gc, vxc, I0 + 1, J0 + 1));
+  }
+  const int J = j / 2;
+  return wy0 * coarse_vx(gc, vxc, I0, J) + wy1 * coarse_vx(gc, vxc, I0 + 1, J);
+}
+
+template <typename T>
+__device__ inline T prolong_vy_inc(const GeomT<T>& gc, int i, int j, const T* vyc) {
+  const int J0 = (j & 1) ? (j - 1) / 2 : j / 2;
+  const T wx0 = (j & 1) ? T(0.25) : T(0.75);
+  const T wx1 = T(1) - wx0;
+  if (i & 1) {
+    const int I0 = (i - 1) / 2;
+    return T(0.5) * (wx0 * coarse_vy(gc, vyc, I0, J0) + wx1 * coarse_vy(gc, vyc, I0, J0 + 1) +
+                     wx0 * coarse_vy(gc, vyc, I0 + 1, J0) + wx1 * coarse_vy(gc, vyc, I0 + 1, J0 + 1));
+  }
+  const int I = i / 2;
+  return wx0 * coarse_vy(gc, vyc, I, J0) + wx1 * coarse_vy(gc, vyc, I, J0 + 1);
+}
+
+template <typename T>
+__device__ inline void prolong_point(const GeomT<T>& gf, const GeomT<T>& gc, int i, int j, T* vxf, T* vyf,
+                                     const T* vxc, const T* vyc) {
+  const size_t c = (size_t)i * gf.ld + j;
+  if (is_vx(gf.nx, gf.ny, i, j)) vxf[c] += prolong_vx_inc(gc, i, j, vxc);
+  if (is_vy(gf.nx, gf.ny, i, j)) vyf[c] += prolong_vy_inc(gc, i, j, vyc);
+}
+
 template <typename T>
 __global__ void k_prolong_add(GeomT<T> gf, GeomT<T> gc, T* __restrict__ vxf, T* __restrict__ vyf,
                               const T* __restrict__ vxc, const T* __restrict__ vyc) {
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (i > gf.ny + 1 || j > gf.nx + 1) return;
-  const size_t c = (size_t)i * gf.ld + j;
-  if (is_vx(gf.nx, gf.ny, i, j)) {
-    // rows: cell-centred (weights 3/4, 1/4); columns: node-centred (1 or 1/2, 1/2)
-    const int I0 = (i & 1) ? (i - 1) / 2 : i / 2;
-    const T wy0 = (i & 1) ? T(0.25) : T(0.75);
-    const T wy1 = T(1) - wy0;
-    T v;
-    if (j & 1) {
-      const int J0 = (j - 1) / 2;
-      v = T(0.5) * (wy0 * coarse_vx(gc, vxc, I0, J0) + wy1 * coarse_vx(gc, vxc, I0 + 1, J0) +
-                    wy0 * coarse_vx(gc, vxc, I0, J0 + 1) + wy1 * coarse_vx(gc, vxc, I0 + 1, J0 + 1));
-    } else {
-      const int J = j / 2;
-      v = wy0 * coarse_vx(gc, vxc, I0, J) + wy1 * coarse_vx(gc, vxc, I0 + 1, J);
-    }
-    vxf[c] += v;
-  }
-  if (is_vy(gf.nx, gf.ny, i, j)) {
-    const int J0 = (j & 1) ? (j - 1) / 2 : j / 2;
-    const T wx0 = (j & 1) ? T(0.25) : T(0.75);
-    const T wx1 = T(1) - wx0;
-    T v;
-    if (i & 1) {
-      const int I0 = (i - 1) / 2;
-      v = T(0.5) * (wx0 * coarse_vy(gc, vyc, I0, J0) + wx1 * coarse_vy(gc, vyc, I0, J0 + 1) +
-                    wx0 * coarse_vy(gc, vyc, I0 + 1, J0) + wx1 * coarse_vy(gc, vyc, I0 + 1, J0 + 1));
-    } else {
-      const int I = i / 2;
-      v = wx0 * coarse_vy(gc, vyc, I, J0) + wx1 * coarse_vy(gc, vyc, I, J0 + 1);
-    }
-    vyf[c] += v;
-  }
+  prolong_point<T>(gf, gc, i, j, vxf, vyf, vxc, vyc);
 }
 
 template <typename T>
@@ -199,6 +253,122 @@ __global__ void k_coarsen_eta(GeomT<T> gf, GeomT<T> gc, const T* __restrict__ en
   }
   enc[C] = on;
   ecc[C] = oc;
+}
+
+// ---- K-cycle (recursive Krylov cycle): the coarse correction of level l is obtained by two
+// flexible-CG steps on level l+1 preconditioned by the level-(l+1) cycle. All vectors live on
+// level l+1. The residual of the CG iteration is kept in f (the cycle's right-hand side).
+// Dot products accumulate in double with one partial per block (fixed block count, fixed order).
+
+template <typename T>
+__device__ inline double kc_block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
+  return s;
+}
+
+// step 1: d1 = z1 (= x), q1 = L d1; partials [rc.d1, d1.q1] -> part[2*blk + {0,1}]
+template <typename T>
+__global__ void k_kc_step1(GeomT<T> g, const T* __restrict__ xx, const T* __restrict__ xy,
+                           const T* __restrict__ fx, const T* __restrict__ fy, const T* __restrict__ en,
+                           const T* __restrict__ ec, T* __restrict__ d1x, T* __restrict__ d1y,
+                           T* __restrict__ q1x, T* __restrict__ q1y, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const size_t P = (size_t)(g.ny + 2) * g.ld;
+  const int cols = g.nx + 2;
+  double a = 0.0, b = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / cols), j = (int)(e % cols);
+    T d, qx = T(0), qy = T(0), zx = T(0), zy = T(0);
+    if (is_vx(g.nx, g.ny, i, j)) { zx = xx[e]; qx = lx_point<T>(g, i, j, xx, xy, en, ec, d); }
+    if (is_vy(g.nx, g.ny, i, j)) { zy = xy[e]; qy = ly_point<T>(g, i, j, xx, xy, en, ec, d); }
+    d1x[e] = zx; d1y[e] = zy; q1x[e] = qx; q1y[e] = qy;
+    a += (double)fx[e] * zx + (double)fy[e] * zy;
+    b += (double)zx * qx + (double)zy * qy;
+  }
+  a = kc_block_sum<T>(a, sh);
+  b = kc_block_sum<T>(b, sh);
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = a; part[2 * blockIdx.x + 1] = b; }
+}
+
+// out[k] = sum_b part[nval*b + k], one block, fixed order
+__global__ void k_kc_reduce(const double* __restrict__ part, int nblk, int nval, double* __restrict__ out) {
+  __shared__ double sh[32];
+  for (int k = 0; k < nval; ++k) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[nval * b + k];
+    s = kc_block_sum<double>(s, sh);
+    if (threadIdx.x == 0) out[k] = s;
+  }
+}
+
+// alpha1 = (rc.d1)/(d1.q1); e = alpha1 d1; rc -= alpha1 q1 (in f); x = 0
+template <typename T>
+__global__ void k_kc_update1(size_t P, const double* __restrict__ s1, const T* __restrict__ d1x,
+                             const T* __restrict__ d1y, const T* __restrict__ q1x, const T* __restrict__ q1y,
+                             T* __restrict__ ex, T* __restrict__ ey, T* __restrict__ fx, T* __restrict__ fy,
+                             T* __restrict__ xx, T* __restrict__ xy) {
+  const double den = s1[1];
+  const T a1 = (den != 0.0 && isfinite(den)) ? (T)(s1[0] / den) : T(0);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
+    ex[e] = a1 * d1x[e];
+    ey[e] = a1 * d1y[e];
+    fx[e] -= a1 * q1x[e];
+    fy[e] -= a1 * q1y[e];
+    xx[e] = T(0);
+    xy[e] = T(0);
+  }
+}
+
+// step 2 (z2 = x): partials [z2.q1, z2.L z2, rc.z2] -> part[3*blk + {0,1,2}]
+template <typename T>
+__global__ void k_kc_step2(GeomT<T> g, const T* __restrict__ xx, const T* __restrict__ xy,
+                           const T* __restrict__ fx, const T* __restrict__ fy, const T* __restrict__ en,
+                           const T* __restrict__ ec, const T* __restrict__ q1x, const T* __restrict__ q1y,
+                           double* __restrict__ part) {
+  __shared__ double sh[32];
+  const size_t P = (size_t)(g.ny + 2) * g.ld;
+  const int cols = g.nx + 2;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / cols), j = (int)(e % cols);
+    T d;
+    if (is_vx(g.nx, g.ny, i, j)) {
+      const T z = xx[e], Lz = lx_point<T>(g, i, j, xx, xy, en, ec, d);
+      a += (double)z * q1x[e]; b += (double)z * Lz; c += (double)fx[e] * z;
+    }
+    if (is_vy(g.nx, g.ny, i, j)) {
+      const T z = xy[e], Lz = ly_point<T>(g, i, j, xx, xy, en, ec, d);
+      a += (double)z * q1y[e]; b += (double)z * Lz; c += (double)fy[e] * z;
+    }
+  }
+  a = kc_block_sum<T>(a, sh);
+  b = kc_block_sum<T>(b, sh);
+  c = kc_block_sum<T>(c, sh);
+  if (threadIdx.x == 0) { part[3 * blockIdx.x] = a; part[3 * blockIdx.x + 1] = b; part[3 * blockIdx.x + 2] = c; }
+}
+
+// d2 = z2 - beta d1 with beta = (z2.q1)/(d1.q1); since rc.d1 = 0 after step 1 and L = L^T,
+// rc.d2 = rc.z2 and d2.L d2 = z2.L z2 - 2 beta z2.q1 + beta^2 d1.q1; x = e + alpha2 d2.
+template <typename T>
+__global__ void k_kc_final(size_t P, const double* __restrict__ s1, const double* __restrict__ s2,
+                           const T* __restrict__ d1x, const T* __restrict__ d1y, const T* __restrict__ ex,
+                           const T* __restrict__ ey, T* __restrict__ xx, T* __restrict__ xy) {
+  const double dq = s1[1];
+  const double beta = (dq != 0.0 && isfinite(dq)) ? s2[0] / dq : 0.0;
+  const double den = s2[1] - 2.0 * beta * s2[0] + beta * beta * dq;
+  const double a2 = (den != 0.0 && isfinite(den)) ? s2[2] / den : 0.0;
+  const T A2 = (T)a2, B = (T)beta;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
+    xx[e] = ex[e] + A2 * (xx[e] - B * d1x[e]);
+    xy[e] = ey[e] + A2 * (xy[e] - B * d1y[e]);
+  }
 }
 
 // ---- coarsest level: unknown numbering vx (row-major over i in [1,ny], j in [1,nx-1]) then vy
@@ -299,14 +469,23 @@ __global__ void k_coarse_solve(Geom g, const double* __restrict__ Ainv, int n, c
 
 // ---- explicit instantiations ---------------------------------------------------------------
 #define PYRO_INST(T)                                                                                         \
-  template __global__ void k_rbgs<T>(GeomT<T>, T*, T*, const T*, const T*, const T*, const T*, int, int, T); \
+  template __global__ void k_rbgs<T>(GeomT<T>, T*, T*, const T*, const T*, const T*, const T*, int, int, T, \
+                                     const T*, const T*);                                                  \
   template __global__ void k_vresidual<T>(GeomT<T>, const T*, const T*, const T*, const T*, const T*,      \
                                           const T*, T*, T*);                                                \
   template __global__ void k_restrict<T>(GeomT<T>, GeomT<T>, const T*, const T*, T*, T*);                  \
   template __global__ void k_prolong_add<T>(GeomT<T>, GeomT<T>, T*, T*, const T*, const T*);               \
   template __global__ void k_coarsen_eta<T>(GeomT<T>, GeomT<T>, const T*, const T*, T*, T*, int);          \
   template __global__ void k_coarse_assemble<T>(Geom, const T*, const T*, double*, int);                   \
-  template __global__ void k_coarse_solve<T>(Geom, const double*, int, const T*, const T*, T*, T*);
+  template __global__ void k_coarse_solve<T>(Geom, const double*, int, const T*, const T*, T*, T*);       \
+  template __global__ void k_kc_step1<T>(GeomT<T>, const T*, const T*, const T*, const T*, const T*,      \
+                                         const T*, T*, T*, T*, T*, double*);                              \
+  template __global__ void k_kc_update1<T>(size_t, const double*, const T*, const T*, const T*, const T*, \
+                                           T*, T*, T*, T*, T*, T*);                                        \
+  template __global__ void k_kc_step2<T>(GeomT<T>, const T*, const T*, const T*, const T*, const T*,      \
+                                         const T*, const T*, const T*, double*);                          \
+  template __global__ void k_kc_final<T>(size_t, const double*, const double*, const T*, const T*,        \
+                                         const T*, const T*, T*, T*);
 PYRO_INST(float)
 PYRO_INST(double)
 #undef PYRO_INST

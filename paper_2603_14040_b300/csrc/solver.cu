@@ -14,6 +14,8 @@
 
 #include "kernels_mg.cuh"
 #include "kernels_krylov.cuh"
+#include "kernels_sub.cuh"
+#include "kernels_tile.cuh"
 
 using namespace pyro;
 
@@ -89,6 +91,15 @@ struct Level {
   GeomT<T> gt;
   size_t P;
   T *vx, *vy, *fx, *fy, *rx, *ry, *en, *ec;
+  // K-cycle vectors (allocated on levels whose coarse correction is Krylov-accelerated from above)
+  T *d1x = nullptr, *d1y = nullptr, *q1x = nullptr, *q1y = nullptr, *ex = nullptr, *ey = nullptr;
+  T *idgx = nullptr, *idgy = nullptr;  // precomputed 1/diag (FP64 levels)
+  T *vx2 = nullptr, *vy2 = nullptr;    // second iterate buffer for the tile sweeps (ping-pong)
+  int cur = 0;                         // which buffer holds the iterate (set while launching)
+  T* X() const { return cur ? vx2 : vx; }
+  T* Y() const { return cur ? vy2 : vy; }
+  double *kpart = nullptr, *ks = nullptr;
+  int kblocks = 0;
 };
 
 template <typename T>
@@ -97,15 +108,24 @@ struct MG {
   double* Ainv = nullptr;  // coarsest (-L)^-1, dense FP64
   int nc = 0;              // coarse unknowns
   int nu1 = 2, nu2 = 2, eta_mode = 0;
+  int kcycle = 0;  // levels l < kcycle get their coarse correction from two flexible-CG steps
+  int ls = -1;     // first level run by the cluster sub-cycle kernel (-1: none)
+  bool tiles = true;                        // tile-fused smoothing / residual+restriction
+  static constexpr long long kFuse64Cells = 65536;
+  SubArgs<T> sub{};
+  double* red = nullptr;
   T omega = T(1);
   const cudaEvent_t* hooks = nullptr;  // level-0 phase events (timing mode), else null
   long long* nlaunch = nullptr;        // kernel-launch counter of the owning handle
   void count(long long k) const { if (nlaunch) *nlaunch += k; }
 
-  static size_t bytes(int nx, int ny, int nlev) {
+  static bool kc_level(int l, int nlev, int kcycle) { return l >= 1 && l - 1 < kcycle && l < nlev - 1; }
+
+  static size_t bytes(int nx, int ny, int nlev, int kcycle = 0) {
     size_t b = 0;
     for (int l = 0; l < nlev; ++l) {
-      b += (size_t)8 * (size_t)(ny + 2) * (nx + 2) * sizeof(T);
+      b += (size_t)(sizeof(T) == 8 ? 12 : 10) * (size_t)(ny + 2) * (nx + 2) * sizeof(T);
+      if (kc_level(l, nlev, kcycle)) b += (size_t)6 * (size_t)(ny + 2) * (nx + 2) * sizeof(T) + 5 * 296 * 8 + 64;
       if (l + 1 < nlev) { nx /= 2; ny /= 2; }
     }
     const size_t nc = (size_t)(ny * (nx - 1) + (ny - 1) * nx);
@@ -123,6 +143,19 @@ struct MG {
       L.rx = A.get<T>(L.P); L.ry = A.get<T>(L.P);
       if (l == 0 && alias_eta0) { L.en = nullptr; L.ec = nullptr; }
       else { L.en = A.get<T>(L.P); L.ec = A.get<T>(L.P); }
+      if (sizeof(T) == 8) { L.idgx = A.get<T>(L.P); L.idgy = A.get<T>(L.P); }
+      if (tiles) {
+        L.vx2 = A.get<T>(L.P); L.vy2 = A.get<T>(L.P);
+        CK(cudaMemset(L.vx2, 0, L.P * sizeof(T)));
+        CK(cudaMemset(L.vy2, 0, L.P * sizeof(T)));
+      }
+      if (kc_level(l, nlev, kcycle)) {
+        L.d1x = A.get<T>(L.P); L.d1y = A.get<T>(L.P); L.q1x = A.get<T>(L.P); L.q1y = A.get<T>(L.P);
+        L.ex = A.get<T>(L.P); L.ey = A.get<T>(L.P);
+        L.kblocks = (int)std::min<size_t>(296, (L.P + 255) / 256);
+        L.kpart = A.get<double>((size_t)5 * 296);
+        L.ks = A.get<double>(8);
+      }
       lv.push_back(L);
       if (l + 1 < nlev) {
         g.nx /= 2; g.ny /= 2; g.ld = g.nx + 2; g.dx *= 2; g.dy *= 2;
@@ -133,6 +166,30 @@ struct MG {
     Ainv = A.get<double>((size_t)nc * nc);
   }
 
+  // choose the first level of the cluster sub-cycle and fill its launch arguments
+  void setup_sub(DevAlloc& A, int cluster_cells) {
+    ls = -1;
+    if (cluster_cells <= 0 || (int)lv.size() > kSubMaxLevels || lv.size() < 2) return;
+    for (int l = 0; l < (int)lv.size(); ++l)
+      if ((long long)lv[l].g.nx * lv[l].g.ny <= cluster_cells) { ls = l; break; }
+    if (ls < 0 || ls == (int)lv.size() - 1) { ls = -1; return; }
+    red = A.get<double>(2 * kSubCluster * 4);
+    sub.nlev = (int)lv.size();
+    sub.nu1 = nu1; sub.nu2 = nu2; sub.kcycle = kcycle; sub.omega = omega;
+    sub.gc = lv.back().g;
+    sub.Ainv = Ainv;
+    sub.nc = nc;
+    sub.red = red;
+    for (size_t l = 0; l < lv.size(); ++l) {
+      const Level<T>& L = lv[l];
+      SubLevel<T>& S = sub.L[l];
+      S.gt = L.gt;
+      S.vx = L.vx; S.vy = L.vy; S.fx = L.fx; S.fy = L.fy; S.rx = L.rx; S.ry = L.ry; S.en = L.en; S.ec = L.ec;
+      S.d1x = L.d1x; S.d1y = L.d1y; S.q1x = L.q1x; S.q1y = L.q1y; S.ex = L.ex; S.ey = L.ey;
+      S.idgx = L.idgx; S.idgy = L.idgy;
+    }
+  }
+
   // viscosity on every level + coarse inverse (eta of level 0 must already be in place)
   void setup(cudaStream_t s, int* flag) {
     for (size_t l = 1; l < lv.size(); ++l) {
@@ -140,6 +197,12 @@ struct MG {
       Level<T>& C = lv[l];
       k_coarsen_eta<T><<<grid2(C.g.nx, C.g.ny, kBlk2), kBlk2, 0, s>>>(F.gt, C.gt, F.en, F.ec, C.en, C.ec, eta_mode);
     }
+    for (size_t l = 0; l < lv.size(); ++l)
+      if (lv[l].idgx) {
+        const Level<T>& L = lv[l];
+        k_invdiag<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, L.en, L.ec, L.idgx, L.idgy);
+        count(1);
+      }
     const Level<T>& C = lv.back();
     CK(cudaMemsetAsync(Ainv, 0, (size_t)nc * nc * sizeof(double), s));
     k_coarse_assemble<T><<<(nc + 127) / 128, 128, 0, s>>>(C.g, C.en, C.ec, Ainv, nc);
@@ -147,36 +210,145 @@ struct MG {
     count((long long)lv.size() - 1 + 2);
   }
 
+  bool fused(int l) const {
+    return tiles && (sizeof(T) == 4 || (long long)lv[l].g.nx * lv[l].g.ny <= kFuse64Cells);
+  }
+
+  // nsweeps RBGS sweeps on level l with tile kernels; with C given, the prolongation of C's
+  // iterate is added when the first tile is loaded
+  void smooth_tiles(int l, int nsweeps, const Level<T>* C, cudaStream_t s) {
+    Level<T>& L = lv[l];
+    const GeomT<T> gc = C ? C->gt : L.gt;
+    const T* cvx = C ? C->X() : nullptr;
+    const T* cvy = C ? C->Y() : nullptr;
+    if (nsweeps == 0 && C) {
+      k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C->gt, L.X(), L.Y(), C->X(), C->Y());
+      count(1);
+      return;
+    }
+    while (nsweeps > 0) {
+      if (sizeof(T) == 4 && nsweeps >= 2) {
+        constexpr int TX = 64, TY = 32;
+        const dim3 gr((L.g.nx + 2 + TX - 1) / TX, (L.g.ny + 2 + TY - 1) / TY);
+        k_rbgs_tile<T, 2, TX, TY><<<gr, kTileThreads, SweepTile<T, 2, TX, TY>::smem_bytes(L.idgx != nullptr), s>>>(
+            L.gt, L.X(), L.Y(), L.cur ? L.vx : L.vx2, L.cur ? L.vy : L.vy2, L.fx, L.fy, L.en, L.ec, L.idgx,
+            L.idgy, omega, gc, cvx, cvy);
+        nsweeps -= 2;
+      } else if (sizeof(T) == 4) {
+        constexpr int TX = 64, TY = 32;
+        const dim3 gr((L.g.nx + 2 + TX - 1) / TX, (L.g.ny + 2 + TY - 1) / TY);
+        k_rbgs_tile<T, 1, TX, TY><<<gr, kTileThreads, SweepTile<T, 1, TX, TY>::smem_bytes(L.idgx != nullptr), s>>>(
+            L.gt, L.X(), L.Y(), L.cur ? L.vx : L.vx2, L.cur ? L.vy : L.vy2, L.fx, L.fy, L.en, L.ec, L.idgx,
+            L.idgy, omega, gc, cvx, cvy);
+        nsweeps -= 1;
+      } else {
+        constexpr int TX = 64, TY = 16;
+        const dim3 gr((L.g.nx + 2 + TX - 1) / TX, (L.g.ny + 2 + TY - 1) / TY);
+        k_rbgs_tile<T, 1, TX, TY><<<gr, kTileThreads, SweepTile<T, 1, TX, TY>::smem_bytes(L.idgx != nullptr), s>>>(
+            L.gt, L.X(), L.Y(), L.cur ? L.vx : L.vx2, L.cur ? L.vy : L.vy2, L.fx, L.fy, L.en, L.ec, L.idgx,
+            L.idgy, omega, gc, cvx, cvy);
+        nsweeps -= 1;
+      }
+      count(1);
+      L.cur ^= 1;
+      cvx = nullptr;
+      cvy = nullptr;
+    }
+  }
+
+  void resrestrict_tiles(int l, cudaStream_t s) {
+    Level<T>& L = lv[l];
+    Level<T>& C = lv[l + 1];
+    constexpr int CTX = 32, CTY = sizeof(T) == 4 ? 16 : 8;
+    const dim3 gr((C.g.nx + 2 + CTX - 1) / CTX, (C.g.ny + 2 + CTY - 1) / CTY);
+    k_resrestrict_tile<T, CTX, CTY><<<gr, kTileThreads, ResTile<T, CTX, CTY>::smem_bytes(), s>>>(
+        L.gt, C.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, C.fx, C.fy, C.vx, C.vy);
+    C.cur = 0;  // the coarse iterate starts from zero in its first buffer
+    count(1);
+  }
+
+  // raise the dynamic shared-memory limit of the tile kernels (once per handle)
+  static void enable_tiles() {
+    if (sizeof(T) == 4) {
+      CK(cudaFuncSetAttribute(k_rbgs_tile<T, 2, 64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SweepTile<T, 2, 64, 32>::smem_bytes(true)));
+      CK(cudaFuncSetAttribute(k_rbgs_tile<T, 1, 64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SweepTile<T, 1, 64, 32>::smem_bytes(true)));
+      CK(cudaFuncSetAttribute(k_resrestrict_tile<T, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)ResTile<T, 32, 16>::smem_bytes()));
+    } else {
+      CK(cudaFuncSetAttribute(k_rbgs_tile<T, 1, 64, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SweepTile<T, 1, 64, 16>::smem_bytes(true)));
+      CK(cudaFuncSetAttribute(k_resrestrict_tile<T, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)ResTile<T, 32, 8>::smem_bytes()));
+    }
+  }
+
   void sweep(int l, cudaStream_t s) {
     Level<T>& L = lv[l];
     const dim3 g = grid_rb(L.g.nx, L.g.ny, kBlk2);
     for (int f = 0; f < 2; ++f)
       for (int c = 0; c < 2; ++c)
-        k_rbgs<T><<<g, kBlk2, 0, s>>>(L.gt, L.vx, L.vy, L.fx, L.fy, L.en, L.ec, f, c, omega);
+        k_rbgs<T><<<g, kBlk2, 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, f, c, omega, L.idgx, L.idgy);
     count(4);
   }
 
   // one V-cycle at level l for L x = f from x = 0 (x_l must be zero on entry)
   void cycle(int l, cudaStream_t s) {
     Level<T>& L = lv[l];
+    // entry: the iterate is zero in the first buffer
+    L.cur = 0;
+    if (l == ls) {
+      k_subcycle<T><<<kSubCluster, kSubThreads, 0, s>>>(sub, l);
+      count(1);
+      return;
+    }
     if (l == (int)lv.size() - 1) {
       k_coarse_solve<T><<<1, 256, nc * sizeof(double), s>>>(L.g, Ainv, nc, L.fx, L.fy, L.vx, L.vy);
       count(1);
       return;
     }
     Level<T>& C = lv[l + 1];
-    for (int k = 0; k < nu1; ++k) sweep(l, s);
-    if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[2], s, cudaEventRecordExternal));
-    k_vresidual<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, L.vx, L.vy, L.fx, L.fy, L.en, L.ec, L.rx, L.ry);
-    k_restrict<T><<<grid2(C.g.nx, C.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C.gt, L.rx, L.ry, C.fx, C.fy);
-    count(2);
-    CK(cudaMemsetAsync(C.vx, 0, C.P * sizeof(T), s));
-    CK(cudaMemsetAsync(C.vy, 0, C.P * sizeof(T), s));
-    cycle(l + 1, s);
-    k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C.gt, L.vx, L.vy, C.vx, C.vy);
-    count(1);
-    if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[3], s, cudaEventRecordExternal));
-    for (int k = 0; k < nu2; ++k) sweep(l, s);
+    const bool fz = fused(l);
+    if (fz) {
+      smooth_tiles(l, nu1, nullptr, s);
+      if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[2], s, cudaEventRecordExternal));
+      resrestrict_tiles(l, s);  // also zeroes the coarse iterate
+    } else {
+      for (int k = 0; k < nu1; ++k) sweep(l, s);
+      if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[2], s, cudaEventRecordExternal));
+      k_vresidual<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, L.rx, L.ry);
+      k_restrict<T><<<grid2(C.g.nx, C.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C.gt, L.rx, L.ry, C.fx, C.fy);
+      count(2);
+      CK(cudaMemsetAsync(C.vx, 0, C.P * sizeof(T), s));
+      CK(cudaMemsetAsync(C.vy, 0, C.P * sizeof(T), s));
+      C.cur = 0;
+    }
+    if (kc_level(l + 1, (int)lv.size(), kcycle)) {
+      // K-cycle: two flexible-CG steps on level l+1, each preconditioned by one level-(l+1) cycle
+      const int nb = C.kblocks;
+      cycle(l + 1, s);
+      k_kc_step1<T><<<nb, 256, 0, s>>>(C.gt, C.X(), C.Y(), C.fx, C.fy, C.en, C.ec, C.d1x, C.d1y, C.q1x, C.q1y, C.kpart);
+      k_kc_reduce<<<1, 256, 0, s>>>(C.kpart, nb, 2, C.ks);
+      // zero the first iterate buffer for the second inner cycle
+      k_kc_update1<T><<<nb, 256, 0, s>>>(C.P, C.ks, C.d1x, C.d1y, C.q1x, C.q1y, C.ex, C.ey, C.fx, C.fy, C.vx, C.vy);
+      cycle(l + 1, s);
+      k_kc_step2<T><<<nb, 256, 0, s>>>(C.gt, C.X(), C.Y(), C.fx, C.fy, C.en, C.ec, C.q1x, C.q1y, C.kpart);
+      k_kc_reduce<<<1, 256, 0, s>>>(C.kpart, nb, 3, C.ks + 2);
+      k_kc_final<T><<<nb, 256, 0, s>>>(C.P, C.ks, C.ks + 2, C.d1x, C.d1y, C.ex, C.ey, C.X(), C.Y());
+      count(6);
+    } else {
+      cycle(l + 1, s);
+    }
+    if (fz) {
+      if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[3], s, cudaEventRecordExternal));
+      smooth_tiles(l, nu2, &C, s);  // prolongation fused into the first post-smoothing tile pass
+    } else {
+      k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C.gt, L.X(), L.Y(), C.X(), C.Y());
+      count(1);
+      if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[3], s, cudaEventRecordExternal));
+      for (int k = 0; k < nu2; ++k) sweep(l, s);
+    }
     if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[4], s, cudaEventRecordExternal));
   }
 };
@@ -240,7 +412,7 @@ void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s) {
   mg.cycle(0, s);
   mg.hooks = nullptr;
   h->launches += 4;
-  k_precond_out<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.vx, L0.vy, h->V, (TZ*)h->Z, h->n3, h->d_j,
+  k_precond_out<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->V, (TZ*)h->Z, h->n3, h->d_j,
                                                            h->ec, h->o.alpha_p, h->part2);
   k_sub_mean<TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, (TZ*)h->Z + 2 * h->P, h->n3, h->d_j, h->part2, kReduceBlocks);
   k_apply<TZ><<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->ec, (const TZ*)h->Z, h->n3, h->d_j, h->w);
@@ -250,16 +422,18 @@ void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s) {
 // one Arnoldi step j (j read on the device): z_j = M^-1 v_j, w = A z_j, CGS2 against v_0..v_j,
 // v_{j+1} = w / ||w||_W, Hessenberg column j into hcol, j += 1.
 void iteration_body(pyro_stokes_s* h, cudaStream_t s) {
-  if (h->mixed) precond_body<float, float>(h, h->mgf, s);
+  if (h->mixed) precond_body<float, double>(h, h->mgf, s);
   else precond_body<double, double>(h, h->mgd, s);
+  // classical Gram-Schmidt with one re-orthogonalisation (CGS2) in the W inner product
   const dim3 gd(kReduceBlocks, (unsigned)h->dot_grid_y);
-  k_multidot<<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial);
-  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, h->h1);
-  k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h1, h->n3, nullptr, nullptr);
-  k_multidot<<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial);
-  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, h->h2);
-  k_multiaxpy<<<kReduceBlocks, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h2, h->n3, h->W, h->part2);
-  k_arnoldi_finish<<<1, kThreads, 0, s>>>(h->d_j, h->h1, h->h2, h->part2, kReduceBlocks, h->hcol, h->inv, h->flag);
+  k_multidot<<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial, nullptr, nullptr);
+  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, h->h1, nullptr);
+  k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h1, h->n3, nullptr, nullptr, nullptr);
+  k_multidot<<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial, nullptr, nullptr);
+  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, h->h2, nullptr);
+  k_multiaxpy<<<kReduceBlocks, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h2, h->n3, h->W, h->part2, nullptr);
+  k_arnoldi_finish<<<1, kThreads, 0, s>>>(h->d_j, h->h1, h->h2, h->part2, kReduceBlocks, h->hcol, h->inv, h->flag,
+                                          nullptr, nullptr);
   k_scale_next<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, h->n3, h->d_j, h->w, h->inv, h->n3);
   k_inc<<<1, 1, 0, s>>>(h->d_j);
   h->launches += 9;
@@ -334,7 +508,7 @@ std::pair<double, double> residual_norms(pyro_stokes_s* h, const double* b, cons
 }
 
 double weighted_norm2(pyro_stokes_s* h, const double* v, cudaStream_t s) {
-  k_multidot<<<dim3(kReduceBlocks, 1), kThreads, 0, s>>>(v, 0, nullptr, 1, v, h->W, h->n3, h->partial);
+  k_multidot<<<dim3(kReduceBlocks, 1), kThreads, 0, s>>>(v, 0, nullptr, 1, v, h->W, h->n3, h->partial, nullptr, nullptr);
   h->launches += 1;
   CK(cudaMemcpyAsync(h->hbuf, h->partial, kReduceBlocks * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -487,10 +661,7 @@ int fgmres(pyro_stokes_s* h, double tol, pyro_stats* st, cudaStream_t s) {
     gv.solve(k, y.data());
     std::memcpy(h->hbuf, y.data(), k * sizeof(double));
     CK(cudaMemcpyAsync(h->ydev, h->hbuf, k * sizeof(double), cudaMemcpyHostToDevice, s));
-    if (h->mixed)
-      k_update_x<float><<<kReduceBlocks * 2, kThreads, 0, s>>>(h->x, (const float*)h->Z, h->n3, k, h->ydev, h->n3);
-    else
-      k_update_x<double><<<kReduceBlocks * 2, kThreads, 0, s>>>(h->x, (const double*)h->Z, h->n3, k, h->ydev, h->n3);
+    k_update_x<double><<<kReduceBlocks * 2, kThreads, 0, s>>>(h->x, (const double*)h->Z, h->n3, k, h->ydev, h->n3);
     h->launches += 1;
     ++restarts;
   }
@@ -535,6 +706,8 @@ void validate_opts(pyro_opts& o) {
   if (o.restart_m > kMaxRestart) o.restart_m = kMaxRestart;
   if (o.max_iter < 1) o.max_iter = 1;
   if (o.coarsest_min < 1) o.coarsest_min = 1;
+  if (o.kcycle < 0) o.kcycle = 0;
+  if (o.kcycle > 16) o.kcycle = 16;
 }
 
 int check_size(int nx, int ny, const pyro_opts& o) {
@@ -557,8 +730,9 @@ size_t footprint_bytes(int nx, int ny, const pyro_opts& o, int L) {
   b += 6 * n3 * 8;                 // b, x, r, w, W, xf
   b += n3 * 8;                     // stage
   b += (m + 1) * n3 * 8;           // V
-  b += m * n3 * (mixed ? 4 : 8);   // Z
-  b += mixed ? MG<float>::bytes(nx, ny, L) : MG<double>::bytes(nx, ny, L) - 2 * P * 8;
+  b += m * n3 * 8;                 // Z (preconditioned vectors; FP32-valued velocities in mixed mode)
+  b += mixed ? MG<float>::bytes(nx, ny, L, o.kcycle) : MG<double>::bytes(nx, ny, L, o.kcycle) - 2 * P * 8;
+  b += 2 * kSubCluster * 4 * 8;
   b += 2 * (kMaxRestart + 2) * 8 + 2 * (size_t)kReduceBlocks * (kMaxRestart + 1) * 8 + 4 * kReduceBlocks * 8 +
        (size_t)kMaxRestart * kHcolStride * 8 + 64;
   return b;
@@ -582,6 +756,9 @@ void pyro_default_opts(pyro_opts* o) {
   o->warm_start = 0;
   o->use_graphs = 1;
   o->timeout_s = 0.0;
+  o->kcycle = 0;
+  o->cluster_cells = 0;
+  o->tile_fusion = 1;
 }
 
 const char* pyro_version(void) { return "pyro-b300 0.1 (sm_103a)"; }
@@ -648,8 +825,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
     h->w = A.get<double>(h->n3); h->W = A.get<double>(h->n3); h->xf = A.get<double>(h->n3);
     h->stage = A.get<double>(h->n3);
     h->V = A.get<double>((size_t)(h->m + 1) * h->n3);
-    if (h->mixed) h->Z = A.get<float>((size_t)h->m * h->n3);
-    else h->Z = A.get<double>((size_t)h->m * h->n3);
+    h->Z = A.get<double>((size_t)h->m * h->n3);
     h->h1 = A.get<double>(kMaxRestart + 2); h->h2 = A.get<double>(kMaxRestart + 2);
     h->partial = A.get<double>((size_t)kReduceBlocks * (kMaxRestart + 1) * 2);
     h->part2 = A.get<double>(4 * kReduceBlocks);
@@ -660,12 +836,21 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
     h->flag = A.get<int>(1);
     if (h->mixed) {
       h->mgf.nu1 = o.nu1; h->mgf.nu2 = o.nu2; h->mgf.omega = (float)o.omega_v; h->mgf.eta_mode = o.eta_coarsen;
+      h->mgf.kcycle = o.kcycle;
+      h->mgf.tiles = o.tile_fusion != 0;
+      if (h->mgf.tiles) MG<float>::enable_tiles();
+      CK(cudaDeviceSynchronize());
       h->mgf.alloc(A, h->g, L, false);
+      h->mgf.setup_sub(A, o.cluster_cells);
     } else {
       h->mgd.nu1 = o.nu1; h->mgd.nu2 = o.nu2; h->mgd.omega = o.omega_v; h->mgd.eta_mode = o.eta_coarsen;
+      h->mgd.kcycle = o.kcycle;
+      h->mgd.tiles = o.tile_fusion != 0;
+      if (h->mgd.tiles) MG<double>::enable_tiles();
       h->mgd.alloc(A, h->g, L, true);
       h->mgd.lv[0].en = h->en;
       h->mgd.lv[0].ec = h->ec;
+      h->mgd.setup_sub(A, o.cluster_cells);
     }
     CK(cudaMallocHost(&h->hbuf, 4 * kReduceBlocks * sizeof(double) + 1024));
     CK(cudaMallocHost(&h->hflag, sizeof(int)));
@@ -706,16 +891,16 @@ int pyro_stokes_precond(pyro_stokes h, const double* eta_n, const double* eta_c,
       Level<float>& L0 = h->mgf.lv[0];
       k_precond_in<float><<<kReduceBlocks, kThreads, 0, s>>>(h->P, h->V, h->n3, h->d_j, L0.fx, L0.fy, L0.vx, L0.vy);
       h->mgf.cycle(0, s);
-      k_precond_out<float, float><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.vx, L0.vy, h->V, (float*)h->Z, h->n3,
-                                                                      h->d_j, h->ec, h->o.alpha_p, h->part2);
-      k_sub_mean<float><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, (float*)h->Z + 2 * h->P, h->n3, h->d_j, h->part2,
-                                                          kReduceBlocks);
-      k_to_double<<<kReduceBlocks, kThreads, 0, s>>>((const float*)h->Z, h->w, h->n3);
+      k_precond_out<float, double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->V, (double*)h->Z,
+                                                                       h->n3, h->d_j, h->ec, h->o.alpha_p, h->part2);
+      k_sub_mean<double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, (double*)h->Z + 2 * h->P, h->n3, h->d_j, h->part2,
+                                                           kReduceBlocks);
+      CK(cudaMemcpyAsync(h->w, h->Z, h->n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     } else {
       Level<double>& L0 = h->mgd.lv[0];
       k_precond_in<double><<<kReduceBlocks, kThreads, 0, s>>>(h->P, h->V, h->n3, h->d_j, L0.fx, L0.fy, L0.vx, L0.vy);
       h->mgd.cycle(0, s);
-      k_precond_out<double, double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.vx, L0.vy, h->V, (double*)h->Z,
+      k_precond_out<double, double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->V, (double*)h->Z,
                                                                         h->n3, h->d_j, h->ec, h->o.alpha_p, h->part2);
       k_sub_mean<double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, (double*)h->Z + 2 * h->P, h->n3, h->d_j, h->part2,
                                                            kReduceBlocks);

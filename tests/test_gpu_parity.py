@@ -41,7 +41,7 @@ def test_apply_matches_oracle(nx, ny, Lx, Ly, bc):
         assert np.abs(host(a) - o).max() <= 1e-13 * scale
 
 
-def _precond_case(nx, ny, Lx, Ly, bc, prec, seed):
+def _precond_case(nx, ny, Lx, Ly, bc, prec, seed, kcycle=0, cluster_cells=0, tile_fusion=1):
     kind, vt = BCS[bc]
     g = S.Grid(nx, ny, Lx, Ly, S.BC(kind, vt))
     en, ec = rand_eta(nx, ny, seed, -1, 1)
@@ -49,30 +49,67 @@ def _precond_case(nx, ny, Lx, Ly, bc, prec, seed):
     r = rng.standard_normal(g.n)
     rx, ry, rp = S.vector_to_fields(g, r, fill_ghosts=False)
     h_or = M.Hierarchy(g, en, ec, coarsest_min=2)
-    z = M.uzawa_precond(h_or, r, ec, alpha=1.0, nu1=2, nu2=2, omega=1.0)
+    z = M.uzawa_precond(h_or, r, ec, alpha=1.0, nu1=2, nu2=2, omega=1.0, kcycle=kcycle)
     zx, zy, zp = S.vector_to_fields(g, z, fill_ghosts=False)
-    h = P.Stokes(nx, ny, Lx, Ly, bc=P.make_bc(kind, vt), prec=prec)
+    h = P.Stokes(nx, ny, Lx, Ly, bc=P.make_bc(kind, vt), prec=prec, kcycle=kcycle, cluster_cells=cluster_cells,
+                 tile_fusion=tile_fusion)
     Zx, Zy, Zp = zeros(ny, nx), zeros(ny, nx), zeros(ny, nx)
     h.precond(dev(en), dev(ec), dev(rx), dev(ry), dev(rp), Zx, Zy, Zp)
     torch.cuda.synchronize()
     return (host(Zx), host(Zy), host(Zp)), (zx, zy, zp), h_or.nlev
 
 
-@pytest.mark.parametrize("nx,ny,Lx,Ly", [(2, 2, 1, 1), (16, 16, 1, 1), (48, 80, 0.6, 1.0), (64, 16, 4, 1)])
+@pytest.mark.parametrize("nx,ny,Lx,Ly", [(2, 2, 1, 1), (16, 16, 1, 1), (48, 80, 0.6, 1.0), (64, 16, 4, 1), (256, 128, 2, 1)])
 @pytest.mark.parametrize("bc", list(BCS))
-def test_preconditioner_fp64_matches_oracle(nx, ny, Lx, Ly, bc):
+@pytest.mark.parametrize("cc,tf", [(0, 0), (0, 1), (4096, 1), (1 << 20, 0)])
+def test_preconditioner_fp64_matches_oracle(nx, ny, Lx, Ly, bc, cc, tf):
     """One Uzawa sweep with an FP64 V-cycle (RBGS, residual, restriction, eta coarsening, coarse
-    direct solve, prolongation, pressure update, mean removal) equals the oracle's step by step."""
-    gpu, ora, nlev = _precond_case(nx, ny, Lx, Ly, bc, P.PREC_FP64, 11)
+    direct solve, prolongation, pressure update, mean removal) equals the oracle's step by step,
+    with one kernel per step, with tile-fused kernels, with the smallest levels in the cluster kernel,
+    and with all levels in the cluster kernel."""
+    gpu, ora, nlev = _precond_case(nx, ny, Lx, Ly, bc, P.PREC_FP64, 11, cluster_cells=cc, tile_fusion=tf)
     for a, b in zip(gpu, ora):
         assert rel(a, b) <= 1e-11, (rel(a, b), nlev)
 
 
-@pytest.mark.parametrize("nx,ny", [(16, 16), (48, 80)])
-def test_preconditioner_fp32_close_to_oracle(nx, ny):
-    gpu, ora, _ = _precond_case(nx, ny, 1.0, 1.0, "free", P.PREC_MIXED, 5)
+@pytest.mark.parametrize("nx,ny,Lx,Ly", [(32, 32, 1, 1), (48, 80, 0.6, 1.0)])
+@pytest.mark.parametrize("kc", [1, 2, 8])
+@pytest.mark.parametrize("cc,tf", [(0, 0), (0, 1), (4096, 1), (1 << 20, 0)])
+def test_preconditioner_kcycle_fp64_matches_oracle(nx, ny, Lx, Ly, kc, cc, tf):
+    """The K-cycle variant (two flexible-CG steps per coarse correction on the top kc levels)."""
+    gpu, ora, nlev = _precond_case(nx, ny, Lx, Ly, "free", P.PREC_FP64, 13, kcycle=kc, cluster_cells=cc,
+                                   tile_fusion=tf)
+    for a, b in zip(gpu, ora):
+        assert rel(a, b) <= 1e-10, (rel(a, b), nlev)
+
+
+@pytest.mark.parametrize("nx,ny", [(16, 16), (48, 80), (320, 192)])
+@pytest.mark.parametrize("tf", [0, 1])
+def test_preconditioner_fp32_close_to_oracle(nx, ny, tf):
+    gpu, ora, _ = _precond_case(nx, ny, 1.0, 1.0, "free", P.PREC_MIXED, 5, tile_fusion=tf)
     for a, b in zip(gpu, ora):
         assert rel(a, b) <= 2e-4
+
+
+@pytest.mark.parametrize("nx,ny,kc", [(16, 16, 0), (48, 80, 2), (320, 192, 3), (1024, 256, 2)])
+def test_fp32_tile_fusion_matches_unfused(nx, ny, kc):
+    """The tile kernels (halo recomputation) and the shared-memory tail reproduce the one-kernel-per-
+    colour FP32 cycle to FP32 rounding (the same point operations; only the compiler's multiply-add
+    contraction may differ between the kernels)."""
+    g = S.Grid(nx, ny)
+    en, ec = rand_eta(nx, ny, 21, -1, 1)
+    rng = np.random.default_rng(22)
+    r = rng.standard_normal(g.n)
+    rx, ry, rp = S.vector_to_fields(g, r, fill_ghosts=False)
+    outs = []
+    for tf in (0, 1):
+        h = P.Stokes(nx, ny, prec=P.PREC_MIXED, kcycle=kc, tile_fusion=tf)
+        Z = [zeros(ny, nx) for _ in range(3)]
+        h.precond(dev(en), dev(ec), dev(rx), dev(ry), dev(rp), *Z)
+        torch.cuda.synchronize()
+        outs.append([host(z) for z in Z])
+    for a, b in zip(*outs):
+        assert rel(a, b) <= (1e-6 if kc == 0 else 1e-5)
 
 
 def _solve_gpu(f, g_vec, tol, prec, bc=None, Lx=1.0, Ly=1.0, host_ptrs=False, **kw):

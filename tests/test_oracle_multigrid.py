@@ -167,3 +167,34 @@ def test_preconditioner_pressure_mean_zero_and_linear():
     z12 = M.uzawa_precond(h, 2 * r1 - 3 * r2, f.eta_c)
     assert abs(z1[g.n_v:].mean()) < 1e-14
     assert np.allclose(z12, 2 * z1 - 3 * z2, atol=1e-10)
+
+
+def test_kcycle_pins():
+    """K-cycle: (a) with only one level below, no K step applies and it is the V-cycle; (b) the
+    first CG direction satisfies Galerkin orthogonality d_1 . (f - L e) = 0 after both steps;
+    (c) it contracts far better than the V-cycle on a rough random viscosity (its purpose)."""
+    from synth import grf_config
+    f = grf_config(64, 64, seed=2)
+    g = S.Grid(64, 64)
+    # (a) three levels: the K-cycle at level 0 uses level-1 cycles whose coarse solve is exact
+    h2 = M.Hierarchy(g, f.eta_n, f.eta_c, n_lev=2)
+    rv = np.random.default_rng(4).standard_normal(g.n_v)
+    assert np.allclose(M.vcycle(h2, rv, kcycle=1), M.vcycle(h2, rv), atol=1e-12)
+    # (b) Galerkin orthogonality on level 1 of a deeper hierarchy
+    h = M.Hierarchy(g, f.eta_n, f.eta_c, coarsest_min=2)
+    fc = np.random.default_rng(5).standard_normal(h.L[1].shape[0])
+    e = M.kcycle_correction(h, fc, 2, 2, 1.0, 1, 99)
+    L1 = h.L[1]
+    z1 = M.vcycle(h, fc, level=1, kcycle=99)
+    res = fc - L1 @ e
+    assert abs(z1 @ res) <= 1e-10 * np.linalg.norm(z1) * np.linalg.norm(fc)
+    # (c) contraction factor of the stationary iteration x += C(f - L x)
+    L = h.L[0]
+    def rate(k):
+        x = np.zeros_like(rv); r0 = None
+        for it in range(8):
+            x = x + M.vcycle(h, rv - L @ x, kcycle=k)
+            if it == 2:
+                r0 = np.linalg.norm(rv - L @ x)
+        return (np.linalg.norm(rv - L @ x) / r0) ** (1 / 5)
+    assert rate(99) < 0.7 * rate(0)
