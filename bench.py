@@ -115,6 +115,142 @@ def oracle_baseline(seconds_budget=20.0, sample_n=128):
             "sample_seconds_per_solve": dt}
 
 
+def vcycle_roofline_4096(peaks, iters=6):
+    """Level-0 FP32 V-cycle kernels at 4096^2 (every level-0 array is 67 MB, far above L2): the
+    tile-fused two-sweep RBGS kernel moves 32 B/cell (reads vx, vy, fx, fy, eta_n, eta_c, writes
+    vx, vy) per launch; achieved = bytes / measured duration (CUDA events inside the solve)."""
+    import torch
+    import paper_2603_14040_b300 as P
+    from synth import layered_config
+    n = 4096
+    f = layered_config(n, n, seed=3)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    en, ec, rho = dev(f.eta_n), dev(f.eta_c), dev(f.rho)
+    del f
+    outs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
+    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=2)
+    h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)           # warm-up (graph capture)
+    h.close()
+    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=iters)
+    h.set_timing(True)
+    st = h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
+    torch.cuda.synchronize()
+    ph, cnt = h.get_timing()
+    it = max(cnt["iterations"], 1)
+    pre_ms = ph["l0_pre_smooth"] / it          # one launch: 2 fused sweeps
+    post_ms = ph["l0_post_smooth"] / it        # one launch: prolongation + 2 fused sweeps
+    cells = n * n
+    bytes_pre = 32.0 * cells
+    bytes_post = 34.0 * cells                  # + the coarse correction read (1/4 size, 2 fields)
+    gbs_pre = bytes_pre / (pre_ms / 1e3) / 1e9
+    gbs_post = bytes_post / (post_ms / 1e3) / 1e9
+    peak = peaks.get("hbm_gbs", 6400.0)
+    h.close()
+    del outs, en, ec, rho
+    torch.cuda.empty_cache()
+    return {"kernel": "k_rbgs_tile<float,2,64,32> level 0 (2 fused RBGS sweeps per launch), 4096x4096 mixed",
+            "bound": "hbm", "achieved": gbs_pre, "peak": peak, "unit": "GB/s", "frac": gbs_pre / peak,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6400 GB/s",
+            "bytes_per_launch": bytes_pre, "launch_ms": pre_ms,
+            "post_smooth_with_prolongation": {"achieved": gbs_post, "frac": gbs_post / peak, "launch_ms": post_ms},
+            "phase_ms_per_iter": {k: v / it for k, v in ph.items()}, "iters_timed": it}
+
+
+def serving_sample(n_req=48, slots=4, max_iter=600, seed=4):
+    """Continuous batching on a bounded sample of the serving workload: requests with n in
+    {128, 256, 512}, aspect in {1, 2, 4}, 16 inclusions of contrast 10^U[2,6], tol 1e-8, Poisson
+    arrivals at 0.8 x the measured single-slot service rate."""
+    import torch
+    from synth import serving_request
+    from paper_2603_14040_b300.serving import SolveServer, Request, PyroBackend, latency_stats, poisson_arrivals
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    reqs = []
+    for k in range(n_req):
+        f, C = serving_request(k, base_seed=seed, sizes=(128, 256, 512))
+        reqs.append((Request(rid=k, nx=f.nx, ny=f.ny, Lx=f.Lx, Ly=f.Ly, eta_n=dev(f.eta_n), eta_c=dev(f.eta_c),
+                             rho=dev(f.rho), g=(0.0, 1.0), tol=1e-8), C))
+    be = PyroBackend(opts_kw={"max_iter": max_iter, "prec": 1})
+    # service rate from a sequential pass over the first requests (also warms the handle pool)
+    srv = SolveServer(be, max_slots=1)
+    t0 = time.perf_counter()
+    probe = 8
+    for r, _ in reqs[:probe]:
+        srv.submit(Request(**{k: getattr(r, k) for k in ("rid", "nx", "ny", "Lx", "Ly", "eta_n", "eta_c", "rho",
+                                                          "g", "tol")}))
+    srv.drain(timeout=600)
+    srv.close()
+    mean_service = (time.perf_counter() - t0) / probe
+    rate = 0.8 / mean_service
+    arr = poisson_arrivals(n_req, rate, seed)
+    srv = SolveServer(be, max_slots=slots)
+    t_start = time.perf_counter()
+    for (r, _), a in zip(reqs, arr):
+        while time.perf_counter() - t_start < a:
+            time.sleep(0.0005)
+        r.arrival = 0.0
+        srv.submit(r)
+    done = srv.drain(timeout=1800)
+    srv.close()
+    st = latency_stats(done)
+    conv = sum(1 for r in done if r.status == 0)
+    st.update({"requests": n_req, "slots": slots, "arrival_rate_per_s": rate, "mean_single_service_ms":
+               mean_service * 1e3, "converged_to_tol": conv, "not_converged_at_max_iter": n_req - conv,
+               "max_iter": max_iter, "max_concurrent": srv.max_concurrent,
+               "mean_iters": float(np.mean([r.iters for r in done]))})
+    return st
+
+
+def adjoint_sample(members=4, n=512):
+    """Adjoint batch sample: forward solve + adjoint (dJ/dlog eta through autograd) per member."""
+    import torch
+    import paper_2603_14040_b300 as P
+    from synth import adjoint_member
+    from paper_2603_14040_b300.autograd import stokes_solve, surface_misfit
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=3000)
+    hp = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=3000)
+    times, norms = [], []
+    for b in range(members):
+        base, pert = adjoint_member(b, n, n)
+        obs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
+        hp.solve(dev(pert.eta_n), dev(pert.eta_c), dev(pert.rho), (0.0, 1.0), 1e-10, *obs)
+        vx_obs = obs[0][1].clone()
+        log_ec = dev(np.log(np.where(base.eta_c > 0, base.eta_c, 1.0))).requires_grad_(True)
+        log_en = dev(np.log(np.where(base.eta_n > 0, base.eta_n, 1.0))).requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mask_c = torch.zeros_like(log_ec); mask_c[1:n + 1, 1:n + 1] = 1
+        mask_n = torch.zeros_like(log_en); mask_n[:n + 1, :n + 1] = 1
+        vx, vy, p = stokes_solve(torch.exp(log_en) * mask_n, torch.exp(log_ec) * mask_c, dev(base.rho), h,
+                                 (0.0, 1.0), 1e-10)
+        J = surface_misfit(vx, vx_obs)
+        J.backward()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        norms.append(float(torch.linalg.norm(log_ec.grad)))
+    return {"members": members, "grid": n, "ms_per_member_forward_plus_adjoint": float(np.mean(times) * 1e3),
+            "grad_norm_log_eta_c": norms, "note": "full batch is 64 members; sample bounded for the bench"}
+
+
+def profile_solve(args):
+    """One solve (for ncu captures): random-viscosity workload at N x N, given precision, restart
+    length and iteration cap; prints a one-line summary."""
+    import torch
+    import paper_2603_14040_b300 as P
+    from synth import grf_config
+    n = args.profile
+    f = grf_config(n, n, seed=2)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    en, ec, rho = dev(f.eta_n), dev(f.eta_c), dev(f.rho)
+    outs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
+    prec = P.PREC_MIXED if args.prec == "mixed" else P.PREC_FP64
+    h = P.Stokes(n, n, prec=prec, max_iter=args.max_iter, restart_m=args.restart)
+    st = h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_solve": n, "prec": args.prec, "iters": st.iters, "status": st.status,
+                      "kernel_launches": st.kernel_launches}))
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -148,10 +284,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the 4096^2, serving and adjoint samples")
+    ap.add_argument("--profile", type=int, default=0, metavar="N",
+                    help="profiling driver: one solve of the random-viscosity workload at N x N, then exit")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--max-iter", type=int, default=3000)
+    ap.add_argument("--restart", type=int, default=30)
     args = ap.parse_args()
     rank, world, local = env_rank()
     import torch
     import torch.distributed as dist
+    if args.profile:
+        return profile_solve(args)
     if world > 1 and not dist.is_initialized():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     if args.impl == "reference":
@@ -272,6 +416,10 @@ def main():
                                    "rel_energy_res": sm.rel_energy_res, "rel_diff_vs_fp64_v": errv,
                                    "rel_diff_vs_fp64_p": errp, "p50_ms": float(np.percentile(ms, 50)),
                                    "p99_ms": float(np.percentile(ms, 99))}
+    if rank == 0 and not args.no_extras:
+        line["vcycle_roofline"] = vcycle_roofline_4096(peaks)
+        line["serving"] = serving_sample()
+        line["adjoint"] = adjoint_sample()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_baseline()
     if rank == 0:
