@@ -115,7 +115,7 @@ def oracle_baseline(seconds_budget=20.0, sample_n=128):
             "sample_seconds_per_solve": dt}
 
 
-def vcycle_roofline_4096(peaks, iters=6):
+def vcycle_roofline_4096(peaks, iters=6, tile_sweeps=2):
     """Level-0 FP32 V-cycle kernels at 4096^2 (every level-0 array is 67 MB, far above L2): the
     tile-fused two-sweep RBGS kernel moves 32 B/cell (reads vx, vy, fx, fy, eta_n, eta_c, writes
     vx, vy) per launch; achieved = bytes / measured duration (CUDA events inside the solve)."""
@@ -128,17 +128,18 @@ def vcycle_roofline_4096(peaks, iters=6):
     en, ec, rho = dev(f.eta_n), dev(f.eta_c), dev(f.rho)
     del f
     outs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
-    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=2)
+    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=2, tile_sweeps=tile_sweeps)
     h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)           # warm-up (graph capture)
     h.close()
-    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=iters)
+    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=iters, tile_sweeps=tile_sweeps)
     h.set_timing(True)
     st = h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
     torch.cuda.synchronize()
     ph, cnt = h.get_timing()
     it = max(cnt["iterations"], 1)
-    pre_ms = ph["l0_pre_smooth"] / it          # one launch: 2 fused sweeps
-    post_ms = ph["l0_post_smooth"] / it        # one launch: prolongation + 2 fused sweeps
+    launches = 2 // tile_sweeps                 # level-0 tile launches per smoothing block (nu = 2)
+    pre_ms = ph["l0_pre_smooth"] / it / launches
+    post_ms = ph["l0_post_smooth"] / it / launches
     cells = n * n
     bytes_pre = 32.0 * cells
     bytes_post = 34.0 * cells                  # + the coarse correction read (1/4 size, 2 fields)
@@ -148,7 +149,7 @@ def vcycle_roofline_4096(peaks, iters=6):
     h.close()
     del outs, en, ec, rho
     torch.cuda.empty_cache()
-    return {"kernel": "k_rbgs_tile<float,2,64,32> level 0 (2 fused RBGS sweeps per launch), 4096x4096 mixed",
+    return {"kernel": f"k_rbgs_tile_cs<{tile_sweeps},64,32> level 0 ({tile_sweeps} fused RBGS sweep(s) per launch), 4096x4096 mixed",
             "bound": "hbm", "achieved": gbs_pre, "peak": peak, "unit": "GB/s", "frac": gbs_pre / peak,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6400 GB/s",
             "bytes_per_launch": bytes_pre, "launch_ms": pre_ms,

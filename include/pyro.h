@@ -97,6 +97,8 @@ typedef struct {
                             as shared-memory tile kernels, one launch each per level visit (all FP32
                             levels; FP64 levels up to 65536 cells); 0: one kernel per colour and
                             step [1] */
+  int tile_sweeps;       /* FP32 tile kernels: sweeps fused per launch, 1 (halo 4, one HBM pass per
+                            sweep) or 2 (halo 8, one pass per two sweeps) [2] */
 } pyro_opts;
 
 typedef struct {

@@ -21,6 +21,11 @@
 
 namespace pyro {
 
+// Division of the smoother update: FP32 levels use the fast approximate division (the smoother is
+// only a preconditioner; every FP32 path uses this same form), FP64 levels divide exactly.
+__device__ inline float sdiv(float a, float b) { return __fdividef(a, b); }
+__device__ inline double sdiv(double a, double b) { return a / b; }
+
 // idg (optional): precomputed 1/diag per field (used on FP64 levels, where a division costs far
 // more than a load); without it the diagonal is divided inline.
 template <typename T>
@@ -32,12 +37,12 @@ __device__ inline void rbgs_point(const GeomT<T>& g, int i, int j, int field, T 
     if (!is_vx(g.nx, g.ny, i, j)) return;
     const T Lv = lx_point<T>(g, i, j, vx, vy, en, ec, diag);
     if (idgx) vx[c] += omega * (fx[c] - Lv) * idgx[c];
-    else vx[c] += omega * (fx[c] - Lv) / diag;
+    else vx[c] += omega * sdiv(fx[c] - Lv, diag);
   } else {
     if (!is_vy(g.nx, g.ny, i, j)) return;
     const T Lv = ly_point<T>(g, i, j, vx, vy, en, ec, diag);
     if (idgy) vy[c] += omega * (fy[c] - Lv) * idgy[c];
-    else vy[c] += omega * (fy[c] - Lv) / diag;
+    else vy[c] += omega * sdiv(fy[c] - Lv, diag);
   }
 }
 

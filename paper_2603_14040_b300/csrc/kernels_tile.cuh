@@ -174,3 +174,219 @@ __global__ void __launch_bounds__(kTileThreads)
 }
 
 }  // namespace pyro
+
+namespace pyro {
+
+// ---------------------------------------------------------------------------------------------
+// FP32 tile sweep on colour-split shared-memory planes.
+//
+// Each array of the tile region is stored as two planes, one per colour (i + j) mod 2, with
+// element (ri, rj) at plane c, column rj >> 1 (the region's first column is even in global
+// terms, so the two points of a column pair always have different colours). A half-sweep then
+// touches 32 consecutive entries of each plane per warp: every shared-memory access of the update
+// is conflict-free, and neighbour positions are fixed per-row offsets instead of index
+// arithmetic. The boundary rules (ghost elimination, zero normal velocity on walls) are applied
+// with selects on the global indices, so one code path serves interior and boundary tiles. The
+// update arithmetic is the same expression as rbgs_point<float>.
+// ---------------------------------------------------------------------------------------------
+template <int NS, int TX, int TY>
+struct SweepTileCS {
+  static constexpr int M = 4 * NS;
+  static constexpr int RX = TX + 2 * M, RY = TY + 2 * M, HX = RX / 2;
+  static constexpr int PLANE = RY * HX;                 // one colour plane of one array
+  // staged coarse block for the fused prolongation: rows/columns (origin / 2) - 1 ... covering
+  // the region, plus one on each side
+  static constexpr int CY = RY / 2 + 2, CX = RX / 2 + 2, CPL = CY * CX;
+  static constexpr size_t smem_bytes() { return ((size_t)PLANE * 2 * 6 + 2 * CPL) * sizeof(float); }
+  static_assert(RX % 2 == 0 && M % 2 == 0, "region must start on an even global column");
+};
+
+// One colour of one field over rows [r0, r1) and columns [c0, c1) of a colour-split tile. Threads
+// take consecutive (row, slot) pairs, so a warp covers 32 consecutive same-colour points. With
+// INTERIOR the boundary rules are provably inactive for every point and are not evaluated.
+template <bool INTERIOR, typename Tl>
+__device__ __forceinline__ void cs_halfsweep(const GeomT<float>& g, float* smf, int fld, int col, float omega,
+                                             int i0, int j0, int r0, int r1, int c0, int c1) {
+  constexpr int HX = Tl::HX, PL = Tl::PLANE;
+  const float* Xo = smf + (0 + (col ^ 1)) * PL;
+  const float* Xs = smf + (0 + col) * PL;
+  const float* Yo = smf + (2 + (col ^ 1)) * PL;
+  const float* Ys = smf + (2 + col) * PL;
+  const float* No = smf + (8 + (col ^ 1)) * PL;
+  const float* Ns = smf + (8 + col) * PL;
+  const float* Eo = smf + (10 + (col ^ 1)) * PL;
+  const float* Es = smf + (10 + col) * PL;
+  float* U = smf + (2 * fld + col) * PL;
+  const float* F = smf + (4 + 2 * fld + col) * PL;
+  const int nrow = r1 - r0;
+  for (int t = threadIdx.x; t < nrow * HX; t += blockDim.x) {
+    const int ri = r0 + t / HX;
+    const int k = t - (ri - r0) * HX;
+    const int gi = i0 + ri;
+    const int p = (col - gi - j0) & 1;
+    const int rj = 2 * k + p;
+    if (rj < c0 || rj >= c1) continue;
+    const int gj = j0 + rj;
+    const int s = ri * HX + k;
+    const int kw = s - 1 + p, ke = s + p;
+    if (fld == 0) {
+      if (!INTERIOR && !is_vx(g.nx, g.ny, gi, gj)) continue;
+      const float vc = Xs[s];
+      const float eA = Es[s], eB = Eo[ke];
+      const float e1 = No[s - HX], e2 = Ns[s];
+      float vw = Xo[kw], ve = Xo[ke], vn = Xo[s - HX], vs = Xo[s + HX];
+      float yA = Yo[s - HX], yB = Ys[s - HX + p], yC = Ys[s], yD = Yo[ke];
+      if (!INTERIOR) {
+        if (gj - 1 < 1) vw = 0.f;
+        if (gj + 1 > g.nx - 1) ve = 0.f;
+        if (gi == 1) vn = g.sN * vc;
+        if (gi == g.ny) vs = g.sS * vc;
+        if (gi - 1 < 1) { yA = 0.f; yB = 0.f; }
+        if (gi > g.ny - 1) { yC = 0.f; yD = 0.f; }
+      }
+      const float sxxE = 2.f * eB * (ve - vc);
+      const float sxxW = 2.f * eA * (vc - vw);
+      const float sxyS = e2 * ((vs - vc) * g.idy2 + (yD - yC) * g.idxdy);
+      const float sxyN = e1 * ((vc - vn) * g.idy2 + (yB - yA) * g.idxdy);
+      float diag = -2.f * (eA + eB) * g.idx2 - (e1 + e2) * g.idy2;
+      if (!INTERIOR) {
+        if (gi == 1) diag += g.sN * e1 * g.idy2;
+        if (gi == g.ny) diag += g.sS * e2 * g.idy2;
+      }
+      const float Lv = (sxxE - sxxW) * g.idx2 + sxyS - sxyN;
+      U[s] = vc + omega * __fdividef(F[s] - Lv, diag);
+    } else {
+      if (!INTERIOR && !is_vy(g.nx, g.ny, gi, gj)) continue;
+      const float vc = Ys[s];
+      const float eA = Es[s], eB = Eo[s + HX];
+      const float e1 = No[kw], e2 = Ns[s];
+      float vn = Yo[s - HX], vs = Yo[s + HX], vw = Yo[kw], ve = Yo[ke];
+      float xA = Xo[kw], xB = Xs[s + HX - 1 + p], xC = Xs[s], xD = Xo[s + HX];
+      if (!INTERIOR) {
+        if (gi - 1 < 1) vn = 0.f;
+        if (gi + 1 > g.ny - 1) vs = 0.f;
+        if (gj == 1) vw = g.sW * vc;
+        if (gj == g.nx) ve = g.sE * vc;
+        if (gj - 1 < 1) { xA = 0.f; xB = 0.f; }
+        if (gj > g.nx - 1) { xC = 0.f; xD = 0.f; }
+      }
+      const float syyS = 2.f * eB * (vs - vc);
+      const float syyN = 2.f * eA * (vc - vn);
+      const float sxyE = e2 * ((ve - vc) * g.idx2 + (xD - xC) * g.idxdy);
+      const float sxyW = e1 * ((vc - vw) * g.idx2 + (xB - xA) * g.idxdy);
+      float diag = -2.f * (eA + eB) * g.idy2 - (e1 + e2) * g.idx2;
+      if (!INTERIOR) {
+        if (gj == 1) diag += g.sW * e1 * g.idx2;
+        if (gj == g.nx) diag += g.sE * e2 * g.idx2;
+      }
+      const float Lv = (syyS - syyN) * g.idy2 + sxyE - sxyW;
+      U[s] = vc + omega * __fdividef(F[s] - Lv, diag);
+    }
+  }
+}
+
+template <int NS, int TX, int TY>
+__global__ void __launch_bounds__(kTileThreads)
+    k_rbgs_tile_cs(GeomT<float> g, const float* __restrict__ vx, const float* __restrict__ vy,
+                   float* __restrict__ ox, float* __restrict__ oy, const float* __restrict__ fx,
+                   const float* __restrict__ fy, const float* __restrict__ en, const float* __restrict__ ec,
+                   float omega, GeomT<float> gc, const float* __restrict__ cvx, const float* __restrict__ cvy) {
+  using Tl = SweepTileCS<NS, TX, TY>;
+  constexpr int M = Tl::M, RX = Tl::RX, RY = Tl::RY, HX = Tl::HX, PL = Tl::PLANE;
+  extern __shared__ __align__(16) float smf[];
+  // plane (array a, colour c) starts at smf + (2 a + c) * PL; arrays: 0 vx, 1 vy, 2 fx, 3 fy, 4 en, 5 ec
+  auto plane = [&](int a, int c) { return smf + (2 * a + c) * PL; };
+  (void)HX;
+  const int i0 = blockIdx.y * TY - M, j0 = blockIdx.x * TX - M;
+  const int rlo = max(0, -i0), rhi = min(RY, g.ny + 2 - i0);
+  const int clo = max(0, -j0), chi = min(RX, g.nx + 2 - j0);
+
+  // coarse correction (post-smoothing): stage the coarse block this region interpolates from,
+  // with the coarse boundary rule already applied, in shared memory behind the planes
+  float* cbx = smf + 12 * PL;
+  float* cby = cbx + Tl::CPL;
+  const int I0 = (i0 >> 1) - 1, J0 = (j0 >> 1) - 1;   // floor division (i0, j0 may be negative)
+  if (cvx) {
+    for (int t = threadIdx.x; t < Tl::CY * Tl::CX; t += blockDim.x) {
+      const int I = I0 + t / Tl::CX, J = J0 + t % Tl::CX;
+      const bool in = I >= 0 && I <= gc.ny + 1 && J >= 0 && J <= gc.nx + 1;
+      cbx[t] = in ? coarse_vx(gc, cvx, I, J) : 0.f;
+      cby[t] = in ? coarse_vy(gc, cvy, I, J) : 0.f;
+    }
+    __syncthreads();
+  }
+  auto cvxs = [&](int I, int J) { return cbx[(I - I0) * Tl::CX + (J - J0)]; };
+  auto cvys = [&](int I, int J) { return cby[(I - I0) * Tl::CX + (J - J0)]; };
+
+  // load the part of the region inside the domain, splitting colours
+#pragma unroll 2
+  for (int t = threadIdx.x; t < (rhi - rlo) * RX; t += blockDim.x) {
+    const int ri = rlo + t / RX, rj = t % RX;
+    if (rj < clo || rj >= chi) continue;
+    const int gi = i0 + ri, gj = j0 + rj;
+    const size_t o = (size_t)gi * g.ld + gj;
+    const int c = (gi + gj) & 1;
+    const int s = ri * HX + (rj >> 1);
+    float a = vx[o], b = vy[o];
+    const float f0 = fx[o], f1 = fy[o], e0 = en[o], e1 = ec[o];
+    if (cvx) {
+      if (is_vx(g.nx, g.ny, gi, gj)) {
+        // same weights as prolong_vx_inc, coarse values from the staged block
+        const int Ia = (gi & 1) ? (gi - 1) / 2 : gi / 2;
+        const float wy0 = (gi & 1) ? 0.25f : 0.75f, wy1 = 1.f - wy0;
+        if (gj & 1) {
+          const int Ja = (gj - 1) / 2;
+          a += 0.5f * (wy0 * cvxs(Ia, Ja) + wy1 * cvxs(Ia + 1, Ja) + wy0 * cvxs(Ia, Ja + 1) + wy1 * cvxs(Ia + 1, Ja + 1));
+        } else {
+          const int Jc = gj / 2;
+          a += wy0 * cvxs(Ia, Jc) + wy1 * cvxs(Ia + 1, Jc);
+        }
+      }
+      if (is_vy(g.nx, g.ny, gi, gj)) {
+        const int Ja = (gj & 1) ? (gj - 1) / 2 : gj / 2;
+        const float wx0 = (gj & 1) ? 0.25f : 0.75f, wx1 = 1.f - wx0;
+        if (gi & 1) {
+          const int Ia = (gi - 1) / 2;
+          b += 0.5f * (wx0 * cvys(Ia, Ja) + wx1 * cvys(Ia, Ja + 1) + wx0 * cvys(Ia + 1, Ja) + wx1 * cvys(Ia + 1, Ja + 1));
+        } else {
+          const int Ic = gi / 2;
+          b += wx0 * cvys(Ic, Ja) + wx1 * cvys(Ic, Ja + 1);
+        }
+      }
+    }
+    plane(0, c)[s] = a;
+    plane(1, c)[s] = b;
+    plane(2, c)[s] = f0;
+    plane(3, c)[s] = f1;
+    plane(4, c)[s] = e0;
+    plane(5, c)[s] = e1;
+  }
+  __syncthreads();
+
+  // a tile whose whole region lies in rows/columns [2, n-2] needs no boundary rule anywhere
+  const bool interior = i0 >= 2 && i0 + RY - 1 <= g.ny - 2 && j0 >= 2 && j0 + RX - 1 <= g.nx - 2;
+  int h = 0;
+  for (int sw = 0; sw < NS; ++sw)
+    for (int fld = 0; fld < 2; ++fld)
+      for (int col = 0; col < 2; ++col, ++h) {
+        const int m = h + 1;
+        const int r0 = max(m, rlo), r1 = min(RY - m, rhi);
+        const int c0 = max(m, clo), c1 = min(RX - m, chi);
+        if (interior) cs_halfsweep<true, Tl>(g, smf, fld, col, omega, i0, j0, r0, r1, c0, c1);
+        else cs_halfsweep<false, Tl>(g, smf, fld, col, omega, i0, j0, r0, r1, c0, c1);
+        __syncthreads();
+      }
+
+  for (int t = threadIdx.x; t < TX * TY; t += blockDim.x) {
+    const int ri = M + t / TX, rj = M + t % TX;
+    const int gi = i0 + ri, gj = j0 + rj;
+    if (gi > g.ny + 1 || gj > g.nx + 1) continue;
+    const size_t o = (size_t)gi * g.ld + gj;
+    const int c = (gi + gj) & 1;
+    const int s = ri * HX + (rj >> 1);
+    if (is_vx(g.nx, g.ny, gi, gj)) ox[o] = plane(0, c)[s];
+    if (is_vy(g.nx, g.ny, gi, gj)) oy[o] = plane(1, c)[s];
+  }
+}
+
+}  // namespace pyro

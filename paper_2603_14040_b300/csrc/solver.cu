@@ -111,6 +111,7 @@ struct MG {
   int kcycle = 0;  // levels l < kcycle get their coarse correction from two flexible-CG steps
   int ls = -1;     // first level run by the cluster sub-cycle kernel (-1: none)
   bool tiles = true;                        // tile-fused smoothing / residual+restriction
+  int tile_sweeps = 2;                      // FP32: sweeps fused per tile launch
   static constexpr long long kFuse64Cells = 65536;
   SubArgs<T> sub{};
   double* red = nullptr;
@@ -227,20 +228,20 @@ struct MG {
       return;
     }
     while (nsweeps > 0) {
-      if (sizeof(T) == 4 && nsweeps >= 2) {
+      if constexpr (sizeof(T) == 4) {
         constexpr int TX = 64, TY = 32;
         const dim3 gr((L.g.nx + 2 + TX - 1) / TX, (L.g.ny + 2 + TY - 1) / TY);
-        k_rbgs_tile<T, 2, TX, TY><<<gr, kTileThreads, SweepTile<T, 2, TX, TY>::smem_bytes(L.idgx != nullptr), s>>>(
-            L.gt, L.X(), L.Y(), L.cur ? L.vx : L.vx2, L.cur ? L.vy : L.vy2, L.fx, L.fy, L.en, L.ec, L.idgx,
-            L.idgy, omega, gc, cvx, cvy);
-        nsweeps -= 2;
-      } else if (sizeof(T) == 4) {
-        constexpr int TX = 64, TY = 32;
-        const dim3 gr((L.g.nx + 2 + TX - 1) / TX, (L.g.ny + 2 + TY - 1) / TY);
-        k_rbgs_tile<T, 1, TX, TY><<<gr, kTileThreads, SweepTile<T, 1, TX, TY>::smem_bytes(L.idgx != nullptr), s>>>(
-            L.gt, L.X(), L.Y(), L.cur ? L.vx : L.vx2, L.cur ? L.vy : L.vy2, L.fx, L.fy, L.en, L.ec, L.idgx,
-            L.idgy, omega, gc, cvx, cvy);
-        nsweeps -= 1;
+        float* ox = L.cur ? L.vx : L.vx2;
+        float* oy = L.cur ? L.vy : L.vy2;
+        if (nsweeps >= 2 && tile_sweeps >= 2) {
+          k_rbgs_tile_cs<2, TX, TY><<<gr, kTileThreads, SweepTileCS<2, TX, TY>::smem_bytes(), s>>>(
+              L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, gc, cvx, cvy);
+          nsweeps -= 2;
+        } else {
+          k_rbgs_tile_cs<1, TX, TY><<<gr, kTileThreads, SweepTileCS<1, TX, TY>::smem_bytes(), s>>>(
+              L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, gc, cvx, cvy);
+          nsweeps -= 1;
+        }
       } else {
         constexpr int TX = 64, TY = 16;
         const dim3 gr((L.g.nx + 2 + TX - 1) / TX, (L.g.ny + 2 + TY - 1) / TY);
@@ -269,11 +270,11 @@ struct MG {
 
   // raise the dynamic shared-memory limit of the tile kernels (once per handle)
   static void enable_tiles() {
-    if (sizeof(T) == 4) {
-      CK(cudaFuncSetAttribute(k_rbgs_tile<T, 2, 64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)SweepTile<T, 2, 64, 32>::smem_bytes(true)));
-      CK(cudaFuncSetAttribute(k_rbgs_tile<T, 1, 64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)SweepTile<T, 1, 64, 32>::smem_bytes(true)));
+    if constexpr (sizeof(T) == 4) {
+      CK(cudaFuncSetAttribute(k_rbgs_tile_cs<2, 64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SweepTileCS<2, 64, 32>::smem_bytes()));
+      CK(cudaFuncSetAttribute(k_rbgs_tile_cs<1, 64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SweepTileCS<1, 64, 32>::smem_bytes()));
       CK(cudaFuncSetAttribute(k_resrestrict_tile<T, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)ResTile<T, 32, 16>::smem_bytes()));
     } else {
@@ -759,6 +760,7 @@ void pyro_default_opts(pyro_opts* o) {
   o->kcycle = 0;
   o->cluster_cells = 0;
   o->tile_fusion = 1;
+  o->tile_sweeps = 2;
 }
 
 const char* pyro_version(void) { return "pyro-b300 0.1 (sm_103a)"; }
@@ -838,6 +840,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->mgf.nu1 = o.nu1; h->mgf.nu2 = o.nu2; h->mgf.omega = (float)o.omega_v; h->mgf.eta_mode = o.eta_coarsen;
       h->mgf.kcycle = o.kcycle;
       h->mgf.tiles = o.tile_fusion != 0;
+      h->mgf.tile_sweeps = o.tile_sweeps;
       if (h->mgf.tiles) MG<float>::enable_tiles();
       CK(cudaDeviceSynchronize());
       h->mgf.alloc(A, h->g, L, false);

@@ -29,7 +29,8 @@ class PyroOpts(ctypes.Structure):
                 ("alpha_p", ctypes.c_double), ("restart_m", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("prec", ctypes.c_int), ("coarsest_min", ctypes.c_int), ("eta_coarsen", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("use_graphs", ctypes.c_int), ("timeout_s", ctypes.c_double),
-                ("kcycle", ctypes.c_int), ("cluster_cells", ctypes.c_int), ("tile_fusion", ctypes.c_int)]
+                ("kcycle", ctypes.c_int), ("cluster_cells", ctypes.c_int), ("tile_fusion", ctypes.c_int),
+                ("tile_sweeps", ctypes.c_int)]
 
 
 class PyroStats(ctypes.Structure):
