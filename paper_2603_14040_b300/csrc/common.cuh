@@ -110,6 +110,45 @@ __device__ inline T ly_point(const GeomT<T>& g, int i, int j, const SV* vx, cons
   return (syyS - syyN) * g.idy2 + sxyE - sxyW;
 }
 
+// Precomputed viscosity coefficients of one level (FP64 levels whose smoothing is ALU-bound):
+// cxx = 2 eta_c/dx^2, cyy = 2 eta_c/dy^2 at cells; nxx = eta_n/dx^2, nyy = eta_n/dy^2,
+// nxy = eta_n/(dx dy) at basic nodes. A null cxx means "use eta directly".
+template <typename T>
+struct Coef {
+  const T *cxx, *cyy, *nxx, *nyy, *nxy;
+};
+
+// lx_point with precomputed coefficients: the same stress differences, about half the multiplies.
+template <typename T, typename SV>
+__device__ inline T lx_coef(const GeomT<T>& g, int i, int j, const SV* vx, const SV* vy, const Coef<T>& k) {
+  const int ld = g.ld;
+  const size_t c = (size_t)i * ld + j;
+  const T vc = (T)vx[c];
+  const T vw = ldvx<T>(vx, ld, g.nx, i, j - 1);
+  const T ve = ldvx<T>(vx, ld, g.nx, i, j + 1);
+  const T vn = (i == 1) ? g.sN * vc : (T)vx[c - ld];
+  const T vs = (i == g.ny) ? g.sS * vc : (T)vx[c + ld];
+  const T yA = ldvy<T>(vy, ld, g.ny, i - 1, j), yB = ldvy<T>(vy, ld, g.ny, i - 1, j + 1);
+  const T yC = ldvy<T>(vy, ld, g.ny, i, j), yD = ldvy<T>(vy, ld, g.ny, i, j + 1);
+  return k.cxx[c + 1] * (ve - vc) - k.cxx[c] * (vc - vw) + k.nyy[c] * (vs - vc) + k.nxy[c] * (yD - yC) -
+         k.nyy[c - ld] * (vc - vn) - k.nxy[c - ld] * (yB - yA);
+}
+
+template <typename T, typename SV>
+__device__ inline T ly_coef(const GeomT<T>& g, int i, int j, const SV* vx, const SV* vy, const Coef<T>& k) {
+  const int ld = g.ld;
+  const size_t c = (size_t)i * ld + j;
+  const T vc = (T)vy[c];
+  const T vn = ldvy<T>(vy, ld, g.ny, i - 1, j);
+  const T vs = ldvy<T>(vy, ld, g.ny, i + 1, j);
+  const T vw = (j == 1) ? g.sW * vc : (T)vy[c - 1];
+  const T ve = (j == g.nx) ? g.sE * vc : (T)vy[c + 1];
+  const T xA = ldvx<T>(vx, ld, g.nx, i, j - 1), xB = ldvx<T>(vx, ld, g.nx, i + 1, j - 1);
+  const T xC = ldvx<T>(vx, ld, g.nx, i, j), xD = ldvx<T>(vx, ld, g.nx, i + 1, j);
+  return k.cyy[c + ld] * (vs - vc) - k.cyy[c] * (vc - vn) + k.nxx[c] * (ve - vc) + k.nxy[c] * (xD - xC) -
+         k.nxx[c - 1] * (vc - vw) - k.nxy[c - 1] * (xB - xA);
+}
+
 // Error flags written by kernels (host reads them after a sync).
 enum : int { FLAG_NONFINITE = 1, FLAG_BREAKDOWN = 2 };
 

@@ -31,14 +31,16 @@ __device__ inline double block_sum(double v, double* sh) {
 template <typename TV>
 __device__ inline void stokes_point(const GeomT<double>& g, int i, int j, const double* en, const double* ec,
                                     const TV* xv, const TV* yv, const TV* pv, double& ox, double& oy,
-                                    double& op) {
+                                    double& op, const Coef<double>& kc = Coef<double>{}) {
   const size_t c = (size_t)i * g.ld + j;
   double d;
   ox = oy = op = 0.0;
   if (is_vx(g.nx, g.ny, i, j))
-    ox = lx_point<double>(g, i, j, xv, yv, en, ec, d) - ((double)pv[c + 1] - (double)pv[c]) * g.idx;
+    ox = (kc.cxx ? lx_coef<double>(g, i, j, xv, yv, kc) : lx_point<double>(g, i, j, xv, yv, en, ec, d)) -
+         ((double)pv[c + 1] - (double)pv[c]) * g.idx;
   if (is_vy(g.nx, g.ny, i, j))
-    oy = ly_point<double>(g, i, j, xv, yv, en, ec, d) - ((double)pv[c + g.ld] - (double)pv[c]) * g.idy;
+    oy = (kc.cxx ? ly_coef<double>(g, i, j, xv, yv, kc) : ly_point<double>(g, i, j, xv, yv, en, ec, d)) -
+         ((double)pv[c + g.ld] - (double)pv[c]) * g.idy;
   if (is_p(g.nx, g.ny, i, j))
     op = (ldvx<double>(xv, g.ld, g.nx, i, j) - ldvx<double>(xv, g.ld, g.nx, i, j - 1)) * g.idx +
          (ldvy<double>(yv, g.ld, g.ny, i, j) - ldvy<double>(yv, g.ld, g.ny, i - 1, j)) * g.idy;
@@ -48,14 +50,14 @@ __device__ inline void stokes_point(const GeomT<double>& g, int i, int j, const 
 template <typename TV>
 __global__ void k_apply(GeomT<double> g, const double* __restrict__ en, const double* __restrict__ ec,
                         const TV* __restrict__ X, size_t stride, const int* __restrict__ d_k,
-                        double* __restrict__ y) {
+                        double* __restrict__ y, Coef<double> kc) {
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (i > g.ny + 1 || j > g.nx + 1) return;
   const size_t P = (size_t)(g.ny + 2) * g.ld;
   const TV* x = X + (d_k ? (size_t)(*d_k) * stride : 0);
   double ox, oy, op;
-  stokes_point<TV>(g, i, j, en, ec, x, x + P, x + 2 * P, ox, oy, op);
+  stokes_point<TV>(g, i, j, en, ec, x, x + P, x + 2 * P, ox, oy, op, kc);
   const size_t c = (size_t)i * g.ld + j;
   y[c] = ox;
   y[P + c] = oy;
@@ -65,7 +67,8 @@ __global__ void k_apply(GeomT<double> g, const double* __restrict__ en, const do
 // r = b - A x; per-block partial sums of sum(W r^2) and sum(r^2) into part[2*blockId + {0,1}]
 __global__ void k_residual(GeomT<double> g, const double* __restrict__ en, const double* __restrict__ ec,
                            const double* __restrict__ b, const double* __restrict__ x,
-                           double* __restrict__ r, const double* __restrict__ W, double* __restrict__ part) {
+                           double* __restrict__ r, const double* __restrict__ W, double* __restrict__ part,
+                           Coef<double> kc) {
   __shared__ double sh[32];
   const size_t P = (size_t)(g.ny + 2) * g.ld;
   const int rows = g.ny + 2, cols = g.nx + 2;
@@ -74,7 +77,7 @@ __global__ void k_residual(GeomT<double> g, const double* __restrict__ en, const
     const int i = (int)(e / cols), j = (int)(e % cols);
     if (i >= rows) break;
     double ox, oy, op;
-    stokes_point<double>(g, i, j, en, ec, x, x + P, x + 2 * P, ox, oy, op);
+    stokes_point<double>(g, i, j, en, ec, x, x + P, x + 2 * P, ox, oy, op, kc);
     const double rx = is_vx(g.nx, g.ny, i, j) ? b[e] - ox : 0.0;
     const double ry = is_vy(g.nx, g.ny, i, j) ? b[P + e] - oy : 0.0;
     const double rp = is_p(g.nx, g.ny, i, j) ? b[2 * P + e] - op : 0.0;
@@ -471,9 +474,7 @@ __global__ void k_rho_grad(GeomT<double> g, const double* __restrict__ lam, doub
 }
 
 template __global__ void k_apply<double>(GeomT<double>, const double*, const double*, const double*, size_t,
-                                         const int*, double*);
-template __global__ void k_apply<float>(GeomT<double>, const double*, const double*, const float*, size_t,
-                                        const int*, double*);
+                                         const int*, double*, Coef<double>);
 template __global__ void k_update_x<double>(double*, const double*, size_t, int, const double*, size_t);
 template __global__ void k_update_x<float>(double*, const float*, size_t, int, const double*, size_t);
 template __global__ void k_precond_in<float>(size_t, const double*, size_t, const int*, float*, float*, float*, float*);

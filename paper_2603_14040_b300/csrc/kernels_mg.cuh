@@ -30,17 +30,18 @@ __device__ inline double sdiv(double a, double b) { return a / b; }
 // more than a load); without it the diagonal is divided inline.
 template <typename T>
 __device__ inline void rbgs_point(const GeomT<T>& g, int i, int j, int field, T omega, T* vx, T* vy, const T* fx,
-                                  const T* fy, const T* en, const T* ec, const T* idgx, const T* idgy) {
+                                  const T* fy, const T* en, const T* ec, const T* idgx, const T* idgy,
+                                  const Coef<T>& kc = Coef<T>{}) {
   const size_t c = (size_t)i * g.ld + j;
   T diag;
   if (field == 0) {
     if (!is_vx(g.nx, g.ny, i, j)) return;
-    const T Lv = lx_point<T>(g, i, j, vx, vy, en, ec, diag);
+    const T Lv = (kc.cxx && idgx) ? lx_coef<T>(g, i, j, vx, vy, kc) : lx_point<T>(g, i, j, vx, vy, en, ec, diag);
     if (idgx) vx[c] += omega * (fx[c] - Lv) * idgx[c];
     else vx[c] += omega * sdiv(fx[c] - Lv, diag);
   } else {
     if (!is_vy(g.nx, g.ny, i, j)) return;
-    const T Lv = ly_point<T>(g, i, j, vx, vy, en, ec, diag);
+    const T Lv = (kc.cxx && idgy) ? ly_coef<T>(g, i, j, vx, vy, kc) : ly_point<T>(g, i, j, vx, vy, en, ec, diag);
     if (idgy) vy[c] += omega * (fy[c] - Lv) * idgy[c];
     else vy[c] += omega * sdiv(fy[c] - Lv, diag);
   }
@@ -73,21 +74,41 @@ __global__ void k_invdiag(GeomT<T> g, const T* __restrict__ en, const T* __restr
 template <typename T>
 __global__ void k_rbgs(GeomT<T> g, T* __restrict__ vx, T* __restrict__ vy, const T* __restrict__ fx,
                        const T* __restrict__ fy, const T* __restrict__ en, const T* __restrict__ ec,
-                       int field, int colour, T omega, const T* __restrict__ idgx, const T* __restrict__ idgy) {
+                       int field, int colour, T omega, const T* __restrict__ idgx, const T* __restrict__ idgy,
+                       Coef<T> kc) {
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   const int jh = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = 2 * jh + ((i + colour) & 1);
   if (i > g.ny + 1 || j > g.nx + 1) return;
-  rbgs_point<T>(g, i, j, field, omega, vx, vy, fx, fy, en, ec, idgx, idgy);
+  rbgs_point<T>(g, i, j, field, omega, vx, vy, fx, fy, en, ec, idgx, idgy, kc);
+}
+
+// coefficient arrays of one level (see Coef)
+template <typename T>
+__global__ void k_coefs(GeomT<T> g, const T* __restrict__ en, const T* __restrict__ ec, T* __restrict__ cxx,
+                        T* __restrict__ cyy, T* __restrict__ nxx, T* __restrict__ nyy, T* __restrict__ nxy) {
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > g.ny + 1 || j > g.nx + 1) return;
+  const size_t c = (size_t)i * g.ld + j;
+  const T e = ec[c], n = en[c];
+  cxx[c] = T(2) * e * g.idx2;
+  cyy[c] = T(2) * e * g.idy2;
+  nxx[c] = n * g.idx2;
+  nyy[c] = n * g.idy2;
+  nxy[c] = n * g.idxdy;
 }
 
 template <typename T>
 __device__ inline void vresid_point(const GeomT<T>& g, int i, int j, const T* vx, const T* vy, const T* fx,
-                                    const T* fy, const T* en, const T* ec, T* rx, T* ry) {
+                                    const T* fy, const T* en, const T* ec, T* rx, T* ry,
+                                    const Coef<T>& kc = Coef<T>{}) {
   const size_t c = (size_t)i * g.ld + j;
   T d, ox = T(0), oy = T(0);
-  if (is_vx(g.nx, g.ny, i, j)) ox = fx[c] - lx_point<T>(g, i, j, vx, vy, en, ec, d);
-  if (is_vy(g.nx, g.ny, i, j)) oy = fy[c] - ly_point<T>(g, i, j, vx, vy, en, ec, d);
+  if (is_vx(g.nx, g.ny, i, j))
+    ox = fx[c] - (kc.cxx ? lx_coef<T>(g, i, j, vx, vy, kc) : lx_point<T>(g, i, j, vx, vy, en, ec, d));
+  if (is_vy(g.nx, g.ny, i, j))
+    oy = fy[c] - (kc.cxx ? ly_coef<T>(g, i, j, vx, vy, kc) : ly_point<T>(g, i, j, vx, vy, en, ec, d));
   rx[c] = ox;
   ry[c] = oy;
 }
@@ -95,11 +116,11 @@ __device__ inline void vresid_point(const GeomT<T>& g, int i, int j, const T* vx
 template <typename T>
 __global__ void k_vresidual(GeomT<T> g, const T* __restrict__ vx, const T* __restrict__ vy,
                             const T* __restrict__ fx, const T* __restrict__ fy, const T* __restrict__ en,
-                            const T* __restrict__ ec, T* __restrict__ rx, T* __restrict__ ry) {
+                            const T* __restrict__ ec, T* __restrict__ rx, T* __restrict__ ry, Coef<T> kc) {
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (i > g.ny + 1 || j > g.nx + 1) return;
-  vresid_point<T>(g, i, j, vx, vy, fx, fy, en, ec, rx, ry);
+  vresid_point<T>(g, i, j, vx, vy, fx, fy, en, ec, rx, ry, kc);
 }
 
 template <typename T>
@@ -475,9 +496,9 @@ __global__ void k_coarse_solve(Geom g, const double* __restrict__ Ainv, int n, c
 // ---- explicit instantiations ---------------------------------------------------------------
 #define PYRO_INST(T)                                                                                         \
   template __global__ void k_rbgs<T>(GeomT<T>, T*, T*, const T*, const T*, const T*, const T*, int, int, T, \
-                                     const T*, const T*);                                                  \
+                                     const T*, const T*, Coef<T>);                                         \
   template __global__ void k_vresidual<T>(GeomT<T>, const T*, const T*, const T*, const T*, const T*,      \
-                                          const T*, T*, T*);                                                \
+                                          const T*, T*, T*, Coef<T>);                                       \
   template __global__ void k_restrict<T>(GeomT<T>, GeomT<T>, const T*, const T*, T*, T*);                  \
   template __global__ void k_prolong_add<T>(GeomT<T>, GeomT<T>, T*, T*, const T*, const T*);               \
   template __global__ void k_coarsen_eta<T>(GeomT<T>, GeomT<T>, const T*, const T*, T*, T*, int);          \

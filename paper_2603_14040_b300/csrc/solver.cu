@@ -95,6 +95,8 @@ struct Level {
   T *d1x = nullptr, *d1y = nullptr, *q1x = nullptr, *q1y = nullptr, *ex = nullptr, *ey = nullptr;
   T *idgx = nullptr, *idgy = nullptr;  // precomputed 1/diag (FP64 levels)
   T *vx2 = nullptr, *vy2 = nullptr;    // second iterate buffer for the tile sweeps (ping-pong)
+  Coef<T> kc{};                        // precomputed coefficients (FP64 levels smoothed per colour)
+  bool own_kc = false;
   int cur = 0;                         // which buffer holds the iterate (set while launching)
   T* X() const { return cur ? vx2 : vx; }
   T* Y() const { return cur ? vy2 : vy; }
@@ -125,7 +127,7 @@ struct MG {
   static size_t bytes(int nx, int ny, int nlev, int kcycle = 0) {
     size_t b = 0;
     for (int l = 0; l < nlev; ++l) {
-      b += (size_t)(sizeof(T) == 8 ? 12 : 10) * (size_t)(ny + 2) * (nx + 2) * sizeof(T);
+      b += (size_t)(sizeof(T) == 8 ? 17 : 10) * (size_t)(ny + 2) * (nx + 2) * sizeof(T);
       if (kc_level(l, nlev, kcycle)) b += (size_t)6 * (size_t)(ny + 2) * (nx + 2) * sizeof(T) + 5 * 296 * 8 + 64;
       if (l + 1 < nlev) { nx /= 2; ny /= 2; }
     }
@@ -145,6 +147,11 @@ struct MG {
       if (l == 0 && alias_eta0) { L.en = nullptr; L.ec = nullptr; }
       else { L.en = A.get<T>(L.P); L.ec = A.get<T>(L.P); }
       if (sizeof(T) == 8) { L.idgx = A.get<T>(L.P); L.idgy = A.get<T>(L.P); }
+      if (sizeof(T) == 8 && (!tiles || (long long)g.nx * g.ny > kFuse64Cells) && !(l == 0 && alias_eta0)) {
+        T* k5 = A.get<T>(5 * L.P);
+        L.kc = Coef<T>{k5, k5 + L.P, k5 + 2 * L.P, k5 + 3 * L.P, k5 + 4 * L.P};
+        L.own_kc = true;
+      }
       if (tiles) {
         L.vx2 = A.get<T>(L.P); L.vy2 = A.get<T>(L.P);
         CK(cudaMemset(L.vx2, 0, L.P * sizeof(T)));
@@ -198,6 +205,13 @@ struct MG {
       Level<T>& C = lv[l];
       k_coarsen_eta<T><<<grid2(C.g.nx, C.g.ny, kBlk2), kBlk2, 0, s>>>(F.gt, C.gt, F.en, F.ec, C.en, C.ec, eta_mode);
     }
+    for (size_t l = 0; l < lv.size(); ++l)
+      if (lv[l].own_kc) {
+        const Level<T>& L = lv[l];
+        k_coefs<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, L.en, L.ec, (T*)L.kc.cxx, (T*)L.kc.cyy,
+                                                                   (T*)L.kc.nxx, (T*)L.kc.nyy, (T*)L.kc.nxy);
+        count(1);
+      }
     for (size_t l = 0; l < lv.size(); ++l)
       if (lv[l].idgx) {
         const Level<T>& L = lv[l];
@@ -290,7 +304,7 @@ struct MG {
     const dim3 g = grid_rb(L.g.nx, L.g.ny, kBlk2);
     for (int f = 0; f < 2; ++f)
       for (int c = 0; c < 2; ++c)
-        k_rbgs<T><<<g, kBlk2, 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, f, c, omega, L.idgx, L.idgy);
+        k_rbgs<T><<<g, kBlk2, 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, f, c, omega, L.idgx, L.idgy, L.kc);
     count(4);
   }
 
@@ -318,7 +332,8 @@ struct MG {
     } else {
       for (int k = 0; k < nu1; ++k) sweep(l, s);
       if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[2], s, cudaEventRecordExternal));
-      k_vresidual<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, L.rx, L.ry);
+      k_vresidual<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, L.rx,
+                                                                       L.ry, L.kc);
       k_restrict<T><<<grid2(C.g.nx, C.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C.gt, L.rx, L.ry, C.fx, C.fy);
       count(2);
       CK(cudaMemsetAsync(C.vx, 0, C.P * sizeof(T), s));
@@ -370,6 +385,7 @@ struct pyro_stokes_s {
   bool mixed = true;
   DevAlloc mem;
   // FP64 state
+  Coef<double> okc{};  // coefficients of the FP64 outer operator (shared with FP64 level 0)
   double *en = nullptr, *ec = nullptr, *rho = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *w = nullptr,
          *W = nullptr, *stage = nullptr, *xf = nullptr, *V = nullptr;
   void* Z = nullptr;
@@ -416,7 +432,8 @@ void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s) {
   k_precond_out<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->V, (TZ*)h->Z, h->n3, h->d_j,
                                                            h->ec, h->o.alpha_p, h->part2);
   k_sub_mean<TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, (TZ*)h->Z + 2 * h->P, h->n3, h->d_j, h->part2, kReduceBlocks);
-  k_apply<TZ><<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->ec, (const TZ*)h->Z, h->n3, h->d_j, h->w);
+  k_apply<TZ><<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->ec, (const TZ*)h->Z, h->n3, h->d_j, h->w,
+                                                            h->okc);
   mark(h, 5, s);
 }
 
@@ -499,7 +516,7 @@ void launch_iteration(pyro_stokes_s* h, cudaStream_t s) {
 
 // host-side sum of the per-block partials (fixed order)
 std::pair<double, double> residual_norms(pyro_stokes_s* h, const double* b, const double* x, double* r, cudaStream_t s) {
-  k_residual<<<kReduceBlocks, kThreads, 0, s>>>(h->g64, h->en, h->ec, b, x, r, h->W, h->partial);
+  k_residual<<<kReduceBlocks, kThreads, 0, s>>>(h->g64, h->en, h->ec, b, x, r, h->W, h->partial, h->okc);
   h->launches += 1;
   CK(cudaMemcpyAsync(h->hbuf, h->partial, 2 * kReduceBlocks * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -555,7 +572,15 @@ void emit(pyro_stokes_s* h, const double* x, double* vx, double* vy, double* p, 
     if (outs[k] && !dev[k]) CK(cudaMemcpyAsync(outs[k], d[k], h->P * sizeof(double), cudaMemcpyDeviceToHost, s));
 }
 
+void outer_coefs(pyro_stokes_s* h, cudaStream_t s) {
+  k_coefs<double><<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->ec, (double*)h->okc.cxx,
+                                                               (double*)h->okc.cyy, (double*)h->okc.nxx,
+                                                               (double*)h->okc.nyy, (double*)h->okc.nxy);
+  h->launches += 1;
+}
+
 void setup_eta(pyro_stokes_s* h, cudaStream_t s) {
+  outer_coefs(h, s);
   // level-0 viscosity of the V-cycle: FP32 copies (mixed) or the FP64 arrays themselves
   if (h->mixed) {
     Level<float>& L0 = h->mgf.lv[0];
@@ -728,6 +753,7 @@ size_t footprint_bytes(int nx, int ny, const pyro_opts& o, int L) {
   const size_t m = (size_t)o.restart_m;
   size_t b = 0;
   b += 3 * P * 8;                  // en, ec, rho
+  b += 5 * P * 8;                  // outer operator coefficients
   b += 6 * n3 * 8;                 // b, x, r, w, W, xf
   b += n3 * 8;                     // stage
   b += (m + 1) * n3 * 8;           // V
@@ -826,6 +852,10 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
     h->b = A.get<double>(h->n3); h->x = A.get<double>(h->n3); h->r = A.get<double>(h->n3);
     h->w = A.get<double>(h->n3); h->W = A.get<double>(h->n3); h->xf = A.get<double>(h->n3);
     h->stage = A.get<double>(h->n3);
+    {
+      double* k5 = A.get<double>(5 * h->P);
+      h->okc = Coef<double>{k5, k5 + h->P, k5 + 2 * h->P, k5 + 3 * h->P, k5 + 4 * h->P};
+    }
     h->V = A.get<double>((size_t)(h->m + 1) * h->n3);
     h->Z = A.get<double>((size_t)h->m * h->n3);
     h->h1 = A.get<double>(kMaxRestart + 2); h->h2 = A.get<double>(kMaxRestart + 2);
@@ -853,6 +883,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->mgd.alloc(A, h->g, L, true);
       h->mgd.lv[0].en = h->en;
       h->mgd.lv[0].ec = h->ec;
+      if (!h->mgd.fused(0)) h->mgd.lv[0].kc = h->okc;  // FP64 level 0 shares the outer coefficients
       h->mgd.setup_sub(A, o.cluster_cells);
     }
     CK(cudaMallocHost(&h->hbuf, 4 * kReduceBlocks * sizeof(double) + 1024));
@@ -965,7 +996,8 @@ int pyro_stokes_apply(pyro_stokes h, const double* eta_n, const double* eta_c, c
     ingest(h, vx, h->r, 4, s);
     ingest(h, vy, h->r + h->P, 5, s);
     ingest(h, p, h->r + 2 * h->P, 2, s);
-    k_apply<double><<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->ec, h->r, 0, nullptr, h->w);
+    outer_coefs(h, s);
+    k_apply<double><<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->ec, h->r, 0, nullptr, h->w, h->okc);
     double* outs[3] = {Ax, Ay, Ap};
     for (int k = 0; k < 3; ++k) {
       if (is_device_ptr(outs[k])) CK(cudaMemcpyAsync(outs[k], h->w + k * h->P, h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
