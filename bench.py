@@ -115,10 +115,11 @@ def oracle_baseline(seconds_budget=20.0, sample_n=128):
             "sample_seconds_per_solve": dt}
 
 
-def vcycle_roofline_4096(peaks, iters=6, tile_sweeps=2):
+def vcycle_roofline_4096(peaks, iters=6, tile_sweeps=2, tile_fusion=2):
     """Level-0 FP32 V-cycle kernels at 4096^2 (every level-0 array is 67 MB, far above L2): the
-    tile-fused two-sweep RBGS kernel moves 32 B/cell (reads vx, vy, fx, fy, eta_n, eta_c, writes
-    vx, vy) per launch; achieved = bytes / measured duration (CUDA events inside the solve)."""
+    two-sweep RBGS pass (row-streaming kernel with tile_fusion=2, shared-memory tiles with 1)
+    moves 32 B/cell (reads vx, vy, fx, fy, eta_n, eta_c, writes vx, vy) per launch; achieved =
+    bytes / measured duration (CUDA events inside the solve)."""
     import torch
     import paper_2603_14040_b300 as P
     from synth import layered_config
@@ -128,10 +129,10 @@ def vcycle_roofline_4096(peaks, iters=6, tile_sweeps=2):
     en, ec, rho = dev(f.eta_n), dev(f.eta_c), dev(f.rho)
     del f
     outs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
-    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=2, tile_sweeps=tile_sweeps)
+    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=2, tile_sweeps=tile_sweeps, tile_fusion=tile_fusion)
     h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)           # warm-up (graph capture)
     h.close()
-    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=iters, tile_sweeps=tile_sweeps)
+    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=iters, tile_sweeps=tile_sweeps, tile_fusion=tile_fusion)
     h.set_timing(True)
     st = h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
     torch.cuda.synchronize()
@@ -149,7 +150,8 @@ def vcycle_roofline_4096(peaks, iters=6, tile_sweeps=2):
     h.close()
     del outs, en, ec, rho
     torch.cuda.empty_cache()
-    return {"kernel": f"k_rbgs_tile_cs<{tile_sweeps},64,32> level 0 ({tile_sweeps} fused RBGS sweep(s) per launch), 4096x4096 mixed",
+    kname = (f"k_rbgs_stream<{tile_sweeps},2>" if tile_fusion >= 2 else f"k_rbgs_tile_cs<{tile_sweeps},64,32>")
+    return {"kernel": f"{kname} level 0 ({tile_sweeps} fused RBGS sweep(s) per launch), 4096x4096 mixed",
             "bound": "hbm", "achieved": gbs_pre, "peak": peak, "unit": "GB/s", "frac": gbs_pre / peak,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6400 GB/s",
             "bytes_per_launch": bytes_pre, "launch_ms": pre_ms,
@@ -245,7 +247,8 @@ def profile_solve(args):
     en, ec, rho = dev(f.eta_n), dev(f.eta_c), dev(f.rho)
     outs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
     prec = P.PREC_MIXED if args.prec == "mixed" else P.PREC_FP64
-    h = P.Stokes(n, n, prec=prec, max_iter=args.max_iter, restart_m=args.restart)
+    h = P.Stokes(n, n, prec=prec, max_iter=args.max_iter, restart_m=args.restart, tile_fusion=args.tile_fusion,
+                 tile_sweeps=args.tile_sweeps)
     st = h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
     torch.cuda.synchronize()
     print(json.dumps({"profile_solve": n, "prec": args.prec, "iters": st.iters, "status": st.status,
@@ -291,6 +294,8 @@ def main():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--max-iter", type=int, default=3000)
     ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--tile-fusion", type=int, default=2, help="pyro_opts.tile_fusion of the --profile solve")
+    ap.add_argument("--tile-sweeps", type=int, default=2, help="pyro_opts.tile_sweeps of the --profile solve")
     args = ap.parse_args()
     rank, world, local = env_rank()
     import torch

@@ -79,7 +79,7 @@ typedef struct {
   int nu1, nu2;          /* pre/post RBGS sweeps per level [2, 2] */
   double omega_v;        /* RBGS damping (eq. sor_update) [1.0] */
   double alpha_p;        /* Uzawa pressure relaxation alpha (eq. uzawa_iteration) [1.0] */
-  int restart_m;         /* FGMRES restart length, 1..64 [30] */
+  int restart_m;         /* FGMRES restart length, 1..256 [30] */
   int max_iter;          /* total FGMRES iterations before PYRO_W_NOT_CONVERGED [500] */
   int prec;              /* pyro_precision [PYRO_PREC_MIXED] */
   int coarsest_min;      /* halve while the short side stays >= this many cells [2] */
@@ -94,11 +94,17 @@ typedef struct {
                             thread-block-cluster launch (8 CTAs, cluster barriers between steps);
                             <= 0 = never, every step is its own kernel [0] */
   int tile_fusion;       /* 1: smoothing sweeps (with the prolongation) and residual+restriction run
-                            as shared-memory tile kernels, one launch each per level visit (all FP32
-                            levels; FP64 levels up to 65536 cells); 0: one kernel per colour and
-                            step [1] */
+                            as shared-memory tile kernels, one launch each per level visit (FP32
+                            levels; FP64 levels see tile_fusion64); 2: as 1, but FP32 levels large
+                            enough for it (row chunks of >= 96 rows at two CTAs per SM) smooth with
+                            the row-streaming wavefront kernel; 3: as 2 on every FP32 level (for
+                            tests and tuning); 0: one kernel per colour and step [1] */
   int tile_sweeps;       /* FP32 tile kernels: sweeps fused per launch, 1 (halo 4, one HBM pass per
                             sweep) or 2 (halo 8, one pass per two sweeps) [2] */
+  int tile_fusion64;     /* 1: FP64 levels of up to 65536 cells also smooth and restrict with the
+                            tile kernels; 0: every FP64 level runs one kernel per colour and step on
+                            precomputed viscosity coefficients (B300's FP64 rate per SM is so low
+                            that one CTA per tile becomes the critical path) [0] */
 } pyro_opts;
 
 typedef struct {

@@ -154,5 +154,7 @@ enum : int { FLAG_NONFINITE = 1, FLAG_BREAKDOWN = 2 };
 
 constexpr int kReduceBlocks = 592;  // 4 x 148 SMs: fixed so reductions are deterministic
 constexpr int kThreads = 256;
+constexpr int kMaxRestart = 256;               // longest FGMRES cycle (Krylov basis length)
+constexpr int kHcolStride = kMaxRestart + 2;   // stride of the Hessenberg columns on the device
 
 }  // namespace pyro

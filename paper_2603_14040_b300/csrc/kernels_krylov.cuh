@@ -231,7 +231,7 @@ __global__ void k_multiaxpy(double* __restrict__ w, const double* __restrict__ V
                             const int* __restrict__ d_j, const double* __restrict__ h, size_t n,
                             const double* __restrict__ W, double* __restrict__ part, const int* __restrict__ d_run) {
   __shared__ double sh[32];
-  __shared__ double hs[128];
+  __shared__ double hs[kMaxRestart + 2];
   if (d_run && *d_run == 0) return;
   const int nvec = *d_j + 1;
   for (int k = threadIdx.x; k < nvec; k += blockDim.x) hs[k] = h[k];
@@ -264,7 +264,7 @@ __global__ void k_arnoldi_finish(const int* __restrict__ d_j, const double* __re
   if (threadIdx.x != 0) return;
   if (!second) s = *nrm2_after1;
   const int j = *d_j;
-  double* col = hcol + (size_t)j * 66;
+  double* col = hcol + (size_t)j * kHcolStride;
   for (int k = 0; k <= j; ++k) col[k] = h1[k] + (second ? h2[k] : 0.0);
   const double nrm = sqrt(s);
   col[j + 1] = nrm;
@@ -292,7 +292,7 @@ __global__ void k_scale(double* __restrict__ dst, const double* __restrict__ src
 template <typename TZ>
 __global__ void k_update_x(double* __restrict__ x, const TZ* __restrict__ Z, size_t stride, int k,
                            const double* __restrict__ y, size_t n) {
-  __shared__ double ys[128];
+  __shared__ double ys[kMaxRestart + 2];
   for (int l = threadIdx.x; l < k; l += blockDim.x) ys[l] = y[l];
   __syncthreads();
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {

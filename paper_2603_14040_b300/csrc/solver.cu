@@ -16,14 +16,14 @@
 #include "kernels_krylov.cuh"
 #include "kernels_sub.cuh"
 #include "kernels_tile.cuh"
+#include "kernels_stream.cuh"
 
 using namespace pyro;
 
 namespace {
 
-constexpr int kMaxRestart = 64;
 constexpr int kMaxCoarse = 1024;
-constexpr int kHcolStride = 66;
+constexpr int kStreamMinRows = 96;  // shortest row chunk worth a streaming pass
 
 struct CudaError {
   cudaError_t e;
@@ -113,6 +113,7 @@ struct MG {
   int kcycle = 0;  // levels l < kcycle get their coarse correction from two flexible-CG steps
   int ls = -1;     // first level run by the cluster sub-cycle kernel (-1: none)
   bool tiles = true;                        // tile-fused smoothing / residual+restriction
+  int stream = 0;                           // FP32 row-streaming sweeps: 0 never, 1 large levels, 2 all
   int tile_sweeps = 2;                      // FP32: sweeps fused per tile launch
   static constexpr long long kFuse64Cells = 65536;
   SubArgs<T> sub{};
@@ -241,6 +242,32 @@ struct MG {
       count(1);
       return;
     }
+    if constexpr (sizeof(T) == 4) {
+      if (stream_level(l)) {
+        if (C) {
+          k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C->gt, L.X(), L.Y(), C->X(), C->Y());
+          count(1);
+        }
+        while (nsweeps > 0) {
+          float* ox = L.cur ? L.vx : L.vx2;
+          float* oy = L.cur ? L.vy : L.vy2;
+          if (nsweeps >= 2 && tile_sweeps >= 2) {
+            const dim3 gr = stream_grid<2>(L);
+            k_rbgs_stream<2, 2><<<gr, StreamCfg<2, 2>::THREADS, StreamCfg<2, 2>::smem_bytes(), s>>>(
+                L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, stream_rows(L, gr.y));
+            nsweeps -= 2;
+          } else {
+            const dim3 gr = stream_grid<1>(L);
+            k_rbgs_stream<1, 2><<<gr, StreamCfg<1, 2>::THREADS, StreamCfg<1, 2>::smem_bytes(), s>>>(
+                L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, stream_rows(L, gr.y));
+            nsweeps -= 1;
+          }
+          count(1);
+          L.cur ^= 1;
+        }
+        return;
+      }
+    }
     while (nsweeps > 0) {
       if constexpr (sizeof(T) == 4) {
         constexpr int TX = 64, TY = 32;
@@ -271,6 +298,33 @@ struct MG {
     }
   }
 
+  // streaming-sweep launch shape: strips of W columns, row chunks sized so the grid fills the
+  // GPU's SMs (two CTAs each) in one wave
+  static int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+      int d = 0;
+      CK(cudaGetDevice(&d));
+      CK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d));
+    }
+    return n;
+  }
+  template <int NS>
+  static dim3 stream_grid(const Level<T>& L) {
+    const int strips = (L.g.nx + 2 + StreamCfg<NS, 2>::W - 1) / StreamCfg<NS, 2>::W;
+    const int chunks = std::max(1, 2 * sm_count() / strips);
+    const int H = (L.g.ny + 2 + chunks - 1) / chunks;
+    return dim3(strips, (L.g.ny + 2 + H - 1) / H);
+  }
+  static int stream_rows(const Level<T>& L, unsigned chunks) { return (L.g.ny + 2 + (int)chunks - 1) / (int)chunks; }
+  bool stream_level(int l) const {
+    const Level<T>& L = lv[l];
+    if (stream == 0 || L.g.nx % 2 != 0) return false;
+    if (stream == 2) return true;
+    const dim3 gr = stream_grid<2>(L);
+    return stream_rows(L, gr.y) >= kStreamMinRows && (int)(gr.x * gr.y) >= sm_count();
+  }
+
   void resrestrict_tiles(int l, cudaStream_t s) {
     Level<T>& L = lv[l];
     Level<T>& C = lv[l + 1];
@@ -291,6 +345,10 @@ struct MG {
                               (int)SweepTileCS<1, 64, 32>::smem_bytes()));
       CK(cudaFuncSetAttribute(k_resrestrict_tile<T, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)ResTile<T, 32, 16>::smem_bytes()));
+      CK(cudaFuncSetAttribute(k_rbgs_stream<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)StreamCfg<2, 2>::smem_bytes()));
+      CK(cudaFuncSetAttribute(k_rbgs_stream<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)StreamCfg<1, 2>::smem_bytes()));
     } else {
       CK(cudaFuncSetAttribute(k_rbgs_tile<T, 1, 64, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)SweepTile<T, 1, 64, 16>::smem_bytes(true)));
@@ -787,6 +845,7 @@ void pyro_default_opts(pyro_opts* o) {
   o->cluster_cells = 0;
   o->tile_fusion = 1;
   o->tile_sweeps = 2;
+  o->tile_fusion64 = 0;
 }
 
 const char* pyro_version(void) { return "pyro-b300 0.1 (sm_103a)"; }
@@ -870,6 +929,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->mgf.nu1 = o.nu1; h->mgf.nu2 = o.nu2; h->mgf.omega = (float)o.omega_v; h->mgf.eta_mode = o.eta_coarsen;
       h->mgf.kcycle = o.kcycle;
       h->mgf.tiles = o.tile_fusion != 0;
+      h->mgf.stream = o.tile_fusion >= 2 ? o.tile_fusion - 1 : 0;
       h->mgf.tile_sweeps = o.tile_sweeps;
       if (h->mgf.tiles) MG<float>::enable_tiles();
       CK(cudaDeviceSynchronize());
@@ -878,7 +938,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
     } else {
       h->mgd.nu1 = o.nu1; h->mgd.nu2 = o.nu2; h->mgd.omega = o.omega_v; h->mgd.eta_mode = o.eta_coarsen;
       h->mgd.kcycle = o.kcycle;
-      h->mgd.tiles = o.tile_fusion != 0;
+      h->mgd.tiles = o.tile_fusion64 != 0;
       if (h->mgd.tiles) MG<double>::enable_tiles();
       h->mgd.alloc(A, h->g, L, true);
       h->mgd.lv[0].en = h->en;

@@ -30,7 +30,7 @@ class PyroOpts(ctypes.Structure):
                 ("prec", ctypes.c_int), ("coarsest_min", ctypes.c_int), ("eta_coarsen", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("use_graphs", ctypes.c_int), ("timeout_s", ctypes.c_double),
                 ("kcycle", ctypes.c_int), ("cluster_cells", ctypes.c_int), ("tile_fusion", ctypes.c_int),
-                ("tile_sweeps", ctypes.c_int)]
+                ("tile_sweeps", ctypes.c_int), ("tile_fusion64", ctypes.c_int)]
 
 
 class PyroStats(ctypes.Structure):

@@ -1,0 +1,137 @@
+"""Parity at the full sizes of the benchmark workloads, in the launch configuration bench.py times.
+
+The oracle's direct solve does not reach these sizes, so the checks are the ones that hold at any
+size, computed by the oracle from the GPU's answer:
+  * 1024 x 1024 random viscosity (FP64 and mixed): the oracle assembles the whole system and
+    recomputes the relative energy residual of the GPU solution (Sec. "Global Relative Energy
+    Residual"), which must meet the tolerance and agree with the value the library reports; zero
+    mean pressure, zero normal velocity on the walls; FP64 and mixed solutions agree.
+  * 4096 x 4096 layered lid + inclusions (mixed): at sampled windows (corners, edges, the lid
+    interface, the interior) every row of the library's FP64 operator applied to its iterate
+    equals the oracle's own row, assembled on the window. The
+    Uzawa/multigrid preconditioner does not take this field (viscosity contrast 1e9 between the
+    lid and the weakest inclusions) to 1e-10 in a practical number of iterations (3000 FGMRES(30)
+    iterations leave about 1e-5; even an exact velocity solve leaves 3e-6 after 400 iterations at
+    64 x 64), so the test runs 600 iterations and checks the iterate it gets.
+  * 512 x 512 adjoint member: dJ/dlog(eta) from the adjoint equals central finite differences of
+    J along random directions (each side a full solve).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import stokes as S
+from synth import grf_config, layered_config, adjoint_member
+from gpu_util import dev, host, zeros, rel
+from window_residual import window_residual, global_positions
+
+import paper_2603_14040_b300 as P
+from paper_2603_14040_b300.autograd import stokes_solve, surface_misfit, node_from_cell
+
+G = (0.0, 1.0)
+
+
+def _solve(f, n, tol, **opts):
+    h = P.Stokes(n, n, **opts)
+    out = [zeros(n, n) for _ in range(3)]
+    st = h.solve(dev(f.eta_n), dev(f.eta_c), dev(f.rho), G, tol, *out)
+    torch.cuda.synchronize()
+    h.close()
+    return out, st
+
+
+def test_random_viscosity_1024_fp64_and_mixed_meet_tolerance_by_oracle():
+    n, tol = 1024, 1e-10
+    f = grf_config(n, n, seed=2)
+    g = S.Grid(n, n)
+    sysm = S.assemble(g, f.eta_n, f.eta_c, f.rho, G)
+    sols = {}
+    for prec in (P.PREC_FP64, P.PREC_MIXED):
+        out, st = _solve(f, n, tol, prec=prec, max_iter=3000)
+        assert st.status == P.PYRO_OK, st.as_dict()
+        vx, vy, p = (host(a) for a in out)
+        x = S.fields_to_vector(g, vx, vy, p)
+        e_or, l2_or = S.energy_residual(sysm, f.eta_c, x)
+        assert e_or <= 1.01 * tol, (prec, e_or, st.as_dict())
+        assert abs(e_or - st.rel_energy_res) <= 1e-3 * e_or
+        assert abs(l2_or - st.rel_l2_res) <= 1e-3 * l2_or + 1e-16
+        assert abs(p[1:n + 1, 1:n + 1].mean()) <= 1e-12 * np.abs(p).max()
+        assert np.all(vx[:, 0] == 0) and np.all(vx[:, n] == 0)
+        assert np.all(vy[0, :] == 0) and np.all(vy[n, :] == 0)
+        sols[prec] = x
+    a, b = sols[P.PREC_FP64], sols[P.PREC_MIXED]
+    assert rel(b[:g.n_v], a[:g.n_v]) <= 1e-8 and rel(b[g.n_v:], a[g.n_v:]) <= 1e-8
+
+
+def test_layered_4096_mixed_operator_rows_match_oracle_windows():
+    n, tol = 4096, 1e-10
+    f = layered_config(n, n, seed=3)
+    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=600)
+    out = [zeros(n, n) for _ in range(3)]
+    en, ec, rho = dev(f.eta_n), dev(f.eta_c), dev(f.rho)
+    st = h.solve(en, ec, rho, G, tol, *out)
+    assert st.status in (P.PYRO_OK, P.PYRO_W_NOT_CONVERGED), st.as_dict()
+    assert 0.0 < st.rel_energy_res < 1e-2, st.as_dict()
+    r = [zeros(n, n) for _ in range(3)]
+    h.apply(en, ec, *out, *r)
+    torch.cuda.synchronize()
+    h.close()
+    vx, vy, p = (host(a) for a in out)
+    R = [host(a) for a in r]
+    lid = int(0.1 * n)
+    blocks = [((1, 12), (1, 12)), ((n - 11, n), (n - 11, n)), ((1, 10), (2000, 2020)),
+              ((lid - 6, lid + 6), (1000, 1016)), ((lid - 6, lid + 6), (n - 9, n)),
+              ((2048, 2064), (2048, 2064)), ((3000, 3010), (1, 9))]
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        i0, j0 = rng.integers(1, n - 16, size=2)
+        blocks.append(((int(i0), int(i0) + 15), (int(j0), int(j0) + 15)))
+    checked = 0
+    for rows, cols in blocks:
+        wx, wy, wp, sx, sy, sp, lo = window_residual(n, n, 1.0, 1.0, S.BC(), f.eta_n, f.eta_c, f.rho, G,
+                                                     vx, vy, p, rows, cols, product=True)
+        for win, sc, ref in ((wx, sx, R[0]), (wy, sy, R[1]), (wp, sp, R[2])):
+            gi, gj, li, lj = global_positions(win, lo)
+            err = np.abs(win[li, lj] - ref[gi, gj])
+            assert np.all(err <= 1e-12 * sc[li, lj] + 1e-300), (rows, cols, err.max())
+            checked += len(gi)
+    assert checked > 2000
+
+
+def test_adjoint_512_directional_derivatives_match_central_differences():
+    n = 512
+    base, pert = adjoint_member(0, n, n)
+    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=3000)
+    rho = dev(base.rho)
+    obs_out = [zeros(n, n) for _ in range(3)]
+    st = h.solve(dev(pert.eta_n), dev(pert.eta_c), rho, G, 1e-12, *obs_out)
+    assert st.status == P.PYRO_OK
+    obs = obs_out[0][1, :].clone()
+    log_ec = dev(np.log(np.where(base.eta_c > 0, base.eta_c, 1.0))).requires_grad_(True)
+
+    def J_of(lec):
+        ec = torch.zeros_like(lec)
+        ec[1:n + 1, 1:n + 1] = torch.exp(lec[1:n + 1, 1:n + 1])
+        en = node_from_cell(ec)
+        vx, vy, p = stokes_solve(en, ec, rho, h, G, 1e-12)
+        return surface_misfit(vx, obs)
+
+    J = J_of(log_ec)
+    J.backward()
+    grad = log_ec.grad.detach().clone()
+    assert torch.isfinite(grad).all()
+    rng = np.random.default_rng(11)
+    eps = 1e-4
+    for k in range(2):
+        d = np.zeros((n + 2, n + 2))
+        d[1:n + 1, 1:n + 1] = rng.standard_normal((n, n))
+        dd = dev(d)
+        with torch.no_grad():
+            jp = J_of(log_ec.detach() + eps * dd).item()
+            jm = J_of(log_ec.detach() - eps * dd).item()
+        fd = (jp - jm) / (2 * eps)
+        an = float((grad * dd).sum())
+        assert abs(fd - an) <= 1e-4 * abs(an) + 1e-14, (k, fd, an)
+    h.close()
