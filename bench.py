@@ -115,7 +115,7 @@ def oracle_baseline(seconds_budget=20.0, sample_n=128):
             "sample_seconds_per_solve": dt}
 
 
-def vcycle_roofline_4096(peaks, iters=6, tile_sweeps=2, tile_fusion=2):
+def vcycle_roofline_4096(peaks, iters=6, tile_sweeps=2, tile_fusion=1):
     """Level-0 FP32 V-cycle kernels at 4096^2 (every level-0 array is 67 MB, far above L2): the
     two-sweep RBGS pass (row-streaming kernel with tile_fusion=2, shared-memory tiles with 1)
     moves 32 B/cell (reads vx, vy, fx, fy, eta_n, eta_c, writes vx, vy) per launch; achieved =
@@ -159,7 +159,7 @@ def vcycle_roofline_4096(peaks, iters=6, tile_sweeps=2, tile_fusion=2):
             "phase_ms_per_iter": {k: v / it for k, v in ph.items()}, "iters_timed": it}
 
 
-def serving_sample(n_req=48, slots=4, max_iter=600, seed=4):
+def serving_sample(n_req=48, slots=4, max_iter=3000, restart_m=200, seed=4):
     """Continuous batching on a bounded sample of the serving workload: requests with n in
     {128, 256, 512}, aspect in {1, 2, 4}, 16 inclusions of contrast 10^U[2,6], tol 1e-8, Poisson
     arrivals at 0.8 x the measured single-slot service rate."""
@@ -172,7 +172,7 @@ def serving_sample(n_req=48, slots=4, max_iter=600, seed=4):
         f, C = serving_request(k, base_seed=seed, sizes=(128, 256, 512))
         reqs.append((Request(rid=k, nx=f.nx, ny=f.ny, Lx=f.Lx, Ly=f.Ly, eta_n=dev(f.eta_n), eta_c=dev(f.eta_c),
                              rho=dev(f.rho), g=(0.0, 1.0), tol=1e-8), C))
-    be = PyroBackend(opts_kw={"max_iter": max_iter, "prec": 1})
+    be = PyroBackend(opts_kw={"max_iter": max_iter, "prec": 1, "restart_m": restart_m})
     # service rate from a sequential pass over the first requests (also warms the handle pool)
     srv = SolveServer(be, max_slots=1)
     t0 = time.perf_counter()
@@ -382,12 +382,14 @@ def main():
     sweep_ms = (phases["l0_pre_smooth"] + phases["l0_post_smooth"]) / sweeps
     cells = n * n
     bytes_per_sweep = 8 * 8 * cells
-    flops_per_sweep = 2 * 40 * cells  # ~40 FP64 flops per velocity point (FMA = 2), vx and vy
+    # coefficient form per velocity point: 6 differences, 6 products, 5 sums, update 4 (21 flop)
+    flops_per_sweep = 2 * 21 * cells
     achieved_flops = flops_per_sweep / (sweep_ms / 1e3) / 1e12
-    fp64_peak = 1.25  # TFLOP/s: 148 SMs x 4 FP64 FMA/clk x 2 x ~2.03 GHz (nominal); probe measured 1.13
+    fp64_peak = 1.25  # TFLOP/s nominal B300 FP64 (about 2 FMA per clock per SM at 2.03 GHz); a probe measured 1.13
     roof = {"kernel": "k_rbgs<double> finest level (one sweep = 4 launches)", "bound": "alu",
             "achieved": achieved_flops, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved_flops / fp64_peak,
-            "traffic": None, "peak_source": "derived FP64 rate (148 SMs x 4 DFMA/clk x 2 flop x 2.03 GHz)",
+            "traffic": None, "peak_source": "nominal B300 FP64 rate 1.25 TFLOP/s (148 SMs x ~2.08 FMA/clk x 2 flop x 2.03 GHz); not in MEASURED_PEAKS.json",
+            "flop_per_cell_sweep": 42,
             "hbm_equiv_GBps": bytes_per_sweep / (sweep_ms / 1e3) / 1e9, "hbm_peak_measured": peaks.get("hbm_gbs"),
             "sweep_ms": sweep_ms, "phase_ms_per_iter": {k: v / max(counts["iterations"], 1) for k, v in phases.items()}}
 
@@ -424,6 +426,9 @@ def main():
                                    "p99_ms": float(np.percentile(ms, 99))}
     if rank == 0 and not args.no_extras:
         line["vcycle_roofline"] = vcycle_roofline_4096(peaks)
+        one = vcycle_roofline_4096(peaks, tile_sweeps=1)
+        line["vcycle_roofline"]["one_sweep_per_launch"] = {k: one[k] for k in ("kernel", "achieved", "frac",
+                                                                                "launch_ms", "phase_ms_per_iter")}
         line["serving"] = serving_sample()
         line["adjoint"] = adjoint_sample()
     if rank == 0 and not args.no_cpu_baseline:

@@ -82,7 +82,7 @@ typedef struct {
   int restart_m;         /* FGMRES restart length, 1..256 [30] */
   int max_iter;          /* total FGMRES iterations before PYRO_W_NOT_CONVERGED [500] */
   int prec;              /* pyro_precision [PYRO_PREC_MIXED] */
-  int coarsest_min;      /* halve while the short side stays >= this many cells [2] */
+  int coarsest_min;      /* halve while the short side stays >= this many cells [4] */
   int eta_coarsen;       /* pyro_eta_coarsening [PYRO_ETA_ARITH] */
   int warm_start;        /* 1: vx, vy, p passed to solve hold the initial guess [0] */
   int use_graphs;        /* 1: capture the FGMRES iteration into a CUDA graph [1] */

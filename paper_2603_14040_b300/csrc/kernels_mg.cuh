@@ -473,10 +473,14 @@ __global__ void k_coarse_invert(double* __restrict__ A, int n, int* __restrict__
   }
 }
 
-// x = L^-1 f = -(-L)^-1 f on the coarsest level (FP64 whatever T is).
+// x = L^-1 f = -(-L)^-1 f on the coarsest level (FP64 whatever T is). One warp per row of the
+// inverse (coalesced row reads, fixed-order shuffle reduction), kCoarseRows rows per CTA, so the
+// matvec spreads over ceil(n / kCoarseRows) SMs (one SM's FP64 rate would make it the critical path).
+constexpr int kCoarseRows = 8;
 template <typename T>
-__global__ void k_coarse_solve(Geom g, const double* __restrict__ Ainv, int n, const T* __restrict__ fx,
-                               const T* __restrict__ fy, T* __restrict__ vx, T* __restrict__ vy) {
+__global__ void __launch_bounds__(32 * kCoarseRows)
+    k_coarse_solve(Geom g, const double* __restrict__ Ainv, int n, const T* __restrict__ fx,
+                   const T* __restrict__ fy, T* __restrict__ vx, T* __restrict__ vy) {
   extern __shared__ double fv[];
   const int nx = g.nx, ny = g.ny, ld = g.ld, nvx = ny * (nx - 1);
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
@@ -484,13 +488,16 @@ __global__ void k_coarse_solve(Geom g, const double* __restrict__ Ainv, int n, c
     else { const int kk = k - nvx; const int i = kk / nx + 1, j = kk % nx + 1; fv[k] = (double)fy[(size_t)i * ld + j]; }
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    double s = 0.0;
-    const double* a = Ainv + (size_t)k * n;
-    for (int l = 0; l < n; ++l) s += a[l] * fv[l];
-    if (k < nvx) { const int i = k / (nx - 1) + 1, j = k % (nx - 1) + 1; vx[(size_t)i * ld + j] = (T)(-s); }
-    else { const int kk = k - nvx; const int i = kk / nx + 1, j = kk % nx + 1; vy[(size_t)i * ld + j] = (T)(-s); }
-  }
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * kCoarseRows + (threadIdx.x >> 5);
+  if (k >= n) return;
+  const double* a = Ainv + (size_t)k * n;
+  double s = 0.0;
+  for (int l = lane; l < n; l += 32) s += a[l] * fv[l];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane != 0) return;
+  if (k < nvx) { const int i = k / (nx - 1) + 1, j = k % (nx - 1) + 1; vx[(size_t)i * ld + j] = (T)(-s); }
+  else { const int kk = k - nvx; const int i = kk / nx + 1, j = kk % nx + 1; vy[(size_t)i * ld + j] = (T)(-s); }
 }
 
 // ---- explicit instantiations ---------------------------------------------------------------

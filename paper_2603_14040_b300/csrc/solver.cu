@@ -377,7 +377,8 @@ struct MG {
       return;
     }
     if (l == (int)lv.size() - 1) {
-      k_coarse_solve<T><<<1, 256, nc * sizeof(double), s>>>(L.g, Ainv, nc, L.fx, L.fy, L.vx, L.vy);
+      k_coarse_solve<T><<<(nc + kCoarseRows - 1) / kCoarseRows, 32 * kCoarseRows, nc * sizeof(double), s>>>(
+          L.g, Ainv, nc, L.fx, L.fy, L.vx, L.vy);
       count(1);
       return;
     }
@@ -836,7 +837,7 @@ void pyro_default_opts(pyro_opts* o) {
   o->restart_m = 30;
   o->max_iter = 500;
   o->prec = PYRO_PREC_MIXED;
-  o->coarsest_min = 2;
+  o->coarsest_min = 4;
   o->eta_coarsen = PYRO_ETA_ARITH;
   o->warm_start = 0;
   o->use_graphs = 1;

@@ -32,7 +32,7 @@ def test_host_logic_without_gpu():
     assert P.lib().pyro_version().startswith(b"pyro-b300")
     assert P.lib().pyro_strerror(-4) == b"non-finite input or iterate"
     o = P.default_opts()
-    assert (o.nu1, o.nu2, o.restart_m, o.prec, o.coarsest_min) == (2, 2, 30, P.PREC_MIXED, 2)
+    assert (o.nu1, o.nu2, o.restart_m, o.prec, o.coarsest_min) == (2, 2, 30, P.PREC_MIXED, 4)
     # footprint: odd / too coarse-unfriendly sizes are rejected, valid ones scale with the grid
     assert P.footprint(100, 100) == 0 and P.footprint(3, 8) == 0
     f1, f2 = P.footprint(512, 512), P.footprint(1024, 1024)
