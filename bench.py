@@ -159,6 +159,36 @@ def vcycle_roofline_4096(peaks, iters=6, tile_sweeps=2, tile_fusion=1):
             "phase_ms_per_iter": {k: v / it for k, v in ph.items()}, "iters_timed": it}
 
 
+def accelerator_sample(f, n, steps=3):
+    """The paper's own outer accelerators on the bench workload (same preconditioner, same 1e-10
+    energy-residual stop): flexible GCR(30) and Anderson AA(m, beta), FP64 and mixed precision."""
+    import torch
+    import paper_2603_14040_b300 as P
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    en, ec, rho = dev(f.eta_n), dev(f.eta_c), dev(f.rho)
+    outs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
+    res = {}
+    for name, kw in [("gcr30", dict(accel=P.ACCEL_GCR, restart_m=30)),
+                     ("anderson10_beta1", dict(accel=P.ACCEL_ANDERSON, restart_m=10, aa_beta=1.0)),
+                     ("anderson15_beta0.8", dict(accel=P.ACCEL_ANDERSON, restart_m=15, aa_beta=0.8))]:
+        for prec, pn in ((P.PREC_FP64, "fp64"), (P.PREC_MIXED, "mixed")):
+            h = P.Stokes(n, n, prec=prec, max_iter=3000, **kw)
+            h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
+            ts = []
+            for _ in range(steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                st = h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            h.close()
+            res[f"{name}_{pn}"] = {"solves_per_s": 1e3 / float(np.median(ts)), "ms": float(np.median(ts)),
+                                   "iters": st.iters, "status": st.status, "rel_energy_res": st.rel_energy_res}
+    return res
+
+
 def serving_sample(n_req=48, slots=4, max_iter=3000, restart_m=200, seed=4):
     """Continuous batching on a bounded sample of the serving workload: requests with n in
     {128, 256, 512}, aspect in {1, 2, 4}, 16 inclusions of contrast 10^U[2,6], tol 1e-8, Poisson
@@ -429,6 +459,7 @@ def main():
         one = vcycle_roofline_4096(peaks, tile_sweeps=1)
         line["vcycle_roofline"]["one_sweep_per_launch"] = {k: one[k] for k in ("kernel", "achieved", "frac",
                                                                                 "launch_ms", "phase_ms_per_iter")}
+        line["accelerators"] = accelerator_sample(f, n)
         line["serving"] = serving_sample()
         line["adjoint"] = adjoint_sample()
     if rank == 0 and not args.no_cpu_baseline:

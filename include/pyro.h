@@ -72,6 +72,18 @@ typedef struct {
 } pyro_bc;
 
 typedef enum { PYRO_PREC_FP64 = 0, PYRO_PREC_MIXED = 1 } pyro_precision;
+
+/* Outer accelerator around the Uzawa/multigrid preconditioner M^-1 (every one stops on the
+ * relative energy residual and recomputes the true FP64 residual before it stops):
+ *   FGMRES   restarted flexible GMRES(m) in the energy inner product (Sec. "Comparison with
+ *            FGMRES"; Arnoldi by classical Gram-Schmidt with one re-orthogonalisation);
+ *   GCR      restarted flexible GCR(m) (Sec. "Generalized Conjugate Residual Method", Algorithm
+ *            gcr) in the energy inner product; the paper's modified Gram-Schmidt is done as
+ *            classical Gram-Schmidt with one re-orthogonalisation (equal in exact arithmetic);
+ *   ANDERSON Anderson acceleration AA(m, aa_beta) of G(x) = x + M^-1 (b - A x) (Sec. "Anderson
+ *            Acceleration", Algorithm anderson), least squares in the 2-norm, depth m =
+ *            restart_m, x^1 = G(x^0). */
+typedef enum { PYRO_ACCEL_FGMRES = 0, PYRO_ACCEL_GCR = 1, PYRO_ACCEL_ANDERSON = 2 } pyro_accel;
 typedef enum { PYRO_ETA_ARITH = 0, PYRO_ETA_GEOM = 1 } pyro_eta_coarsening;
 
 /* Solver options. pyro_default_opts() fills the defaults given in brackets. */
@@ -79,7 +91,7 @@ typedef struct {
   int nu1, nu2;          /* pre/post RBGS sweeps per level [2, 2] */
   double omega_v;        /* RBGS damping (eq. sor_update) [1.0] */
   double alpha_p;        /* Uzawa pressure relaxation alpha (eq. uzawa_iteration) [1.0] */
-  int restart_m;         /* FGMRES restart length, 1..256 [30] */
+  int restart_m;         /* FGMRES / GCR restart length, Anderson depth; 1..256 [30] */
   int max_iter;          /* total FGMRES iterations before PYRO_W_NOT_CONVERGED [500] */
   int prec;              /* pyro_precision [PYRO_PREC_MIXED] */
   int coarsest_min;      /* halve while the short side stays >= this many cells [4] */
@@ -105,6 +117,8 @@ typedef struct {
                             tile kernels; 0: every FP64 level runs one kernel per colour and step on
                             precomputed viscosity coefficients (B300's FP64 rate per SM is so low
                             that one CTA per tile becomes the critical path) [0] */
+  int accel;             /* pyro_accel: outer accelerator [PYRO_ACCEL_FGMRES] */
+  double aa_beta;        /* Anderson mixing beta in (0, 1] (the paper suggests 0.5-0.8) [1.0] */
 } pyro_opts;
 
 typedef struct {

@@ -184,10 +184,11 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
 // nvec = *d_j + 1 (or nfix when d_j is null). blockIdx.y selects the group of 8 vectors.
 __global__ void k_multidot(const double* __restrict__ V, size_t stride, const int* __restrict__ d_j, int nfix,
                            const double* __restrict__ w, const double* __restrict__ W, size_t n,
-                           double* __restrict__ partial, const int* __restrict__ d_run, double* __restrict__ part_ww) {
+                           double* __restrict__ partial, const int* __restrict__ d_run, double* __restrict__ part_ww,
+                           int off = 0) {
   __shared__ double sh[32];
   if (d_run && *d_run == 0) return;  // optional device-side switch
-  const int nvec = d_j ? (*d_j + 1) : nfix;
+  const int nvec = d_j ? (*d_j + 1 + off) : nfix;
   const int k0 = blockIdx.y * 8;
   if (k0 >= nvec) return;
   const int kn = min(8, nvec - k0);
@@ -196,7 +197,7 @@ __global__ void k_multidot(const double* __restrict__ V, size_t stride, const in
   double aww = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const double we = w[e];
-    const double t = W[e] * we;
+    const double t = W ? W[e] * we : we;
     if (ww) aww += t * we;
 #pragma unroll
     for (int q = 0; q < 8; ++q)
@@ -214,10 +215,10 @@ __global__ void k_multidot(const double* __restrict__ V, size_t stride, const in
 
 // out[k] = sum_b partial[k * nblk + b] for k < nvec (one block per k, fixed order)
 __global__ void k_reduce(const double* __restrict__ partial, int nblk, const int* __restrict__ d_j, int nfix,
-                         double* __restrict__ out, const int* __restrict__ d_run) {
+                         double* __restrict__ out, const int* __restrict__ d_run, int off = 0) {
   __shared__ double sh[32];
   if (d_run && *d_run == 0) return;
-  const int nvec = d_j ? (*d_j + 1) : nfix;
+  const int nvec = d_j ? (*d_j + 1 + off) : nfix;
   const int k = blockIdx.x;
   if (k >= nvec) return;
   double s = 0.0;
@@ -229,11 +230,12 @@ __global__ void k_reduce(const double* __restrict__ partial, int nblk, const int
 // w -= sum_{k<nvec} h[k] V_k; if part != null also per-block sum(W w^2) into part[blockIdx.x]
 __global__ void k_multiaxpy(double* __restrict__ w, const double* __restrict__ V, size_t stride,
                             const int* __restrict__ d_j, const double* __restrict__ h, size_t n,
-                            const double* __restrict__ W, double* __restrict__ part, const int* __restrict__ d_run) {
+                            const double* __restrict__ W, double* __restrict__ part, const int* __restrict__ d_run,
+                            int off = 0) {
   __shared__ double sh[32];
   __shared__ double hs[kMaxRestart + 2];
   if (d_run && *d_run == 0) return;
-  const int nvec = *d_j + 1;
+  const int nvec = *d_j + 1 + off;
   for (int k = threadIdx.x; k < nvec; k += blockDim.x) hs[k] = h[k];
   __syncthreads();
   double acc = 0.0;
@@ -320,12 +322,12 @@ __global__ void k_precond_in(size_t P, const double* __restrict__ V, size_t stri
 // (Uzawa pressure block with the sign reading); per-block partial sums of z_p for its mean.
 template <typename T, typename TZ>
 __global__ void k_precond_out(GeomT<double> g, const T* __restrict__ vx, const T* __restrict__ vy,
-                              const double* __restrict__ V, TZ* __restrict__ Z, size_t stride,
+                              const double* __restrict__ V, size_t vstride, TZ* __restrict__ Z, size_t stride,
                               const int* __restrict__ d_j, const double* __restrict__ ec, double alpha,
                               double* __restrict__ part) {
   __shared__ double sh[32];
   const size_t P = (size_t)(g.ny + 2) * g.ld;
-  const double* v = V + (size_t)(*d_j) * stride;
+  const double* v = V + (size_t)(*d_j) * vstride;
   TZ* z = Z + (size_t)(*d_j) * stride;
   const int cols = g.nx + 2;
   double acc = 0.0;
@@ -473,6 +475,85 @@ __global__ void k_rho_grad(GeomT<double> g, const double* __restrict__ lam, doub
   gr[c] = s;
 }
 
+// ---- flexible GCR(m) (Sec. "Generalized Conjugate Residual Method", Algorithm gcr) -----------------
+// After the Gram-Schmidt passes: w_j = w / nu and z_j = z / nu go to slot j of the two bases,
+// with per-block partials of <r, w_j>_W (alpha = that, since ||w_j||_W = 1).
+__global__ void k_gcr_scale(double* __restrict__ Wb, double* __restrict__ Zb, size_t stride, const int* __restrict__ d_j,
+                            const double* __restrict__ w, const double* __restrict__ zc, const double* __restrict__ inv,
+                            const double* __restrict__ r, const double* __restrict__ W, size_t n,
+                            double* __restrict__ part) {
+  __shared__ double sh[32];
+  const double a = *inv;
+  double* wd = Wb + (size_t)(*d_j) * stride;
+  double* zd = Zb + (size_t)(*d_j) * stride;
+  double acc = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const double we = w[e] * a;
+    wd[e] = we;
+    zd[e] = zc[e] * a;
+    acc += W[e] * r[e] * we;
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// x += alpha z_j, r -= alpha w_j; per-block partials of ||r||_W^2 (alpha reduced on the device)
+__global__ void k_gcr_update(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ Wb,
+                             const double* __restrict__ Zb, size_t stride, const int* __restrict__ d_j,
+                             const double* __restrict__ alpha, const double* __restrict__ W, size_t n,
+                             double* __restrict__ part) {
+  __shared__ double sh[32];
+  const double a = *alpha;
+  const double* wj = Wb + (size_t)(*d_j) * stride;
+  const double* zj = Zb + (size_t)(*d_j) * stride;
+  double acc = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    x[e] += a * zj[e];
+    const double re = r[e] - a * wj[e];
+    r[e] = re;
+    acc += W[e] * re * re;
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// ---- Anderson acceleration AA(m, beta) (Sec. "Anderson Acceleration", Algorithm anderson) -------
+// out[q] = sum_b part[2 b + q], q = 0, 1 (the energy / l2 partials of k_residual), fixed order
+__global__ void k_sum_pairs(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+  __shared__ double sh[32];
+  for (int q = 0; q < 2; ++q) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[2 * b + q];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) out[q] = s;
+    __syncthreads();
+  }
+}
+
+// history slot d_slot <- (x, z): the iterate and its fixed-point residual G(x) - x = M^-1 (b - A x)
+__global__ void k_aa_store(double* __restrict__ Xh, double* __restrict__ Zh, size_t stride, const int* __restrict__ d_slot,
+                           const double* __restrict__ x, const double* __restrict__ zc, size_t n) {
+  double* xd = Xh + (size_t)(*d_slot) * stride;
+  double* zd = Zh + (size_t)(*d_slot) * stride;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    xd[e] = x[e];
+    zd[e] = zc[e];
+  }
+}
+
+// x = sum_i a_i ((1 - beta) x_i + beta G(x_i)) = sum_i a_i (x_i + beta z_i) over the cnt stored slots
+__global__ void k_aa_combine(double* __restrict__ x, const double* __restrict__ Xh, const double* __restrict__ Zh,
+                             size_t stride, int cnt, const double* __restrict__ a, double beta, size_t n) {
+  __shared__ double as[kMaxRestart + 2];
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) as[k] = a[k];
+  __syncthreads();
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int k = 0; k < cnt; ++k) v += as[k] * (Xh[(size_t)k * stride + e] + beta * Zh[(size_t)k * stride + e]);
+    x[e] = v;
+  }
+}
+
 template __global__ void k_apply<double>(GeomT<double>, const double*, const double*, const double*, size_t,
                                          const int*, double*, Coef<double>);
 template __global__ void k_update_x<double>(double*, const double*, size_t, int, const double*, size_t);
@@ -481,9 +562,11 @@ template __global__ void k_precond_in<float>(size_t, const double*, size_t, cons
 template __global__ void k_precond_in<double>(size_t, const double*, size_t, const int*, double*, double*, double*,
                                               double*);
 template __global__ void k_precond_out<float, double>(GeomT<double>, const float*, const float*, const double*,
-                                                      double*, size_t, const int*, const double*, double, double*);
+                                                      size_t, double*, size_t, const int*, const double*, double,
+                                                      double*);
 template __global__ void k_precond_out<double, double>(GeomT<double>, const double*, const double*, const double*,
-                                                       double*, size_t, const int*, const double*, double, double*);
+                                                       size_t, double*, size_t, const int*, const double*, double,
+                                                       double*);
 template __global__ void k_sub_mean<float>(GeomT<double>, float*, size_t, const int*, const double*, int);
 template __global__ void k_sub_mean<double>(GeomT<double>, double*, size_t, const int*, const double*, int);
 

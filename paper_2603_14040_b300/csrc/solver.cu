@@ -451,6 +451,8 @@ struct pyro_stokes_s {
   double *h1 = nullptr, *h2 = nullptr, *partial = nullptr, *part2 = nullptr, *hcol = nullptr, *inv = nullptr,
          *ydev = nullptr;
   int *d_j = nullptr, *flag = nullptr;
+  double* zc = nullptr;                    // GCR / Anderson: the current preconditioned residual
+  int *d_slot = nullptr, *d_cnt = nullptr;  // Anderson: history slot of this step, pairs stored
   // pinned host scratch
   double* hbuf = nullptr;
   int* hflag = nullptr;
@@ -477,30 +479,41 @@ inline void mark(pyro_stokes_s* h, int k, cudaStream_t s) {
   if (h->timing) CK(cudaEventRecordWithFlags(h->tev[k], s, cudaEventRecordExternal));
 }
 
+// z = M^-1 v with v = in + (*d_idx) in_stride and z = out + (*d_idx) out_stride (device index), and
+// optionally w = A z.
 template <typename T, typename TZ>
-void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s) {
+void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s, const double* in, size_t in_stride, TZ* out,
+                  size_t out_stride, const int* d_idx, bool with_apply) {
   Level<T>& L0 = mg.lv[0];
   mark(h, 0, s);
-  k_precond_in<T><<<kReduceBlocks, kThreads, 0, s>>>(h->P, h->V, h->n3, h->d_j, L0.fx, L0.fy, L0.vx, L0.vy);
+  k_precond_in<T><<<kReduceBlocks, kThreads, 0, s>>>(h->P, in, in_stride, d_idx, L0.fx, L0.fy, L0.vx, L0.vy);
   mark(h, 1, s);
   mg.hooks = h->timing ? h->tev : nullptr;
   mg.nlaunch = &h->launches;
   mg.cycle(0, s);
   mg.hooks = nullptr;
-  h->launches += 4;
-  k_precond_out<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->V, (TZ*)h->Z, h->n3, h->d_j,
+  h->launches += 3;
+  k_precond_out<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), in, in_stride, out, out_stride, d_idx,
                                                            h->ec, h->o.alpha_p, h->part2);
-  k_sub_mean<TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, (TZ*)h->Z + 2 * h->P, h->n3, h->d_j, h->part2, kReduceBlocks);
-  k_apply<TZ><<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->ec, (const TZ*)h->Z, h->n3, h->d_j, h->w,
-                                                            h->okc);
+  k_sub_mean<TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, out + 2 * h->P, out_stride, d_idx, h->part2, kReduceBlocks);
+  if (with_apply) {
+    k_apply<TZ><<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->ec, (const TZ*)out, out_stride, d_idx,
+                                                              h->w, h->okc);
+    h->launches += 1;
+  }
   mark(h, 5, s);
+}
+
+void precond_any(pyro_stokes_s* h, cudaStream_t s, const double* in, size_t in_stride, double* out,
+                 size_t out_stride, const int* d_idx, bool with_apply) {
+  if (h->mixed) precond_body<float, double>(h, h->mgf, s, in, in_stride, out, out_stride, d_idx, with_apply);
+  else precond_body<double, double>(h, h->mgd, s, in, in_stride, out, out_stride, d_idx, with_apply);
 }
 
 // one Arnoldi step j (j read on the device): z_j = M^-1 v_j, w = A z_j, CGS2 against v_0..v_j,
 // v_{j+1} = w / ||w||_W, Hessenberg column j into hcol, j += 1.
-void iteration_body(pyro_stokes_s* h, cudaStream_t s) {
-  if (h->mixed) precond_body<float, double>(h, h->mgf, s);
-  else precond_body<double, double>(h, h->mgd, s);
+void fgmres_body(pyro_stokes_s* h, cudaStream_t s) {
+  precond_any(h, s, h->V, h->n3, (double*)h->Z, h->n3, h->d_j, true);
   // classical Gram-Schmidt with one re-orthogonalisation (CGS2) in the W inner product
   const dim3 gd(kReduceBlocks, (unsigned)h->dot_grid_y);
   k_multidot<<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial, nullptr, nullptr);
@@ -515,6 +528,61 @@ void iteration_body(pyro_stokes_s* h, cudaStream_t s) {
   k_inc<<<1, 1, 0, s>>>(h->d_j);
   h->launches += 9;
   mark(h, 6, s);
+}
+
+// one flexible GCR step j (Algorithm gcr; j on the device): z = M^-1 r, w = A z, CGS2 of w against
+// the normalised images w_0..w_{j-1} (V) with the same coefficients applied to z against
+// z_0..z_{j-1} (Z), normalisation, then x += alpha z_j, r -= alpha w_j with alpha = <r, w_j>_W
+// (the W inner product: the method minimises the energy residual, as FGMRES does here).
+void gcr_body(pyro_stokes_s* h, cudaStream_t s) {
+  precond_any(h, s, h->r, 0, h->zc, 0, h->d_j, true);
+  const dim3 gd(kReduceBlocks, (unsigned)h->dot_grid_y);
+  double* Zb = (double*)h->Z;
+  for (int pass = 0; pass < 2; ++pass) {
+    double* hc = pass == 0 ? h->h1 : h->h2;
+    k_multidot<<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial, nullptr, nullptr, -1);
+    k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, hc, nullptr, -1);
+    k_multiaxpy<<<kReduceBlocks, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, hc, h->n3, pass ? h->W : nullptr,
+                                                   pass ? h->part2 : nullptr, nullptr, -1);
+    k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->zc, Zb, h->n3, h->d_j, hc, h->n3, nullptr, nullptr, nullptr,
+                                                       -1);
+  }
+  // ||w||_W: the second pass left its per-block partials in part2 (also when j = 0 and no vector is
+  // subtracted); the Hessenberg column it also writes is not used by GCR
+  k_arnoldi_finish<<<1, kThreads, 0, s>>>(h->d_j, h->h1, h->h2, h->part2, kReduceBlocks, h->hcol, h->inv, h->flag,
+                                          nullptr, nullptr);
+  k_gcr_scale<<<kReduceBlocks, kThreads, 0, s>>>(h->V, Zb, h->n3, h->d_j, h->w, h->zc, h->inv, h->r, h->W, h->n3,
+                                                 h->partial);
+  k_reduce<<<1, kThreads, 0, s>>>(h->partial, kReduceBlocks, nullptr, 1, h->ydev, nullptr);
+  k_gcr_update<<<kReduceBlocks, kThreads, 0, s>>>(h->x, h->r, h->V, Zb, h->n3, h->d_j, h->ydev, h->W, h->n3,
+                                                  h->part2);
+  k_reduce<<<1, kThreads, 0, s>>>(h->part2, kReduceBlocks, nullptr, 1, h->ydev + 1, nullptr);
+  k_inc<<<1, 1, 0, s>>>(h->d_j);
+  h->launches += 15;
+  mark(h, 6, s);
+}
+
+// one Anderson step (Algorithm anderson, the fixed-point map G(x) = x + M^-1 (b - A x)):
+// r = b - A x with its energy / l2 norms, z = M^-1 r, history slot d_slot <- (x, z), and the dots
+// <z, z_i> (2-norm) with the d_cnt stored residuals; the host then solves the constrained
+// least-squares problem and combines (k_aa_combine).
+void aa_body(pyro_stokes_s* h, cudaStream_t s) {
+  k_residual<<<kReduceBlocks, kThreads, 0, s>>>(h->g64, h->en, h->ec, h->b, h->x, h->r, h->W, h->partial, h->okc);
+  k_sum_pairs<<<1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->ydev);
+  precond_any(h, s, h->r, 0, h->zc, 0, h->d_j, false);
+  k_aa_store<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, (double*)h->Z, h->n3, h->d_slot, h->x, h->zc, h->n3);
+  const dim3 gd(kReduceBlocks, (unsigned)h->dot_grid_y);
+  k_multidot<<<gd, kThreads, 0, s>>>((double*)h->Z, h->n3, h->d_cnt, 0, h->zc, nullptr, h->n3, h->partial, nullptr,
+                                     nullptr, -1);
+  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_cnt, 0, h->h1, nullptr, -1);
+  h->launches += 6;
+  mark(h, 6, s);
+}
+
+void iteration_body(pyro_stokes_s* h, cudaStream_t s) {
+  if (h->o.accel == PYRO_ACCEL_GCR) gcr_body(h, s);
+  else if (h->o.accel == PYRO_ACCEL_ANDERSON) aa_body(h, s);
+  else fgmres_body(h, s);
 }
 
 // after the iteration's sync: accumulate the phase times
@@ -783,6 +851,162 @@ int fgmres(pyro_stokes_s* h, double tol, pyro_stats* st, cudaStream_t s) {
   return status;
 }
 
+// common end of an outer solve: zero-mean pressure, final true residuals, statistics
+int finish_solve(pyro_stokes_s* h, double tol, pyro_stats* st, cudaStream_t s, int status, int total, int restarts,
+                 double nb, double rel_e, double per_it_vectors) {
+  k_psum<<<kReduceBlocks, kThreads, 0, s>>>(h->g64, h->x + 2 * h->P, h->part2);
+  k_sub_mean<double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, h->x + 2 * h->P, 0, nullptr, h->part2, kReduceBlocks);
+  h->launches += 2;
+  auto rn = residual_norms(h, h->b, h->x, h->r, s);
+  CK(cudaEventRecord(h->ev[3], s));
+  CK(cudaStreamSynchronize(s));
+  if (st) {
+    st->iters += total;
+    st->restarts += restarts;
+    st->vcycles += total;
+    st->rel_energy_res = nb > 0 ? std::sqrt(rn.first) / nb : 0.0;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]);
+    st->t_solve_ms += ms;
+    const double cells = (double)h->nx * h->ny;
+    const double tb = h->mixed ? 4.0 : 8.0;
+    const double vcycle = (h->o.nu1 + h->o.nu2) * 8.0 * tb * 4.0 / 3.0 + 10.0 * tb;
+    st->alg_bytes += cells * (vcycle + 64.0 + 24.0 * per_it_vectors) * total;
+  }
+  if (status == PYRO_OK && !(rel_e <= tol) && nb > 0) {
+    const double fin = std::sqrt(rn.first) / nb;
+    if (!(fin <= tol)) status = PYRO_W_NOT_CONVERGED;
+  }
+  if (st) {
+    const double l2b = l2_norm2(h, h->b, s);
+    st->rel_l2_res = l2b > 0 ? std::sqrt(rn.second / l2b) : 0.0;
+  }
+  return status;
+}
+
+bool out_of_time(const pyro_stokes_s* h, std::chrono::steady_clock::time_point t0) {
+  if (h->o.timeout_s <= 0) return false;
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > h->o.timeout_s;
+}
+
+// Flexible GCR(m) (Algorithm gcr) in the W inner product; every restart recomputes the true FP64
+// residual (refinement step), within a cycle the residual is updated recursively.
+int gcr(pyro_stokes_s* h, double tol, pyro_stats* st, cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  CK(cudaEventRecord(h->ev[2], s));
+  const double nb = std::sqrt(weighted_norm2(h, h->b, s));
+  int total = 0, restarts = 0, status = PYRO_OK;
+  double rel_e = 1.0;
+  if (nb == 0.0) {
+    CK(cudaMemsetAsync(h->x, 0, h->n3 * sizeof(double), s));
+    rel_e = 0.0;
+  }
+  while (nb > 0.0) {
+    auto rn = residual_norms(h, h->b, h->x, h->r, s);
+    rel_e = std::sqrt(rn.first) / nb;
+    if (!std::isfinite(rel_e)) { status = PYRO_E_NONFINITE; break; }
+    if (rel_e <= tol) break;
+    if (total >= h->o.max_iter) { status = PYRO_W_NOT_CONVERGED; break; }
+    if (out_of_time(h, t0)) { status = PYRO_E_TIMEOUT; break; }
+    CK(cudaMemsetAsync(h->d_j, 0, sizeof(int), s));
+    bool stop = false;
+    for (int j = 0; j < h->m; ++j) {
+      launch_iteration(h, s);
+      CK(cudaMemcpyAsync(h->hbuf, h->ydev, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(h->hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      collect_timing(h);
+      ++total;
+      const double est = std::sqrt(std::fabs(h->hbuf[1])) / nb;
+      if ((*h->hflag & FLAG_NONFINITE) || !std::isfinite(est)) { status = PYRO_E_NONFINITE; stop = true; break; }
+      if (est <= 0.5 * tol || total >= h->o.max_iter || out_of_time(h, t0)) break;
+    }
+    if (stop) break;
+    ++restarts;
+  }
+  return finish_solve(h, tol, st, s, status, total, restarts, nb, rel_e, 6.0 * (h->m / 4.0 + 1) + 4.0);
+}
+
+// Anderson acceleration AA(m, beta) of the Uzawa fixed-point map (Algorithm anderson). The
+// constrained least-squares problem min ||F a||_2, sum a = 1 over the newest cnt = min(m, k) + 1
+// fixed-point residuals is solved on the host from their Gram matrix: a = G^-1 1 / (1^T G^-1 1),
+// with G regularised by 1e-13 of its largest diagonal entry; the first step is x^1 = G(x^0).
+int anderson(pyro_stokes_s* h, double tol, pyro_stats* st, cudaStream_t s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  CK(cudaEventRecord(h->ev[2], s));
+  const double nb = std::sqrt(weighted_norm2(h, h->b, s));
+  const int depth = h->m;                 // AA depth m: up to m + 1 stored pairs
+  const int nslot = depth + 1;
+  std::vector<double> Gm((size_t)nslot * nslot, 0.0), a(nslot);
+  int total = 0, status = PYRO_OK;
+  double rel_e = nb > 0 ? 1.0 : 0.0;
+  if (nb == 0.0) CK(cudaMemsetAsync(h->x, 0, h->n3 * sizeof(double), s));
+  for (int k = 0; nb > 0.0; ++k) {
+    const int slot = k % nslot, cnt = std::min(k + 1, nslot);
+    int idx[2] = {slot, cnt};
+    CK(cudaMemcpyAsync(h->d_slot, &idx[0], sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->d_cnt, &idx[1], sizeof(int), cudaMemcpyHostToDevice, s));
+    launch_iteration(h, s);
+    CK(cudaMemcpyAsync(h->hbuf, h->ydev, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->hbuf + 2, h->h1, cnt * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    collect_timing(h);
+    rel_e = std::sqrt(h->hbuf[0]) / nb;       // energy residual of the current iterate x^k
+    if ((*h->hflag & FLAG_NONFINITE) || !std::isfinite(rel_e)) { status = PYRO_E_NONFINITE; break; }
+    if (rel_e <= tol) break;
+    if (total >= h->o.max_iter) { status = PYRO_W_NOT_CONVERGED; break; }
+    if (out_of_time(h, t0)) { status = PYRO_E_TIMEOUT; break; }
+    ++total;
+    for (int i = 0; i < cnt; ++i) { Gm[(size_t)slot * nslot + i] = h->hbuf[2 + i]; Gm[(size_t)i * nslot + slot] = h->hbuf[2 + i]; }
+    // solve (G + eps I) y = 1 on the cnt stored slots by Gaussian elimination with partial pivoting
+    std::vector<long double> M((size_t)cnt * (cnt + 1));
+    double dmax = 0.0;
+    for (int i = 0; i < cnt; ++i) dmax = std::max(dmax, Gm[(size_t)i * nslot + i]);
+    for (int i = 0; i < cnt; ++i) {
+      for (int j = 0; j < cnt; ++j) M[(size_t)i * (cnt + 1) + j] = Gm[(size_t)i * nslot + j];
+      M[(size_t)i * (cnt + 1) + i] += 1e-13L * dmax;
+      M[(size_t)i * (cnt + 1) + cnt] = 1.0L;
+    }
+    for (int c = 0; c < cnt; ++c) {
+      int piv = c;
+      for (int i = c + 1; i < cnt; ++i)
+        if (std::fabs((double)M[(size_t)i * (cnt + 1) + c]) > std::fabs((double)M[(size_t)piv * (cnt + 1) + c])) piv = i;
+      if (piv != c)
+        for (int j = 0; j <= cnt; ++j) std::swap(M[(size_t)c * (cnt + 1) + j], M[(size_t)piv * (cnt + 1) + j]);
+      const long double d = M[(size_t)c * (cnt + 1) + c];
+      if (d == 0.0L) continue;
+      for (int i = c + 1; i < cnt; ++i) {
+        const long double f = M[(size_t)i * (cnt + 1) + c] / d;
+        for (int j = c; j <= cnt; ++j) M[(size_t)i * (cnt + 1) + j] -= f * M[(size_t)c * (cnt + 1) + j];
+      }
+    }
+    std::vector<long double> y(cnt, 0.0L);
+    for (int i = cnt - 1; i >= 0; --i) {
+      long double t = M[(size_t)i * (cnt + 1) + cnt];
+      for (int j = i + 1; j < cnt; ++j) t -= M[(size_t)i * (cnt + 1) + j] * y[j];
+      const long double d = M[(size_t)i * (cnt + 1) + i];
+      y[i] = d != 0.0L ? t / d : 0.0L;
+    }
+    long double sy = 0.0L;
+    for (int i = 0; i < cnt; ++i) sy += y[i];
+    for (int i = 0; i < cnt; ++i) a[i] = (sy != 0.0L) ? (double)(y[i] / sy) : (i == slot ? 1.0 : 0.0);
+    std::memcpy(h->hbuf, a.data(), cnt * sizeof(double));
+    CK(cudaMemcpyAsync(h->ydev + 2, h->hbuf, cnt * sizeof(double), cudaMemcpyHostToDevice, s));
+    const double beta = k == 0 ? 1.0 : h->o.aa_beta;     // x^1 = G(x^0)
+    k_aa_combine<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->x, h->V, (double*)h->Z, h->n3, cnt, h->ydev + 2, beta,
+                                                        h->n3);
+    h->launches += 1;
+  }
+  return finish_solve(h, tol, st, s, status, total, 0, nb, rel_e, 3.0 * (h->m + 1) + 4.0);
+}
+
+int outer_solve(pyro_stokes_s* h, double tol, pyro_stats* st, cudaStream_t s) {
+  if (h->o.accel == PYRO_ACCEL_GCR) return gcr(h, tol, st, s);
+  if (h->o.accel == PYRO_ACCEL_ANDERSON) return anderson(h, tol, st, s);
+  return fgmres(h, tol, st, s);
+}
+
 void validate_opts(pyro_opts& o) {
   if (o.nu1 < 0) o.nu1 = 0;
   if (o.nu2 < 0) o.nu2 = 0;
@@ -793,6 +1017,8 @@ void validate_opts(pyro_opts& o) {
   if (o.coarsest_min < 1) o.coarsest_min = 1;
   if (o.kcycle < 0) o.kcycle = 0;
   if (o.kcycle > 16) o.kcycle = 16;
+  if (o.accel < PYRO_ACCEL_FGMRES || o.accel > PYRO_ACCEL_ANDERSON) o.accel = PYRO_ACCEL_FGMRES;
+  if (!(o.aa_beta > 0.0) || o.aa_beta > 1.0) o.aa_beta = 1.0;
 }
 
 int check_size(int nx, int ny, const pyro_opts& o) {
@@ -816,7 +1042,8 @@ size_t footprint_bytes(int nx, int ny, const pyro_opts& o, int L) {
   b += 6 * n3 * 8;                 // b, x, r, w, W, xf
   b += n3 * 8;                     // stage
   b += (m + 1) * n3 * 8;           // V
-  b += m * n3 * 8;                 // Z (preconditioned vectors; FP32-valued velocities in mixed mode)
+  b += (m + 1) * n3 * 8;           // Z (preconditioned vectors; FP32-valued velocities in mixed mode)
+  b += n3 * 8 + 16;                // GCR / Anderson current direction, Anderson slot indices
   b += mixed ? MG<float>::bytes(nx, ny, L, o.kcycle) : MG<double>::bytes(nx, ny, L, o.kcycle) - 2 * P * 8;
   b += 2 * kSubCluster * 4 * 8;
   b += 2 * (kMaxRestart + 2) * 8 + 2 * (size_t)kReduceBlocks * (kMaxRestart + 1) * 8 + 4 * kReduceBlocks * 8 +
@@ -847,6 +1074,8 @@ void pyro_default_opts(pyro_opts* o) {
   o->tile_fusion = 1;
   o->tile_sweeps = 2;
   o->tile_fusion64 = 0;
+  o->accel = PYRO_ACCEL_FGMRES;
+  o->aa_beta = 1.0;
 }
 
 const char* pyro_version(void) { return "pyro-b300 0.1 (sm_103a)"; }
@@ -917,7 +1146,10 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->okc = Coef<double>{k5, k5 + h->P, k5 + 2 * h->P, k5 + 3 * h->P, k5 + 4 * h->P};
     }
     h->V = A.get<double>((size_t)(h->m + 1) * h->n3);
-    h->Z = A.get<double>((size_t)h->m * h->n3);
+    h->Z = A.get<double>((size_t)(h->m + 1) * h->n3);   // m for FGMRES / GCR, m + 1 for Anderson
+    h->zc = A.get<double>(h->n3);
+    h->d_slot = A.get<int>(2);
+    h->d_cnt = h->d_slot + 1;
     h->h1 = A.get<double>(kMaxRestart + 2); h->h2 = A.get<double>(kMaxRestart + 2);
     h->partial = A.get<double>((size_t)kReduceBlocks * (kMaxRestart + 1) * 2);
     h->part2 = A.get<double>(4 * kReduceBlocks);
@@ -986,8 +1218,9 @@ int pyro_stokes_precond(pyro_stokes h, const double* eta_n, const double* eta_c,
       Level<float>& L0 = h->mgf.lv[0];
       k_precond_in<float><<<kReduceBlocks, kThreads, 0, s>>>(h->P, h->V, h->n3, h->d_j, L0.fx, L0.fy, L0.vx, L0.vy);
       h->mgf.cycle(0, s);
-      k_precond_out<float, double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->V, (double*)h->Z,
-                                                                       h->n3, h->d_j, h->ec, h->o.alpha_p, h->part2);
+      k_precond_out<float, double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->V, h->n3,
+                                                                       (double*)h->Z, h->n3, h->d_j, h->ec,
+                                                                       h->o.alpha_p, h->part2);
       k_sub_mean<double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, (double*)h->Z + 2 * h->P, h->n3, h->d_j, h->part2,
                                                            kReduceBlocks);
       CK(cudaMemcpyAsync(h->w, h->Z, h->n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -995,8 +1228,9 @@ int pyro_stokes_precond(pyro_stokes h, const double* eta_n, const double* eta_c,
       Level<double>& L0 = h->mgd.lv[0];
       k_precond_in<double><<<kReduceBlocks, kThreads, 0, s>>>(h->P, h->V, h->n3, h->d_j, L0.fx, L0.fy, L0.vx, L0.vy);
       h->mgd.cycle(0, s);
-      k_precond_out<double, double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->V, (double*)h->Z,
-                                                                        h->n3, h->d_j, h->ec, h->o.alpha_p, h->part2);
+      k_precond_out<double, double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->V, h->n3,
+                                                                        (double*)h->Z, h->n3, h->d_j, h->ec,
+                                                                        h->o.alpha_p, h->part2);
       k_sub_mean<double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, (double*)h->Z + 2 * h->P, h->n3, h->d_j, h->part2,
                                                            kReduceBlocks);
       CK(cudaMemcpyAsync(h->w, h->Z, h->n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1114,7 +1348,7 @@ int pyro_stokes_solve(pyro_stokes h, const double* eta_n, const double* eta_c, c
       cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
       st.t_setup_ms = ms;
       if (*h->hflag & FLAG_BREAKDOWN) status = PYRO_E_BREAKDOWN;
-      else status = fgmres(h, tol, &st, s);
+      else status = outer_solve(h, tol, &st, s);
     }
     if (status >= 0) {
       CK(cudaMemcpyAsync(h->xf, h->x, h->n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1157,7 +1391,7 @@ int pyro_stokes_adjoint(pyro_stokes h, const double* dJ_dvx, const double* dJ_dv
     CK(cudaMemcpyAsync(h->hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (*h->hflag & FLAG_NONFINITE) status = PYRO_E_NONFINITE;
-    else status = fgmres(h, tol, &st, s);   // eta and the hierarchy of the last solve are still in place
+    else status = outer_solve(h, tol, &st, s);   // eta and the hierarchy of the last solve are still in place
     if (status >= 0) {
       // lambda is in h->x, the forward solution in h->xf
       double* on = dJ_deta_n; double* oc = dJ_deta_c; double* orh = dJ_drho;

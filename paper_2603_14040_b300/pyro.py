@@ -14,6 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libpyro.so")
 
 PYRO_OK, PYRO_W_NOT_CONVERGED = 0, 1
+ACCEL_FGMRES, ACCEL_GCR, ACCEL_ANDERSON = 0, 1, 2
 PYRO_E_INVALID, PYRO_E_NOMEM, PYRO_E_CUDA, PYRO_E_NONFINITE, PYRO_E_TIMEOUT, PYRO_E_BREAKDOWN = -1, -2, -3, -4, -5, -6
 FREE_SLIP, NO_SLIP, PERIODIC, VELOCITY = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
@@ -30,7 +31,8 @@ class PyroOpts(ctypes.Structure):
                 ("prec", ctypes.c_int), ("coarsest_min", ctypes.c_int), ("eta_coarsen", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("use_graphs", ctypes.c_int), ("timeout_s", ctypes.c_double),
                 ("kcycle", ctypes.c_int), ("cluster_cells", ctypes.c_int), ("tile_fusion", ctypes.c_int),
-                ("tile_sweeps", ctypes.c_int), ("tile_fusion64", ctypes.c_int)]
+                ("tile_sweeps", ctypes.c_int), ("tile_fusion64", ctypes.c_int), ("accel", ctypes.c_int),
+                ("aa_beta", ctypes.c_double)]
 
 
 class PyroStats(ctypes.Structure):
