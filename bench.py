@@ -115,11 +115,13 @@ def oracle_baseline(seconds_budget=20.0, sample_n=128):
             "sample_seconds_per_solve": dt}
 
 
-def vcycle_roofline_4096(peaks, iters=6, tile_sweeps=2, tile_fusion=1):
-    """Level-0 FP32 V-cycle kernels at 4096^2 (every level-0 array is 67 MB, far above L2): the
-    two-sweep RBGS pass (row-streaming kernel with tile_fusion=2, shared-memory tiles with 1)
-    moves 32 B/cell (reads vx, vy, fx, fy, eta_n, eta_c, writes vx, vy) per launch; achieved =
-    bytes / measured duration (CUDA events inside the solve)."""
+def vcycle_roofline_4096(peaks, iters=6, label="", launches=1, **opts):
+    """Level-0 FP32 V-cycle smoother kernels at 4096^2 (every level-0 array is 67 MB, far above
+    L2), inside a mixed-precision solve of the layered workload. Each smoothing launch moves
+    32 B/cell of algorithmic traffic (reads vx, vy, fx, fy, eta_n, eta_c, writes vx, vy): one RBGS
+    sweep or two (tile kernels), one damped Jacobi sweep, or one RAS pass of `ras_inner` local
+    Jacobi iterations. achieved = bytes / measured launch duration (CUDA events inside the solve,
+    l0_pre_smooth phase / launches per pre-smoothing)."""
     import torch
     import paper_2603_14040_b300 as P
     from synth import layered_config
@@ -129,39 +131,52 @@ def vcycle_roofline_4096(peaks, iters=6, tile_sweeps=2, tile_fusion=1):
     en, ec, rho = dev(f.eta_n), dev(f.eta_c), dev(f.rho)
     del f
     outs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
-    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=2, tile_sweeps=tile_sweeps, tile_fusion=tile_fusion)
+    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=2, **opts)
     h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)           # warm-up (graph capture)
     h.close()
-    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=iters, tile_sweeps=tile_sweeps, tile_fusion=tile_fusion)
+    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=iters, **opts)
     h.set_timing(True)
-    st = h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
+    h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
     torch.cuda.synchronize()
     ph, cnt = h.get_timing()
     it = max(cnt["iterations"], 1)
-    launches = 2 // tile_sweeps                 # level-0 tile launches per smoothing block (nu = 2)
     pre_ms = ph["l0_pre_smooth"] / it / launches
-    post_ms = ph["l0_post_smooth"] / it / launches
     cells = n * n
     bytes_pre = 32.0 * cells
-    bytes_post = 34.0 * cells                  # + the coarse correction read (1/4 size, 2 fields)
     gbs_pre = bytes_pre / (pre_ms / 1e3) / 1e9
-    gbs_post = bytes_post / (post_ms / 1e3) / 1e9
     peak = peaks.get("hbm_gbs", 6400.0)
     h.close()
     del outs, en, ec, rho
     torch.cuda.empty_cache()
-    kname = (f"k_rbgs_stream<{tile_sweeps},2>" if tile_fusion >= 2 else f"k_rbgs_tile_cs<{tile_sweeps},64,32>")
-    return {"kernel": f"{kname} level 0 ({tile_sweeps} fused RBGS sweep(s) per launch), 4096x4096 mixed",
+    return {"kernel": f"{label} level 0, 4096x4096 layered, mixed", "opts": opts,
             "bound": "hbm", "achieved": gbs_pre, "peak": peak, "unit": "GB/s", "frac": gbs_pre / peak,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6400 GB/s",
             "bytes_per_launch": bytes_pre, "launch_ms": pre_ms,
-            "post_smooth_with_prolongation": {"achieved": gbs_post, "frac": gbs_post / peak, "launch_ms": post_ms},
+            "vcycle_ms_per_iter": (ph["l0_pre_smooth"] + ph["coarse_levels"] + ph["l0_post_smooth"]) / it,
             "phase_ms_per_iter": {k: v / it for k, v in ph.items()}, "iters_timed": it}
 
 
+def vcycle_rooflines(peaks):
+    """The damped-Jacobi smoother's kernel (the paper's fully parallel smoother, one HBM pass per
+    sweep) heads the object; the default RBGS tile kernels and the RAS-type pass are variants."""
+    main = vcycle_roofline_4096(peaks, label="k_jacobi<float> (damped Jacobi sweep, smoother=JACOBI, omega 0.6)",
+                                launches=2, smoother=1, omega_v=0.6)
+    main["variants"] = {}
+    for key, label, launches, opts in [
+            ("rbgs_tiles_2_sweeps_default", "k_rbgs_tile_cs<2,64,32> (2 RBGS sweeps per launch, the default)", 1,
+             dict(tile_sweeps=2)),
+            ("rbgs_tiles_1_sweep", "k_rbgs_tile_cs<1,64,32> (1 RBGS sweep per launch)", 2, dict(tile_sweeps=1)),
+            ("ras_inner_2", "k_ras_tile<float,32,32> (RAS pass of 2 local Jacobi iterations)", 1,
+             dict(smoother=2, ras_inner=2, omega_v=0.6))]:
+        v = vcycle_roofline_4096(peaks, label=label, launches=launches, **opts)
+        main["variants"][key] = {k: v[k] for k in ("kernel", "achieved", "frac", "launch_ms", "vcycle_ms_per_iter")}
+    return main
+
+
 def accelerator_sample(f, n, steps=3):
-    """The paper's own outer accelerators on the bench workload (same preconditioner, same 1e-10
-    energy-residual stop): flexible GCR(30) and Anderson AA(m, beta), FP64 and mixed precision."""
+    """The paper's own outer accelerators and smoothers on the bench workload (same 1e-10
+    energy-residual stop): flexible GCR(30) and Anderson AA(m, beta) around the default
+    preconditioner (FP64 and mixed), and the damped-Jacobi / RAS-type smoothers (mixed)."""
     import torch
     import paper_2603_14040_b300 as P
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -170,8 +185,14 @@ def accelerator_sample(f, n, steps=3):
     res = {}
     for name, kw in [("gcr30", dict(accel=P.ACCEL_GCR, restart_m=30)),
                      ("anderson10_beta1", dict(accel=P.ACCEL_ANDERSON, restart_m=10, aa_beta=1.0)),
-                     ("anderson15_beta0.8", dict(accel=P.ACCEL_ANDERSON, restart_m=15, aa_beta=0.8))]:
+                     ("anderson15_beta0.8", dict(accel=P.ACCEL_ANDERSON, restart_m=15, aa_beta=0.8)),
+                     ("fgmres30_jacobi_smoother", dict(smoother=P.SMOOTH_JACOBI, omega_v=0.6)),
+                     ("fgmres30_ras4_smoother", dict(smoother=P.SMOOTH_RAS, ras_inner=4, omega_v=0.6)),
+                     ("anderson15_beta0.8_jacobi_smoother", dict(accel=P.ACCEL_ANDERSON, restart_m=15, aa_beta=0.8,
+                                                                 smoother=P.SMOOTH_JACOBI, omega_v=0.6))]:
         for prec, pn in ((P.PREC_FP64, "fp64"), (P.PREC_MIXED, "mixed")):
+            if "smoother" in name and prec == P.PREC_FP64:
+                continue
             h = P.Stokes(n, n, prec=prec, max_iter=3000, **kw)
             h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
             ts = []
@@ -455,10 +476,7 @@ def main():
                                    "rel_diff_vs_fp64_p": errp, "p50_ms": float(np.percentile(ms, 50)),
                                    "p99_ms": float(np.percentile(ms, 99))}
     if rank == 0 and not args.no_extras:
-        line["vcycle_roofline"] = vcycle_roofline_4096(peaks)
-        one = vcycle_roofline_4096(peaks, tile_sweeps=1)
-        line["vcycle_roofline"]["one_sweep_per_launch"] = {k: one[k] for k in ("kernel", "achieved", "frac",
-                                                                                "launch_ms", "phase_ms_per_iter")}
+        line["vcycle_roofline"] = vcycle_rooflines(peaks)
         line["accelerators"] = accelerator_sample(f, n)
         line["serving"] = serving_sample()
         line["adjoint"] = adjoint_sample()

@@ -84,6 +84,17 @@ typedef enum { PYRO_PREC_FP64 = 0, PYRO_PREC_MIXED = 1 } pyro_precision;
  *            Acceleration", Algorithm anderson), least squares in the 2-norm, depth m =
  *            restart_m, x^1 = G(x^0). */
 typedef enum { PYRO_ACCEL_FGMRES = 0, PYRO_ACCEL_GCR = 1, PYRO_ACCEL_ANDERSON = 2 } pyro_accel;
+
+/* Velocity smoother of the V-cycle (Sec. "Smoothers"), damping omega_v for all three:
+ *   RBGS    red-black Gauss-Seidel (eq. sor_update), colour order vx-red, vx-black, vy-red, vy-black;
+ *   JACOBI  damped Jacobi sweeps of the coupled velocity block (eq. damped_jacobi); needs
+ *           omega_v well below 1 (0.5-0.7) to smooth;
+ *   RAS     RAS-type temporally blocked Jacobi (Algorithm ras_temporal): ceil(nu / ras_inner)
+ *           passes over 32 x 32-cell tiles, each tile running ras_inner local damped Jacobi
+ *           iterations in shared memory with its one-cell ring held at the pass-start values; the
+ *           tiling shift of each pass comes from SplitMix64 of (level, pre/post, pass), so the
+ *           V-cycle is the same linear operator at every application. */
+typedef enum { PYRO_SMOOTH_RBGS = 0, PYRO_SMOOTH_JACOBI = 1, PYRO_SMOOTH_RAS = 2 } pyro_smoother;
 typedef enum { PYRO_ETA_ARITH = 0, PYRO_ETA_GEOM = 1 } pyro_eta_coarsening;
 
 /* Solver options. pyro_default_opts() fills the defaults given in brackets. */
@@ -119,6 +130,8 @@ typedef struct {
                             that one CTA per tile becomes the critical path) [0] */
   int accel;             /* pyro_accel: outer accelerator [PYRO_ACCEL_FGMRES] */
   double aa_beta;        /* Anderson mixing beta in (0, 1] (the paper suggests 0.5-0.8) [1.0] */
+  int smoother;          /* pyro_smoother [PYRO_SMOOTH_RBGS] */
+  int ras_inner;         /* RAS smoother: local Jacobi iterations per tile pass (T_inner) [4] */
 } pyro_opts;
 
 typedef struct {

@@ -9,7 +9,9 @@ step at a time:
   * restriction = normalised bilinear-weighted accumulation (Sec. "Restriction and Prolongation
     Operators", the normalised-sum equation), built here by brute force from the staggered
     positions; prolongation = bilinear interpolation from the four surrounding coarse points;
-  * damped red-black Gauss-Seidel (Sec. "Smoothers", eq. sor_update) on the velocity block;
+  * damped red-black Gauss-Seidel (Sec. "Smoothers", eq. sor_update) on the velocity block, or
+    damped Jacobi (eq. damped_jacobi), or the RAS-type temporally blocked Jacobi smoother
+    (Algorithm ras_temporal);
   * the V-cycle of eq. multigrid_levels with a direct coarsest solve;
   * one Uzawa sweep as the preconditioner M^-1 (Sec. "Uzawa Iteration as a Fixed Point Method").
 
@@ -20,6 +22,10 @@ Readings (the paper is silent or inconsistent; each is listed with the design no
   * viscosity is coarsened with the same normalised bilinear weights, arithmetically or on
     log(eta) (geometric mean);
   * RBGS colour order: vx-red, vx-black, vy-red, vy-black with colour (i + j) mod 2;
+  * RAS-type Jacobi: a tile owns the unknowns of its cells, its outer boundary is held at the
+    pass-start values, ceil(nu / T_inner) passes (no rounding to an even count: the evenness in
+    the paper's algorithm only returns the result to the first of two global buffers), tiles
+    clipped at the domain edge, shifts from SplitMix64 of (level, pre/post, pass);
   * pressure sign of M^-1: the paper's splitting puts -(alpha eta)^-1 in the pressure block, but
     with L negative definite (as the paper states) D L^-1 G is negative semi-definite and that
     sign makes the stationary Uzawa iteration diverge. We take z_p = alpha eta_c (r_p - D z_v),
@@ -190,9 +196,77 @@ def rbgs_sweep(L, f, x, sets, omega):
     return x
 
 
+def jacobi_sweep(L, f, x, omega):
+    """One damped Jacobi sweep over every unknown of L x = f (eq. damped_jacobi):
+    x + omega (f - L x) / diag(L), all from the old iterate."""
+    return x + omega * (f - L @ x) / L.diagonal()
+
+
+def splitmix64(z):
+    """SplitMix64 (Steele, Lea & Flood, OOPSLA 2014), on Python integers modulo 2^64."""
+    m = (1 << 64) - 1
+    z = (z + 0x9E3779B97F4A7C15) & m
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return z ^ (z >> 31)
+
+
+RAS_SEED = 0x5EED
+
+
+def ras_shift(level, phase, t, TI, TJ):
+    """Tiling shift (s_i, s_j) of pass t of the pre (phase 0) / post (phase 1) smoothing on a level:
+    the random shift of Algorithm ras_temporal, drawn from SplitMix64 of a counter so that the
+    smoother is the same operator at every application."""
+    v = splitmix64(RAS_SEED + (((level * 2 + phase) << 16) + t))
+    return (v & 0xFFFFFFFF) % TI, (v >> 32) % TJ
+
+
+def ras_pass(g, L, f, x, omega, inner, TI, TJ, si, sj):
+    """One pass of the RAS-type temporally blocked Jacobi smoother (Algorithm ras_temporal).
+    The cells are tiled TI x TJ, tile k covering rows [k_i TI - si, (k_i + 1) TI - si) and the
+    same for columns; a tile owns the unknowns of its cells (vx(i, j) and vy(i, j) belong to cell
+    (i, j)); each tile runs `inner` damped Jacobi iterations on its own unknowns with every other
+    unknown held at its value from the start of the pass (the tile's outer boundary is fixed), and
+    the owned results make up the new iterate."""
+    vi = np.concatenate([g.vx_i, g.vy_i]); vj = np.concatenate([g.vx_j, g.vy_j])
+    tile = ((vi + si) // TI) * 1_000_003 + (vj + sj) // TJ
+    C = L.tocoo()
+    same = tile[C.row] == tile[C.col]
+    Ls = sp.csr_matrix((C.data[same], (C.row[same], C.col[same])), shape=L.shape)
+    Lo = sp.csr_matrix((C.data[~same], (C.row[~same], C.col[~same])), shape=L.shape)
+    d = L.diagonal()
+    rhs = f - Lo @ x                      # other tiles' unknowns at their pass-start values
+    y = x.copy()
+    for _ in range(inner):
+        y = y + omega * (rhs - Ls @ y) / d
+    return y
+
+
+def smooth(h, level, f, x, nu, omega, phase):
+    """nu smoothing steps on `level` with the hierarchy's smoother: damped RBGS sweeps (default),
+    damped Jacobi sweeps, or ceil(nu / inner) RAS passes of `inner` local Jacobi iterations."""
+    L = h.L[level]
+    if h.smoother == "rbgs":
+        for _ in range(nu):
+            x = rbgs_sweep(L, f, x, h.sets[level], omega)
+        return x
+    if h.smoother == "jacobi":
+        for _ in range(nu):
+            x = jacobi_sweep(L, f, x, omega)
+        return x
+    npass = -(-nu // h.ras_inner)
+    for t in range(npass):
+        si, sj = ras_shift(level, phase, t, h.ras_tile, h.ras_tile)
+        x = ras_pass(h.grids[level], L, f, x, omega, h.ras_inner, h.ras_tile, h.ras_tile, si, sj)
+    return x
+
+
 # ---- hierarchy and V-cycle ---------------------------------------------------------------------
 class Hierarchy:
-    def __init__(self, grid, eta_n, eta_c, coarsest_min=4, eta_mode=ETA_ARITH, n_lev=None):
+    def __init__(self, grid, eta_n, eta_c, coarsest_min=4, eta_mode=ETA_ARITH, n_lev=None, smoother="rbgs",
+                 ras_inner=4, ras_tile=32):
+        self.smoother, self.ras_inner, self.ras_tile = smoother, ras_inner, ras_tile
         L = n_levels(grid.nx, grid.ny, coarsest_min) if n_lev is None else n_lev
         self.grids = [grid]; self.eta = [(eta_n, eta_c)]
         for _ in range(L - 1):
@@ -223,8 +297,7 @@ def vcycle(h, f, nu1=2, nu2=2, omega=1.0, level=0, kcycle=0):
         return h.coarse_lu.solve(f)
     L = h.L[level]
     x = np.zeros_like(f)
-    for _ in range(nu1):
-        x = rbgs_sweep(L, f, x, h.sets[level], omega)             # (1) pre-smoothing
+    x = smooth(h, level, f, x, nu1, omega, 0)                     # (1) pre-smoothing
     r = f - L @ x                                                 # (2) residual
     fc = h.R[level] @ r                                           # (3) restriction
     if level < kcycle and level + 1 < h.nlev - 1:                 # (4) by two flexible-CG steps
@@ -232,8 +305,7 @@ def vcycle(h, f, nu1=2, nu2=2, omega=1.0, level=0, kcycle=0):
     else:                                                         # (4) coarse solve / recursion
         dc = vcycle(h, fc, nu1, nu2, omega, level + 1, kcycle)
     x = x + h.P[level] @ dc                                       # (5) prolongation + correction
-    for _ in range(nu2):
-        x = rbgs_sweep(L, f, x, h.sets[level], omega)             # (6) post-smoothing
+    x = smooth(h, level, f, x, nu2, omega, 1)                     # (6) post-smoothing
     return x
 
 

@@ -60,20 +60,21 @@ __device__ inline T ldvy(const S* vy, int ld, int ny, int i, int j) {
 //   (sxx(i,j+1) - sxx(i,j))/dx + (sxy(i,j) - sxy(i-1,j))/dy
 // with sxx = 2 eta_c d vx/dx at cells and sxy = eta_n (d vx/dy + d vy/dx) at basic nodes.
 // Returns the value and the diagonal coefficient (boundary elimination included).
+// The _at form reads every array at c + offset with row stride ld (a copy of part of the grid,
+// e.g. a shared-memory tile); (i, j) stay global indices for the boundary rules.
 template <typename T, typename SV, typename SE>
-__device__ inline T lx_point(const GeomT<T>& g, int i, int j, const SV* vx, const SV* vy,
-                             const SE* en, const SE* ec, T& diag) {
-  const int ld = g.ld;
-  const size_t c = (size_t)i * ld + j;
+__device__ inline T lx_point_at(const GeomT<T>& g, int i, int j, size_t c, int ld, const SV* vx, const SV* vy,
+                                const SE* en, const SE* ec, T& diag) {
   const T eA = (T)ec[c], eB = (T)ec[c + 1];       // cells west / east of vx(i,j)
   const T e1 = (T)en[c - ld], e2 = (T)en[c];       // nodes above / below
   const T vc = (T)vx[c];
-  const T vw = ldvx<T>(vx, ld, g.nx, i, j - 1);
-  const T ve = ldvx<T>(vx, ld, g.nx, i, j + 1);
+  const T vw = (j - 1 <= 0) ? T(0) : (T)vx[c - 1];
+  const T ve = (j + 1 >= g.nx) ? T(0) : (T)vx[c + 1];
   const T vn = (i == 1) ? g.sN * vc : (T)vx[c - ld];
   const T vs = (i == g.ny) ? g.sS * vc : (T)vx[c + ld];
-  const T yA = ldvy<T>(vy, ld, g.ny, i - 1, j), yB = ldvy<T>(vy, ld, g.ny, i - 1, j + 1);
-  const T yC = ldvy<T>(vy, ld, g.ny, i, j), yD = ldvy<T>(vy, ld, g.ny, i, j + 1);
+  const bool rn = i - 1 <= 0 || i - 1 >= g.ny, r0 = i <= 0 || i >= g.ny;
+  const T yA = rn ? T(0) : (T)vy[c - ld], yB = rn ? T(0) : (T)vy[c - ld + 1];
+  const T yC = r0 ? T(0) : (T)vy[c], yD = r0 ? T(0) : (T)vy[c + 1];
   const T sxxE = T(2) * eB * (ve - vc);
   const T sxxW = T(2) * eA * (vc - vw);
   const T sxyS = e2 * ((vs - vc) * g.idy2 + (yD - yC) * g.idxdy);
@@ -83,23 +84,27 @@ __device__ inline T lx_point(const GeomT<T>& g, int i, int j, const SV* vx, cons
   if (i == g.ny) diag += g.sS * e2 * g.idy2;
   return (sxxE - sxxW) * g.idx2 + sxyS - sxyN;
 }
+template <typename T, typename SV, typename SE>
+__device__ inline T lx_point(const GeomT<T>& g, int i, int j, const SV* vx, const SV* vy,
+                             const SE* en, const SE* ec, T& diag) {
+  return lx_point_at<T>(g, i, j, (size_t)i * g.ld + j, g.ld, vx, vy, en, ec, diag);
+}
 
 // y-momentum velocity part at the vy unknown (i, j):
 //   (syy(i+1,j) - syy(i,j))/dy + (sxy(i,j) - sxy(i,j-1))/dx
 template <typename T, typename SV, typename SE>
-__device__ inline T ly_point(const GeomT<T>& g, int i, int j, const SV* vx, const SV* vy,
-                             const SE* en, const SE* ec, T& diag) {
-  const int ld = g.ld;
-  const size_t c = (size_t)i * ld + j;
+__device__ inline T ly_point_at(const GeomT<T>& g, int i, int j, size_t c, int ld, const SV* vx, const SV* vy,
+                                const SE* en, const SE* ec, T& diag) {
   const T eA = (T)ec[c], eB = (T)ec[c + ld];      // cells above / below vy(i,j)
   const T e1 = (T)en[c - 1], e2 = (T)en[c];        // nodes west / east
   const T vc = (T)vy[c];
-  const T vn = ldvy<T>(vy, ld, g.ny, i - 1, j);
-  const T vs = ldvy<T>(vy, ld, g.ny, i + 1, j);
+  const T vn = (i - 1 <= 0) ? T(0) : (T)vy[c - ld];
+  const T vs = (i + 1 >= g.ny) ? T(0) : (T)vy[c + ld];
   const T vw = (j == 1) ? g.sW * vc : (T)vy[c - 1];
   const T ve = (j == g.nx) ? g.sE * vc : (T)vy[c + 1];
-  const T xA = ldvx<T>(vx, ld, g.nx, i, j - 1), xB = ldvx<T>(vx, ld, g.nx, i + 1, j - 1);
-  const T xC = ldvx<T>(vx, ld, g.nx, i, j), xD = ldvx<T>(vx, ld, g.nx, i + 1, j);
+  const bool cw = j - 1 <= 0 || j - 1 >= g.nx, c0 = j <= 0 || j >= g.nx;
+  const T xA = cw ? T(0) : (T)vx[c - 1], xB = cw ? T(0) : (T)vx[c + ld - 1];
+  const T xC = c0 ? T(0) : (T)vx[c], xD = c0 ? T(0) : (T)vx[c + ld];
   const T syyS = T(2) * eB * (vs - vc);
   const T syyN = T(2) * eA * (vc - vn);
   const T sxyE = e2 * ((ve - vc) * g.idx2 + (xD - xC) * g.idxdy);
@@ -108,6 +113,11 @@ __device__ inline T ly_point(const GeomT<T>& g, int i, int j, const SV* vx, cons
   if (j == 1) diag += g.sW * e1 * g.idx2;
   if (j == g.nx) diag += g.sE * e2 * g.idx2;
   return (syyS - syyN) * g.idy2 + sxyE - sxyW;
+}
+template <typename T, typename SV, typename SE>
+__device__ inline T ly_point(const GeomT<T>& g, int i, int j, const SV* vx, const SV* vy,
+                             const SE* en, const SE* ec, T& diag) {
+  return ly_point_at<T>(g, i, j, (size_t)i * g.ld + j, g.ld, vx, vy, en, ec, diag);
 }
 
 // Precomputed viscosity coefficients of one level (FP64 levels whose smoothing is ALU-bound):

@@ -182,6 +182,7 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
 // ---- Krylov building blocks -------------------------------------------------------------------
 // partial[k * gridDim.x + blockIdx.x] = sum_e W[e] w[e] V_k[e] for k in [k0, k0+8) and k < nvec,
 // nvec = *d_j + 1 (or nfix when d_j is null). blockIdx.y selects the group of 8 vectors.
+template <bool WEIGHTED>
 __global__ void k_multidot(const double* __restrict__ V, size_t stride, const int* __restrict__ d_j, int nfix,
                            const double* __restrict__ w, const double* __restrict__ W, size_t n,
                            double* __restrict__ partial, const int* __restrict__ d_run, double* __restrict__ part_ww,
@@ -197,7 +198,7 @@ __global__ void k_multidot(const double* __restrict__ V, size_t stride, const in
   double aww = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const double we = w[e];
-    const double t = W ? W[e] * we : we;
+    const double t = WEIGHTED ? W[e] * we : we;
     if (ww) aww += t * we;
 #pragma unroll
     for (int q = 0; q < 8; ++q)

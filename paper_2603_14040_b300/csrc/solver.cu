@@ -17,6 +17,7 @@
 #include "kernels_sub.cuh"
 #include "kernels_tile.cuh"
 #include "kernels_stream.cuh"
+#include "kernels_jacobi.cuh"
 
 using namespace pyro;
 
@@ -24,6 +25,7 @@ namespace {
 
 constexpr int kMaxCoarse = 1024;
 constexpr int kStreamMinRows = 96;  // shortest row chunk worth a streaming pass
+constexpr int kRasTile = 32;        // RAS-type Jacobi tile edge (cells), the paper's 32 x 32
 
 struct CudaError {
   cudaError_t e;
@@ -114,6 +116,8 @@ struct MG {
   int ls = -1;     // first level run by the cluster sub-cycle kernel (-1: none)
   bool tiles = true;                        // tile-fused smoothing / residual+restriction
   int stream = 0;                           // FP32 row-streaming sweeps: 0 never, 1 large levels, 2 all
+  int smoother = PYRO_SMOOTH_RBGS;          // velocity smoother of every level
+  int ras_inner = 4;                        // RAS-type Jacobi: local iterations per tile pass
   int tile_sweeps = 2;                      // FP32: sweeps fused per tile launch
   static constexpr long long kFuse64Cells = 65536;
   SubArgs<T> sub{};
@@ -153,7 +157,7 @@ struct MG {
         L.kc = Coef<T>{k5, k5 + L.P, k5 + 2 * L.P, k5 + 3 * L.P, k5 + 4 * L.P};
         L.own_kc = true;
       }
-      if (tiles) {
+      if (tiles || smoother != PYRO_SMOOTH_RBGS) {
         L.vx2 = A.get<T>(L.P); L.vy2 = A.get<T>(L.P);
         CK(cudaMemset(L.vx2, 0, L.P * sizeof(T)));
         CK(cudaMemset(L.vy2, 0, L.P * sizeof(T)));
@@ -178,7 +182,7 @@ struct MG {
   // choose the first level of the cluster sub-cycle and fill its launch arguments
   void setup_sub(DevAlloc& A, int cluster_cells) {
     ls = -1;
-    if (cluster_cells <= 0 || (int)lv.size() > kSubMaxLevels || lv.size() < 2) return;
+    if (cluster_cells <= 0 || (int)lv.size() > kSubMaxLevels || lv.size() < 2 || smoother != PYRO_SMOOTH_RBGS) return;
     for (int l = 0; l < (int)lv.size(); ++l)
       if ((long long)lv[l].g.nx * lv[l].g.ny <= cluster_cells) { ls = l; break; }
     if (ls < 0 || ls == (int)lv.size() - 1) { ls = -1; return; }
@@ -357,6 +361,50 @@ struct MG {
     }
   }
 
+  // nsweeps smoothing steps on level l with the configured smoother; with C given, the coarse
+  // correction (prolongation of C's iterate) is added first. phase: 0 pre, 1 post (RAS shifts).
+  void smooth(int l, int nsweeps, const Level<T>* C, int phase, cudaStream_t s) {
+    Level<T>& L = lv[l];
+    if (smoother == PYRO_SMOOTH_RBGS && fused(l)) {
+      smooth_tiles(l, nsweeps, C, s);
+      return;
+    }
+    if (C) {
+      k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C->gt, L.X(), L.Y(), C->X(), C->Y());
+      count(1);
+    }
+    if (smoother == PYRO_SMOOTH_RBGS) {
+      for (int k = 0; k < nsweeps; ++k) sweep(l, s);
+      return;
+    }
+    if (smoother == PYRO_SMOOTH_JACOBI) {
+      for (int k = 0; k < nsweeps; ++k) {
+        k_jacobi<T><<<jacobi_grid(L.g.nx, L.g.ny), jacobi_block(), 0, s>>>(L.gt, L.X(), L.Y(), L.cur ? L.vx : L.vx2,
+                                                                     L.cur ? L.vy : L.vy2, L.fx, L.fy, L.en, L.ec,
+                                                                     omega);
+        L.cur ^= 1;
+      }
+      count(nsweeps);
+      return;
+    }
+    const int npass = (nsweeps + ras_inner - 1) / ras_inner;
+    for (int t = 0; t < npass; ++t) {
+      int si = 0, sj = 0;
+      ras_shift(l, phase, t, kRasTile, kRasTile, si, sj);
+      const dim3 gr((L.g.nx + 2 + sj + kRasTile - 1) / kRasTile, (L.g.ny + 2 + si + kRasTile - 1) / kRasTile);
+      k_ras_tile<T, kRasTile, kRasTile><<<gr, 256, RasTile<kRasTile, kRasTile>::template smem_bytes<T>(), s>>>(
+          L.gt, L.X(), L.Y(), L.cur ? L.vx : L.vx2, L.cur ? L.vy : L.vy2, L.fx, L.fy, L.en, L.ec, omega, si, sj,
+          ras_inner);
+      L.cur ^= 1;
+    }
+    count(npass);
+  }
+
+  static void enable_ras() {
+    CK(cudaFuncSetAttribute(k_ras_tile<T, kRasTile, kRasTile>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)RasTile<kRasTile, kRasTile>::template smem_bytes<T>()));
+  }
+
   void sweep(int l, cudaStream_t s) {
     Level<T>& L = lv[l];
     const dim3 g = grid_rb(L.g.nx, L.g.ny, kBlk2);
@@ -384,13 +432,11 @@ struct MG {
     }
     Level<T>& C = lv[l + 1];
     const bool fz = fused(l);
+    smooth(l, nu1, nullptr, 0, s);
+    if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[2], s, cudaEventRecordExternal));
     if (fz) {
-      smooth_tiles(l, nu1, nullptr, s);
-      if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[2], s, cudaEventRecordExternal));
       resrestrict_tiles(l, s);  // also zeroes the coarse iterate
     } else {
-      for (int k = 0; k < nu1; ++k) sweep(l, s);
-      if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[2], s, cudaEventRecordExternal));
       k_vresidual<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, L.rx,
                                                                        L.ry, L.kc);
       k_restrict<T><<<grid2(C.g.nx, C.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C.gt, L.rx, L.ry, C.fx, C.fy);
@@ -415,15 +461,14 @@ struct MG {
     } else {
       cycle(l + 1, s);
     }
-    if (fz) {
-      if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[3], s, cudaEventRecordExternal));
-      smooth_tiles(l, nu2, &C, s);  // prolongation fused into the first post-smoothing tile pass
-    } else {
+    // prolongation + correction (fused into the first post-smoothing pass of the RBGS tiles)
+    const bool fused_post = smoother == PYRO_SMOOTH_RBGS && fz;
+    if (!fused_post) {
       k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C.gt, L.X(), L.Y(), C.X(), C.Y());
       count(1);
-      if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[3], s, cudaEventRecordExternal));
-      for (int k = 0; k < nu2; ++k) sweep(l, s);
     }
+    if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[3], s, cudaEventRecordExternal));
+    smooth(l, nu2, fused_post ? &C : nullptr, 1, s);
     if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[4], s, cudaEventRecordExternal));
   }
 };
@@ -516,10 +561,10 @@ void fgmres_body(pyro_stokes_s* h, cudaStream_t s) {
   precond_any(h, s, h->V, h->n3, (double*)h->Z, h->n3, h->d_j, true);
   // classical Gram-Schmidt with one re-orthogonalisation (CGS2) in the W inner product
   const dim3 gd(kReduceBlocks, (unsigned)h->dot_grid_y);
-  k_multidot<<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial, nullptr, nullptr);
+  k_multidot<true><<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial, nullptr, nullptr);
   k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, h->h1, nullptr);
   k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h1, h->n3, nullptr, nullptr, nullptr);
-  k_multidot<<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial, nullptr, nullptr);
+  k_multidot<true><<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial, nullptr, nullptr);
   k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, h->h2, nullptr);
   k_multiaxpy<<<kReduceBlocks, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h2, h->n3, h->W, h->part2, nullptr);
   k_arnoldi_finish<<<1, kThreads, 0, s>>>(h->d_j, h->h1, h->h2, h->part2, kReduceBlocks, h->hcol, h->inv, h->flag,
@@ -540,7 +585,7 @@ void gcr_body(pyro_stokes_s* h, cudaStream_t s) {
   double* Zb = (double*)h->Z;
   for (int pass = 0; pass < 2; ++pass) {
     double* hc = pass == 0 ? h->h1 : h->h2;
-    k_multidot<<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial, nullptr, nullptr, -1);
+    k_multidot<true><<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial, nullptr, nullptr, -1);
     k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, hc, nullptr, -1);
     k_multiaxpy<<<kReduceBlocks, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, hc, h->n3, pass ? h->W : nullptr,
                                                    pass ? h->part2 : nullptr, nullptr, -1);
@@ -572,7 +617,7 @@ void aa_body(pyro_stokes_s* h, cudaStream_t s) {
   precond_any(h, s, h->r, 0, h->zc, 0, h->d_j, false);
   k_aa_store<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, (double*)h->Z, h->n3, h->d_slot, h->x, h->zc, h->n3);
   const dim3 gd(kReduceBlocks, (unsigned)h->dot_grid_y);
-  k_multidot<<<gd, kThreads, 0, s>>>((double*)h->Z, h->n3, h->d_cnt, 0, h->zc, nullptr, h->n3, h->partial, nullptr,
+  k_multidot<false><<<gd, kThreads, 0, s>>>((double*)h->Z, h->n3, h->d_cnt, 0, h->zc, nullptr, h->n3, h->partial, nullptr,
                                      nullptr, -1);
   k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_cnt, 0, h->h1, nullptr, -1);
   h->launches += 6;
@@ -653,7 +698,7 @@ std::pair<double, double> residual_norms(pyro_stokes_s* h, const double* b, cons
 }
 
 double weighted_norm2(pyro_stokes_s* h, const double* v, cudaStream_t s) {
-  k_multidot<<<dim3(kReduceBlocks, 1), kThreads, 0, s>>>(v, 0, nullptr, 1, v, h->W, h->n3, h->partial, nullptr, nullptr);
+  k_multidot<true><<<dim3(kReduceBlocks, 1), kThreads, 0, s>>>(v, 0, nullptr, 1, v, h->W, h->n3, h->partial, nullptr, nullptr);
   h->launches += 1;
   CK(cudaMemcpyAsync(h->hbuf, h->partial, kReduceBlocks * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -1019,6 +1064,8 @@ void validate_opts(pyro_opts& o) {
   if (o.kcycle > 16) o.kcycle = 16;
   if (o.accel < PYRO_ACCEL_FGMRES || o.accel > PYRO_ACCEL_ANDERSON) o.accel = PYRO_ACCEL_FGMRES;
   if (!(o.aa_beta > 0.0) || o.aa_beta > 1.0) o.aa_beta = 1.0;
+  if (o.smoother < PYRO_SMOOTH_RBGS || o.smoother > PYRO_SMOOTH_RAS) o.smoother = PYRO_SMOOTH_RBGS;
+  if (o.ras_inner < 1) o.ras_inner = 1;
 }
 
 int check_size(int nx, int ny, const pyro_opts& o) {
@@ -1076,6 +1123,8 @@ void pyro_default_opts(pyro_opts* o) {
   o->tile_fusion64 = 0;
   o->accel = PYRO_ACCEL_FGMRES;
   o->aa_beta = 1.0;
+  o->smoother = PYRO_SMOOTH_RBGS;
+  o->ras_inner = 4;
 }
 
 const char* pyro_version(void) { return "pyro-b300 0.1 (sm_103a)"; }
@@ -1161,6 +1210,9 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
     if (h->mixed) {
       h->mgf.nu1 = o.nu1; h->mgf.nu2 = o.nu2; h->mgf.omega = (float)o.omega_v; h->mgf.eta_mode = o.eta_coarsen;
       h->mgf.kcycle = o.kcycle;
+      h->mgf.smoother = o.smoother;
+      h->mgf.ras_inner = o.ras_inner;
+      if (o.smoother == PYRO_SMOOTH_RAS) MG<float>::enable_ras();
       h->mgf.tiles = o.tile_fusion != 0;
       h->mgf.stream = o.tile_fusion >= 2 ? o.tile_fusion - 1 : 0;
       h->mgf.tile_sweeps = o.tile_sweeps;
@@ -1171,6 +1223,9 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
     } else {
       h->mgd.nu1 = o.nu1; h->mgd.nu2 = o.nu2; h->mgd.omega = o.omega_v; h->mgd.eta_mode = o.eta_coarsen;
       h->mgd.kcycle = o.kcycle;
+      h->mgd.smoother = o.smoother;
+      h->mgd.ras_inner = o.ras_inner;
+      if (o.smoother == PYRO_SMOOTH_RAS) MG<double>::enable_ras();
       h->mgd.tiles = o.tile_fusion64 != 0;
       if (h->mgd.tiles) MG<double>::enable_tiles();
       h->mgd.alloc(A, h->g, L, true);

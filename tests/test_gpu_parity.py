@@ -42,18 +42,20 @@ def test_apply_matches_oracle(nx, ny, Lx, Ly, bc):
 
 
 def _precond_case(nx, ny, Lx, Ly, bc, prec, seed, kcycle=0, cluster_cells=0, tile_fusion=1, eta_coarsen=0,
-                  eta=None):
+                  eta=None, smoother=0, ras_inner=4, omega=1.0):
     kind, vt = BCS[bc]
     g = S.Grid(nx, ny, Lx, Ly, S.BC(kind, vt))
     en, ec = rand_eta(nx, ny, seed, -1, 1) if eta is None else eta
     rng = np.random.default_rng(seed + 1)
     r = rng.standard_normal(g.n)
     rx, ry, rp = S.vector_to_fields(g, r, fill_ghosts=False)
-    h_or = M.Hierarchy(g, en, ec, coarsest_min=2, eta_mode=eta_coarsen)
-    z = M.uzawa_precond(h_or, r, ec, alpha=1.0, nu1=2, nu2=2, omega=1.0, kcycle=kcycle)
+    h_or = M.Hierarchy(g, en, ec, coarsest_min=2, eta_mode=eta_coarsen, smoother=("rbgs", "jacobi", "ras")[smoother],
+                       ras_inner=ras_inner, ras_tile=32)
+    z = M.uzawa_precond(h_or, r, ec, alpha=1.0, nu1=2, nu2=2, omega=omega, kcycle=kcycle)
     zx, zy, zp = S.vector_to_fields(g, z, fill_ghosts=False)
     h = P.Stokes(nx, ny, Lx, Ly, bc=P.make_bc(kind, vt), prec=prec, kcycle=kcycle, cluster_cells=cluster_cells,
-                 tile_fusion=tile_fusion, tile_fusion64=tile_fusion, eta_coarsen=eta_coarsen, coarsest_min=2)
+                 tile_fusion=tile_fusion, tile_fusion64=tile_fusion, eta_coarsen=eta_coarsen, coarsest_min=2,
+                 smoother=smoother, ras_inner=ras_inner, omega_v=omega)
     Zx, Zy, Zp = zeros(ny, nx), zeros(ny, nx), zeros(ny, nx)
     h.precond(dev(en), dev(ec), dev(rx), dev(ry), dev(rp), Zx, Zy, Zp)
     torch.cuda.synchronize()
@@ -89,6 +91,26 @@ def test_preconditioner_geometric_eta_coarsening_matches_oracle(prec, tf, field)
         # FP32: the cycle's rounding is amplified by the field's contrast (1e9 for the layered one)
         tol = 1e-11 if prec == P.PREC_FP64 else (2e-4 if field == "random" else 5e-3)
         assert rel(a, b) <= tol, (rel(a, b), nlev)
+
+
+@pytest.mark.parametrize("nx,ny,Lx,Ly", [(48, 80, 0.6, 1.0), (64, 64, 1, 1), (256, 96, 2, 0.75)])
+@pytest.mark.parametrize("smoother,inner", [(P.SMOOTH_JACOBI, 1), (P.SMOOTH_RAS, 1), (P.SMOOTH_RAS, 2),
+                                            (P.SMOOTH_RAS, 4)])
+@pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
+def test_preconditioner_jacobi_smoothers_match_oracle(nx, ny, Lx, Ly, smoother, inner, prec):
+    """The paper's damped Jacobi and RAS-type temporally blocked Jacobi smoothers (32 x 32 tiles,
+    shifted tilings, inner local iterations) inside the V-cycle, step by step against the oracle."""
+    gpu, ora, nlev = _precond_case(nx, ny, Lx, Ly, "free", prec, 19, smoother=smoother, ras_inner=inner, omega=0.6)
+    for a, b in zip(gpu, ora):
+        assert rel(a, b) <= (1e-11 if prec == P.PREC_FP64 else 2e-4), (rel(a, b), nlev)
+
+
+@pytest.mark.parametrize("smoother,inner", [(P.SMOOTH_JACOBI, 1), (P.SMOOTH_RAS, 2)])
+@pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
+def test_sinker_with_jacobi_smoothers_matches_direct_oracle(smoother, inner, prec):
+    f = sinker(64, 64)
+    out, st = _solve_gpu(f, (0.0, 1.0), 1e-12, prec, smoother=smoother, ras_inner=inner, omega_v=0.6, max_iter=3000)
+    _check_against_direct(f, out, st, tol=1e-12, tol_err=1e-8)
 
 
 @pytest.mark.parametrize("nx,ny,Lx,Ly", [(32, 32, 1, 1), (48, 80, 0.6, 1.0)])

@@ -198,3 +198,83 @@ def test_kcycle_pins():
                 r0 = np.linalg.norm(rv - L @ x)
         return (np.linalg.norm(rv - L @ x) / r0) ** (1 / 5)
     assert rate(99) < 0.7 * rate(0)
+
+
+# ---- the paper's other smoothers (damped Jacobi, RAS-type temporally blocked Jacobi) -------------
+def _small_velocity_system(nx=12, ny=10, seed=41):
+    g = S.Grid(nx, ny, 1.0, 0.8)
+    rng = np.random.default_rng(seed)
+    en = 10.0 ** rng.uniform(-1, 1, (ny + 2, nx + 2))
+    ec = 10.0 ** rng.uniform(-1, 1, (ny + 2, nx + 2))
+    L = S.assemble(g, en, ec, velocity_only=True).A.tocsr()
+    f = rng.standard_normal(g.n_v)
+    x0 = rng.standard_normal(g.n_v)
+    return g, L, f, x0
+
+
+def test_splitmix64_matches_published_reference_outputs():
+    """First five outputs of the public-domain reference implementation (splitmix64.c, S. Vigna;
+    generator of Steele, Lea & Flood, OOPSLA 2014) for seed 1234567."""
+    ref = [6457827717110365317, 3203168211198807973, 9817491932198370423, 4593380528125082431,
+           16408922859458223821]
+    z = 1234567
+    for r in ref:
+        assert M.splitmix64(z) == r
+        z = (z + 0x9E3779B97F4A7C15) % (1 << 64)
+
+
+def test_damped_jacobi_converges_to_the_direct_solution():
+    g, L, f, x0 = _small_velocity_system()
+    x = x0.copy()
+    for _ in range(6000):
+        x = M.jacobi_sweep(L, f, x, 0.5)
+    xs = spla.spsolve(L.tocsc(), f)
+    assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("si,sj,T", [(0, 0, 4), (3, 1, 4), (2, 5, 6)])
+def test_ras_with_one_inner_iteration_is_one_jacobi_sweep(si, sj, T):
+    g, L, f, x0 = _small_velocity_system()
+    a = M.ras_pass(g, L, f, x0, 0.7, 1, T, T, si, sj)
+    b = M.jacobi_sweep(L, f, x0, 0.7)
+    assert np.allclose(a, b, rtol=1e-13, atol=1e-13)
+
+
+def test_ras_with_one_tile_is_plain_jacobi():
+    g, L, f, x0 = _small_velocity_system()
+    a = M.ras_pass(g, L, f, x0, 0.6, 5, 1000, 1000, 0, 0)
+    b = x0
+    for _ in range(5):
+        b = M.jacobi_sweep(L, f, b, 0.6)
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-12)
+
+
+def test_ras_with_single_cell_tiles_converges_to_block_jacobi():
+    """Tiles of one cell own vx(i, j) and vy(i, j); many local iterations solve each cell's 1x1 or
+    2x2 block exactly with everything else held: block Jacobi, computed here by direct solves."""
+    g, L, f, x0 = _small_velocity_system()
+    a = M.ras_pass(g, L, f, x0, 1.0, 200, 1, 1, 0, 0)
+    vi = np.concatenate([g.vx_i, g.vy_i]); vj = np.concatenate([g.vx_j, g.vy_j])
+    Ld = L.toarray()
+    b = x0.copy()
+    for key in set(zip(vi, vj)):
+        S_ = np.nonzero((vi == key[0]) & (vj == key[1]))[0]
+        O_ = np.setdiff1d(np.arange(len(x0)), S_)
+        rhs = f[S_] - Ld[np.ix_(S_, O_)] @ x0[O_]
+        b[S_] = np.linalg.solve(Ld[np.ix_(S_, S_)], rhs)
+    assert np.allclose(a, b, rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "ras"])
+def test_vcycle_with_jacobi_smoothers_contracts(smoother):
+    g = S.Grid(32, 32)
+    rng = np.random.default_rng(43)
+    en = 10.0 ** rng.uniform(-0.5, 0.5, (34, 34)); ec = 10.0 ** rng.uniform(-0.5, 0.5, (34, 34))
+    h = M.Hierarchy(g, en, ec, coarsest_min=4, smoother=smoother, ras_inner=2, ras_tile=8)
+    L = h.L[0]
+    e = rng.standard_normal(L.shape[0])
+    for _ in range(6):
+        e_new = e - M.vcycle(h, L @ e, 2, 2, 0.6)
+        rate = np.linalg.norm(e_new) / np.linalg.norm(e)
+        e = e_new
+    assert rate < 0.8
