@@ -299,7 +299,7 @@ def profile_solve(args):
     outs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
     prec = P.PREC_MIXED if args.prec == "mixed" else P.PREC_FP64
     h = P.Stokes(n, n, prec=prec, max_iter=args.max_iter, restart_m=args.restart, tile_fusion=args.tile_fusion,
-                 tile_sweeps=args.tile_sweeps)
+                 tile_sweeps=args.tile_sweeps, smoother=args.smoother, omega_v=args.omega, accel=args.accel)
     st = h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
     torch.cuda.synchronize()
     print(json.dumps({"profile_solve": n, "prec": args.prec, "iters": st.iters, "status": st.status,
@@ -347,6 +347,9 @@ def main():
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--tile-fusion", type=int, default=2, help="pyro_opts.tile_fusion of the --profile solve")
     ap.add_argument("--tile-sweeps", type=int, default=2, help="pyro_opts.tile_sweeps of the --profile solve")
+    ap.add_argument("--smoother", type=int, default=0, help="pyro_opts.smoother of the --profile solve")
+    ap.add_argument("--omega", type=float, default=1.0, help="pyro_opts.omega_v of the --profile solve")
+    ap.add_argument("--accel", type=int, default=0, help="pyro_opts.accel of the --profile solve")
     args = ap.parse_args()
     rank, world, local = env_rank()
     import torch
