@@ -161,6 +161,8 @@ def vcycle_rooflines(peaks):
     sweep) heads the object; the default RBGS tile kernels and the RAS-type pass are variants."""
     main = vcycle_roofline_4096(peaks, label="k_jacobi<float> (damped Jacobi sweep, smoother=JACOBI, omega 0.6)",
                                 launches=2, smoother=1, omega_v=0.6)
+    main["traffic"] = 525.78e6
+    main["traffic_source"] = "ncu dram__bytes_read+write of one launch (profiles/k_jacobi_fp32_4096_level0.md)"
     main["variants"] = {}
     for key, label, launches, opts in [
             ("rbgs_tiles_2_sweeps_default", "k_rbgs_tile_cs<2,64,32> (2 RBGS sweeps per launch, the default)", 1,
@@ -442,7 +444,10 @@ def main():
     fp64_peak = 1.25  # TFLOP/s nominal B300 FP64 (about 2 FMA per clock per SM at 2.03 GHz); a probe measured 1.13
     roof = {"kernel": "k_rbgs<double> finest level (one sweep = 4 launches)", "bound": "alu",
             "achieved": achieved_flops, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved_flops / fp64_peak,
-            "traffic": None, "peak_source": "nominal B300 FP64 rate 1.25 TFLOP/s (148 SMs x ~2.08 FMA/clk x 2 flop x 2.03 GHz); not in MEASURED_PEAKS.json",
+            "traffic": 4 * 59.67e6, "traffic_unit": "B per sweep",
+            "traffic_source": "ncu dram__bytes_read+write of the level-0 vx-red launch (59.67 MB, profiles/k_rbgs_fp64_1024_level0.md) x 4 half-sweeps",
+            "fp64_pipe_active_pct_ncu": 80.5,
+            "peak_source": "nominal B300 FP64 rate 1.25 TFLOP/s (148 SMs x ~2.08 FMA/clk x 2 flop x 2.03 GHz); not in MEASURED_PEAKS.json",
             "flop_per_cell_sweep": 42,
             "hbm_equiv_GBps": bytes_per_sweep / (sweep_ms / 1e3) / 1e9, "hbm_peak_measured": peaks.get("hbm_gbs"),
             "sweep_ms": sweep_ms, "phase_ms_per_iter": {k: v / max(counts["iterations"], 1) for k, v in phases.items()}}

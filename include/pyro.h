@@ -132,6 +132,14 @@ typedef struct {
   double aa_beta;        /* Anderson mixing beta in (0, 1] (the paper suggests 0.5-0.8) [1.0] */
   int smoother;          /* pyro_smoother [PYRO_SMOOTH_RBGS] */
   int ras_inner;         /* RAS smoother: local Jacobi iterations per tile pass (T_inner) [4] */
+  int litho_guess;       /* 1: start the pressure from the lithostatic column integral of rho g_y
+                            (Sec. "Viscosity Rescaling and Initial Guess"; cell pressures going down
+                            differ by dy g_y times the vy-node density) when not warm-starting [0] */
+  int cont_stages;       /* viscosity-contrast continuation (same section): > 0 runs cont_stages
+                            stages with eta_comp = (1 - theta) eta_min + theta eta, theta = k /
+                            cont_stages, each cont_iters outer iterations from the previous stage's
+                            iterate, then the full-contrast solve; 0 = off [0] */
+  int cont_iters;        /* outer iterations per continuation stage (the paper: 25) [25] */
 } pyro_opts;
 
 typedef struct {

@@ -351,6 +351,33 @@ def solve_fields(nx, ny, Lx, Ly, eta_n, eta_c, rho, g, bc=None):
 
 
 # ---- adjoint by linearity of the assembly in eta -----------------------------------------------
+def blend_viscosity(eta_n, eta_c, theta, nx, ny):
+    """Viscosity-contrast continuation (Sec. "Viscosity Rescaling and Initial Guess"):
+    eta_comp = (1 - theta) eta_min + theta eta, eta_min the smallest viscosity of the real nodes
+    (i in [0, ny], j in [0, nx]) and cells (i, j in [1, n]). Padding entries are left as given."""
+    emin = min(eta_n[:ny + 1, :nx + 1].min(), eta_c[1:ny + 1, 1:nx + 1].min())
+    en = eta_n.copy(); ec = eta_c.copy()
+    en[:ny + 1, :nx + 1] = (1 - theta) * emin + theta * eta_n[:ny + 1, :nx + 1]
+    ec[1:ny + 1, 1:nx + 1] = (1 - theta) * emin + theta * eta_c[1:ny + 1, 1:nx + 1]
+    return en, ec
+
+
+def lithostatic_pressure(grid, rho, g):
+    """Lithostatic initial pressure p = int_0^y rho g_y dy' (Sec. "Viscosity Rescaling and Initial
+    Guess"), in this discretisation: going down a column, consecutive cell pressures differ by
+    dy g_y rho_vy with rho_vy the density of the vy node between them (the mean of its two basic
+    nodes, as in the y-momentum right-hand side); zero volume-weighted mean. Returns the padded
+    (ny+2) x (nx+2) pressure array (cells only)."""
+    nx, ny, dy = grid.nx, grid.ny, grid.dy
+    p = np.zeros((ny + 2, nx + 2))
+    for j in range(1, nx + 1):
+        for i in range(1, ny):
+            rho_vy = 0.5 * (rho[i, j - 1] + rho[i, j])
+            p[i + 1, j] = p[i, j] + dy * g[1] * rho_vy
+    p[1:ny + 1, 1:nx + 1] -= p[1:ny + 1, 1:nx + 1].mean()
+    return p
+
+
 def eta_gradient_by_linearity(grid, eta_n, eta_c, x, lam, cells=None, nodes=None):
     """dJ/d eta_k = -lam^T A_k x with A_k = A(e_k) - A(0), both from this module's assembler.
 

@@ -476,6 +476,57 @@ __global__ void k_rho_grad(GeomT<double> g, const double* __restrict__ lam, doub
   gr[c] = s;
 }
 
+// ---- viscosity-contrast continuation and lithostatic initial guess (Sec. "Viscosity Rescaling
+// and Initial Guess") ---------------------------------------------------------------------------
+// per-block minimum of the real nodes (i in [0, ny], j in [0, nx]) and cells of eta
+__global__ void k_eta_min(GeomT<double> g, const double* __restrict__ en, const double* __restrict__ ec,
+                          double* __restrict__ part) {
+  __shared__ double sh[32];
+  const size_t P = (size_t)(g.ny + 2) * g.ld;
+  const int cols = g.nx + 2;
+  double m = INFINITY;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / cols), j = (int)(e % cols);
+    if (i <= g.ny && j <= g.nx) m = fmin(m, en[e]);
+    if (is_p(g.nx, g.ny, i, j)) m = fmin(m, ec[e]);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = sh[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmin(r, sh[w]);
+    part[blockIdx.x] = r;
+  }
+}
+
+// eta_comp = (1 - theta) eta_min + theta eta on the real nodes and cells, padding copied
+__global__ void k_eta_blend(GeomT<double> g, const double* __restrict__ en_full, const double* __restrict__ ec_full,
+                            double* __restrict__ en, double* __restrict__ ec, double theta, double emin) {
+  const size_t P = (size_t)(g.ny + 2) * g.ld;
+  const int cols = g.nx + 2;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / cols), j = (int)(e % cols);
+    en[e] = (i <= g.ny && j <= g.nx) ? (1.0 - theta) * emin + theta * en_full[e] : en_full[e];
+    ec[e] = is_p(g.nx, g.ny, i, j) ? (1.0 - theta) * emin + theta * ec_full[e] : ec_full[e];
+  }
+}
+
+// lithostatic pressure down each column: p(1, j) = 0, p(i+1, j) = p(i, j) + dy g_y rho_vy(i, j),
+// rho_vy the mean of the two basic nodes of the vy node between the cells (one thread per column;
+// the mean is removed afterwards)
+__global__ void k_litho(GeomT<double> g, const double* __restrict__ rho, double gy, double dy, double* __restrict__ p) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  if (j > g.nx) return;
+  double acc = 0.0;
+  p[(size_t)1 * g.ld + j] = 0.0;
+  for (int i = 1; i < g.ny; ++i) {
+    const size_t c = (size_t)i * g.ld + j;
+    acc += dy * gy * (0.5 * (rho[c - 1] + rho[c]));
+    p[c + g.ld] = acc;
+  }
+}
+
 // ---- flexible GCR(m) (Sec. "Generalized Conjugate Residual Method", Algorithm gcr) -----------------
 // After the Gram-Schmidt passes: w_j = w / nu and z_j = z / nu go to slot j of the two bases,
 // with per-block partials of <r, w_j>_W (alpha = that, since ||w_j||_W = 1).

@@ -497,6 +497,7 @@ struct pyro_stokes_s {
          *ydev = nullptr;
   int *d_j = nullptr, *flag = nullptr;
   double* zc = nullptr;                    // GCR / Anderson: the current preconditioned residual
+  double *en_full = nullptr, *ec_full = nullptr;  // continuation: the full-contrast viscosity
   int *d_slot = nullptr, *d_cnt = nullptr;  // Anderson: history slot of this step, pairs stored
   // pinned host scratch
   double* hbuf = nullptr;
@@ -1052,6 +1053,36 @@ int outer_solve(pyro_stokes_s* h, double tol, pyro_stats* st, cudaStream_t s) {
   return fgmres(h, tol, st, s);
 }
 
+// Viscosity-contrast continuation: cont_stages stages with theta = k / cont_stages (k = 0 ..
+// cont_stages - 1), each cont_iters iterations of the outer solver on eta_comp = (1 - theta)
+// eta_min + theta eta from the previous stage's iterate, then the full-contrast solve to tol.
+int continuation_solve(pyro_stokes_s* h, double tol, pyro_stats* st, cudaStream_t s) {
+  CK(cudaMemcpyAsync(h->en_full, h->en, h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->ec_full, h->ec, h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  k_eta_min<<<kReduceBlocks, kThreads, 0, s>>>(h->g64, h->en, h->ec, h->partial);
+  h->launches += 1;
+  CK(cudaMemcpyAsync(h->hbuf, h->partial, kReduceBlocks * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double emin = h->hbuf[0];
+  for (int b = 1; b < kReduceBlocks; ++b) emin = std::min(emin, h->hbuf[b]);
+  const int max_iter = h->o.max_iter;
+  int status = PYRO_OK;
+  for (int k = 0; k < h->o.cont_stages; ++k) {
+    const double theta = (double)k / h->o.cont_stages;
+    k_eta_blend<<<kReduceBlocks, kThreads, 0, s>>>(h->g64, h->en_full, h->ec_full, h->en, h->ec, theta, emin);
+    h->launches += 1;
+    setup_eta(h, s);
+    h->o.max_iter = h->o.cont_iters;
+    status = outer_solve(h, tol, st, s);
+    h->o.max_iter = max_iter;
+    if (status < 0) return status;
+  }
+  CK(cudaMemcpyAsync(h->en, h->en_full, h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->ec, h->ec_full, h->P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  setup_eta(h, s);
+  return outer_solve(h, tol, st, s);
+}
+
 void validate_opts(pyro_opts& o) {
   if (o.nu1 < 0) o.nu1 = 0;
   if (o.nu2 < 0) o.nu2 = 0;
@@ -1066,6 +1097,8 @@ void validate_opts(pyro_opts& o) {
   if (!(o.aa_beta > 0.0) || o.aa_beta > 1.0) o.aa_beta = 1.0;
   if (o.smoother < PYRO_SMOOTH_RBGS || o.smoother > PYRO_SMOOTH_RAS) o.smoother = PYRO_SMOOTH_RBGS;
   if (o.ras_inner < 1) o.ras_inner = 1;
+  if (o.cont_stages < 0) o.cont_stages = 0;
+  if (o.cont_iters < 1) o.cont_iters = 1;
 }
 
 int check_size(int nx, int ny, const pyro_opts& o) {
@@ -1091,6 +1124,7 @@ size_t footprint_bytes(int nx, int ny, const pyro_opts& o, int L) {
   b += (m + 1) * n3 * 8;           // V
   b += (m + 1) * n3 * 8;           // Z (preconditioned vectors; FP32-valued velocities in mixed mode)
   b += n3 * 8 + 16;                // GCR / Anderson current direction, Anderson slot indices
+  if (o.cont_stages > 0) b += 2 * P * 8;   // full-contrast viscosity kept during continuation
   b += mixed ? MG<float>::bytes(nx, ny, L, o.kcycle) : MG<double>::bytes(nx, ny, L, o.kcycle) - 2 * P * 8;
   b += 2 * kSubCluster * 4 * 8;
   b += 2 * (kMaxRestart + 2) * 8 + 2 * (size_t)kReduceBlocks * (kMaxRestart + 1) * 8 + 4 * kReduceBlocks * 8 +
@@ -1125,6 +1159,9 @@ void pyro_default_opts(pyro_opts* o) {
   o->aa_beta = 1.0;
   o->smoother = PYRO_SMOOTH_RBGS;
   o->ras_inner = 4;
+  o->litho_guess = 0;
+  o->cont_stages = 0;
+  o->cont_iters = 25;
 }
 
 const char* pyro_version(void) { return "pyro-b300 0.1 (sm_103a)"; }
@@ -1197,6 +1234,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
     h->V = A.get<double>((size_t)(h->m + 1) * h->n3);
     h->Z = A.get<double>((size_t)(h->m + 1) * h->n3);   // m for FGMRES / GCR, m + 1 for Anderson
     h->zc = A.get<double>(h->n3);
+    if (o.cont_stages > 0) { h->en_full = A.get<double>(h->P); h->ec_full = A.get<double>(h->P); }
     h->d_slot = A.get<int>(2);
     h->d_cnt = h->d_slot + 1;
     h->h1 = A.get<double>(kMaxRestart + 2); h->h2 = A.get<double>(kMaxRestart + 2);
@@ -1403,7 +1441,16 @@ int pyro_stokes_solve(pyro_stokes h, const double* eta_n, const double* eta_c, c
       cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
       st.t_setup_ms = ms;
       if (*h->hflag & FLAG_BREAKDOWN) status = PYRO_E_BREAKDOWN;
-      else status = outer_solve(h, tol, &st, s);
+      else {
+        if (h->o.litho_guess && !h->o.warm_start) {
+          k_litho<<<(h->nx + 127) / 128, 128, 0, s>>>(h->g64, h->rho, gy, h->g.dy, h->x + 2 * h->P);
+          k_psum<<<kReduceBlocks, kThreads, 0, s>>>(h->g64, h->x + 2 * h->P, h->part2);
+          k_sub_mean<double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, h->x + 2 * h->P, 0, nullptr, h->part2,
+                                                                kReduceBlocks);
+          h->launches += 3;
+        }
+        status = h->o.cont_stages > 0 ? continuation_solve(h, tol, &st, s) : outer_solve(h, tol, &st, s);
+      }
     }
     if (status >= 0) {
       CK(cudaMemcpyAsync(h->xf, h->x, h->n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));

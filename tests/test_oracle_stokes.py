@@ -187,3 +187,34 @@ def test_energy_residual_special_values():
     rr = S.System(g, sysm.A, sysm.b + r)
     e1, _ = S.energy_residual(rr, f.eta_c, x)
     assert e1 == pytest.approx(np.sqrt(9.0 * wp / fw), rel=1e-6)
+
+
+def test_lithostatic_pressure_balances_horizontally_layered_density():
+    """For rho varying with depth only (any viscosity, any horizontal gravity-free column), the
+    lithostatic pressure with v = 0 is the exact discrete solution: the oracle's assembled
+    residual vanishes."""
+    nx, ny = 12, 16
+    en, ec = rand_eta(nx, ny, 8)
+    rho = np.repeat(1.0 + 0.3 * np.sin(np.arange(ny + 2) * 0.7)[:, None], nx + 2, axis=1)
+    g = S.Grid(nx, ny, 1.0, 1.4)
+    p = S.lithostatic_pressure(g, rho, (0.0, 2.5))
+    sysm = S.assemble(g, en, ec, rho, (0.0, 2.5))
+    x = S.fields_to_vector(g, np.zeros_like(p), np.zeros_like(p), p)
+    r = sysm.b - sysm.A @ x
+    assert np.abs(r).max() <= 1e-12 * np.abs(sysm.b).max()
+    sol = S.solve_fields(nx, ny, 1.0, 1.4, en, ec, rho, (0.0, 2.5))
+    assert np.abs(sol.p[1:ny + 1, 1:nx + 1] - p[1:ny + 1, 1:nx + 1]).max() <= 1e-10 * np.abs(p).max()
+
+
+def test_viscosity_blend_end_points_and_contrast():
+    nx, ny = 10, 8
+    en, ec = rand_eta(nx, ny, 9)
+    emin = min(en[:ny + 1, :nx + 1].min(), ec[1:ny + 1, 1:nx + 1].min())
+    a_n, a_c = S.blend_viscosity(en, ec, 0.0, nx, ny)
+    assert np.all(a_n[:ny + 1, :nx + 1] == emin) and np.all(a_c[1:ny + 1, 1:nx + 1] == emin)
+    b_n, b_c = S.blend_viscosity(en, ec, 1.0, nx, ny)
+    assert np.array_equal(b_n, en) and np.array_equal(b_c, ec)
+    h_n, h_c = S.blend_viscosity(en, ec, 0.5, nx, ny)
+    emax = max(en[:ny + 1, :nx + 1].max(), ec[1:ny + 1, 1:nx + 1].max())
+    # the contrast of the blend is (emin + emax) / (2 emin), monotone in theta
+    assert np.isclose(max(h_n[:ny + 1, :nx + 1].max(), h_c[1:ny + 1, 1:nx + 1].max()) / emin, (emin + emax) / (2 * emin))
