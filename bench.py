@@ -212,6 +212,42 @@ def accelerator_sample(f, n, steps=3):
     return res
 
 
+def marker_sample(n=1024, per_cell=16, reps=5):
+    """Marker <-> grid interpolation (the marker-in-cell step around the solve): 16 markers per cell
+    on 1024^2, uniform random positions; marker -> basic nodes (deterministic bucketed gather) and
+    grid -> markers (bilinear), CUDA events. Minimal traffic: 24 B per marker read (x, y, phi) for
+    the scatter, 24 B per marker (x, y in, phi out) for the gather."""
+    import torch
+    import paper_2603_14040_b300 as P
+    m = per_cell * n * n
+    g = torch.Generator(device="cuda").manual_seed(5)
+    xm = torch.rand(m, dtype=torch.float64, device="cuda", generator=g)
+    ym = torch.rand(m, dtype=torch.float64, device="cuda", generator=g)
+    ph = torch.rand(m, dtype=torch.float64, device="cuda", generator=g)
+    grid = torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda")
+    back = torch.zeros(m, dtype=torch.float64, device="cuda")
+    mk = P.Markers(n, n, 1.0, 1.0, max_markers=m)
+    res = {}
+    for name, fn in (("markers_to_grid", lambda: mk.to_grid(P.LATTICE_NODES, xm, ym, ph, grid)),
+                     ("grid_to_markers", lambda: mk.to_markers(P.LATTICE_NODES, xm, ym, grid, back))):
+        fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        res[name] = {"ms": ms, "markers_per_s": m / (ms / 1e3), "min_traffic_GBps": 24.0 * m / (ms / 1e3) / 1e9}
+    mk.close()
+    res["markers"] = m
+    res["grid"] = [n, n]
+    return res
+
+
 def serving_sample(n_req=48, slots=4, max_iter=3000, restart_m=200, seed=4):
     """Continuous batching on a bounded sample of the serving workload: requests with n in
     {128, 256, 512}, aspect in {1, 2, 4}, 16 inclusions of contrast 10^U[2,6], tol 1e-8, Poisson
@@ -486,6 +522,7 @@ def main():
     if rank == 0 and not args.no_extras:
         line["vcycle_roofline"] = vcycle_rooflines(peaks)
         line["accelerators"] = accelerator_sample(f, n)
+        line["markers"] = marker_sample()
         line["serving"] = serving_sample()
         line["adjoint"] = adjoint_sample()
     if rank == 0 and not args.no_cpu_baseline:

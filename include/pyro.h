@@ -257,6 +257,41 @@ const char* pyro_strerror(int status);
 /* Library version string. */
 const char* pyro_version(void);
 
+/* ---- marker <-> grid interpolation (the marker-in-cell step that feeds eta and rho to the solve:
+ * Sec. "Marker-to-grid interpolation" and "Grid-to-marker interpolation") ---------------------
+ * Lattices in the padded (ny+2) x (nx+2) layout, row i with y:
+ *   PYRO_LATTICE_NODES  basic nodes  x_j = j dx,         y_i = i dy,         i in [0,ny], j in [0,nx]
+ *   PYRO_LATTICE_CELLS  cell centres x_j = (j - 1/2) dx, y_i = (i - 1/2) dy, i in [1,ny], j in [1,nx]
+ * A marker belongs to the lattice cell whose top-left node lies at or left/above it (clamped into
+ * the outermost cell when it lies beyond the lattice). Bilinear weights: that node (1-fx)(1-fy),
+ * its right neighbour fx(1-fy), the node below (1-fx)fy, the diagonal fx fy, with fx = r_x/dx,
+ * fy = r_y/dy the offsets from the top-left node. */
+typedef enum { PYRO_LATTICE_NODES = 0, PYRO_LATTICE_CELLS = 1 } pyro_lattice;
+typedef struct pyro_markers_s* pyro_markers;  /* opaque; owns the bucketing workspace */
+
+/* Workspace for an nx x ny grid of size Lx x Ly and up to max_markers markers (about
+ * 24 B x max_markers + 12 B x cells of device memory). PYRO_E_INVALID on bad sizes,
+ * PYRO_E_NOMEM if allocation fails. */
+int pyro_markers_create(int nx, int ny, double Lx, double Ly, long long max_markers, pyro_markers* out);
+
+/* Marker -> grid weighted average: grid(i,j) = sum_m w_m(i,j) phi_m / sum_m w_m(i,j) over the
+ * markers of the four lattice cells around the node; nodes no marker reaches keep their input
+ * value; wsum (optional) receives the weight sums (0 where no marker reaches). Deterministic: the
+ * markers are bucketed by cell with integer atomics, each bucket sorted by marker index, and each
+ * node sums its four cells in a fixed order. xm, ym, phim: n device doubles; grid, wsum: device
+ * (ny+2) x (nx+2) arrays. Synchronises cuda_stream before it returns. PYRO_E_INVALID for host
+ * pointers, n > max_markers or an unknown lattice; PYRO_E_NONFINITE if a position is not finite. */
+int pyro_markers_to_grid(pyro_markers h, int lattice, long long n, const double* xm, const double* ym,
+                         const double* phim, double* grid, double* wsum, void* cuda_stream);
+
+/* Grid -> marker bilinear interpolation phi_m = sum over the four corners of w grid (the weights
+ * sum to one). Device pointers; stream-ordered, returns after enqueueing. */
+int pyro_grid_to_markers(pyro_markers h, int lattice, long long n, const double* xm, const double* ym,
+                         const double* grid, double* phim, void* cuda_stream);
+
+/* Release the workspace (NULL is a no-op). */
+void pyro_markers_destroy(pyro_markers h);
+
 #ifdef __cplusplus
 }
 #endif

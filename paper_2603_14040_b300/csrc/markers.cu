@@ -1,0 +1,269 @@
+// Marker <-> grid interpolation of the marker-in-cell loop (Sec. "Marker-to-grid interpolation"
+// and "Grid-to-marker interpolation"), the step that feeds eta and rho to the Stokes solve.
+//
+// Marker -> grid is a weighted average over the markers around each lattice node with bilinear
+// weights. The paper accumulates with atomics; floating-point atomics make the result depend on
+// the arrival order, so here the markers are bucketed by lattice cell (integer atomics only: the
+// counts and slots), each bucket is sorted by marker index, and every node gathers from the four
+// cells around it in a fixed order. The result is deterministic and independent of the launch.
+//
+// Lattices: basic nodes (x_j = j dx, y_i = i dy, i in [0, ny], j in [0, nx]) or cell centres
+// (x_j = (j - 1/2) dx, y_i = (i - 1/2) dy, i, j in [1, n]) in the padded (ny+2) x (nx+2) layout;
+// row i goes with y. A marker belongs to the lattice cell whose top-left node is at or left/above
+// it (clamped into the outermost cell when it lies beyond the lattice); that node takes the weight
+// (1 - fx)(1 - fy), its right neighbour fx (1 - fy), the one below (1 - fx) fy, the diagonal fx fy.
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <new>
+
+#include "../../include/pyro.h"
+#include "common.cuh"
+
+struct pyro_markers_s {
+  int dev = 0;
+  int nx = 0, ny = 0;
+  double Lx = 1, Ly = 1;
+  long long cap = 0;       // marker capacity
+  int* count = nullptr;    // per lattice cell (largest lattice: (ny + 1) x (nx + 1) cells)
+  int* offset = nullptr;   // exclusive prefix of count (+1 entry)
+  int* fill = nullptr;     // slots handed out per cell
+  int* bsum = nullptr;     // per-block sums of the scan
+  int* idx = nullptr;      // marker indices bucketed by cell
+  int* cell = nullptr;     // cell of each marker
+  double* frac = nullptr;  // (fx, fy) of each marker
+  int* flag = nullptr;
+};
+
+namespace {
+
+using namespace pyro;
+constexpr int kMkThreads = 256;
+constexpr int kScanBlock = 1024;
+
+struct Lat {
+  double x0, y0, idx, idy;
+  int ilo, ihi, jlo, jhi;  // lattice index range (inclusive)
+  int ncx, ncy;            // lattice cells per row / column
+};
+
+Lat make_lat(const pyro_markers_s* h, int kind) {
+  Lat L;
+  const double dx = h->Lx / h->nx, dy = h->Ly / h->ny;
+  L.idx = 1.0 / dx;
+  L.idy = 1.0 / dy;
+  if (kind == PYRO_LATTICE_CELLS) {
+    L.x0 = -0.5 * dx; L.y0 = -0.5 * dy; L.ilo = 1; L.ihi = h->ny; L.jlo = 1; L.jhi = h->nx;
+  } else {
+    L.x0 = 0.0; L.y0 = 0.0; L.ilo = 0; L.ihi = h->ny; L.jlo = 0; L.jhi = h->nx;
+  }
+  L.ncx = L.jhi - L.jlo;
+  L.ncy = L.ihi - L.ilo;
+  return L;
+}
+
+__device__ inline void locate(const Lat& L, double x, double y, int& i, int& j, double& fx, double& fy) {
+  const double u = (x - L.x0) * L.idx, v = (y - L.y0) * L.idy;
+  const double fu = floor(u), fv = floor(v);
+  j = (int)fmin(fmax(fu, (double)L.jlo), (double)(L.jhi - 1));
+  i = (int)fmin(fmax(fv, (double)L.ilo), (double)(L.ihi - 1));
+  fx = fmin(fmax(u - j, 0.0), 1.0);
+  fy = fmin(fmax(v - i, 0.0), 1.0);
+}
+
+__global__ void k_mk_count(Lat L, long long n, const double* __restrict__ xm, const double* __restrict__ ym,
+                           int* __restrict__ cell, double* __restrict__ frac, int* __restrict__ count,
+                           int* __restrict__ flag) {
+  for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (long long)gridDim.x * blockDim.x) {
+    const double x = xm[m], y = ym[m];
+    if (!isfinite(x) || !isfinite(y)) { atomicOr(flag, FLAG_NONFINITE); cell[m] = -1; continue; }
+    int i, j;
+    double fx, fy;
+    locate(L, x, y, i, j, fx, fy);
+    const int c = (i - L.ilo) * L.ncx + (j - L.jlo);
+    cell[m] = c;
+    frac[2 * m] = fx;
+    frac[2 * m + 1] = fy;
+    atomicAdd(&count[c], 1);
+  }
+}
+
+// exclusive scan of count[0..n) into offset[0..n]: per-block scans, then the block sums
+__global__ void k_scan_blocks(const int* __restrict__ in, int* __restrict__ out, int n, int* __restrict__ bsum) {
+  __shared__ int s[kScanBlock];
+  const int g = blockIdx.x * kScanBlock + threadIdx.x;
+  s[threadIdx.x] = g < n ? in[g] : 0;
+  __syncthreads();
+  for (int d = 1; d < kScanBlock; d <<= 1) {     // Hillis-Steele inclusive scan
+    const int t = threadIdx.x >= d ? s[threadIdx.x - d] : 0;
+    __syncthreads();
+    s[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (g < n) out[g] = s[threadIdx.x] - (g < n ? in[g] : 0);
+  if (threadIdx.x == kScanBlock - 1) bsum[blockIdx.x] = s[threadIdx.x];
+}
+
+__global__ void k_scan_sums(int* __restrict__ bsum, int nb) {   // one thread, nb small
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int acc = 0;
+  for (int b = 0; b < nb; ++b) { const int t = bsum[b]; bsum[b] = acc; acc += t; }
+  bsum[nb] = acc;
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__ bsum) {
+  const int g = blockIdx.x * kScanBlock + threadIdx.x;
+  if (g < n) out[g] += bsum[blockIdx.x];
+  if (g == 0) out[n] = bsum[gridDim.x];
+}
+
+__global__ void k_mk_scatter(long long n, const int* __restrict__ cell, const int* __restrict__ offset,
+                             int* __restrict__ fill, int* __restrict__ idx) {
+  for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (long long)gridDim.x * blockDim.x) {
+    const int c = cell[m];
+    if (c < 0) continue;
+    idx[offset[c] + atomicAdd(&fill[c], 1)] = (int)m;
+  }
+}
+
+// insertion sort of each cell's bucket by marker index (buckets hold a few to a few tens)
+__global__ void k_mk_sort(int ncell, const int* __restrict__ offset, int* __restrict__ idx) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int a = offset[c], b = offset[c + 1];
+  for (int k = a + 1; k < b; ++k) {
+    const int v = idx[k];
+    int q = k - 1;
+    while (q >= a && idx[q] > v) { idx[q + 1] = idx[q]; --q; }
+    idx[q + 1] = v;
+  }
+}
+
+// phi(i, j) = sum w phi_m / sum w over the markers of the four cells around node (i, j), cells in
+// the order (i-1, j-1), (i-1, j), (i, j-1), (i, j), markers in index order within a cell
+__global__ void k_mk_gather(Lat L, int ld, const int* __restrict__ offset, const int* __restrict__ idx,
+                            const double* __restrict__ frac, const double* __restrict__ phim,
+                            double* __restrict__ grid, double* __restrict__ wsum) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x + L.jlo;
+  const int i = blockIdx.y * blockDim.y + threadIdx.y + L.ilo;
+  if (i > L.ihi || j > L.jhi) return;
+  double num = 0.0, den = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    const int ci = i - 1 + (q >> 1), cj = j - 1 + (q & 1);     // cell with top-left node (ci, cj)
+    if (ci < L.ilo || ci > L.ihi - 1 || cj < L.jlo || cj > L.jhi - 1) continue;
+    const int c = (ci - L.ilo) * L.ncx + (cj - L.jlo);
+    const bool right = cj < j, below = ci < i;                   // this node is the cell's right / lower corner
+    for (int k = offset[c]; k < offset[c + 1]; ++k) {
+      const int m = idx[k];
+      const double fx = frac[2 * m], fy = frac[2 * m + 1];
+      const double w = (right ? fx : 1.0 - fx) * (below ? fy : 1.0 - fy);
+      num += w * phim[m];
+      den += w;
+    }
+  }
+  const size_t o = (size_t)i * ld + j;
+  if (den > 0.0) grid[o] = num / den;
+  if (wsum) wsum[o] = den;
+}
+
+__global__ void k_mk_to_markers(Lat L, int ld, long long n, const double* __restrict__ xm, const double* __restrict__ ym,
+                                const double* __restrict__ grid, double* __restrict__ phim) {
+  for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    double fx, fy;
+    locate(L, xm[m], ym[m], i, j, fx, fy);
+    const size_t o = (size_t)i * ld + j;
+    phim[m] = (1.0 - fx) * (1.0 - fy) * grid[o] + fx * (1.0 - fy) * grid[o + 1] + (1.0 - fx) * fy * grid[o + ld] +
+              fx * fy * grid[o + ld + 1];
+  }
+}
+
+bool on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int grid_blocks(long long n) { return (int)((n + kMkThreads - 1) / kMkThreads < 4 * 148 * 8 ? (n + kMkThreads - 1) / kMkThreads : 4 * 148 * 8); }
+
+}  // namespace
+
+extern "C" {
+
+int pyro_markers_create(int nx, int ny, double Lx, double Ly, long long max_markers, pyro_markers* out) {
+  if (!out || nx < 2 || ny < 2 || !(Lx > 0) || !(Ly > 0) || max_markers < 1 || max_markers > 2000000000LL)
+    return PYRO_E_INVALID;
+  *out = nullptr;
+  pyro_markers_s* h = new (std::nothrow) pyro_markers_s;
+  if (!h) return PYRO_E_NOMEM;
+  h->nx = nx; h->ny = ny; h->Lx = Lx; h->Ly = Ly; h->cap = max_markers;
+  cudaGetDevice(&h->dev);
+  const size_t ncell = (size_t)(nx + 1) * (ny + 1);
+  const size_t nb = (ncell + kScanBlock - 1) / kScanBlock + 1;
+  bool ok = cudaMalloc(&h->count, ncell * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->offset, (ncell + 1) * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->fill, ncell * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->bsum, nb * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->idx, (size_t)max_markers * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->cell, (size_t)max_markers * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->frac, (size_t)max_markers * 2 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&h->flag, sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    pyro_markers_destroy(h);
+    return PYRO_E_NOMEM;
+  }
+  *out = h;
+  return PYRO_OK;
+}
+
+int pyro_markers_to_grid(pyro_markers h, int lattice, long long n, const double* xm, const double* ym,
+                         const double* phim, double* grid, double* wsum, void* cuda_stream) {
+  if (!h || n < 0 || n > h->cap || (lattice != PYRO_LATTICE_NODES && lattice != PYRO_LATTICE_CELLS)) return PYRO_E_INVALID;
+  if (!grid || !on_device(grid) || (wsum && !on_device(wsum))) return PYRO_E_INVALID;
+  if (n > 0 && (!on_device(xm) || !on_device(ym) || !on_device(phim))) return PYRO_E_INVALID;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const Lat L = make_lat(h, lattice);
+  const int ncell = L.ncx * L.ncy;
+  const int nb = (ncell + kScanBlock - 1) / kScanBlock;
+  cudaSetDevice(h->dev);
+  cudaMemsetAsync(h->count, 0, (size_t)ncell * sizeof(int), s);
+  cudaMemsetAsync(h->fill, 0, (size_t)ncell * sizeof(int), s);
+  cudaMemsetAsync(h->flag, 0, sizeof(int), s);
+  if (n > 0) k_mk_count<<<grid_blocks(n), kMkThreads, 0, s>>>(L, n, xm, ym, h->cell, h->frac, h->count, h->flag);
+  k_scan_blocks<<<nb, kScanBlock, 0, s>>>(h->count, h->offset, ncell, h->bsum);
+  k_scan_sums<<<1, 32, 0, s>>>(h->bsum, nb);
+  k_scan_add<<<nb, kScanBlock, 0, s>>>(h->offset, ncell, h->bsum);
+  if (n > 0) k_mk_scatter<<<grid_blocks(n), kMkThreads, 0, s>>>(n, h->cell, h->offset, h->fill, h->idx);
+  k_mk_sort<<<(ncell + kMkThreads - 1) / kMkThreads, kMkThreads, 0, s>>>(ncell, h->offset, h->idx);
+  const dim3 b(32, 8), gr((L.jhi - L.jlo + 1 + 31) / 32, (L.ihi - L.ilo + 1 + 7) / 8);
+  k_mk_gather<<<gr, b, 0, s>>>(L, h->nx + 2, h->offset, h->idx, h->frac, n > 0 ? phim : nullptr, grid, wsum);
+  int flag = 0;
+  if (cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return PYRO_E_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return PYRO_E_CUDA;
+  return (flag & FLAG_NONFINITE) ? PYRO_E_NONFINITE : PYRO_OK;
+}
+
+int pyro_grid_to_markers(pyro_markers h, int lattice, long long n, const double* xm, const double* ym,
+                         const double* grid, double* phim, void* cuda_stream) {
+  if (!h || n < 0 || (lattice != PYRO_LATTICE_NODES && lattice != PYRO_LATTICE_CELLS)) return PYRO_E_INVALID;
+  if (n == 0) return PYRO_OK;
+  if (!on_device(grid) || !on_device(xm) || !on_device(ym) || !on_device(phim)) return PYRO_E_INVALID;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaSetDevice(h->dev);
+  const Lat L = make_lat(h, lattice);
+  k_mk_to_markers<<<grid_blocks(n), kMkThreads, 0, s>>>(L, h->nx + 2, n, xm, ym, grid, phim);
+  if (cudaGetLastError() != cudaSuccess) return PYRO_E_CUDA;
+  return PYRO_OK;
+}
+
+void pyro_markers_destroy(pyro_markers h) {
+  if (!h) return;
+  cudaFree(h->count); cudaFree(h->offset); cudaFree(h->fill); cudaFree(h->bsum);
+  cudaFree(h->idx); cudaFree(h->cell); cudaFree(h->frac); cudaFree(h->flag);
+  delete h;
+}
+
+}  // extern "C"

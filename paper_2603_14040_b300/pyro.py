@@ -49,7 +49,8 @@ class PyroStats(ctypes.Structure):
 
 EXPORTED = ["pyro_default_opts", "pyro_stokes_create", "pyro_stokes_footprint", "pyro_stokes_apply",
             "pyro_stokes_solve", "pyro_stokes_precond", "pyro_stokes_set_timing", "pyro_stokes_get_timing",
-            "pyro_stokes_residual_noalloc", "pyro_stokes_adjoint", "pyro_stokes_destroy", "pyro_strerror", "pyro_version"]
+            "pyro_stokes_residual_noalloc", "pyro_stokes_adjoint", "pyro_stokes_destroy", "pyro_strerror", "pyro_version",
+            "pyro_markers_create", "pyro_markers_to_grid", "pyro_grid_to_markers", "pyro_markers_destroy"]
 
 
 def load_library(path=_LIB_PATH):
@@ -84,6 +85,14 @@ def load_library(path=_LIB_PATH):
     lib.pyro_strerror.restype = ctypes.c_char_p
     lib.pyro_version.argtypes = []
     lib.pyro_version.restype = ctypes.c_char_p
+    lib.pyro_markers_create.argtypes = [I, I, D, D, ctypes.c_longlong, ctypes.POINTER(P)]
+    lib.pyro_markers_create.restype = I
+    lib.pyro_markers_to_grid.argtypes = [P, I, ctypes.c_longlong, P, P, P, P, P, P]
+    lib.pyro_markers_to_grid.restype = I
+    lib.pyro_grid_to_markers.argtypes = [P, I, ctypes.c_longlong, P, P, P, P, P]
+    lib.pyro_grid_to_markers.restype = I
+    lib.pyro_markers_destroy.argtypes = [P]
+    lib.pyro_markers_destroy.restype = None
     return lib
 
 
@@ -169,6 +178,50 @@ def residual_noalloc(nx, ny, Lx, Ly, bc, eta_n, eta_c, rho, g, vx, vy, p, r_vx, 
                                               _ptr(eta_n, s), _ptr(eta_c, s), _ptr(rho, s), float(g[0]),
                                               float(g[1]), _ptr(vx, s), _ptr(vy, s), _ptr(p, s), _ptr(r_vx, s),
                                               _ptr(r_vy, s), _ptr(r_p, s), _ptr(rel_res), _stream_handle(stream))
+
+
+LATTICE_NODES, LATTICE_CELLS = 0, 1
+
+
+class Markers:
+    """Marker <-> grid interpolation workspace (pyro_markers): CUDA float64 tensors in and out."""
+
+    def __init__(self, nx, ny, Lx=1.0, Ly=1.0, max_markers=1):
+        self.nx, self.ny, self.Lx, self.Ly = int(nx), int(ny), float(Lx), float(Ly)
+        h = ctypes.c_void_p()
+        st = lib().pyro_markers_create(self.nx, self.ny, self.Lx, self.Ly, int(max_markers), ctypes.byref(h))
+        if st != PYRO_OK:
+            raise PyroError(st, "pyro_markers_create")
+        self._h = h
+        self.shape = (self.ny + 2, self.nx + 2)
+
+    def to_grid(self, lattice, xm, ym, phim, grid, wsum=None, stream=None):
+        n = xm.numel()
+        st = lib().pyro_markers_to_grid(self._h, int(lattice), n, _ptr(xm, (n,)), _ptr(ym, (n,)), _ptr(phim, (n,)),
+                                        _ptr(grid, self.shape), _ptr(wsum, self.shape) if wsum is not None else None,
+                                        _stream_handle(stream))
+        if st < 0:
+            raise PyroError(st, "pyro_markers_to_grid")
+        return st
+
+    def to_markers(self, lattice, xm, ym, grid, phim, stream=None):
+        n = xm.numel()
+        st = lib().pyro_grid_to_markers(self._h, int(lattice), n, _ptr(xm, (n,)), _ptr(ym, (n,)),
+                                        _ptr(grid, self.shape), _ptr(phim, (n,)), _stream_handle(stream))
+        if st < 0:
+            raise PyroError(st, "pyro_grid_to_markers")
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pyro_markers_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Stokes:
