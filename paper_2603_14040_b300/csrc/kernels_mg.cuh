@@ -165,12 +165,18 @@ __device__ inline void restrict_point(const GeomT<T>& gf, const GeomT<T>& gc, in
 
 
 template <typename T>
+// with vxc / vyc given, the coarse iterate is zeroed in the same pass (the cycle starts from 0)
 __global__ void k_restrict(GeomT<T> gf, GeomT<T> gc, const T* __restrict__ rx, const T* __restrict__ ry,
-                           T* __restrict__ fxc, T* __restrict__ fyc) {
+                           T* __restrict__ fxc, T* __restrict__ fyc, T* __restrict__ vxc, T* __restrict__ vyc) {
   const int I = blockIdx.y * blockDim.y + threadIdx.y;
   const int J = blockIdx.x * blockDim.x + threadIdx.x;
   if (I > gc.ny + 1 || J > gc.nx + 1) return;
   restrict_point<T>(gf, gc, I, J, rx, ry, fxc, fyc);
+  if (vxc) {
+    const size_t C = (size_t)I * gc.ld + J;
+    vxc[C] = T(0);
+    vyc[C] = T(0);
+  }
 }
 
 template <typename T>
@@ -506,7 +512,7 @@ __global__ void __launch_bounds__(32 * kCoarseRows)
                                      const T*, const T*, Coef<T>);                                         \
   template __global__ void k_vresidual<T>(GeomT<T>, const T*, const T*, const T*, const T*, const T*,      \
                                           const T*, T*, T*, Coef<T>);                                       \
-  template __global__ void k_restrict<T>(GeomT<T>, GeomT<T>, const T*, const T*, T*, T*);                  \
+  template __global__ void k_restrict<T>(GeomT<T>, GeomT<T>, const T*, const T*, T*, T*, T*, T*);          \
   template __global__ void k_prolong_add<T>(GeomT<T>, GeomT<T>, T*, T*, const T*, const T*);               \
   template __global__ void k_coarsen_eta<T>(GeomT<T>, GeomT<T>, const T*, const T*, T*, T*, int);          \
   template __global__ void k_coarse_assemble<T>(Geom, const T*, const T*, double*, int);                   \

@@ -26,6 +26,7 @@ namespace {
 constexpr int kMaxCoarse = 1024;
 constexpr int kStreamMinRows = 96;  // shortest row chunk worth a streaming pass
 constexpr int kRasTile = 32;        // RAS-type Jacobi tile edge (cells), the paper's 32 x 32
+constexpr long long kSmallTileCells = 65536;  // FP32 levels up to 256^2 smooth with 32 x 16 tiles
 
 struct CudaError {
   cudaError_t e;
@@ -126,6 +127,11 @@ struct MG {
   const cudaEvent_t* hooks = nullptr;  // level-0 phase events (timing mode), else null
   long long* nlaunch = nullptr;        // kernel-launch counter of the owning handle
   void count(long long k) const { if (nlaunch) *nlaunch += k; }
+  // FP64 levels of up to 65536 cells: blocks of 64 threads, so even a tiny level spreads over many
+  // SMs (one SM's FP64 pipe, about 2 FMA per clock, would otherwise serialise the whole level)
+  static dim3 blk(const Level<T>& L) {
+    return (sizeof(T) == 8 && (long long)L.g.nx * L.g.ny <= 65536) ? dim3(32, 2) : kBlk2;
+  }
 
   static bool kc_level(int l, int nlev, int kcycle) { return l >= 1 && l - 1 < kcycle && l < nlev - 1; }
 
@@ -242,14 +248,14 @@ struct MG {
     const T* cvx = C ? C->X() : nullptr;
     const T* cvy = C ? C->Y() : nullptr;
     if (nsweeps == 0 && C) {
-      k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C->gt, L.X(), L.Y(), C->X(), C->Y());
+      k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, C->gt, L.X(), L.Y(), C->X(), C->Y());
       count(1);
       return;
     }
     if constexpr (sizeof(T) == 4) {
       if (stream_level(l)) {
         if (C) {
-          k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C->gt, L.X(), L.Y(), C->X(), C->Y());
+          k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, C->gt, L.X(), L.Y(), C->X(), C->Y());
           count(1);
         }
         while (nsweeps > 0) {
@@ -274,19 +280,30 @@ struct MG {
     }
     while (nsweeps > 0) {
       if constexpr (sizeof(T) == 4) {
-        constexpr int TX = 64, TY = 32;
-        const dim3 gr((L.g.nx + 2 + TX - 1) / TX, (L.g.ny + 2 + TY - 1) / TY);
         float* ox = L.cur ? L.vx : L.vx2;
         float* oy = L.cur ? L.vy : L.vy2;
-        if (nsweeps >= 2 && tile_sweeps >= 2) {
-          k_rbgs_tile_cs<2, TX, TY><<<gr, kTileThreads, SweepTileCS<2, TX, TY>::smem_bytes(), s>>>(
-              L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, gc, cvx, cvy);
-          nsweeps -= 2;
+        const int ns = (nsweeps >= 2 && tile_sweeps >= 2) ? 2 : 1;
+        if ((long long)L.g.nx * L.g.ny > kSmallTileCells) {
+          constexpr int TX = 64, TY = 32;   // large levels: the least halo recomputation
+          const dim3 gr((L.g.nx + 2 + TX - 1) / TX, (L.g.ny + 2 + TY - 1) / TY);
+          if (ns == 2)
+            k_rbgs_tile_cs<2, TX, TY><<<gr, kTileThreads, SweepTileCS<2, TX, TY>::smem_bytes(), s>>>(
+                L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, gc, cvx, cvy);
+          else
+            k_rbgs_tile_cs<1, TX, TY><<<gr, kTileThreads, SweepTileCS<1, TX, TY>::smem_bytes(), s>>>(
+                L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, gc, cvx, cvy);
         } else {
-          k_rbgs_tile_cs<1, TX, TY><<<gr, kTileThreads, SweepTileCS<1, TX, TY>::smem_bytes(), s>>>(
-              L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, gc, cvx, cvy);
-          nsweeps -= 1;
+          constexpr int TX = 32, TY = 16;   // small levels: more, shorter CTAs (one CTA's chain of
+                                            // half-sweeps is the critical path there)
+          const dim3 gr((L.g.nx + 2 + TX - 1) / TX, (L.g.ny + 2 + TY - 1) / TY);
+          if (ns == 2)
+            k_rbgs_tile_cs<2, TX, TY><<<gr, kTileThreads, SweepTileCS<2, TX, TY>::smem_bytes(), s>>>(
+                L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, gc, cvx, cvy);
+          else
+            k_rbgs_tile_cs<1, TX, TY><<<gr, kTileThreads, SweepTileCS<1, TX, TY>::smem_bytes(), s>>>(
+                L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, gc, cvx, cvy);
         }
+        nsweeps -= ns;
       } else {
         constexpr int TX = 64, TY = 16;
         const dim3 gr((L.g.nx + 2 + TX - 1) / TX, (L.g.ny + 2 + TY - 1) / TY);
@@ -347,6 +364,10 @@ struct MG {
                               (int)SweepTileCS<2, 64, 32>::smem_bytes()));
       CK(cudaFuncSetAttribute(k_rbgs_tile_cs<1, 64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)SweepTileCS<1, 64, 32>::smem_bytes()));
+      CK(cudaFuncSetAttribute(k_rbgs_tile_cs<2, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SweepTileCS<2, 32, 16>::smem_bytes()));
+      CK(cudaFuncSetAttribute(k_rbgs_tile_cs<1, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SweepTileCS<1, 32, 16>::smem_bytes()));
       CK(cudaFuncSetAttribute(k_resrestrict_tile<T, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)ResTile<T, 32, 16>::smem_bytes()));
       CK(cudaFuncSetAttribute(k_rbgs_stream<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -370,7 +391,7 @@ struct MG {
       return;
     }
     if (C) {
-      k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C->gt, L.X(), L.Y(), C->X(), C->Y());
+      k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, C->gt, L.X(), L.Y(), C->X(), C->Y());
       count(1);
     }
     if (smoother == PYRO_SMOOTH_RBGS) {
@@ -407,10 +428,10 @@ struct MG {
 
   void sweep(int l, cudaStream_t s) {
     Level<T>& L = lv[l];
-    const dim3 g = grid_rb(L.g.nx, L.g.ny, kBlk2);
+    const dim3 b = blk(L), g = grid_rb(L.g.nx, L.g.ny, b);
     for (int f = 0; f < 2; ++f)
       for (int c = 0; c < 2; ++c)
-        k_rbgs<T><<<g, kBlk2, 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, f, c, omega, L.idgx, L.idgy, L.kc);
+        k_rbgs<T><<<g, b, 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, f, c, omega, L.idgx, L.idgy, L.kc);
     count(4);
   }
 
@@ -437,12 +458,11 @@ struct MG {
     if (fz) {
       resrestrict_tiles(l, s);  // also zeroes the coarse iterate
     } else {
-      k_vresidual<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, L.rx,
+      k_vresidual<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, L.rx,
                                                                        L.ry, L.kc);
-      k_restrict<T><<<grid2(C.g.nx, C.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C.gt, L.rx, L.ry, C.fx, C.fy);
+      k_restrict<T><<<grid2(C.g.nx, C.g.ny, blk(C)), blk(C), 0, s>>>(L.gt, C.gt, L.rx, L.ry, C.fx, C.fy, C.vx,
+                                                                       C.vy);   // also zeroes the coarse iterate
       count(2);
-      CK(cudaMemsetAsync(C.vx, 0, C.P * sizeof(T), s));
-      CK(cudaMemsetAsync(C.vy, 0, C.P * sizeof(T), s));
       C.cur = 0;
     }
     if (kc_level(l + 1, (int)lv.size(), kcycle)) {
@@ -464,7 +484,7 @@ struct MG {
     // prolongation + correction (fused into the first post-smoothing pass of the RBGS tiles)
     const bool fused_post = smoother == PYRO_SMOOTH_RBGS && fz;
     if (!fused_post) {
-      k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, C.gt, L.X(), L.Y(), C.X(), C.Y());
+      k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, C.gt, L.X(), L.Y(), C.X(), C.Y());
       count(1);
     }
     if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[3], s, cudaEventRecordExternal));
