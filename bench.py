@@ -369,6 +369,19 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def job_throughput(local_ms, steps, world, device):
+    """Whole-job throughput of independent replicas: every rank ran `steps` solves in local_ms; the
+    job took the slowest rank's time (max over ranks), and all ranks' solves count."""
+    total_ms = local_ms
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * steps / (total_ms / 1e3), total_ms
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -444,12 +457,7 @@ def main():
     clk = clocks.stop()
     phases, counts = h.get_timing()
     h.set_timing(False)
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    value, total_ms = job_throughput(float(np.sum(step_ms)), args.steps, world, "cuda")
 
     # end to end through the public API with host (pinned) buffers: H2D of the inputs and D2H of
     # the solution happen inside the C-ABI call
