@@ -140,6 +140,10 @@ typedef struct {
                             cont_stages, each cont_iters outer iterations from the previous stage's
                             iterate, then the full-contrast solve; 0 = off [0] */
   int cont_iters;        /* outer iterations per continuation stage (the paper: 25) [25] */
+  int coarse_sweeps;     /* when the coarsest level has more than 1024 velocity unknowns (grids that
+                            do not halve down far, e.g. odd sizes), this many smoothing sweeps from
+                            zero stand in for its direct solve (Sec. "Multigrid Cycles": direct
+                            method or a few smoothing iterations) [40] */
 } pyro_opts;
 
 typedef struct {
@@ -153,7 +157,7 @@ typedef struct {
   double t_solve_ms;     /* Krylov loop time (device) */
   double alg_bytes;      /* algorithmic HBM bytes of the call (model, see the design notes) */
   int levels;            /* multigrid levels */
-  int coarse_n;          /* unknowns of the coarsest direct solve */
+  int coarse_n;          /* velocity unknowns of the coarsest level (direct solve if <= 1024) */
   long long kernel_launches; /* CUDA kernels this call launched (graph kernel nodes included) */
 } pyro_stats;
 
@@ -165,8 +169,10 @@ void pyro_default_opts(pyro_opts* opts);
 /* Create a solver for an nx x ny cell grid on an Lx x Ly box with boundary `bc` (NULL = free slip
  * on all sides) and options `opts` (NULL = defaults). Allocates the whole multigrid hierarchy, the
  * Krylov bases and all workspaces on the current CUDA device; they stay resident until destroy,
- * so repeated solves of one shape reuse them. nx, ny >= 2 and even; the coarsest level must hold
- * at most 1024 velocity unknowns (sizes with few factors of 2 are rejected: PYRO_E_INVALID).
+ * so repeated solves of one shape reuse them. nx, ny >= 2 (any parity): levels halve while both
+ * counts are even and the short side stays >= coarsest_min; a coarsest level of at most 1024
+ * velocity unknowns is solved by a dense FP64 inverse, a larger one by coarse_sweeps smoothing
+ * sweeps (odd sizes or sizes with few factors of 2 get a weaker preconditioner, not an error).
  * Returns PYRO_OK and *out, or an error (then *out = NULL). */
 int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc,
                        const pyro_opts* opts, pyro_stokes* out);

@@ -39,6 +39,7 @@ import scipy.sparse.linalg as spla
 from .stokes import Grid, assemble
 
 ETA_ARITH, ETA_GEOM = 0, 1
+MAX_COARSE = 1024
 
 
 def coarsen_grid(g):
@@ -265,8 +266,9 @@ def smooth(h, level, f, x, nu, omega, phase):
 # ---- hierarchy and V-cycle ---------------------------------------------------------------------
 class Hierarchy:
     def __init__(self, grid, eta_n, eta_c, coarsest_min=4, eta_mode=ETA_ARITH, n_lev=None, smoother="rbgs",
-                 ras_inner=4, ras_tile=32):
+                 ras_inner=4, ras_tile=32, coarse_sweeps=40):
         self.smoother, self.ras_inner, self.ras_tile = smoother, ras_inner, ras_tile
+        self.coarse_sweeps = coarse_sweeps
         L = n_levels(grid.nx, grid.ny, coarsest_min) if n_lev is None else n_lev
         self.grids = [grid]; self.eta = [(eta_n, eta_c)]
         for _ in range(L - 1):
@@ -279,7 +281,11 @@ class Hierarchy:
         for f, c in zip(self.grids[:-1], self.grids[1:]):
             self.R.append(sp.block_diag([restriction_matrix(f, c, "vx"), restriction_matrix(f, c, "vy")]).tocsr())
             self.P.append(sp.block_diag([prolongation_matrix(f, c, "vx"), prolongation_matrix(f, c, "vy")]).tocsr())
-        self.coarse_lu = spla.splu(self.L[-1].tocsc())
+        # the coarsest level is solved directly when it is small (<= MAX_COARSE velocity unknowns),
+        # else by coarse_sweeps smoothing steps from zero (Sec. "Multigrid Cycles": a direct
+        # method or a few smoothing iterations on the coarsest level)
+        self.coarse_direct = self.L[-1].shape[0] <= MAX_COARSE
+        self.coarse_lu = spla.splu(self.L[-1].tocsc()) if self.coarse_direct else None
 
     @property
     def nlev(self):
@@ -294,7 +300,9 @@ def vcycle(h, f, nu1=2, nu2=2, omega=1.0, level=0, kcycle=0):
     15, 2008): two flexible conjugate-gradient steps on the next level's correction equation,
     each preconditioned by one cycle of that level (not part of the paper)."""
     if level == h.nlev - 1:
-        return h.coarse_lu.solve(f)
+        if h.coarse_direct:
+            return h.coarse_lu.solve(f)
+        return smooth(h, level, f, np.zeros_like(f), h.coarse_sweeps, omega, 2)
     L = h.L[level]
     x = np.zeros_like(f)
     x = smooth(h, level, f, x, nu1, omega, 0)                     # (1) pre-smoothing

@@ -110,7 +110,9 @@ struct Level {
 template <typename T>
 struct MG {
   std::vector<Level<T>> lv;
-  double* Ainv = nullptr;  // coarsest (-L)^-1, dense FP64
+  double* Ainv = nullptr;  // coarsest (-L)^-1, dense FP64 (when coarse_direct)
+  bool coarse_direct = true;  // coarsest level solved by the dense inverse, else by smoothing
+  int coarse_sweeps = 40;     // smoothing sweeps on a coarsest level too large for the inverse
   int nc = 0;              // coarse unknowns
   int nu1 = 2, nu2 = 2, eta_mode = 0;
   int kcycle = 0;  // levels l < kcycle get their coarse correction from two flexible-CG steps
@@ -143,7 +145,7 @@ struct MG {
       if (l + 1 < nlev) { nx /= 2; ny /= 2; }
     }
     const size_t nc = (size_t)(ny * (nx - 1) + (ny - 1) * nx);
-    return b + nc * nc * sizeof(double);
+    return b + (nc <= (size_t)kMaxCoarse ? nc * nc * sizeof(double) : 0);
   }
 
   void alloc(DevAlloc& A, const Geom& g0, int nlev, bool alias_eta0) {
@@ -182,13 +184,16 @@ struct MG {
     }
     const Geom& gc = lv.back().g;
     nc = gc.ny * (gc.nx - 1) + (gc.ny - 1) * gc.nx;
-    Ainv = A.get<double>((size_t)nc * nc);
+    coarse_direct = nc <= kMaxCoarse;
+    if (coarse_direct) Ainv = A.get<double>((size_t)nc * nc);
   }
 
   // choose the first level of the cluster sub-cycle and fill its launch arguments
   void setup_sub(DevAlloc& A, int cluster_cells) {
     ls = -1;
-    if (cluster_cells <= 0 || (int)lv.size() > kSubMaxLevels || lv.size() < 2 || smoother != PYRO_SMOOTH_RBGS) return;
+    if (cluster_cells <= 0 || (int)lv.size() > kSubMaxLevels || lv.size() < 2 || smoother != PYRO_SMOOTH_RBGS ||
+        !coarse_direct)
+      return;
     for (int l = 0; l < (int)lv.size(); ++l)
       if ((long long)lv[l].g.nx * lv[l].g.ny <= cluster_cells) { ls = l; break; }
     if (ls < 0 || ls == (int)lv.size() - 1) { ls = -1; return; }
@@ -230,6 +235,7 @@ struct MG {
         count(1);
       }
     const Level<T>& C = lv.back();
+    if (!coarse_direct) return;
     CK(cudaMemsetAsync(Ainv, 0, (size_t)nc * nc * sizeof(double), s));
     k_coarse_assemble<T><<<(nc + 127) / 128, 128, 0, s>>>(C.g, C.en, C.ec, Ainv, nc);
     k_coarse_invert<<<1, 1024, nc * sizeof(double), s>>>(Ainv, nc, flag);
@@ -446,9 +452,15 @@ struct MG {
       return;
     }
     if (l == (int)lv.size() - 1) {
-      k_coarse_solve<T><<<(nc + kCoarseRows - 1) / kCoarseRows, 32 * kCoarseRows, nc * sizeof(double), s>>>(
-          L.g, Ainv, nc, L.fx, L.fy, L.vx, L.vy);
-      count(1);
+      if (coarse_direct) {
+        k_coarse_solve<T><<<(nc + kCoarseRows - 1) / kCoarseRows, 32 * kCoarseRows, nc * sizeof(double), s>>>(
+            L.g, Ainv, nc, L.fx, L.fy, L.vx, L.vy);
+        count(1);
+      } else {
+        // too many coarsest unknowns for the dense inverse: smoothing sweeps from zero stand in for
+        // the coarsest solve (the paper's "direct method or a few smoothing iterations")
+        smooth(l, coarse_sweeps, nullptr, 2, s);
+      }
       return;
     }
     Level<T>& C = lv[l + 1];
@@ -1119,17 +1131,15 @@ void validate_opts(pyro_opts& o) {
   if (o.ras_inner < 1) o.ras_inner = 1;
   if (o.cont_stages < 0) o.cont_stages = 0;
   if (o.cont_iters < 1) o.cont_iters = 1;
+  if (o.coarse_sweeps < 1) o.coarse_sweeps = 1;
 }
 
 int check_size(int nx, int ny, const pyro_opts& o) {
-  if (nx < 2 || ny < 2 || (nx & 1) || (ny & 1)) return PYRO_E_INVALID;
-  int L = count_levels(nx, ny, o.coarsest_min);
-  int cx = nx, cy = ny;
-  for (int l = 1; l < L; ++l) { cx /= 2; cy /= 2; }
-  const int nc = cy * (cx - 1) + (cy - 1) * cx;
-  if (nc > kMaxCoarse || nc < 1) return PYRO_E_INVALID;
-  return L;
+  (void)o;
+  if (nx < 2 || ny < 2 || (long long)(nx + 2) * (ny + 2) > (1LL << 31)) return PYRO_E_INVALID;
+  return count_levels(nx, ny, o.coarsest_min);
 }
+
 
 size_t footprint_bytes(int nx, int ny, const pyro_opts& o, int L) {
   const size_t P = (size_t)(ny + 2) * (nx + 2);
@@ -1182,6 +1192,7 @@ void pyro_default_opts(pyro_opts* o) {
   o->litho_guess = 0;
   o->cont_stages = 0;
   o->cont_iters = 25;
+  o->coarse_sweeps = 40;
 }
 
 const char* pyro_version(void) { return "pyro-b300 0.1 (sm_103a)"; }
@@ -1267,6 +1278,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
     h->flag = A.get<int>(1);
     if (h->mixed) {
       h->mgf.nu1 = o.nu1; h->mgf.nu2 = o.nu2; h->mgf.omega = (float)o.omega_v; h->mgf.eta_mode = o.eta_coarsen;
+      h->mgf.coarse_sweeps = o.coarse_sweeps;
       h->mgf.kcycle = o.kcycle;
       h->mgf.smoother = o.smoother;
       h->mgf.ras_inner = o.ras_inner;
@@ -1280,6 +1292,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->mgf.setup_sub(A, o.cluster_cells);
     } else {
       h->mgd.nu1 = o.nu1; h->mgd.nu2 = o.nu2; h->mgd.omega = o.omega_v; h->mgd.eta_mode = o.eta_coarsen;
+      h->mgd.coarse_sweeps = o.coarse_sweeps;
       h->mgd.kcycle = o.kcycle;
       h->mgd.smoother = o.smoother;
       h->mgd.ras_inner = o.ras_inner;

@@ -33,8 +33,11 @@ def test_host_logic_without_gpu():
     assert P.lib().pyro_strerror(-4) == b"non-finite input or iterate"
     o = P.default_opts()
     assert (o.nu1, o.nu2, o.restart_m, o.prec, o.coarsest_min) == (2, 2, 30, P.PREC_MIXED, 4)
-    # footprint: odd / too coarse-unfriendly sizes are rejected, valid ones scale with the grid
-    assert P.footprint(100, 100) == 0 and P.footprint(3, 8) == 0
+    # footprint: degenerate sizes are rejected; odd and coarse-unfriendly sizes are served (their
+    # coarsest level is smoothed instead of inverted, so it needs no dense inverse)
+    assert P.footprint(1, 8) == 0 and P.footprint(8, 0) == 0
+    assert P.footprint(3, 8) > 0 and P.footprint(100, 100) > 0
+    assert P.footprint(100, 100) < P.footprint(128, 128)
     f1, f2 = P.footprint(512, 512), P.footprint(1024, 1024)
     assert 3.5 < f2 / f1 < 4.5
     o64 = P.default_opts(prec=P.PREC_FP64)

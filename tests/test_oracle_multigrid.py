@@ -278,3 +278,20 @@ def test_vcycle_with_jacobi_smoothers_contracts(smoother):
         rate = np.linalg.norm(e_new) / np.linalg.norm(e)
         e = e_new
     assert rate < 0.8
+
+
+def test_large_coarsest_level_is_smoothed_and_the_cycle_still_contracts():
+    """90 x 66 halves once to 45 x 33 (2892 velocity unknowns, above the direct-solve limit): the
+    coarsest level gets smoothing sweeps from zero; the cycle must still contract."""
+    g = S.Grid(90, 66, 1.0, 66 / 90)
+    rng = np.random.default_rng(47)
+    en = 10.0 ** rng.uniform(-0.5, 0.5, (68, 92)); ec = 10.0 ** rng.uniform(-0.5, 0.5, (68, 92))
+    h = M.Hierarchy(g, en, ec, coarsest_min=4, coarse_sweeps=40)
+    assert h.nlev == 2 and not h.coarse_direct
+    L = h.L[0]
+    e = rng.standard_normal(L.shape[0])
+    for _ in range(5):
+        e_new = e - M.vcycle(h, L @ e, 2, 2, 1.0)
+        rate = np.linalg.norm(e_new) / np.linalg.norm(e)
+        e = e_new
+    assert rate < 0.9
