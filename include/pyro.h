@@ -144,6 +144,13 @@ typedef struct {
                             do not halve down far, e.g. odd sizes), this many smoothing sweeps from
                             zero stand in for its direct solve (Sec. "Multigrid Cycles": direct
                             method or a few smoothing iterations) [40] */
+  double coarsen_ratio;  /* 2: halve while possible; any other value in [1.5, 8] coarsens every level
+                            by that ratio, n_c = ceil(n / ratio) (the paper's arbitrary ratio, e.g.
+                            2.5) [2.0] */
+  int coarsen_general;   /* 1: when halving stops with more than 1024 coarsest velocity unknowns
+                            (odd sizes, few factors of 2), keep coarsening by coarsen_ratio with the
+                            general transfer operators (normalised bilinear restriction, bilinear
+                            prolongation at any ratio); 0: stop there [1] */
 } pyro_opts;
 
 typedef struct {
@@ -170,9 +177,10 @@ void pyro_default_opts(pyro_opts* opts);
  * on all sides) and options `opts` (NULL = defaults). Allocates the whole multigrid hierarchy, the
  * Krylov bases and all workspaces on the current CUDA device; they stay resident until destroy,
  * so repeated solves of one shape reuse them. nx, ny >= 2 (any parity): levels halve while both
- * counts are even and the short side stays >= coarsest_min; a coarsest level of at most 1024
- * velocity unknowns is solved by a dense FP64 inverse, a larger one by coarse_sweeps smoothing
- * sweeps (odd sizes or sizes with few factors of 2 get a weaker preconditioner, not an error).
+ * counts are even and the short side stays >= coarsest_min, then coarsen by coarsen_ratio while
+ * the coarsest level has more than 1024 velocity unknowns (coarsen_general); a coarsest level of
+ * at most 1024 velocity unknowns is solved by a dense FP64 inverse, a larger one by coarse_sweeps
+ * smoothing sweeps.
  * Returns PYRO_OK and *out, or an error (then *out = NULL). */
 int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc,
                        const pyro_opts* opts, pyro_stokes* out);

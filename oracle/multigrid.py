@@ -42,19 +42,49 @@ ETA_ARITH, ETA_GEOM = 0, 1
 MAX_COARSE = 1024
 
 
-def coarsen_grid(g):
-    if g.nx % 2 or g.ny % 2:
-        raise ValueError("factor-2 coarsening needs even cell counts")
-    return Grid(g.nx // 2, g.ny // 2, g.Lx, g.Ly, g.bc)
+def coarsen_grid(g, nxc=None, nyc=None):
+    """The next level: halved by default, or nxc x nyc cells on the same box (general ratio)."""
+    if nxc is None:
+        if g.nx % 2 or g.ny % 2:
+            raise ValueError("factor-2 coarsening needs even cell counts")
+        nxc, nyc = g.nx // 2, g.ny // 2
+    return Grid(nxc, nyc, g.Lx, g.Ly, g.bc)
 
 
-def n_levels(nx, ny, coarsest_min):
-    """Levels of a factor-2 hierarchy: halve while both counts are even and the short side stays
-    >= coarsest_min after halving."""
-    L = 1
-    while nx % 2 == 0 and ny % 2 == 0 and min(nx, ny) // 2 >= coarsest_min:
-        nx //= 2; ny //= 2; L += 1
-    return L
+def velocity_unknowns(nx, ny):
+    return ny * (nx - 1) + (ny - 1) * nx
+
+
+def level_sizes(nx, ny, coarsest_min, ratio=2.0, general=True):
+    """Cell counts of every level. Halve while the ratio is 2, both counts are even and the short
+    side stays >= coarsest_min; then, while the coarsest level is too large for the direct solve
+    (more than MAX_COARSE velocity unknowns), coarsen by the ratio: n_c = ceil(n / ratio) (the
+    paper's arbitrary coarsening ratio, Algorithms find_lower_index / restriction_checkerboard)."""
+    sizes = [(nx, ny)]
+    while True:
+        nx, ny = sizes[-1]
+        if ratio == 2.0 and nx % 2 == 0 and ny % 2 == 0 and min(nx, ny) // 2 >= coarsest_min:
+            sizes.append((nx // 2, ny // 2))
+            continue
+        if general and velocity_unknowns(nx, ny) > MAX_COARSE:
+            cx, cy = int(np.ceil(nx / ratio - 1e-9)), int(np.ceil(ny / ratio - 1e-9))
+            if min(cx, cy) >= 2 and (cx, cy) != (nx, ny):
+                sizes.append((cx, cy))
+                continue
+        return sizes
+
+
+def n_levels(nx, ny, coarsest_min, ratio=2.0, general=True):
+    return len(level_sizes(nx, ny, coarsest_min, ratio, general))
+
+
+def _candidates(c, r, centred, lo, hi):
+    """Fine indices whose position may lie within one coarse spacing of coarse index c (r = coarse
+    spacing / fine spacing; positions c * h for nodes/faces, (c - 1/2) h for centred families)."""
+    off = 0.5 if centred else 0.0
+    a = np.floor((c - off - 1) * r + off).astype(np.int64) - 1
+    b = np.ceil((c - off + 1) * r + off).astype(np.int64) + 1
+    return np.maximum(a, lo), np.minimum(b, hi)
 
 
 # ---- staggered positions --------------------------------------------------------------------
@@ -79,12 +109,16 @@ def restriction_matrix(fine, coarse, fld):
     # candidate fine indices: every fine unknown whose position is within one coarse spacing
     ci = coarse.vx_i if fld == "vx" else coarse.vy_i
     cj = coarse.vx_j if fld == "vx" else coarse.vy_j
+    rx, ry = coarse.dx / fine.dx, coarse.dy / fine.dy
+    ilo, ihi = _candidates(ci, ry, fld == "vx", 0, fine.ny + 1)    # vx rows are cell-centred
+    jlo, jhi = _candidates(cj, rx, fld == "vy", 0, fine.nx + 1)    # vy columns are cell-centred
+    span_i, span_j = int((ihi - ilo).max()) + 1, int((jhi - jlo).max()) + 1
     rows, cols, vals = [], [], []
-    for di in range(-3, 4):
-        for dj in range(-3, 4):
-            fi = 2 * ci + di
-            fj = 2 * cj + dj
-            ok = (fi >= 0) & (fi < fine.ny + 2) & (fj >= 0) & (fj < fine.nx + 2)
+    for di in range(span_i):
+        for dj in range(span_j):
+            fi = ilo + di
+            fj = jlo + dj
+            ok = (fi <= ihi) & (fj <= jhi) & (fi >= 0) & (fi < fine.ny + 2) & (fj >= 0) & (fj < fine.nx + 2)
             fi_ = np.where(ok, fi, 0); fj_ = np.where(ok, fj, 0)
             col = idx[fi_, fj_]
             ok &= col >= 0
@@ -150,10 +184,14 @@ def _material_restrict(fine, coarse, a, centred):
         lo_i, hi_i, lo_j, hi_j = 0, fine.ny, 0, fine.nx
         posf = lambda i, j: (j * fine.dx, i * fine.dy)
     acc = np.zeros(I.shape); wsum = np.zeros(I.shape)
-    for di in range(-3, 4):
-        for dj in range(-3, 4):
-            fi = 2 * I + di; fj = 2 * J + dj
-            ok = (fi >= lo_i) & (fi <= hi_i) & (fj >= lo_j) & (fj <= hi_j)
+    rx, ry = coarse.dx / fine.dx, coarse.dy / fine.dy
+    ilo, ihi = _candidates(I, ry, centred, lo_i, hi_i)
+    jlo, jhi = _candidates(J, rx, centred, lo_j, hi_j)
+    span_i, span_j = int((ihi - ilo).max()) + 1, int((jhi - jlo).max()) + 1
+    for di in range(span_i):
+        for dj in range(span_j):
+            fi = ilo + di; fj = jlo + dj
+            ok = (fi <= ihi) & (fj <= jhi) & (fi >= lo_i) & (fi <= hi_i) & (fj >= lo_j) & (fj <= hi_j)
             xf, yf = posf(fi, fj)
             wx = 1 - np.abs(xf - Xc) / coarse.dx
             wy = 1 - np.abs(yf - Yc) / coarse.dy
@@ -266,13 +304,15 @@ def smooth(h, level, f, x, nu, omega, phase):
 # ---- hierarchy and V-cycle ---------------------------------------------------------------------
 class Hierarchy:
     def __init__(self, grid, eta_n, eta_c, coarsest_min=4, eta_mode=ETA_ARITH, n_lev=None, smoother="rbgs",
-                 ras_inner=4, ras_tile=32, coarse_sweeps=40):
+                 ras_inner=4, ras_tile=32, coarse_sweeps=40, coarsen_ratio=2.0, coarsen_general=True):
         self.smoother, self.ras_inner, self.ras_tile = smoother, ras_inner, ras_tile
         self.coarse_sweeps = coarse_sweeps
-        L = n_levels(grid.nx, grid.ny, coarsest_min) if n_lev is None else n_lev
+        sizes = level_sizes(grid.nx, grid.ny, coarsest_min, coarsen_ratio, coarsen_general)
+        if n_lev is not None:
+            sizes = sizes[:n_lev]
         self.grids = [grid]; self.eta = [(eta_n, eta_c)]
-        for _ in range(L - 1):
-            c = coarsen_grid(self.grids[-1])
+        for (cx, cy) in sizes[1:]:
+            c = coarsen_grid(self.grids[-1], cx, cy)
             en, ec = coarsen_eta(self.grids[-1], c, *self.eta[-1], mode=eta_mode)
             self.grids.append(c); self.eta.append((en, ec))
         self.L = [assemble(g, en, ec, velocity_only=True).A.tocsr() for g, (en, ec) in zip(self.grids, self.eta)]

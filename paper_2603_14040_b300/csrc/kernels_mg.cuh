@@ -506,6 +506,155 @@ __global__ void __launch_bounds__(32 * kCoarseRows)
   else { const int kk = k - nvx; const int i = kk / nx + 1, j = kk % nx + 1; vy[(size_t)i * ld + j] = (T)(-s); }
 }
 
+// ---- transfers between levels of any size ratio ---------------------------------------------
+// (the paper's arbitrary coarsening ratio; factor-2 levels use the kernels above). Positions and
+// weights are formed in double from the box and the cell counts of both levels: vx at (j dx,
+// (i - 1/2) dy), vy at ((j - 1/2) dx, i dy), basic nodes at (j dx, i dy), cells at ((j - 1/2) dx,
+// (i - 1/2) dy). The bilinear weight of a fine point for a coarse point is (1 - |x - X|/DX)
+// (1 - |y - Y|/DY) where both factors exceed 1e-9 (inside the support), else 0.
+
+// first and last fine index whose position can lie within one coarse spacing of coarse index c
+// (r = coarse spacing / fine spacing; off = 1/2 for a cell-centred direction)
+__device__ inline void gen_candidates(int c, double r, double off, int lo, int hi, int& a, int& b) {
+  a = max((int)floor((c - off - 1.0) * r + off) - 1, lo);
+  b = min((int)ceil((c - off + 1.0) * r + off) + 1, hi);
+}
+
+__device__ inline double gen_w(double xf, double xc, double H) { return 1.0 - fabs(xf - xc) / H; }
+
+// normalised bilinear restriction of the level residual to every coarse unknown; with vxc / vyc
+// given the coarse iterate is zeroed in the same pass
+template <typename T>
+__global__ void k_restrict_gen(Geom fd, Geom cd, GeomT<T> gf, const T* __restrict__ rx, const T* __restrict__ ry,
+                               T* __restrict__ fxc, T* __restrict__ fyc, T* __restrict__ vxc, T* __restrict__ vyc) {
+  const int I = blockIdx.y * blockDim.y + threadIdx.y;
+  const int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I > cd.ny + 1 || J > cd.nx + 1) return;
+  const size_t C = (size_t)I * cd.ld + J;
+  const double rxr = cd.dx / fd.dx, ryr = cd.dy / fd.dy;
+  T ox = T(0), oy = T(0);
+  if (is_vx(cd.nx, cd.ny, I, J)) {
+    const double X = J * cd.dx, Y = (I - 0.5) * cd.dy;
+    int i0, i1, j0, j1;
+    gen_candidates(I, ryr, 0.5, 0, fd.ny + 1, i0, i1);
+    gen_candidates(J, rxr, 0.0, 0, fd.nx + 1, j0, j1);
+    double s = 0.0, ws = 0.0;
+    for (int i = i0; i <= i1; ++i) {
+      const double wy = gen_w((i - 0.5) * fd.dy, Y, cd.dy);
+      if (!(wy > 1e-9)) continue;
+      for (int j = j0; j <= j1; ++j) {
+        if (!is_vx(fd.nx, fd.ny, i, j)) continue;
+        const double wx = gen_w(j * fd.dx, X, cd.dx);
+        if (!(wx > 1e-9)) continue;
+        s += wx * wy * (double)rx[(size_t)i * fd.ld + j];
+        ws += wx * wy;
+      }
+    }
+    ox = (T)(s / ws);
+  }
+  if (is_vy(cd.nx, cd.ny, I, J)) {
+    const double X = (J - 0.5) * cd.dx, Y = I * cd.dy;
+    int i0, i1, j0, j1;
+    gen_candidates(I, ryr, 0.0, 0, fd.ny + 1, i0, i1);
+    gen_candidates(J, rxr, 0.5, 0, fd.nx + 1, j0, j1);
+    double s = 0.0, ws = 0.0;
+    for (int i = i0; i <= i1; ++i) {
+      const double wy = gen_w(i * fd.dy, Y, cd.dy);
+      if (!(wy > 1e-9)) continue;
+      for (int j = j0; j <= j1; ++j) {
+        if (!is_vy(fd.nx, fd.ny, i, j)) continue;
+        const double wx = gen_w((j - 0.5) * fd.dx, X, cd.dx);
+        if (!(wx > 1e-9)) continue;
+        s += wx * wy * (double)ry[(size_t)i * fd.ld + j];
+        ws += wx * wy;
+      }
+    }
+    oy = (T)(s / ws);
+  }
+  fxc[C] = ox;
+  fyc[C] = oy;
+  if (vxc) { vxc[C] = T(0); vyc[C] = T(0); }
+}
+
+// x_fine += P x_coarse: bilinear interpolation from the four surrounding coarse points of the
+// same family, coarse ghosts by the homogeneous boundary rule (coarse_vx / coarse_vy)
+template <typename T>
+__global__ void k_prolong_gen(Geom fd, Geom cd, GeomT<T> gc, T* __restrict__ vx, T* __restrict__ vy,
+                              const T* __restrict__ cvx, const T* __restrict__ cvy) {
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > fd.ny + 1 || j > fd.nx + 1) return;
+  const size_t c = (size_t)i * fd.ld + j;
+  for (int fld = 0; fld < 2; ++fld) {
+    if (fld == 0 ? !is_vx(fd.nx, fd.ny, i, j) : !is_vy(fd.nx, fd.ny, i, j)) continue;
+    const double fx = fld == 0 ? (j * fd.dx) / cd.dx : ((j - 0.5) * fd.dx) / cd.dx + 0.5;
+    const double fy = fld == 0 ? ((i - 0.5) * fd.dy) / cd.dy + 0.5 : (i * fd.dy) / cd.dy;
+    const int J0 = (int)floor(fx + 1e-12), I0 = (int)floor(fy + 1e-12);
+    const double tx = fx - J0, ty = fy - I0;
+    double v = 0.0;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        const double w = (a ? ty : 1.0 - ty) * (b ? tx : 1.0 - tx);
+        if (!(w > 1e-14)) continue;
+        const T cv = fld == 0 ? coarse_vx(gc, cvx, I0 + a, J0 + b) : coarse_vy(gc, cvy, I0 + a, J0 + b);
+        v += w * (double)cv;
+      }
+    if (fld == 0) vx[c] += (T)v;
+    else vy[c] += (T)v;
+  }
+}
+
+// eta on the next level of any ratio: normalised bilinear weights over the real fine nodes /
+// cells, arithmetic or on log(eta)
+template <typename T>
+__global__ void k_coarsen_eta_gen(Geom fd, Geom cd, const T* __restrict__ enf, const T* __restrict__ ecf,
+                                  T* __restrict__ enc, T* __restrict__ ecc, int geometric) {
+  const int I = blockIdx.y * blockDim.y + threadIdx.y;
+  const int J = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I > cd.ny + 1 || J > cd.nx + 1) return;
+  const size_t C = (size_t)I * cd.ld + J;
+  const double rxr = cd.dx / fd.dx, ryr = cd.dy / fd.dy;
+  T on = T(0), oc = T(0);
+  if (I <= cd.ny && J <= cd.nx) {
+    int i0, i1, j0, j1;
+    gen_candidates(I, ryr, 0.0, 0, fd.ny, i0, i1);
+    gen_candidates(J, rxr, 0.0, 0, fd.nx, j0, j1);
+    double s = 0.0, ws = 0.0;
+    for (int i = i0; i <= i1; ++i) {
+      const double wy = gen_w(i * fd.dy, I * cd.dy, cd.dy);
+      if (!(wy > 1e-9)) continue;
+      for (int j = j0; j <= j1; ++j) {
+        const double wx = gen_w(j * fd.dx, J * cd.dx, cd.dx);
+        if (!(wx > 1e-9)) continue;
+        const double e = (double)enf[(size_t)i * fd.ld + j];
+        s += wx * wy * (geometric ? log(e) : e);
+        ws += wx * wy;
+      }
+    }
+    on = (T)(geometric ? exp(s / ws) : s / ws);
+  }
+  if (I >= 1 && I <= cd.ny && J >= 1 && J <= cd.nx) {
+    int i0, i1, j0, j1;
+    gen_candidates(I, ryr, 0.5, 1, fd.ny, i0, i1);
+    gen_candidates(J, rxr, 0.5, 1, fd.nx, j0, j1);
+    double s = 0.0, ws = 0.0;
+    for (int i = i0; i <= i1; ++i) {
+      const double wy = gen_w((i - 0.5) * fd.dy, (I - 0.5) * cd.dy, cd.dy);
+      if (!(wy > 1e-9)) continue;
+      for (int j = j0; j <= j1; ++j) {
+        const double wx = gen_w((j - 0.5) * fd.dx, (J - 0.5) * cd.dx, cd.dx);
+        if (!(wx > 1e-9)) continue;
+        const double e = (double)ecf[(size_t)i * fd.ld + j];
+        s += wx * wy * (geometric ? log(e) : e);
+        ws += wx * wy;
+      }
+    }
+    oc = (T)(geometric ? exp(s / ws) : s / ws);
+  }
+  enc[C] = on;
+  ecc[C] = oc;
+}
+
 // ---- explicit instantiations ---------------------------------------------------------------
 #define PYRO_INST(T)                                                                                         \
   template __global__ void k_rbgs<T>(GeomT<T>, T*, T*, const T*, const T*, const T*, const T*, int, int, T, \
@@ -513,6 +662,9 @@ __global__ void __launch_bounds__(32 * kCoarseRows)
   template __global__ void k_vresidual<T>(GeomT<T>, const T*, const T*, const T*, const T*, const T*,      \
                                           const T*, T*, T*, Coef<T>);                                       \
   template __global__ void k_restrict<T>(GeomT<T>, GeomT<T>, const T*, const T*, T*, T*, T*, T*);          \
+  template __global__ void k_restrict_gen<T>(Geom, Geom, GeomT<T>, const T*, const T*, T*, T*, T*, T*);   \
+  template __global__ void k_prolong_gen<T>(Geom, Geom, GeomT<T>, T*, T*, const T*, const T*);            \
+  template __global__ void k_coarsen_eta_gen<T>(Geom, Geom, const T*, const T*, T*, T*, int);             \
   template __global__ void k_prolong_add<T>(GeomT<T>, GeomT<T>, T*, T*, const T*, const T*);               \
   template __global__ void k_coarsen_eta<T>(GeomT<T>, GeomT<T>, const T*, const T*, T*, T*, int);          \
   template __global__ void k_coarse_assemble<T>(Geom, const T*, const T*, double*, int);                   \

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "../../include/pyro.h"
@@ -81,10 +82,28 @@ Geom make_geom(int nx, int ny, double Lx, double Ly, const pyro_bc& bc) {
   return g;
 }
 
-int count_levels(int nx, int ny, int cmin) {
-  int L = 1;
-  while (nx % 2 == 0 && ny % 2 == 0 && std::min(nx, ny) / 2 >= cmin) { nx /= 2; ny /= 2; ++L; }
-  return L;
+inline long long velocity_unknowns(int nx, int ny) { return (long long)ny * (nx - 1) + (long long)(ny - 1) * nx; }
+
+// Cell counts of every level: halve while the ratio is 2, both counts are even and the short side
+// stays >= cmin; then, while the coarsest level is too large for the dense inverse, coarsen by
+// the ratio, n_c = ceil(n / ratio) (the paper's arbitrary coarsening ratio).
+std::vector<std::pair<int, int>> level_sizes(int nx, int ny, int cmin, double ratio, bool general) {
+  std::vector<std::pair<int, int>> sz{{nx, ny}};
+  for (;;) {
+    const int a = sz.back().first, b = sz.back().second;
+    if (ratio == 2.0 && a % 2 == 0 && b % 2 == 0 && std::min(a, b) / 2 >= cmin) {
+      sz.push_back({a / 2, b / 2});
+      continue;
+    }
+    if (general && velocity_unknowns(a, b) > kMaxCoarse) {
+      const int cx = (int)std::ceil(a / ratio - 1e-9), cy = (int)std::ceil(b / ratio - 1e-9);
+      if (std::min(cx, cy) >= 2 && (cx != a || cy != b)) {
+        sz.push_back({cx, cy});
+        continue;
+      }
+    }
+    return sz;
+  }
 }
 
 // ---- multigrid hierarchy on one arithmetic type --------------------------------------------
@@ -110,6 +129,7 @@ struct Level {
 template <typename T>
 struct MG {
   std::vector<Level<T>> lv;
+  std::vector<char> f2;    // f2[l]: level l+1 is level l halved (factor-2 kernels), else any ratio
   double* Ainv = nullptr;  // coarsest (-L)^-1, dense FP64 (when coarse_direct)
   bool coarse_direct = true;  // coarsest level solved by the dense inverse, else by smoothing
   int coarse_sweeps = 40;     // smoothing sweeps on a coarsest level too large for the inverse
@@ -137,20 +157,26 @@ struct MG {
 
   static bool kc_level(int l, int nlev, int kcycle) { return l >= 1 && l - 1 < kcycle && l < nlev - 1; }
 
-  static size_t bytes(int nx, int ny, int nlev, int kcycle = 0) {
+  static size_t bytes(const std::vector<std::pair<int, int>>& sz, int kcycle = 0) {
     size_t b = 0;
+    const int nlev = (int)sz.size();
     for (int l = 0; l < nlev; ++l) {
-      b += (size_t)(sizeof(T) == 8 ? 17 : 10) * (size_t)(ny + 2) * (nx + 2) * sizeof(T);
-      if (kc_level(l, nlev, kcycle)) b += (size_t)6 * (size_t)(ny + 2) * (nx + 2) * sizeof(T) + 5 * 296 * 8 + 64;
-      if (l + 1 < nlev) { nx /= 2; ny /= 2; }
+      const size_t P = (size_t)(sz[l].second + 2) * (sz[l].first + 2);
+      b += (size_t)(sizeof(T) == 8 ? 17 : 10) * P * sizeof(T);
+      if (kc_level(l, nlev, kcycle)) b += (size_t)6 * P * sizeof(T) + 5 * 296 * 8 + 64;
     }
-    const size_t nc = (size_t)(ny * (nx - 1) + (ny - 1) * nx);
+    const size_t nc = (size_t)velocity_unknowns(sz.back().first, sz.back().second);
     return b + (nc <= (size_t)kMaxCoarse ? nc * nc * sizeof(double) : 0);
   }
 
-  void alloc(DevAlloc& A, const Geom& g0, int nlev, bool alias_eta0) {
+  void alloc(DevAlloc& A, const Geom& g0, double Lx, double Ly, const std::vector<std::pair<int, int>>& sz,
+             bool alias_eta0) {
     Geom g = g0;
+    const int nlev = (int)sz.size();
     for (int l = 0; l < nlev; ++l) {
+      g.nx = sz[l].first; g.ny = sz[l].second; g.ld = g.nx + 2;
+      g.dx = Lx / g.nx; g.dy = Ly / g.ny;
+      f2.push_back(l + 1 < nlev && sz[l + 1].first * 2 == g.nx && sz[l + 1].second * 2 == g.ny);
       Level<T> L;
       L.g = g;
       L.gt = geomT<T>(g);
@@ -178,9 +204,6 @@ struct MG {
         L.ks = A.get<double>(8);
       }
       lv.push_back(L);
-      if (l + 1 < nlev) {
-        g.nx /= 2; g.ny /= 2; g.ld = g.nx + 2; g.dx *= 2; g.dy *= 2;
-      }
     }
     const Geom& gc = lv.back().g;
     nc = gc.ny * (gc.nx - 1) + (gc.ny - 1) * gc.nx;
@@ -194,6 +217,8 @@ struct MG {
     if (cluster_cells <= 0 || (int)lv.size() > kSubMaxLevels || lv.size() < 2 || smoother != PYRO_SMOOTH_RBGS ||
         !coarse_direct)
       return;
+    for (size_t l = 0; l + 1 < lv.size(); ++l)
+      if (!f2[l]) return;
     for (int l = 0; l < (int)lv.size(); ++l)
       if ((long long)lv[l].g.nx * lv[l].g.ny <= cluster_cells) { ls = l; break; }
     if (ls < 0 || ls == (int)lv.size() - 1) { ls = -1; return; }
@@ -219,7 +244,11 @@ struct MG {
     for (size_t l = 1; l < lv.size(); ++l) {
       const Level<T>& F = lv[l - 1];
       Level<T>& C = lv[l];
-      k_coarsen_eta<T><<<grid2(C.g.nx, C.g.ny, kBlk2), kBlk2, 0, s>>>(F.gt, C.gt, F.en, F.ec, C.en, C.ec, eta_mode);
+      if (f2[l - 1])
+        k_coarsen_eta<T><<<grid2(C.g.nx, C.g.ny, kBlk2), kBlk2, 0, s>>>(F.gt, C.gt, F.en, F.ec, C.en, C.ec, eta_mode);
+      else
+        k_coarsen_eta_gen<T><<<grid2(C.g.nx, C.g.ny, kBlk2), kBlk2, 0, s>>>(F.g, C.g, F.en, F.ec, C.en, C.ec,
+                                                                             eta_mode);
     }
     for (size_t l = 0; l < lv.size(); ++l)
       if (lv[l].own_kc) {
@@ -467,8 +496,15 @@ struct MG {
     const bool fz = fused(l);
     smooth(l, nu1, nullptr, 0, s);
     if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[2], s, cudaEventRecordExternal));
-    if (fz) {
+    if (fz && f2[l]) {
       resrestrict_tiles(l, s);  // also zeroes the coarse iterate
+    } else if (!f2[l]) {
+      k_vresidual<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, L.rx,
+                                                                       L.ry, L.kc);
+      k_restrict_gen<T><<<grid2(C.g.nx, C.g.ny, blk(C)), blk(C), 0, s>>>(L.g, C.g, L.gt, L.rx, L.ry, C.fx, C.fy, C.vx,
+                                                                          C.vy);
+      count(2);
+      C.cur = 0;
     } else {
       k_vresidual<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, L.rx,
                                                                        L.ry, L.kc);
@@ -494,9 +530,12 @@ struct MG {
       cycle(l + 1, s);
     }
     // prolongation + correction (fused into the first post-smoothing pass of the RBGS tiles)
-    const bool fused_post = smoother == PYRO_SMOOTH_RBGS && fz;
+    const bool fused_post = smoother == PYRO_SMOOTH_RBGS && fz && f2[l];
     if (!fused_post) {
-      k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, C.gt, L.X(), L.Y(), C.X(), C.Y());
+      if (f2[l])
+        k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, C.gt, L.X(), L.Y(), C.X(), C.Y());
+      else
+        k_prolong_gen<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.g, C.g, C.gt, L.X(), L.Y(), C.X(), C.Y());
       count(1);
     }
     if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[3], s, cudaEventRecordExternal));
@@ -1132,12 +1171,16 @@ void validate_opts(pyro_opts& o) {
   if (o.cont_stages < 0) o.cont_stages = 0;
   if (o.cont_iters < 1) o.cont_iters = 1;
   if (o.coarse_sweeps < 1) o.coarse_sweeps = 1;
+  if (!(o.coarsen_ratio >= 1.5) || o.coarsen_ratio > 8.0) o.coarsen_ratio = 2.0;
+}
+
+std::vector<std::pair<int, int>> sizes_of(int nx, int ny, const pyro_opts& o) {
+  return level_sizes(nx, ny, o.coarsest_min, o.coarsen_ratio, o.coarsen_general != 0);
 }
 
 int check_size(int nx, int ny, const pyro_opts& o) {
-  (void)o;
   if (nx < 2 || ny < 2 || (long long)(nx + 2) * (ny + 2) > (1LL << 31)) return PYRO_E_INVALID;
-  return count_levels(nx, ny, o.coarsest_min);
+  return (int)sizes_of(nx, ny, o).size();
 }
 
 
@@ -1155,7 +1198,9 @@ size_t footprint_bytes(int nx, int ny, const pyro_opts& o, int L) {
   b += (m + 1) * n3 * 8;           // Z (preconditioned vectors; FP32-valued velocities in mixed mode)
   b += n3 * 8 + 16;                // GCR / Anderson current direction, Anderson slot indices
   if (o.cont_stages > 0) b += 2 * P * 8;   // full-contrast viscosity kept during continuation
-  b += mixed ? MG<float>::bytes(nx, ny, L, o.kcycle) : MG<double>::bytes(nx, ny, L, o.kcycle) - 2 * P * 8;
+  (void)L;
+  const auto sz = sizes_of(nx, ny, o);
+  b += mixed ? MG<float>::bytes(sz, o.kcycle) : MG<double>::bytes(sz, o.kcycle) - 2 * P * 8;
   b += 2 * kSubCluster * 4 * 8;
   b += 2 * (kMaxRestart + 2) * 8 + 2 * (size_t)kReduceBlocks * (kMaxRestart + 1) * 8 + 4 * kReduceBlocks * 8 +
        (size_t)kMaxRestart * kHcolStride * 8 + 64;
@@ -1193,6 +1238,8 @@ void pyro_default_opts(pyro_opts* o) {
   o->cont_stages = 0;
   o->cont_iters = 25;
   o->coarse_sweeps = 40;
+  o->coarsen_ratio = 2.0;
+  o->coarsen_general = 1;
 }
 
 const char* pyro_version(void) { return "pyro-b300 0.1 (sm_103a)"; }
@@ -1288,7 +1335,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->mgf.tile_sweeps = o.tile_sweeps;
       if (h->mgf.tiles) MG<float>::enable_tiles();
       CK(cudaDeviceSynchronize());
-      h->mgf.alloc(A, h->g, L, false);
+      h->mgf.alloc(A, h->g, Lx, Ly, sizes_of(nx, ny, o), false);
       h->mgf.setup_sub(A, o.cluster_cells);
     } else {
       h->mgd.nu1 = o.nu1; h->mgd.nu2 = o.nu2; h->mgd.omega = o.omega_v; h->mgd.eta_mode = o.eta_coarsen;
@@ -1299,7 +1346,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       if (o.smoother == PYRO_SMOOTH_RAS) MG<double>::enable_ras();
       h->mgd.tiles = o.tile_fusion64 != 0;
       if (h->mgd.tiles) MG<double>::enable_tiles();
-      h->mgd.alloc(A, h->g, L, true);
+      h->mgd.alloc(A, h->g, Lx, Ly, sizes_of(nx, ny, o), true);
       h->mgd.lv[0].en = h->en;
       h->mgd.lv[0].ec = h->ec;
       if (!h->mgd.fused(0)) h->mgd.lv[0].kc = h->okc;  // FP64 level 0 shares the outer coefficients

@@ -42,7 +42,7 @@ def test_apply_matches_oracle(nx, ny, Lx, Ly, bc):
 
 
 def _precond_case(nx, ny, Lx, Ly, bc, prec, seed, kcycle=0, cluster_cells=0, tile_fusion=1, eta_coarsen=0,
-                  eta=None, smoother=0, ras_inner=4, omega=1.0):
+                  eta=None, smoother=0, ras_inner=4, omega=1.0, coarsen_general=1, coarsen_ratio=2.0):
     kind, vt = BCS[bc]
     g = S.Grid(nx, ny, Lx, Ly, S.BC(kind, vt))
     en, ec = rand_eta(nx, ny, seed, -1, 1) if eta is None else eta
@@ -50,12 +50,14 @@ def _precond_case(nx, ny, Lx, Ly, bc, prec, seed, kcycle=0, cluster_cells=0, til
     r = rng.standard_normal(g.n)
     rx, ry, rp = S.vector_to_fields(g, r, fill_ghosts=False)
     h_or = M.Hierarchy(g, en, ec, coarsest_min=2, eta_mode=eta_coarsen, smoother=("rbgs", "jacobi", "ras")[smoother],
-                       ras_inner=ras_inner, ras_tile=32)
+                       ras_inner=ras_inner, ras_tile=32, coarsen_ratio=coarsen_ratio,
+                       coarsen_general=bool(coarsen_general))
     z = M.uzawa_precond(h_or, r, ec, alpha=1.0, nu1=2, nu2=2, omega=omega, kcycle=kcycle)
     zx, zy, zp = S.vector_to_fields(g, z, fill_ghosts=False)
     h = P.Stokes(nx, ny, Lx, Ly, bc=P.make_bc(kind, vt), prec=prec, kcycle=kcycle, cluster_cells=cluster_cells,
                  tile_fusion=tile_fusion, tile_fusion64=tile_fusion, eta_coarsen=eta_coarsen, coarsest_min=2,
-                 smoother=smoother, ras_inner=ras_inner, omega_v=omega)
+                 smoother=smoother, ras_inner=ras_inner, omega_v=omega, coarsen_general=coarsen_general,
+                 coarsen_ratio=coarsen_ratio)
     Zx, Zy, Zp = zeros(ny, nx), zeros(ny, nx), zeros(ny, nx)
     h.precond(dev(en), dev(ec), dev(rx), dev(ry), dev(rp), Zx, Zy, Zp)
     torch.cuda.synchronize()
@@ -115,10 +117,24 @@ def test_sinker_with_jacobi_smoothers_matches_direct_oracle(smoother, inner, pre
 
 @pytest.mark.parametrize("nx,ny", [(45, 33), (90, 66), (250, 150), (7, 5)])
 @pytest.mark.parametrize("prec,tf", [(P.PREC_FP64, 0), (P.PREC_MIXED, 1)])
-def test_preconditioner_on_odd_and_coarse_unfriendly_sizes_matches_oracle(nx, ny, prec, tf):
+@pytest.mark.parametrize("general", [0, 1])
+def test_preconditioner_on_odd_and_coarse_unfriendly_sizes_matches_oracle(nx, ny, prec, tf, general):
     """Grids that do not halve down to a small coarsest level (odd counts; 250 x 150 stops at
-    125 x 75): the coarsest level is smoothed (40 sweeps) instead of inverted."""
-    gpu, ora, nlev = _precond_case(nx, ny, 1.0, ny / nx, "free", prec, 29, tile_fusion=tf)
+    125 x 75): with general coarsening they continue at ratio 2 with the any-ratio transfers
+    (23 x 17, 63 x 38, ...); without it the coarsest level is smoothed (40 sweeps)."""
+    gpu, ora, nlev = _precond_case(nx, ny, 1.0, ny / nx, "free", prec, 29, tile_fusion=tf, coarsen_general=general)
+    for a, b in zip(gpu, ora):
+        assert rel(a, b) <= (1e-11 if prec == P.PREC_FP64 else 2e-4), (rel(a, b), nlev)
+
+
+@pytest.mark.parametrize("nx,ny,ratio", [(100, 80, 2.5), (120, 96, 3.0), (64, 48, 2.5), (101, 77, 2.0)])
+@pytest.mark.parametrize("prec,tf", [(P.PREC_FP64, 0), (P.PREC_MIXED, 1)])
+def test_preconditioner_with_arbitrary_coarsening_ratio_matches_oracle(nx, ny, ratio, prec, tf):
+    """The paper's arbitrary coarsening ratio (e.g. 2.5): every level n_c = ceil(n / ratio), the
+    normalised bilinear restriction and bilinear prolongation at that ratio, eta transferred the
+    same way, direct solve once the coarsest level is small."""
+    gpu, ora, nlev = _precond_case(nx, ny, 1.0, ny / nx, "free", prec, 31, tile_fusion=tf, coarsen_ratio=ratio)
+    assert nlev >= 2
     for a, b in zip(gpu, ora):
         assert rel(a, b) <= (1e-11 if prec == P.PREC_FP64 else 2e-4), (rel(a, b), nlev)
 

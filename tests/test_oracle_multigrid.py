@@ -286,7 +286,7 @@ def test_large_coarsest_level_is_smoothed_and_the_cycle_still_contracts():
     g = S.Grid(90, 66, 1.0, 66 / 90)
     rng = np.random.default_rng(47)
     en = 10.0 ** rng.uniform(-0.5, 0.5, (68, 92)); ec = 10.0 ** rng.uniform(-0.5, 0.5, (68, 92))
-    h = M.Hierarchy(g, en, ec, coarsest_min=4, coarse_sweeps=40)
+    h = M.Hierarchy(g, en, ec, coarsest_min=4, coarse_sweeps=40, coarsen_general=False)
     assert h.nlev == 2 and not h.coarse_direct
     L = h.L[0]
     e = rng.standard_normal(L.shape[0])
@@ -295,3 +295,63 @@ def test_large_coarsest_level_is_smoothed_and_the_cycle_still_contracts():
         rate = np.linalg.norm(e_new) / np.linalg.norm(e)
         e = e_new
     assert rate < 0.9
+
+
+
+# ---- arbitrary coarsening ratio ------------------------------------------------------------------
+@pytest.mark.parametrize("ratio", [2.0, 2.5, 3.0])
+def test_level_sizes_rule(ratio):
+    sizes = M.level_sizes(500, 600, 4, ratio)
+    assert sizes[0] == (500, 600)
+    assert M.velocity_unknowns(*sizes[-1]) <= M.MAX_COARSE
+    for (a, b), (c, d) in zip(sizes, sizes[1:]):
+        if ratio == 2.0 and a % 2 == 0 and b % 2 == 0 and min(a, b) // 2 >= 4:
+            assert (c, d) == (a // 2, b // 2)
+        else:
+            assert (c, d) == (int(np.ceil(a / ratio - 1e-9)), int(np.ceil(b / ratio - 1e-9)))
+    assert M.level_sizes(45, 33, 4) == [(45, 33), (23, 17)]
+
+
+@pytest.mark.parametrize("nf,nc", [((45, 33), (23, 17)), ((100, 80), (40, 32)), ((37, 29), (13, 10))])
+def test_general_transfer_operators(nf, nc):
+    """Any ratio: the normalised restriction maps constants to constants; bilinear prolongation
+    reproduces a bilinear function at every fine unknown whose interpolation stencil avoids the
+    wall ghosts; R and P have the supports of one coarse spacing."""
+    fine = S.Grid(nf[0], nf[1], 1.3, 0.9)
+    coarse = M.coarsen_grid(fine, *nc)
+    for fld in ("vx", "vy"):
+        R = M.restriction_matrix(fine, coarse, fld)
+        P = M.prolongation_matrix(fine, coarse, fld)
+        nF = R.shape[1]
+        assert np.allclose(R @ np.ones(nF), 1.0, atol=1e-13)
+        Xc, Yc = M.positions(coarse, fld)
+        Xf, Yf = M.positions(fine, fld)
+        f = lambda x, y: 0.4 + 1.1 * x - 0.7 * y + 0.9 * x * y
+        pf = P @ f(Xc, Yc)
+        H, K = coarse.dx, coarse.dy
+        if fld == "vx":
+            inner = (Xf > H) & (Xf < fine.Lx - H) & (Yf > K / 2) & (Yf < fine.Ly - K / 2)
+        else:
+            inner = (Xf > H / 2) & (Xf < fine.Lx - H / 2) & (Yf > K) & (Yf < fine.Ly - K)
+        assert inner.sum() > 10
+        assert np.allclose(pf[inner], f(Xf, Yf)[inner], atol=1e-12)
+        C = R.tocoo()
+        assert np.all(np.abs(Xf[C.col] - Xc[C.row]) < H) and np.all(np.abs(Yf[C.col] - Yc[C.row]) < K)
+    en, ec = M.coarsen_eta(fine, coarse, np.full((nf[1] + 2, nf[0] + 2), 2.5), np.full((nf[1] + 2, nf[0] + 2), 2.5))
+    assert np.allclose(en[:nc[1] + 1, :nc[0] + 1], 2.5) and np.allclose(ec[1:nc[1] + 1, 1:nc[0] + 1], 2.5)
+
+
+@pytest.mark.parametrize("ratio", [2.0, 2.5])
+def test_vcycle_with_general_levels_contracts(ratio):
+    g = S.Grid(90, 66, 1.0, 66 / 90)
+    rng = np.random.default_rng(53)
+    en = 10.0 ** rng.uniform(-0.5, 0.5, (68, 92)); ec = 10.0 ** rng.uniform(-0.5, 0.5, (68, 92))
+    h = M.Hierarchy(g, en, ec, coarsest_min=4, coarsen_ratio=ratio)
+    assert h.coarse_direct and h.nlev >= 2
+    L = h.L[0]
+    e = rng.standard_normal(L.shape[0])
+    for _ in range(6):
+        e_new = e - M.vcycle(h, L @ e, 2, 2, 1.0)
+        rate = np.linalg.norm(e_new) / np.linalg.norm(e)
+        e = e_new
+    assert rate < 0.6
