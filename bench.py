@@ -248,6 +248,35 @@ def marker_sample(n=1024, per_cell=16, reps=5):
     return res
 
 
+def sinker_e1_sample():
+    """The robustness sinker at the paper's grid (501 x 601 nodes = 500 x 600 cells, box 1 x 1.2,
+    contrast 1e8, density contrast 1.03125), mixed precision, lithostatic start, tol 1e-8: the
+    default hierarchy (halving, then ratio-2 general coarsening) and the paper's ratio 2.5."""
+    import torch
+    import paper_2603_14040_b300 as P
+    from synth import sinker
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    nx, ny = 500, 600
+    f = sinker(nx, ny, 1.0, 1.2, eta_bg=1.0, rho_bg=1.0, eta_inc=1e8, rho_inc=1.03125, r=0.2)
+    en, ec, rho = dev(f.eta_n), dev(f.eta_c), dev(f.rho)
+    outs = [torch.zeros((ny + 2, nx + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
+    res = {}
+    for name, kw in (("ratio2_default", {}), ("ratio2.5", {"coarsen_ratio": 2.5}),
+                     ("ratio2.5_restart100", {"coarsen_ratio": 2.5, "restart_m": 100})):
+        h = P.Stokes(nx, ny, 1.0, 1.2, prec=P.PREC_MIXED, max_iter=3000, litho_guess=1, **kw)
+        h.solve(en, ec, rho, (0.0, 1.0), 1e-8, *outs)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        st = h.solve(en, ec, rho, (0.0, 1.0), 1e-8, *outs)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = {"ms": e0.elapsed_time(e1), "iters": st.iters, "status": st.status, "levels": st.levels,
+                     "rel_energy_res": st.rel_energy_res}
+        h.close()
+    return res
+
+
 def serving_sample(n_req=48, slots=4, max_iter=3000, restart_m=200, seed=4):
     """Continuous batching on a bounded sample of the serving workload: requests with n in
     {128, 256, 512}, aspect in {1, 2, 4}, 16 inclusions of contrast 10^U[2,6], tol 1e-8, Poisson
@@ -531,6 +560,7 @@ def main():
         line["vcycle_roofline"] = vcycle_rooflines(peaks)
         line["accelerators"] = accelerator_sample(f, n)
         line["markers"] = marker_sample()
+        line["sinker_1e8_500x600"] = sinker_e1_sample()
         line["serving"] = serving_sample()
         line["adjoint"] = adjoint_sample()
     if rank == 0 and not args.no_cpu_baseline:

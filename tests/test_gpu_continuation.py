@@ -70,3 +70,18 @@ def test_sinker_contrast_1e8_stress(stages):
     assert rel(xg[:g.n_v], sol.x[:g.n_v]) <= 2e-5 and rel(xg[g.n_v:], sol.x[g.n_v:]) <= 2e-5
     print("contrast 1e8 sinker", "stages", stages, "iters", st.iters, "err v", rel(xg[:g.n_v], sol.x[:g.n_v]),
           "err p", rel(xg[g.n_v:], sol.x[g.n_v:]))
+
+
+def test_sinker_at_the_papers_grid_size():
+    """The robustness sinker at the paper's grid of 501 x 601 nodes (500 x 600 cells, box 1 x 1.2,
+    contrast 1e8), mixed precision with the lithostatic start: 500 x 600 halves twice to 125 x 150
+    and then coarsens at ratio 2 with the any-ratio transfers (63 x 75, 32 x 38, 16 x 19). It must
+    reach a 1e-8 energy residual, which the oracle recomputes from its own assembly."""
+    nx, ny, tol = 500, 600, 1e-8
+    f = sinker(nx, ny, 1.0, 1.2, eta_bg=1.0, rho_bg=1.0, eta_inc=1e8, rho_inc=1.03125, r=0.2)
+    out, st = _solve_gpu(f, (0.0, 1.0), tol, P.PREC_MIXED, Lx=1.0, Ly=1.2, litho_guess=1, max_iter=1000)
+    assert st.status == P.PYRO_OK and st.levels == 6, st.as_dict()
+    g = S.Grid(nx, ny, 1.0, 1.2)
+    sysm = S.assemble(g, f.eta_n, f.eta_c, f.rho, (0.0, 1.0))
+    e_or, _ = S.energy_residual(sysm, f.eta_c, S.fields_to_vector(g, *out))
+    assert e_or <= 1.01 * tol and abs(e_or - st.rel_energy_res) <= 1e-3 * e_or + 1e-12
