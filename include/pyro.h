@@ -121,7 +121,9 @@ typedef struct {
                             levels; FP64 levels see tile_fusion64); 2: as 1, but FP32 levels large
                             enough for it (row chunks of >= 96 rows at two CTAs per SM) smooth with
                             the row-streaming wavefront kernel; 3: as 2 on every FP32 level (for
-                            tests and tuning); 0: one kernel per colour and step [1] */
+                            tests and tuning); 4: as 1 with the 64 x 32 colour-split tiles on large
+                            levels instead of the warp-per-row tiles; 0: one kernel per colour and
+                            step [1] */
   int tile_sweeps;       /* FP32 tile kernels: sweeps fused per launch, 1 (halo 4, one HBM pass per
                             sweep) or 2 (halo 8, one pass per two sweeps) [2] */
   int tile_fusion64;     /* 1: FP64 levels of up to 65536 cells also smooth and restrict with the

@@ -389,4 +389,227 @@ __global__ void __launch_bounds__(kTileThreads)
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP32 tile sweep, warp-per-row form. The region is 64 columns wide (a tile of TX = 64 - 8 NS
+// owned columns plus the 4 NS halo on each side), so each colour plane row has exactly 32 slots:
+// lane k of a warp owns slot k of a row, warps stride over rows. No per-point division or
+// modulo, and the region loads and the final stores move column pairs (one 8-byte access for
+// the two colours of a pair when the row stride is even). Same point arithmetic as
+// cs_halfsweep.
+// ---------------------------------------------------------------------------------------------
+template <int NS, int TY>
+struct SweepTileW {
+  static constexpr int M = 4 * NS;
+  static constexpr int RX = 64, TX = RX - 2 * M, RY = TY + 2 * M, HX = 32;
+  static constexpr int PLANE = RY * HX;
+  static constexpr int CY = RY / 2 + 2, CX = RX / 2 + 2, CPL = CY * CX;
+  static constexpr size_t smem_bytes() { return ((size_t)PLANE * 2 * 6 + 2 * CPL) * sizeof(float); }
+};
+
+template <bool INTERIOR, typename Tl>
+__device__ __forceinline__ void w_halfsweep(const GeomT<float>& g, float* smf, int fld, int col, float omega,
+                                            int i0, int j0, int r0, int r1, int c0, int c1) {
+  constexpr int HX = Tl::HX, PL = Tl::PLANE;
+  const float* Xo = smf + (0 + (col ^ 1)) * PL;
+  const float* Xs = smf + (0 + col) * PL;
+  const float* Yo = smf + (2 + (col ^ 1)) * PL;
+  const float* Ys = smf + (2 + col) * PL;
+  const float* No = smf + (8 + (col ^ 1)) * PL;
+  const float* Ns = smf + (8 + col) * PL;
+  const float* Eo = smf + (10 + (col ^ 1)) * PL;
+  const float* Es = smf + (10 + col) * PL;
+  float* U = smf + (2 * fld + col) * PL;
+  const float* F = smf + (4 + 2 * fld + col) * PL;
+  const int k = threadIdx.x & 31;
+  for (int ri = r0 + (int)(threadIdx.x >> 5); ri < r1; ri += (int)(blockDim.x >> 5)) {
+    const int gi = i0 + ri;
+    const int p = (col + gi) & 1;          // j0 is even
+    const int rj = 2 * k + p;
+    if (rj < c0 || rj >= c1) continue;
+    const int gj = j0 + rj;
+    const int s = ri * HX + k;
+    const int kw = s - 1 + p, ke = s + p;
+    if (fld == 0) {
+      if (!INTERIOR && !is_vx(g.nx, g.ny, gi, gj)) continue;
+      const float vc = Xs[s];
+      const float eA = Es[s], eB = Eo[ke];
+      const float e1 = No[s - HX], e2 = Ns[s];
+      float vw = Xo[kw], ve = Xo[ke], vn = Xo[s - HX], vs = Xo[s + HX];
+      float yA = Yo[s - HX], yB = Ys[s - HX + p], yC = Ys[s], yD = Yo[ke];
+      if (!INTERIOR) {
+        if (gj - 1 < 1) vw = 0.f;
+        if (gj + 1 > g.nx - 1) ve = 0.f;
+        if (gi == 1) vn = g.sN * vc;
+        if (gi == g.ny) vs = g.sS * vc;
+        if (gi - 1 < 1) { yA = 0.f; yB = 0.f; }
+        if (gi > g.ny - 1) { yC = 0.f; yD = 0.f; }
+      }
+      const float sxxE = 2.f * eB * (ve - vc);
+      const float sxxW = 2.f * eA * (vc - vw);
+      const float sxyS = e2 * ((vs - vc) * g.idy2 + (yD - yC) * g.idxdy);
+      const float sxyN = e1 * ((vc - vn) * g.idy2 + (yB - yA) * g.idxdy);
+      float diag = -2.f * (eA + eB) * g.idx2 - (e1 + e2) * g.idy2;
+      if (!INTERIOR) {
+        if (gi == 1) diag += g.sN * e1 * g.idy2;
+        if (gi == g.ny) diag += g.sS * e2 * g.idy2;
+      }
+      const float Lv = (sxxE - sxxW) * g.idx2 + sxyS - sxyN;
+      U[s] = vc + omega * __fdividef(F[s] - Lv, diag);
+    } else {
+      if (!INTERIOR && !is_vy(g.nx, g.ny, gi, gj)) continue;
+      const float vc = Ys[s];
+      const float eA = Es[s], eB = Eo[s + HX];
+      const float e1 = No[kw], e2 = Ns[s];
+      float vn = Yo[s - HX], vs = Yo[s + HX], vw = Yo[kw], ve = Yo[ke];
+      float xA = Xo[kw], xB = Xs[s + HX - 1 + p], xC = Xs[s], xD = Xo[s + HX];
+      if (!INTERIOR) {
+        if (gi - 1 < 1) vn = 0.f;
+        if (gi + 1 > g.ny - 1) vs = 0.f;
+        if (gj == 1) vw = g.sW * vc;
+        if (gj == g.nx) ve = g.sE * vc;
+        if (gj - 1 < 1) { xA = 0.f; xB = 0.f; }
+        if (gj > g.nx - 1) { xC = 0.f; xD = 0.f; }
+      }
+      const float syyS = 2.f * eB * (vs - vc);
+      const float syyN = 2.f * eA * (vc - vn);
+      const float sxyE = e2 * ((ve - vc) * g.idx2 + (xD - xC) * g.idxdy);
+      const float sxyW = e1 * ((vc - vw) * g.idx2 + (xB - xA) * g.idxdy);
+      float diag = -2.f * (eA + eB) * g.idy2 - (e1 + e2) * g.idx2;
+      if (!INTERIOR) {
+        if (gj == 1) diag += g.sW * e1 * g.idx2;
+        if (gj == g.nx) diag += g.sE * e2 * g.idx2;
+      }
+      const float Lv = (syyS - syyN) * g.idy2 + sxyE - sxyW;
+      U[s] = vc + omega * __fdividef(F[s] - Lv, diag);
+    }
+  }
+}
+
+template <int NS, int TY>
+__global__ void __launch_bounds__(kTileThreads)
+    k_rbgs_tile_w(GeomT<float> g, const float* __restrict__ vx, const float* __restrict__ vy,
+                  float* __restrict__ ox, float* __restrict__ oy, const float* __restrict__ fx,
+                  const float* __restrict__ fy, const float* __restrict__ en, const float* __restrict__ ec,
+                  float omega, GeomT<float> gc, const float* __restrict__ cvx, const float* __restrict__ cvy) {
+  using Tl = SweepTileW<NS, TY>;
+  constexpr int M = Tl::M, RX = Tl::RX, RY = Tl::RY, HX = Tl::HX, PL = Tl::PLANE, TX = Tl::TX;
+  extern __shared__ __align__(16) float smf[];
+  const int i0 = blockIdx.y * TY - M, j0 = blockIdx.x * TX - M;   // j0 even (TX, M even)
+  const int rlo = max(0, -i0), rhi = min(RY, g.ny + 2 - i0);
+  const int clo = max(0, -j0), chi = min(RX, g.nx + 2 - j0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+
+  float* cbx = smf + 12 * PL;
+  float* cby = cbx + Tl::CPL;
+  const int I0 = (i0 >> 1) - 1, J0 = (j0 >> 1) - 1;
+  if (cvx) {
+    for (int t = threadIdx.x; t < Tl::CY * Tl::CX; t += blockDim.x) {
+      const int I = I0 + t / Tl::CX, J = J0 + t % Tl::CX;
+      const bool in = I >= 0 && I <= gc.ny + 1 && J >= 0 && J <= gc.nx + 1;
+      cbx[t] = in ? coarse_vx(gc, cvx, I, J) : 0.f;
+      cby[t] = in ? coarse_vy(gc, cvy, I, J) : 0.f;
+    }
+    __syncthreads();
+  }
+  auto cvxs = [&](int I, int J) { return cbx[(I - I0) * Tl::CX + (J - J0)]; };
+  auto cvys = [&](int I, int J) { return cby[(I - I0) * Tl::CX + (J - J0)]; };
+  auto prolong = [&](int gi, int gj, float& a, float& b) {
+    if (is_vx(g.nx, g.ny, gi, gj)) {
+      const int Ia = (gi & 1) ? (gi - 1) / 2 : gi / 2;
+      const float wy0 = (gi & 1) ? 0.25f : 0.75f, wy1 = 1.f - wy0;
+      if (gj & 1) {
+        const int Ja = (gj - 1) / 2;
+        a += 0.5f * (wy0 * cvxs(Ia, Ja) + wy1 * cvxs(Ia + 1, Ja) + wy0 * cvxs(Ia, Ja + 1) + wy1 * cvxs(Ia + 1, Ja + 1));
+      } else {
+        const int Jc = gj / 2;
+        a += wy0 * cvxs(Ia, Jc) + wy1 * cvxs(Ia + 1, Jc);
+      }
+    }
+    if (is_vy(g.nx, g.ny, gi, gj)) {
+      const int Ja = (gj & 1) ? (gj - 1) / 2 : gj / 2;
+      const float wx0 = (gj & 1) ? 0.25f : 0.75f, wx1 = 1.f - wx0;
+      if (gi & 1) {
+        const int Ia = (gi - 1) / 2;
+        b += 0.5f * (wx0 * cvys(Ia, Ja) + wx1 * cvys(Ia, Ja + 1) + wx0 * cvys(Ia + 1, Ja) + wx1 * cvys(Ia + 1, Ja + 1));
+      } else {
+        const int Ic = gi / 2;
+        b += wx0 * cvys(Ic, Ja) + wx1 * cvys(Ic, Ja + 1);
+      }
+    }
+  };
+
+  // load: lane takes the column pair (2 lane, 2 lane + 1); element (ri, 2k + h) goes to the plane
+  // of its colour at slot k
+  const bool even_ld = (g.ld & 1) == 0;
+  for (int ri = rlo + warp; ri < rhi; ri += nw) {
+    const int gi = i0 + ri;
+    const int c = gi & 1;                    // colour of the pair's even column (j0 even)
+    const int s = ri * HX + lane;
+    const int rj = 2 * lane, gj = j0 + rj;
+    float a[2] = {0.f, 0.f}, b[2] = {0.f, 0.f}, f0[2] = {0.f, 0.f}, f1[2] = {0.f, 0.f}, e0[2] = {0.f, 0.f},
+          e1[2] = {0.f, 0.f};
+    const size_t o = (size_t)gi * g.ld + gj;
+    if (even_ld && rj >= clo && rj + 1 < chi) {
+      const float2 va = *reinterpret_cast<const float2*>(vx + o), vb = *reinterpret_cast<const float2*>(vy + o);
+      const float2 vf0 = *reinterpret_cast<const float2*>(fx + o), vf1 = *reinterpret_cast<const float2*>(fy + o);
+      const float2 ve0 = *reinterpret_cast<const float2*>(en + o), ve1 = *reinterpret_cast<const float2*>(ec + o);
+      a[0] = va.x; a[1] = va.y; b[0] = vb.x; b[1] = vb.y; f0[0] = vf0.x; f0[1] = vf0.y;
+      f1[0] = vf1.x; f1[1] = vf1.y; e0[0] = ve0.x; e0[1] = ve0.y; e1[0] = ve1.x; e1[1] = ve1.y;
+    } else {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (rj + h < clo || rj + h >= chi) continue;
+        a[h] = vx[o + h]; b[h] = vy[o + h]; f0[h] = fx[o + h]; f1[h] = fy[o + h]; e0[h] = en[o + h]; e1[h] = ec[o + h];
+      }
+    }
+    if (cvx) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (rj + h >= clo && rj + h < chi) prolong(gi, gj + h, a[h], b[h]);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int pc = c ^ h;
+      smf[(0 + pc) * PL + s] = a[h];
+      smf[(2 + pc) * PL + s] = b[h];
+      smf[(4 + pc) * PL + s] = f0[h];
+      smf[(6 + pc) * PL + s] = f1[h];
+      smf[(8 + pc) * PL + s] = e0[h];
+      smf[(10 + pc) * PL + s] = e1[h];
+    }
+  }
+  __syncthreads();
+
+  const bool interior = i0 >= 2 && i0 + RY - 1 <= g.ny - 2 && j0 >= 2 && j0 + RX - 1 <= g.nx - 2;
+  int hs = 0;
+  for (int sw = 0; sw < NS; ++sw)
+    for (int fld = 0; fld < 2; ++fld)
+      for (int col = 0; col < 2; ++col, ++hs) {
+        const int m = hs + 1;
+        const int r0 = max(m, rlo), r1 = min(RY - m, rhi);
+        const int c0 = max(m, clo), c1 = min(RX - m, chi);
+        if (interior) w_halfsweep<true, Tl>(g, smf, fld, col, omega, i0, j0, r0, r1, c0, c1);
+        else w_halfsweep<false, Tl>(g, smf, fld, col, omega, i0, j0, r0, r1, c0, c1);
+        __syncthreads();
+      }
+
+  // store the owned columns [M, M + TX) of rows [M, M + TY) at the unknowns
+  for (int ri = M + warp; ri < M + TY; ri += nw) {
+    const int gi = i0 + ri;
+    if (gi > g.ny + 1) break;
+    const int c = gi & 1;
+    const int rj = 2 * lane, gj = j0 + rj;
+    if (rj < M || rj >= M + TX) continue;   // M even: a pair is wholly owned or not
+    const int s = ri * HX + lane;
+    const size_t o = (size_t)gi * g.ld + gj;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (gj + h > g.nx + 1) continue;
+      const int pc = c ^ h;
+      if (is_vx(g.nx, g.ny, gi, gj + h)) ox[o + h] = smf[(0 + pc) * PL + s];
+      if (is_vy(g.nx, g.ny, gi, gj + h)) oy[o + h] = smf[(2 + pc) * PL + s];
+    }
+  }
+}
+
 }  // namespace pyro

@@ -28,6 +28,7 @@ constexpr int kMaxCoarse = 1024;
 constexpr int kStreamMinRows = 96;  // shortest row chunk worth a streaming pass
 constexpr int kRasTile = 32;        // RAS-type Jacobi tile edge (cells), the paper's 32 x 32
 constexpr long long kSmallTileCells = 65536;  // FP32 levels up to 256^2 smooth with 32 x 16 tiles
+constexpr int kWTileY2 = 32;        // owned rows of the two-sweep warp-per-row tile
 
 struct CudaError {
   cudaError_t e;
@@ -139,6 +140,7 @@ struct MG {
   int ls = -1;     // first level run by the cluster sub-cycle kernel (-1: none)
   bool tiles = true;                        // tile-fused smoothing / residual+restriction
   int stream = 0;                           // FP32 row-streaming sweeps: 0 never, 1 large levels, 2 all
+  int tile_form = 0;                        // FP32 large levels: 0 warp-per-row tiles, 1 64 x 32 colour-split
   int smoother = PYRO_SMOOTH_RBGS;          // velocity smoother of every level
   int ras_inner = 4;                        // RAS-type Jacobi: local iterations per tile pass
   int tile_sweeps = 2;                      // FP32: sweeps fused per tile launch
@@ -318,7 +320,20 @@ struct MG {
         float* ox = L.cur ? L.vx : L.vx2;
         float* oy = L.cur ? L.vy : L.vy2;
         const int ns = (nsweeps >= 2 && tile_sweeps >= 2) ? 2 : 1;
-        if ((long long)L.g.nx * L.g.ny > kSmallTileCells) {
+        if ((long long)L.g.nx * L.g.ny > kSmallTileCells && tile_form == 0) {
+          // large levels: warp-per-row tiles (64-column regions, 32-slot colour rows)
+          if (ns == 2) {
+            using Tl = SweepTileW<2, kWTileY2>;
+            const dim3 gr((L.g.nx + 2 + Tl::TX - 1) / Tl::TX, (L.g.ny + 2 + kWTileY2 - 1) / kWTileY2);
+            k_rbgs_tile_w<2, kWTileY2><<<gr, kTileThreads, Tl::smem_bytes(), s>>>(
+                L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, gc, cvx, cvy);
+          } else {
+            using Tl = SweepTileW<1, 32>;
+            const dim3 gr((L.g.nx + 2 + Tl::TX - 1) / Tl::TX, (L.g.ny + 2 + 31) / 32);
+            k_rbgs_tile_w<1, 32><<<gr, kTileThreads, Tl::smem_bytes(), s>>>(
+                L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, gc, cvx, cvy);
+          }
+        } else if ((long long)L.g.nx * L.g.ny > kSmallTileCells) {
           constexpr int TX = 64, TY = 32;   // large levels: the least halo recomputation
           const dim3 gr((L.g.nx + 2 + TX - 1) / TX, (L.g.ny + 2 + TY - 1) / TY);
           if (ns == 2)
@@ -399,6 +414,10 @@ struct MG {
                               (int)SweepTileCS<2, 64, 32>::smem_bytes()));
       CK(cudaFuncSetAttribute(k_rbgs_tile_cs<1, 64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)SweepTileCS<1, 64, 32>::smem_bytes()));
+      CK(cudaFuncSetAttribute(k_rbgs_tile_w<2, kWTileY2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SweepTileW<2, kWTileY2>::smem_bytes()));
+      CK(cudaFuncSetAttribute(k_rbgs_tile_w<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SweepTileW<1, 32>::smem_bytes()));
       CK(cudaFuncSetAttribute(k_rbgs_tile_cs<2, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)SweepTileCS<2, 32, 16>::smem_bytes()));
       CK(cudaFuncSetAttribute(k_rbgs_tile_cs<1, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1331,7 +1350,8 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->mgf.ras_inner = o.ras_inner;
       if (o.smoother == PYRO_SMOOTH_RAS) MG<float>::enable_ras();
       h->mgf.tiles = o.tile_fusion != 0;
-      h->mgf.stream = o.tile_fusion >= 2 ? o.tile_fusion - 1 : 0;
+      h->mgf.stream = (o.tile_fusion == 2 || o.tile_fusion == 3) ? o.tile_fusion - 1 : 0;
+      h->mgf.tile_form = o.tile_fusion == 4 ? 1 : 0;
       h->mgf.tile_sweeps = o.tile_sweeps;
       if (h->mgf.tiles) MG<float>::enable_tiles();
       CK(cudaDeviceSynchronize());

@@ -157,8 +157,8 @@ def test_preconditioner_kcycle_fp64_matches_oracle(nx, ny, Lx, Ly, kc, cc, tf):
         assert rel(a, b) <= 1e-10, (rel(a, b), nlev)
 
 
-@pytest.mark.parametrize("nx,ny", [(16, 16), (48, 80), (320, 192)])
-@pytest.mark.parametrize("tf", [0, 1, 3])
+@pytest.mark.parametrize("nx,ny", [(16, 16), (48, 80), (320, 192), (512, 386)])
+@pytest.mark.parametrize("tf", [0, 1, 3, 4])
 def test_preconditioner_fp32_close_to_oracle(nx, ny, tf):
     gpu, ora, _ = _precond_case(nx, ny, 1.0, 1.0, "free", P.PREC_MIXED, 5, tile_fusion=tf)
     for a, b in zip(gpu, ora):
@@ -179,7 +179,7 @@ def test_fp32_tile_fusion_matches_unfused(nx, ny, kc):
     r = rng.standard_normal(g.n)
     rx, ry, rp = S.vector_to_fields(g, r, fill_ghosts=False)
     outs = []
-    for tf in (0, 1, 2, 3):
+    for tf in (0, 1, 2, 3, 4):
         h = P.Stokes(nx, ny, prec=P.PREC_MIXED, kcycle=kc, tile_fusion=tf)
         Z = [zeros(ny, nx) for _ in range(3)]
         h.precond(dev(en), dev(ec), dev(rx), dev(ry), dev(rp), *Z)
