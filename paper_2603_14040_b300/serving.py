@@ -232,15 +232,22 @@ def poisson_arrivals(n, rate, seed):
 
 
 class PyroBackend:
-    """libpyro backend: handles are pyro.Stokes objects; inputs/outputs are CUDA tensors."""
+    """libpyro backend: handles are pyro.Stokes objects; inputs/outputs are CUDA tensors.
 
-    def __init__(self, opts_kw=None, device=0):
+    With restart_choices (descending FGMRES restart lengths), each shape gets the longest restart
+    whose handle fits in per_handle_bytes (default: the budget shared by four slots), so large
+    grids still admit several concurrent solves while small ones keep long Krylov cycles (the
+    high-contrast requests need them)."""
+
+    def __init__(self, opts_kw=None, device=0, restart_choices=None, per_handle_bytes=None):
         import torch
         from . import pyro as P
         self.P = P
         self.torch = torch
         self.device = device
         self.opts_kw = dict(opts_kw or {})
+        self.restart_choices = tuple(restart_choices) if restart_choices else None
+        self.per_handle_bytes = per_handle_bytes
         self._fp = {}
 
     def default_budget(self):
@@ -250,14 +257,26 @@ class PyroBackend:
     def make_stream(self):
         return self.torch.cuda.Stream(device=self.device)
 
-    def footprint(self, shape):
+    def opts_for(self, shape):
+        """Options of the handle for `shape` (the restart length chosen for it)."""
         if shape not in self._fp:
-            self._fp[shape] = self.P.footprint(shape[0], shape[1], self.P.default_opts(**self.opts_kw))
-        return self._fp[shape]
+            kw = dict(self.opts_kw)
+            if self.restart_choices:
+                cap = self.per_handle_bytes if self.per_handle_bytes is not None else self.default_budget() // 4
+                for m in self.restart_choices:
+                    kw["restart_m"] = m
+                    if self.P.footprint(shape[0], shape[1], self.P.default_opts(**kw)) <= cap:
+                        break
+            self._fp[shape] = (kw, self.P.footprint(shape[0], shape[1], self.P.default_opts(**kw)))
+        return self._fp[shape][0]
+
+    def footprint(self, shape):
+        self.opts_for(shape)
+        return self._fp[shape][1]
 
     def create(self, shape):
         nx, ny, Lx, Ly = shape
-        return self.P.Stokes(nx, ny, Lx, Ly, **self.opts_kw)
+        return self.P.Stokes(nx, ny, Lx, Ly, **self.opts_for(shape))
 
     def destroy(self, h):
         h.close()

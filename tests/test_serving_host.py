@@ -168,3 +168,18 @@ def test_poisson_arrivals_and_latency_stats():
     st = latency_stats(reqs)
     assert st["n"] == 100 and st["p50_ms"] == pytest.approx(50.5, rel=1e-6)
     assert st["p99_ms"] == pytest.approx(99.01, rel=1e-4)
+
+
+def test_restart_length_is_chosen_per_shape_to_fit():
+    """The libpyro backend picks, per grid shape, the longest restart whose handle fits the
+    per-handle share of the budget (host-side footprint only; no GPU)."""
+    pytest.importorskip("torch")
+    from paper_2603_14040_b300.serving import PyroBackend
+    import paper_2603_14040_b300 as P
+    be = PyroBackend(opts_kw={"prec": 1}, restart_choices=(200, 100, 50, 30), per_handle_bytes=4 * 2**30)
+    small, big = (256, 256, 1.0, 1.0), (4096, 1024, 4.0, 1.0)
+    assert be.opts_for(small)["restart_m"] == 200
+    m_big = be.opts_for(big)["restart_m"]
+    assert m_big < 200
+    assert be.footprint(big) <= 4 * 2**30 or m_big == 30
+    assert be.footprint(small) == P.footprint(256, 256, P.default_opts(prec=1, restart_m=200))
