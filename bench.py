@@ -41,7 +41,8 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"pyro_bench_clocks_rank{gpu_index}_{os.getpid()}.csv")
 
     def start(self):
         try:
