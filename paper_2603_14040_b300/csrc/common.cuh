@@ -159,6 +159,39 @@ __device__ inline T ly_coef(const GeomT<T>& g, int i, int j, const SV* vx, const
          k.nxx[c - 1] * (vc - vw) - k.nxy[c - 1] * (xB - xA);
 }
 
+// Off-diagonal part of the velocity rows with precomputed coefficients: L v = off + diag v_c,
+// where the ghost-eliminated neighbour (vn at i = 1, vs at i = ny for vx; vw at j = 1, ve at
+// j = nx for vy) belongs to the diagonal and is left out here. With 1/diag the damped
+// Gauss-Seidel update is v <- (1 - omega) v + omega (f - off) / diag: about a third fewer FP64
+// operations than forming L v in full.
+template <typename T, typename SV>
+__device__ inline T lx_off(const GeomT<T>& g, int i, int j, const SV* vx, const SV* vy, const Coef<T>& k) {
+  const int ld = g.ld;
+  const size_t c = (size_t)i * ld + j;
+  const T vw = ldvx<T>(vx, ld, g.nx, i, j - 1);
+  const T ve = ldvx<T>(vx, ld, g.nx, i, j + 1);
+  const T yA = ldvy<T>(vy, ld, g.ny, i - 1, j), yB = ldvy<T>(vy, ld, g.ny, i - 1, j + 1);
+  const T yC = ldvy<T>(vy, ld, g.ny, i, j), yD = ldvy<T>(vy, ld, g.ny, i, j + 1);
+  T s = k.cxx[c + 1] * ve + k.cxx[c] * vw + k.nxy[c] * (yD - yC) - k.nxy[c - ld] * (yB - yA);
+  if (i != 1) s += k.nyy[c - ld] * (T)vx[c - ld];
+  if (i != g.ny) s += k.nyy[c] * (T)vx[c + ld];
+  return s;
+}
+
+template <typename T, typename SV>
+__device__ inline T ly_off(const GeomT<T>& g, int i, int j, const SV* vx, const SV* vy, const Coef<T>& k) {
+  const int ld = g.ld;
+  const size_t c = (size_t)i * ld + j;
+  const T vn = ldvy<T>(vy, ld, g.ny, i - 1, j);
+  const T vs = ldvy<T>(vy, ld, g.ny, i + 1, j);
+  const T xA = ldvx<T>(vx, ld, g.nx, i, j - 1), xB = ldvx<T>(vx, ld, g.nx, i + 1, j - 1);
+  const T xC = ldvx<T>(vx, ld, g.nx, i, j), xD = ldvx<T>(vx, ld, g.nx, i + 1, j);
+  T s = k.cyy[c + ld] * vs + k.cyy[c] * vn + k.nxy[c] * (xD - xC) - k.nxy[c - 1] * (xB - xA);
+  if (j != 1) s += k.nxx[c - 1] * (T)vy[c - 1];
+  if (j != g.nx) s += k.nxx[c] * (T)vy[c + 1];
+  return s;
+}
+
 // Error flags written by kernels (host reads them after a sync).
 enum : int { FLAG_NONFINITE = 1, FLAG_BREAKDOWN = 2 };
 

@@ -36,12 +36,22 @@ __device__ inline void rbgs_point(const GeomT<T>& g, int i, int j, int field, T 
   T diag;
   if (field == 0) {
     if (!is_vx(g.nx, g.ny, i, j)) return;
-    const T Lv = (kc.cxx && idgx) ? lx_coef<T>(g, i, j, vx, vy, kc) : lx_point<T>(g, i, j, vx, vy, en, ec, diag);
+    if (kc.cxx && idgx) {
+      const T t = idgx[c] * (fx[c] - lx_off<T>(g, i, j, vx, vy, kc));
+      vx[c] = omega == T(1) ? t : (T(1) - omega) * vx[c] + omega * t;
+      return;
+    }
+    const T Lv = lx_point<T>(g, i, j, vx, vy, en, ec, diag);
     if (idgx) vx[c] += omega * (fx[c] - Lv) * idgx[c];
     else vx[c] += omega * sdiv(fx[c] - Lv, diag);
   } else {
     if (!is_vy(g.nx, g.ny, i, j)) return;
-    const T Lv = (kc.cxx && idgy) ? ly_coef<T>(g, i, j, vx, vy, kc) : ly_point<T>(g, i, j, vx, vy, en, ec, diag);
+    if (kc.cxx && idgy) {
+      const T t = idgy[c] * (fy[c] - ly_off<T>(g, i, j, vx, vy, kc));
+      vy[c] = omega == T(1) ? t : (T(1) - omega) * vy[c] + omega * t;
+      return;
+    }
+    const T Lv = ly_point<T>(g, i, j, vx, vy, en, ec, diag);
     if (idgy) vy[c] += omega * (fy[c] - Lv) * idgy[c];
     else vy[c] += omega * sdiv(fy[c] - Lv, diag);
   }
