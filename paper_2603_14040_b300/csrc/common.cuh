@@ -11,8 +11,18 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <mutex>
 
 namespace pyro {
+
+// Host side. A device-wide synchronisation (cudaDeviceSynchronize, cudaFree) issued while any
+// stream of the device is being captured into a graph is invalid and ends that capture, so the
+// calls that do either, and may run on different host threads, serialise on this lock: handle
+// creation and destruction, and the one-time capture of the iteration graph.
+inline std::recursive_mutex& device_sync_lock() {
+  static std::recursive_mutex m;
+  return m;
+}
 
 struct Geom {
   int nx, ny;      // cell counts

@@ -214,6 +214,63 @@ __global__ void k_multidot(const double* __restrict__ V, size_t stride, const in
   }
 }
 
+// The same partial sums as k_multidot<WEIGHTED> for nvec <= kDotRegs, in a single pass over w and
+// W: each thread keeps one accumulator per vector in registers. The code path is chosen from nvec
+// in steps of 4 (the FP64 pipe, not memory, bounds these passes, so a path sized to the vector
+// count avoids issuing FMAs for absent vectors). Launch with kThreads threads; gridDim.x blocks
+// write partial[k * gridDim.x + blockIdx.x].
+constexpr int kDotRegs = 32;
+
+template <int G, bool WEIGHTED>
+__device__ __forceinline__ void multidot_regs(const double* __restrict__ V, size_t stride, int nvec,
+                                              const double* __restrict__ w, const double* __restrict__ W, size_t n,
+                                              double* __restrict__ partial, double (*red)[kThreads / 32]) {
+  double acc[G];
+#pragma unroll
+  for (int q = 0; q < G; ++q) acc[q] = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const double t = WEIGHTED ? W[e] * w[e] : w[e];
+#pragma unroll
+    for (int q = 0; q < G; ++q)
+      if (q < G - 4 || q < nvec) acc[q] += t * V[(size_t)q * stride + e];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < G; ++q) {
+    if (q >= G - 4 && q >= nvec) continue;
+    double v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[q][wid] = v;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nvec) {
+    double s = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) s += red[threadIdx.x][k];
+    partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+template <bool WEIGHTED>
+__global__ void __launch_bounds__(kThreads) k_multidot_r(const double* __restrict__ V, size_t stride,
+                                                         const int* __restrict__ d_j, const double* __restrict__ w,
+                                                         const double* __restrict__ W, size_t n,
+                                                         double* __restrict__ partial, int off) {
+  __shared__ double red[kDotRegs][kThreads / 32];
+  const int nvec = *d_j + 1 + off;
+  if (nvec <= 0 || nvec > kDotRegs) return;
+  switch ((nvec + 3) >> 2) {
+    case 1: multidot_regs<4, WEIGHTED>(V, stride, nvec, w, W, n, partial, red); break;
+    case 2: multidot_regs<8, WEIGHTED>(V, stride, nvec, w, W, n, partial, red); break;
+    case 3: multidot_regs<12, WEIGHTED>(V, stride, nvec, w, W, n, partial, red); break;
+    case 4: multidot_regs<16, WEIGHTED>(V, stride, nvec, w, W, n, partial, red); break;
+    case 5: multidot_regs<20, WEIGHTED>(V, stride, nvec, w, W, n, partial, red); break;
+    case 6: multidot_regs<24, WEIGHTED>(V, stride, nvec, w, W, n, partial, red); break;
+    case 7: multidot_regs<28, WEIGHTED>(V, stride, nvec, w, W, n, partial, red); break;
+    default: multidot_regs<32, WEIGHTED>(V, stride, nvec, w, W, n, partial, red); break;
+  }
+}
+
 // out[k] = sum_b partial[k * nblk + b] for k < nvec (one block per k, fixed order)
 __global__ void k_reduce(const double* __restrict__ partial, int nblk, const int* __restrict__ d_j, int nfix,
                          double* __restrict__ out, const int* __restrict__ d_run, int off = 0) {

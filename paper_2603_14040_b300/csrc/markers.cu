@@ -194,6 +194,7 @@ int pyro_markers_create(int nx, int ny, double Lx, double Ly, long long max_mark
   if (!out || nx < 2 || ny < 2 || !(Lx > 0) || !(Ly > 0) || max_markers < 1 || max_markers > 2000000000LL)
     return PYRO_E_INVALID;
   *out = nullptr;
+  std::lock_guard<std::recursive_mutex> lk(pyro::device_sync_lock());
   pyro_markers_s* h = new (std::nothrow) pyro_markers_s;
   if (!h) return PYRO_E_NOMEM;
   h->nx = nx; h->ny = ny; h->Lx = Lx; h->Ly = Ly; h->cap = max_markers;
@@ -261,6 +262,7 @@ int pyro_grid_to_markers(pyro_markers h, int lattice, long long n, const double*
 
 void pyro_markers_destroy(pyro_markers h) {
   if (!h) return;
+  std::lock_guard<std::recursive_mutex> lk(pyro::device_sync_lock());
   cudaFree(h->count); cudaFree(h->offset); cudaFree(h->fill); cudaFree(h->bsum);
   cudaFree(h->idx); cudaFree(h->cell); cudaFree(h->frac); cudaFree(h->flag);
   delete h;

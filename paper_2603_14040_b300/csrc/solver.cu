@@ -615,6 +615,17 @@ inline void mark(pyro_stokes_s* h, int k, cudaStream_t s) {
   if (h->timing) CK(cudaEventRecordWithFlags(h->tev[k], s, cudaEventRecordExternal));
 }
 
+// partial[k * kReduceBlocks + b] = block b's share of sum_e (W[e]) w[e] V_k[e], k < *d_cnt + 1 + off:
+// the one-pass register kernel while the basis fits (m + 1 <= kDotRegs), else groups of 8 vectors.
+template <bool WEIGHTED>
+void multidot(pyro_stokes_s* h, cudaStream_t s, const double* V, const int* d_cnt, const double* w, int off) {
+  if (h->m + 1 <= kDotRegs)
+    k_multidot_r<WEIGHTED><<<kReduceBlocks, kThreads, 0, s>>>(V, h->n3, d_cnt, w, h->W, h->n3, h->partial, off);
+  else
+    k_multidot<WEIGHTED><<<dim3(kReduceBlocks, (unsigned)h->dot_grid_y), kThreads, 0, s>>>(
+        V, h->n3, d_cnt, 0, w, h->W, h->n3, h->partial, nullptr, nullptr, off);
+}
+
 // z = M^-1 v with v = in + (*d_idx) in_stride and z = out + (*d_idx) out_stride (device index), and
 // optionally w = A z.
 template <typename T, typename TZ>
@@ -651,14 +662,13 @@ void precond_any(pyro_stokes_s* h, cudaStream_t s, const double* in, size_t in_s
 void fgmres_body(pyro_stokes_s* h, cudaStream_t s) {
   precond_any(h, s, h->V, h->n3, (double*)h->Z, h->n3, h->d_j, true);
   // classical Gram-Schmidt with one re-orthogonalisation (CGS2) in the W inner product
-  const dim3 gd(kReduceBlocks, (unsigned)h->dot_grid_y);
-  k_multidot<true><<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial, nullptr, nullptr);
+  multidot<true>(h, s, h->V, h->d_j, h->w, 0);
   k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, h->h1, nullptr);
   k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h1, h->n3, nullptr, nullptr, nullptr);
-  k_multidot<true><<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial, nullptr, nullptr);
+  multidot<true>(h, s, h->V, h->d_j, h->w, 0);
   k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, h->h2, nullptr);
-  k_multiaxpy<<<kReduceBlocks, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h2, h->n3, h->W, h->part2, nullptr);
-  k_arnoldi_finish<<<1, kThreads, 0, s>>>(h->d_j, h->h1, h->h2, h->part2, kReduceBlocks, h->hcol, h->inv, h->flag,
+  k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h2, h->n3, h->W, h->part2, nullptr);
+  k_arnoldi_finish<<<1, kThreads, 0, s>>>(h->d_j, h->h1, h->h2, h->part2, 2 * kReduceBlocks, h->hcol, h->inv, h->flag,
                                           nullptr, nullptr);
   k_scale_next<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, h->n3, h->d_j, h->w, h->inv, h->n3);
   k_inc<<<1, 1, 0, s>>>(h->d_j);
@@ -672,11 +682,10 @@ void fgmres_body(pyro_stokes_s* h, cudaStream_t s) {
 // (the W inner product: the method minimises the energy residual, as FGMRES does here).
 void gcr_body(pyro_stokes_s* h, cudaStream_t s) {
   precond_any(h, s, h->r, 0, h->zc, 0, h->d_j, true);
-  const dim3 gd(kReduceBlocks, (unsigned)h->dot_grid_y);
   double* Zb = (double*)h->Z;
   for (int pass = 0; pass < 2; ++pass) {
     double* hc = pass == 0 ? h->h1 : h->h2;
-    k_multidot<true><<<gd, kThreads, 0, s>>>(h->V, h->n3, h->d_j, 0, h->w, h->W, h->n3, h->partial, nullptr, nullptr, -1);
+    multidot<true>(h, s, h->V, h->d_j, h->w, -1);
     k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, hc, nullptr, -1);
     k_multiaxpy<<<kReduceBlocks, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, hc, h->n3, pass ? h->W : nullptr,
                                                    pass ? h->part2 : nullptr, nullptr, -1);
@@ -707,9 +716,7 @@ void aa_body(pyro_stokes_s* h, cudaStream_t s) {
   k_sum_pairs<<<1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->ydev);
   precond_any(h, s, h->r, 0, h->zc, 0, h->d_j, false);
   k_aa_store<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, (double*)h->Z, h->n3, h->d_slot, h->x, h->zc, h->n3);
-  const dim3 gd(kReduceBlocks, (unsigned)h->dot_grid_y);
-  k_multidot<false><<<gd, kThreads, 0, s>>>((double*)h->Z, h->n3, h->d_cnt, 0, h->zc, nullptr, h->n3, h->partial, nullptr,
-                                     nullptr, -1);
+  multidot<false>(h, s, (double*)h->Z, h->d_cnt, h->zc, -1);
   k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_cnt, 0, h->h1, nullptr, -1);
   h->launches += 6;
   mark(h, 6, s);
@@ -745,6 +752,7 @@ void launch_iteration(pyro_stokes_s* h, cudaStream_t s) {
       h->graph = nullptr;
     }
     if (!h->graph) {
+      std::lock_guard<std::recursive_mutex> lk(device_sync_lock());
       const long long saved = h->launches;  // capture records kernels, it does not launch them
       h->graph_timing = h->timing;
       cudaStream_t cs;
@@ -1292,6 +1300,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
   if (!out) return PYRO_E_INVALID;
   *out = nullptr;
   if (!(Lx > 0) || !(Ly > 0)) return PYRO_E_INVALID;
+  std::lock_guard<std::recursive_mutex> lk(device_sync_lock());
   pyro_opts o;
   pyro_default_opts(&o);
   if (opts) o = *opts;
@@ -1460,6 +1469,7 @@ int pyro_stokes_get_timing(pyro_stokes h, double* ms, long long* counts) {
 
 void pyro_stokes_destroy(pyro_stokes h) {
   if (!h) return;
+  std::lock_guard<std::recursive_mutex> lk(device_sync_lock());
   cudaSetDevice(h->dev);
   if (h->graph) cudaGraphExecDestroy(h->graph);
   for (int k = 0; k < 4; ++k)

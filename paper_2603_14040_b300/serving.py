@@ -156,7 +156,7 @@ class SolveServer:
                 item = self._pending[0]
                 try:
                     h = self.pool.acquire(item.req.shape)
-                except ValueError as e:
+                except Exception as e:              # unservable shape or a failed handle creation
                     heapq.heappop(self._pending)
                     item.req.error = str(e)
                     item.req.status = -1

@@ -121,6 +121,32 @@ def test_oversized_and_failing_requests_do_not_stop_the_server():
     assert sum(r.error is None for r in done) == 9
 
 
+def test_a_failed_handle_creation_fails_only_its_request():
+    """A backend whose handle creation raises (as a CUDA error from the library would) ends that
+    request with an error; the server keeps serving the others and drains."""
+    class CreateFails(FakeBackend):
+        def create(self, shape):
+            if shape[0] == 32:
+                raise RuntimeError("pyro_stokes_create: CUDA runtime error")
+            return super().create(shape)
+
+    be = CreateFails()
+    srv = SolveServer(be, max_slots=2)
+    reqs = _reqs(12, seed=7, sizes=(16, 32))
+    for r in reqs:
+        srv.submit(r)
+    done = srv.drain(timeout=60)
+    srv.close()
+    assert len(done) == 12
+    for r in reqs:
+        if r.nx == 32:
+            assert r.error is not None and "CUDA runtime error" in r.error and r.status == -1
+        else:
+            assert r.error is None
+    assert any(r.nx == 32 for r in reqs) and any(r.nx != 32 for r in reqs)
+    assert srv.pool.bytes_in_use == 0
+
+
 def test_requests_arriving_while_others_run_are_admitted_continuously():
     """Continuous batching: a request submitted while slots are busy starts before earlier long
     solves finish (it takes a freed slot), and arrival order is kept among waiting requests."""
