@@ -4,15 +4,20 @@
 // kernel per step (sweep colour, residual, restriction, prolongation, K-cycle dot products) makes
 // the cycle latency-bound. Here the whole cycle from level `ls` down to the coarsest — including
 // the recursive Krylov (K-cycle) corrections and the FP64 coarse direct solve — runs inside ONE
-// launch of kSubCluster CTAs forming a thread-block cluster. Steps are separated by cluster
-// barriers (release/acquire at cluster scope, so global-memory writes of one CTA are visible to
-// the others after the barrier). Levels with at most kSoloPoints padded points are finished by
-// CTA 0 alone with block barriers while the other CTAs wait at the next cluster barrier.
+// launch of one thread-block cluster (16 CTAs where the GPU can schedule a cluster that large,
+// else 8; the size is read at run time). Steps are separated by cluster barriers (release/acquire
+// at cluster scope, so global-memory writes of one CTA are visible to the others after the
+// barrier). Levels with at most SubArgs::solo_points padded points are finished by CTA 0 alone
+// with block barriers while the other CTAs wait at the next cluster barrier (FP32 arithmetic is
+// cheap enough on one SM for 64^2 cells; FP64, at about 2 FMA per clock per SM, only for the
+// tiniest levels).
 //
-// The arithmetic is the same per-point code as the one-kernel-per-step path (rbgs_point,
-// vresid_point, restrict_point, prolong_point, lx_point/ly_point), so both paths produce
-// bitwise-identical results for the same level sequence; only the dot-product partials of the
-// K-cycle are grouped differently (fixed order in both).
+// The arithmetic is the same per-point code as the one-kernel-per-step path (rbgs_point and
+// vresid_point with the level's precomputed coefficients and inverse diagonal where it has them,
+// restrict_point, prolong_point, lx_point/ly_point), and the coarse matvec sums in the same
+// lane order as k_coarse_solve, so both paths produce bitwise-identical results for the same level
+// sequence; only the dot-product partials of the K-cycle are grouped differently (fixed order in
+// both).
 #pragma once
 #include <cooperative_groups.h>
 
@@ -22,10 +27,9 @@ namespace pyro {
 
 namespace cg = cooperative_groups;
 
-constexpr int kSubCluster = 8;
+constexpr int kSubClusterMax = 16;  // largest cluster tried (non-portable size); 8 is the fallback
 constexpr int kSubThreads = 1024;
 constexpr int kSubMaxLevels = 16;
-constexpr int kSoloPoints = 4096;
 
 template <typename T>
 struct SubLevel {
@@ -33,6 +37,7 @@ struct SubLevel {
   T *vx, *vy, *fx, *fy, *rx, *ry, *en, *ec;
   T *d1x, *d1y, *q1x, *q1y, *ex, *ey;
   T *idgx, *idgy;
+  Coef<T> kc;
 };
 
 template <typename T>
@@ -43,13 +48,14 @@ struct SubArgs {
   Geom gc;            // coarsest geometry (unknown numbering of the direct solve)
   const double* Ainv;  // (-L_coarsest)^-1
   int nc;
-  double* red;        // cross-CTA reduction slots: 2 banks x kSubCluster x 4
+  double* red;        // cross-CTA reduction slots: 2 banks x kSubClusterMax x 4
+  int solo_points;    // levels with at most this many padded points run on CTA 0 alone
 };
 
 template <typename T>
 struct SubCtx {
   const SubArgs<T>* a;
-  int tid, nthr, rank, bank;
+  int tid, nthr, rank, bank, ncta;
   bool solo;
   double* sh;   // 32 doubles of shared memory
   double* shv;  // broadcast slots (4 doubles)
@@ -66,6 +72,13 @@ __device__ inline double sub_block_sum(double v, double* sh) {
   if (threadIdx.x == 0)
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
   return s;
+}
+
+// Cluster-wide thread index: consecutive warps of work go to different CTAs (warp w of CTA r is
+// global warp w * ncta + r), so a small level's points spread over every SM of the cluster
+// instead of filling the first CTAs, while each warp still touches 32 consecutive points.
+__device__ inline int sub_tid(int rank, int ncta) {
+  return ((int)(threadIdx.x >> 5) * ncta + rank) * 32 + (int)(threadIdx.x & 31);
 }
 
 template <typename T>
@@ -87,13 +100,13 @@ __device__ inline void sub_reduce(SubCtx<T>& c, double (&v)[NV]) {
     __syncthreads();
     return;
   }
-  double* slot = c.a->red + ((size_t)c.bank * kSubCluster) * 4;
+  double* slot = c.a->red + ((size_t)c.bank * kSubClusterMax) * 4;
   if (threadIdx.x == 0)
     for (int k = 0; k < NV; ++k) slot[c.rank * 4 + k] = v[k];
   cg::this_cluster().sync();
   for (int k = 0; k < NV; ++k) {
     double s = 0.0;
-    for (int r = 0; r < kSubCluster; ++r) s += ((volatile double*)slot)[r * 4 + k];
+    for (int r = 0; r < c.ncta; ++r) s += ((volatile double*)slot)[r * 4 + k];
     v[k] = s;
   }
   c.bank ^= 1;
@@ -109,7 +122,8 @@ __device__ void sub_sweep(SubCtx<T>& c, const SubLevel<T>& L, T omega) {
       for (int e = c.tid; e < total; e += c.nthr) {
         const int i = e / hw, jh = e % hw;
         const int j = 2 * jh + ((i + col) & 1);
-        if (j <= g.nx + 1) rbgs_point<T>(g, i, j, f, omega, L.vx, L.vy, L.fx, L.fy, L.en, L.ec, L.idgx, L.idgy);
+        if (j <= g.nx + 1)
+          rbgs_point<T>(g, i, j, f, omega, L.vx, L.vy, L.fx, L.fy, L.en, L.ec, L.idgx, L.idgy, L.kc);
       }
       sub_sync(c);
     }
@@ -125,10 +139,14 @@ __device__ void sub_coarse_solve(SubCtx<T>& c) {
     else { const int kk = k - nvx; const int i = kk / nx + 1, j = kk % nx + 1; c.fv[k] = (double)L.fy[(size_t)i * ld + j]; }
   }
   __syncthreads();
-  for (int k = c.tid; k < n; k += c.nthr) {
+  // one warp per row, lane-strided products and the xor-shuffle tree of k_coarse_solve
+  const int lane = threadIdx.x & 31;
+  for (int k = c.tid >> 5; k < n; k += c.nthr >> 5) {
     double s = 0.0;
     const double* row = a.Ainv + (size_t)k * n;
-    for (int l = 0; l < n; ++l) s += row[l] * c.fv[l];
+    for (int l = lane; l < n; l += 32) s += row[l] * c.fv[l];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane != 0) continue;
     if (k < nvx) { const int i = k / (nx - 1) + 1, j = k % (nx - 1) + 1; L.vx[(size_t)i * ld + j] = (T)(-s); }
     else { const int kk = k - nvx; const int i = kk / nx + 1, j = kk % nx + 1; L.vy[(size_t)i * ld + j] = (T)(-s); }
   }
@@ -208,7 +226,7 @@ __device__ void sub_down(SubCtx<T>& c, int l) {
   const GeomT<T>& g = L.gt;
   const int total = (g.ny + 2) * (g.nx + 2);
   for (int e = c.tid; e < total; e += c.nthr)
-    vresid_point<T>(g, e / (g.nx + 2), e % (g.nx + 2), L.vx, L.vy, L.fx, L.fy, L.en, L.ec, L.rx, L.ry);
+    vresid_point<T>(g, e / (g.nx + 2), e % (g.nx + 2), L.vx, L.vy, L.fx, L.fy, L.en, L.ec, L.rx, L.ry, L.kc);
   sub_sync(c);
   const GeomT<T>& gc = C.gt;
   const int tc = (gc.ny + 2) * (gc.nx + 2);
@@ -256,7 +274,7 @@ __device__ void sub_run(SubCtx<T>& c, int ls) {
         if (l == a.nlev - 1) {
           sub_coarse_solve(c);
           pop = true;
-        } else if (!c.solo && (a.L[l].gt.ny + 2) * a.L[l].gt.ld <= kSoloPoints) {
+        } else if (!c.solo && (a.L[l].gt.ny + 2) * a.L[l].gt.ld <= a.solo_points) {
           // tiny level: CTA 0 finishes this subtree alone, the others wait for it
           if (c.rank == 0) {
             c.solo = true;
@@ -302,8 +320,8 @@ __device__ void sub_run(SubCtx<T>& c, int ls) {
       --sp;
       if (c.solo && sp == solo_sp) {  // subtree run by CTA 0 alone is complete: rejoin
         c.solo = false;
-        c.tid = c.rank * blockDim.x + threadIdx.x;
-        c.nthr = kSubCluster * blockDim.x;
+        c.tid = sub_tid(c.rank, c.ncta);
+        c.nthr = c.ncta * blockDim.x;
         solo_sp = -1;
         cg::this_cluster().sync();
       }
@@ -312,17 +330,19 @@ __device__ void sub_run(SubCtx<T>& c, int ls) {
 }
 
 // The cycle from level ls (x_ls must be zero, f_ls set) down to the coarsest, in one cluster.
+// Launch: one cluster of gridDim.x CTAs (cluster dimension = grid dimension, at most
+// kSubClusterMax) of kSubThreads threads.
 template <typename T>
-__global__ void __cluster_dims__(kSubCluster, 1, 1) __launch_bounds__(kSubThreads, 1)
-    k_subcycle(const __grid_constant__ SubArgs<T> a, int ls) {
+__global__ void __launch_bounds__(kSubThreads, 1) k_subcycle(const __grid_constant__ SubArgs<T> a, int ls) {
   __shared__ double sh[32];
   __shared__ double shv[4];
   __shared__ double fv[1024];
   SubCtx<T> c;
   c.a = &a;
   c.rank = (int)cg::this_cluster().block_rank();
-  c.tid = c.rank * blockDim.x + threadIdx.x;
-  c.nthr = kSubCluster * blockDim.x;
+  c.ncta = (int)cg::this_cluster().num_blocks();
+  c.tid = sub_tid(c.rank, c.ncta);
+  c.nthr = c.ncta * blockDim.x;
   c.bank = 0;
   c.solo = false;
   c.sh = sh;

@@ -146,6 +146,7 @@ struct MG {
   int tile_sweeps = 2;                      // FP32: sweeps fused per tile launch
   static constexpr long long kFuse64Cells = 65536;
   SubArgs<T> sub{};
+  int sub_ncta = 8;  // CTAs of the sub-cycle cluster
   double* red = nullptr;
   T omega = T(1);
   const cudaEvent_t* hooks = nullptr;  // level-0 phase events (timing mode), else null
@@ -224,7 +225,9 @@ struct MG {
     for (int l = 0; l < (int)lv.size(); ++l)
       if ((long long)lv[l].g.nx * lv[l].g.ny <= cluster_cells) { ls = l; break; }
     if (ls < 0 || ls == (int)lv.size() - 1) { ls = -1; return; }
-    red = A.get<double>(2 * kSubCluster * 4);
+    red = A.get<double>(2 * kSubClusterMax * 4);
+    sub_ncta = sub_cluster_size();
+    sub.solo_points = sizeof(T) == 4 ? 4096 : 324;
     sub.nlev = (int)lv.size();
     sub.nu1 = nu1; sub.nu2 = nu2; sub.kcycle = kcycle; sub.omega = omega;
     sub.gc = lv.back().g;
@@ -238,7 +241,50 @@ struct MG {
       S.vx = L.vx; S.vy = L.vy; S.fx = L.fx; S.fy = L.fy; S.rx = L.rx; S.ry = L.ry; S.en = L.en; S.ec = L.ec;
       S.d1x = L.d1x; S.d1y = L.d1y; S.q1x = L.q1x; S.q1y = L.q1y; S.ex = L.ex; S.ey = L.ey;
       S.idgx = L.idgx; S.idgy = L.idgy;
+      S.kc = L.kc;
     }
+  }
+
+  // 16 CTAs if a cluster of 16 (non-portable size) with kSubThreads threads each can be resident,
+  // else the portable 8
+  static int sub_cluster_size() {
+    static int n = 0;
+    if (n) return n;
+    n = 8;
+    if (cudaFuncSetAttribute(k_subcycle<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return n;
+    }
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at{};
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = kSubClusterMax;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(kSubClusterMax);
+    cfg.blockDim = dim3(kSubThreads);
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int active = 0;
+    if (cudaOccupancyMaxActiveClusters(&active, k_subcycle<T>, &cfg) == cudaSuccess && active > 0) n = kSubClusterMax;
+    cudaGetLastError();
+    return n;
+  }
+
+  void launch_sub(int l, cudaStream_t s) {
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at{};
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = (unsigned)sub_ncta;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)sub_ncta);
+    cfg.blockDim = dim3(kSubThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, k_subcycle<T>, sub, l));
   }
 
   // viscosity on every level + coarse inverse (eta of level 0 must already be in place)
@@ -495,7 +541,7 @@ struct MG {
     // entry: the iterate is zero in the first buffer
     L.cur = 0;
     if (l == ls) {
-      k_subcycle<T><<<kSubCluster, kSubThreads, 0, s>>>(sub, l);
+      launch_sub(l, s);
       count(1);
       return;
     }
@@ -1228,7 +1274,7 @@ size_t footprint_bytes(int nx, int ny, const pyro_opts& o, int L) {
   (void)L;
   const auto sz = sizes_of(nx, ny, o);
   b += mixed ? MG<float>::bytes(sz, o.kcycle) : MG<double>::bytes(sz, o.kcycle) - 2 * P * 8;
-  b += 2 * kSubCluster * 4 * 8;
+  b += 2 * kSubClusterMax * 4 * 8;
   b += 2 * (kMaxRestart + 2) * 8 + 2 * (size_t)kReduceBlocks * (kMaxRestart + 1) * 8 + 4 * kReduceBlocks * 8 +
        (size_t)kMaxRestart * kHcolStride * 8 + 64;
   return b;
