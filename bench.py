@@ -179,7 +179,8 @@ def vcycle_rooflines(peaks):
 def accelerator_sample(f, n, steps=3):
     """The paper's own outer accelerators and smoothers on the bench workload (same 1e-10
     energy-residual stop): flexible GCR(30) and Anderson AA(m, beta) around the default
-    preconditioner (FP64 and mixed), and the damped-Jacobi / RAS-type smoothers (mixed)."""
+    preconditioner (FP64 and mixed), and the damped-Jacobi / RAS-type smoothers and the paper's
+    "Mixed" smoother configuration (Jacobi on the finest level, RAS below; mixed precision)."""
     import torch
     import paper_2603_14040_b300 as P
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -191,6 +192,7 @@ def accelerator_sample(f, n, steps=3):
                      ("anderson15_beta0.8", dict(accel=P.ACCEL_ANDERSON, restart_m=15, aa_beta=0.8)),
                      ("fgmres30_jacobi_smoother", dict(smoother=P.SMOOTH_JACOBI, omega_v=0.6)),
                      ("fgmres30_ras4_smoother", dict(smoother=P.SMOOTH_RAS, ras_inner=4, omega_v=0.6)),
+                     ("fgmres30_mixed_jacobi_ras4_smoother", dict(smoother=P.SMOOTH_MIXED, ras_inner=4, omega_v=0.6)),
                      ("anderson15_beta0.8_jacobi_smoother", dict(accel=P.ACCEL_ANDERSON, restart_m=15, aa_beta=0.8,
                                                                  smoother=P.SMOOTH_JACOBI, omega_v=0.6))]:
         for prec, pn in ((P.PREC_FP64, "fp64"), (P.PREC_MIXED, "mixed")):

@@ -93,8 +93,10 @@ typedef enum { PYRO_ACCEL_FGMRES = 0, PYRO_ACCEL_GCR = 1, PYRO_ACCEL_ANDERSON = 
  *           passes over 32 x 32-cell tiles, each tile running ras_inner local damped Jacobi
  *           iterations in shared memory with its one-cell ring held at the pass-start values; the
  *           tiling shift of each pass comes from SplitMix64 of (level, pre/post, pass), so the
- *           V-cycle is the same linear operator at every application. */
-typedef enum { PYRO_SMOOTH_RBGS = 0, PYRO_SMOOTH_JACOBI = 1, PYRO_SMOOTH_RAS = 2 } pyro_smoother;
+ *           V-cycle is the same linear operator at every application;
+ *   MIXED   the "Mixed" configuration of the robustness study (Sec. "Numerical Stability and
+ *           Solver Robustness"): JACOBI on the finest level, RAS on every coarser level. */
+typedef enum { PYRO_SMOOTH_RBGS = 0, PYRO_SMOOTH_JACOBI = 1, PYRO_SMOOTH_RAS = 2, PYRO_SMOOTH_MIXED = 3 } pyro_smoother;
 typedef enum { PYRO_ETA_ARITH = 0, PYRO_ETA_GEOM = 1 } pyro_eta_coarsening;
 
 /* Solver options. pyro_default_opts() fills the defaults given in brackets. */

@@ -11,7 +11,9 @@ step at a time:
     positions; prolongation = bilinear interpolation from the four surrounding coarse points;
   * damped red-black Gauss-Seidel (Sec. "Smoothers", eq. sor_update) on the velocity block, or
     damped Jacobi (eq. damped_jacobi), or the RAS-type temporally blocked Jacobi smoother
-    (Algorithm ras_temporal);
+    (Algorithm ras_temporal), or the "Mixed" configuration of the robustness study (Sec.
+    "Numerical Stability and Solver Robustness": Jacobi on the finest level, RAS-type Jacobi on
+    every coarser level);
   * the V-cycle of eq. multigrid_levels with a direct coarsest solve;
   * one Uzawa sweep as the preconditioner M^-1 (Sec. "Uzawa Iteration as a Fixed Point Method").
 
@@ -282,15 +284,24 @@ def ras_pass(g, L, f, x, omega, inner, TI, TJ, si, sj):
     return y
 
 
+def level_smoother(smoother, level):
+    """The smoother used on `level`: the hierarchy's own, except that "mixed" means damped Jacobi
+    on the finest level and the RAS-type Jacobi smoother on the coarser ones."""
+    if smoother == "mixed":
+        return "jacobi" if level == 0 else "ras"
+    return smoother
+
+
 def smooth(h, level, f, x, nu, omega, phase):
-    """nu smoothing steps on `level` with the hierarchy's smoother: damped RBGS sweeps (default),
+    """nu smoothing steps on `level` with the level's smoother: damped RBGS sweeps (default),
     damped Jacobi sweeps, or ceil(nu / inner) RAS passes of `inner` local Jacobi iterations."""
     L = h.L[level]
-    if h.smoother == "rbgs":
+    kind = level_smoother(h.smoother, level)
+    if kind == "rbgs":
         for _ in range(nu):
             x = rbgs_sweep(L, f, x, h.sets[level], omega)
         return x
-    if h.smoother == "jacobi":
+    if kind == "jacobi":
         for _ in range(nu):
             x = jacobi_sweep(L, f, x, omega)
         return x

@@ -6,9 +6,10 @@ Python binding plus the autograd wrapper and the continuous-batching solve serve
 from .pyro import (Stokes, Markers, LATTICE_NODES, LATTICE_CELLS, PyroError, PyroOpts, PyroBC, PyroStats, default_opts, make_bc, footprint, lib,
                    load_library, EXPORTED, FREE_SLIP, NO_SLIP, PERIODIC, VELOCITY, PREC_FP64, PREC_MIXED,
                    ETA_ARITH, ETA_GEOM, PYRO_OK, PYRO_W_NOT_CONVERGED, ACCEL_FGMRES, ACCEL_GCR, ACCEL_ANDERSON, SMOOTH_RBGS, SMOOTH_JACOBI,
-                   SMOOTH_RAS)
+                   SMOOTH_RAS, SMOOTH_MIXED)
 
 __all__ = ["Stokes", "Markers", "LATTICE_NODES", "LATTICE_CELLS", "PyroError", "PyroOpts", "PyroBC", "PyroStats", "default_opts", "make_bc", "footprint", "lib",
            "load_library", "EXPORTED", "FREE_SLIP", "NO_SLIP", "PERIODIC", "VELOCITY", "PREC_FP64", "PREC_MIXED",
            "ETA_ARITH", "ETA_GEOM", "PYRO_OK", "PYRO_W_NOT_CONVERGED", "ACCEL_FGMRES", "ACCEL_GCR",
-           "ACCEL_ANDERSON", "SMOOTH_RBGS", "SMOOTH_JACOBI", "SMOOTH_RAS"]
+           "ACCEL_ANDERSON", "SMOOTH_RBGS", "SMOOTH_JACOBI", "SMOOTH_RAS",
+           "SMOOTH_MIXED"]

@@ -141,7 +141,7 @@ struct MG {
   bool tiles = true;                        // tile-fused smoothing / residual+restriction
   int stream = 0;                           // FP32 row-streaming sweeps: 0 never, 1 large levels, 2 all
   int tile_form = 0;                        // FP32 large levels: 0 warp-per-row tiles, 1 64 x 32 colour-split
-  int smoother = PYRO_SMOOTH_RBGS;          // velocity smoother of every level
+  int smoother = PYRO_SMOOTH_RBGS;          // velocity smoother (MIXED: Jacobi on level 0, RAS below)
   int ras_inner = 4;                        // RAS-type Jacobi: local iterations per tile pass
   int tile_sweeps = 2;                      // FP32: sweeps fused per tile launch
   static constexpr long long kFuse64Cells = 65536;
@@ -482,11 +482,19 @@ struct MG {
     }
   }
 
-  // nsweeps smoothing steps on level l with the configured smoother; with C given, the coarse
+  // the smoother of level l: the configured one, or for MIXED Jacobi on the finest level and the
+  // RAS-type Jacobi smoother on the coarser ones
+  int level_smoother(int l) const {
+    if (smoother == PYRO_SMOOTH_MIXED) return l == 0 ? PYRO_SMOOTH_JACOBI : PYRO_SMOOTH_RAS;
+    return smoother;
+  }
+
+  // nsweeps smoothing steps on level l with the level's smoother; with C given, the coarse
   // correction (prolongation of C's iterate) is added first. phase: 0 pre, 1 post (RAS shifts).
   void smooth(int l, int nsweeps, const Level<T>* C, int phase, cudaStream_t s) {
     Level<T>& L = lv[l];
-    if (smoother == PYRO_SMOOTH_RBGS && fused(l)) {
+    const int sm = level_smoother(l);
+    if (sm == PYRO_SMOOTH_RBGS && fused(l)) {
       smooth_tiles(l, nsweeps, C, s);
       return;
     }
@@ -494,11 +502,11 @@ struct MG {
       k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, C->gt, L.X(), L.Y(), C->X(), C->Y());
       count(1);
     }
-    if (smoother == PYRO_SMOOTH_RBGS) {
+    if (sm == PYRO_SMOOTH_RBGS) {
       for (int k = 0; k < nsweeps; ++k) sweep(l, s);
       return;
     }
-    if (smoother == PYRO_SMOOTH_JACOBI) {
+    if (sm == PYRO_SMOOTH_JACOBI) {
       for (int k = 0; k < nsweeps; ++k) {
         k_jacobi<T><<<jacobi_grid(L.g.nx, L.g.ny), jacobi_block(), 0, s>>>(L.gt, L.X(), L.Y(), L.cur ? L.vx : L.vx2,
                                                                      L.cur ? L.vy : L.vy2, L.fx, L.fy, L.en, L.ec,
@@ -595,7 +603,7 @@ struct MG {
       cycle(l + 1, s);
     }
     // prolongation + correction (fused into the first post-smoothing pass of the RBGS tiles)
-    const bool fused_post = smoother == PYRO_SMOOTH_RBGS && fz && f2[l];
+    const bool fused_post = level_smoother(l) == PYRO_SMOOTH_RBGS && fz && f2[l];
     if (!fused_post) {
       if (f2[l])
         k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, C.gt, L.X(), L.Y(), C.X(), C.Y());
@@ -1239,7 +1247,7 @@ void validate_opts(pyro_opts& o) {
   if (o.kcycle > 16) o.kcycle = 16;
   if (o.accel < PYRO_ACCEL_FGMRES || o.accel > PYRO_ACCEL_ANDERSON) o.accel = PYRO_ACCEL_FGMRES;
   if (!(o.aa_beta > 0.0) || o.aa_beta > 1.0) o.aa_beta = 1.0;
-  if (o.smoother < PYRO_SMOOTH_RBGS || o.smoother > PYRO_SMOOTH_RAS) o.smoother = PYRO_SMOOTH_RBGS;
+  if (o.smoother < PYRO_SMOOTH_RBGS || o.smoother > PYRO_SMOOTH_MIXED) o.smoother = PYRO_SMOOTH_RBGS;
   if (o.ras_inner < 1) o.ras_inner = 1;
   if (o.cont_stages < 0) o.cont_stages = 0;
   if (o.cont_iters < 1) o.cont_iters = 1;
@@ -1403,7 +1411,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->mgf.kcycle = o.kcycle;
       h->mgf.smoother = o.smoother;
       h->mgf.ras_inner = o.ras_inner;
-      if (o.smoother == PYRO_SMOOTH_RAS) MG<float>::enable_ras();
+      if (o.smoother == PYRO_SMOOTH_RAS || o.smoother == PYRO_SMOOTH_MIXED) MG<float>::enable_ras();
       h->mgf.tiles = o.tile_fusion != 0;
       h->mgf.stream = (o.tile_fusion == 2 || o.tile_fusion == 3) ? o.tile_fusion - 1 : 0;
       h->mgf.tile_form = o.tile_fusion == 4 ? 1 : 0;
@@ -1418,7 +1426,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->mgd.kcycle = o.kcycle;
       h->mgd.smoother = o.smoother;
       h->mgd.ras_inner = o.ras_inner;
-      if (o.smoother == PYRO_SMOOTH_RAS) MG<double>::enable_ras();
+      if (o.smoother == PYRO_SMOOTH_RAS || o.smoother == PYRO_SMOOTH_MIXED) MG<double>::enable_ras();
       h->mgd.tiles = o.tile_fusion64 != 0;
       if (h->mgd.tiles) MG<double>::enable_tiles();
       h->mgd.alloc(A, h->g, Lx, Ly, sizes_of(nx, ny, o), true);

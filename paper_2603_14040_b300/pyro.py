@@ -15,7 +15,7 @@ _LIB_PATH = os.path.join(_HERE, "libpyro.so")
 
 PYRO_OK, PYRO_W_NOT_CONVERGED = 0, 1
 ACCEL_FGMRES, ACCEL_GCR, ACCEL_ANDERSON = 0, 1, 2
-SMOOTH_RBGS, SMOOTH_JACOBI, SMOOTH_RAS = 0, 1, 2
+SMOOTH_RBGS, SMOOTH_JACOBI, SMOOTH_RAS, SMOOTH_MIXED = 0, 1, 2, 3
 PYRO_E_INVALID, PYRO_E_NOMEM, PYRO_E_CUDA, PYRO_E_NONFINITE, PYRO_E_TIMEOUT, PYRO_E_BREAKDOWN = -1, -2, -3, -4, -5, -6
 FREE_SLIP, NO_SLIP, PERIODIC, VELOCITY = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1

@@ -49,7 +49,7 @@ def _precond_case(nx, ny, Lx, Ly, bc, prec, seed, kcycle=0, cluster_cells=0, til
     rng = np.random.default_rng(seed + 1)
     r = rng.standard_normal(g.n)
     rx, ry, rp = S.vector_to_fields(g, r, fill_ghosts=False)
-    h_or = M.Hierarchy(g, en, ec, coarsest_min=2, eta_mode=eta_coarsen, smoother=("rbgs", "jacobi", "ras")[smoother],
+    h_or = M.Hierarchy(g, en, ec, coarsest_min=2, eta_mode=eta_coarsen, smoother=("rbgs", "jacobi", "ras", "mixed")[smoother],
                        ras_inner=ras_inner, ras_tile=32, coarsen_ratio=coarsen_ratio,
                        coarsen_general=bool(coarsen_general))
     z = M.uzawa_precond(h_or, r, ec, alpha=1.0, nu1=2, nu2=2, omega=omega, kcycle=kcycle)
@@ -97,17 +97,18 @@ def test_preconditioner_geometric_eta_coarsening_matches_oracle(prec, tf, field)
 
 @pytest.mark.parametrize("nx,ny,Lx,Ly", [(48, 80, 0.6, 1.0), (64, 64, 1, 1), (256, 96, 2, 0.75)])
 @pytest.mark.parametrize("smoother,inner", [(P.SMOOTH_JACOBI, 1), (P.SMOOTH_RAS, 1), (P.SMOOTH_RAS, 2),
-                                            (P.SMOOTH_RAS, 4)])
+                                            (P.SMOOTH_RAS, 4), (P.SMOOTH_MIXED, 4), (P.SMOOTH_MIXED, 2)])
 @pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
 def test_preconditioner_jacobi_smoothers_match_oracle(nx, ny, Lx, Ly, smoother, inner, prec):
     """The paper's damped Jacobi and RAS-type temporally blocked Jacobi smoothers (32 x 32 tiles,
-    shifted tilings, inner local iterations) inside the V-cycle, step by step against the oracle."""
+    shifted tilings, inner local iterations), and its "Mixed" configuration (Jacobi on the finest
+    level, RAS below), inside the V-cycle, step by step against the oracle."""
     gpu, ora, nlev = _precond_case(nx, ny, Lx, Ly, "free", prec, 19, smoother=smoother, ras_inner=inner, omega=0.6)
     for a, b in zip(gpu, ora):
         assert rel(a, b) <= (1e-11 if prec == P.PREC_FP64 else 2e-4), (rel(a, b), nlev)
 
 
-@pytest.mark.parametrize("smoother,inner", [(P.SMOOTH_JACOBI, 1), (P.SMOOTH_RAS, 2)])
+@pytest.mark.parametrize("smoother,inner", [(P.SMOOTH_JACOBI, 1), (P.SMOOTH_RAS, 2), (P.SMOOTH_MIXED, 4)])
 @pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
 def test_sinker_with_jacobi_smoothers_matches_direct_oracle(smoother, inner, prec):
     f = sinker(64, 64)

@@ -265,7 +265,38 @@ def test_ras_with_single_cell_tiles_converges_to_block_jacobi():
     assert np.allclose(a, b, rtol=1e-10, atol=1e-10)
 
 
-@pytest.mark.parametrize("smoother", ["jacobi", "ras"])
+def _mixed_case(nx=24, ny=16, n_lev=None, smoother="mixed", seed=53):
+    g = S.Grid(nx, ny, 1.0, ny / nx)
+    rng = np.random.default_rng(seed)
+    en = 10.0 ** rng.uniform(-0.5, 0.5, (ny + 2, nx + 2)); ec = 10.0 ** rng.uniform(-0.5, 0.5, (ny + 2, nx + 2))
+    return M.Hierarchy(g, en, ec, coarsest_min=2, n_lev=n_lev, smoother=smoother, ras_inner=2, ras_tile=4), rng
+
+
+def test_mixed_smoother_is_damped_jacobi_on_the_finest_level():
+    """Two levels with a direct coarsest solve: only the finest level is smoothed, so the "Mixed"
+    configuration must give exactly the damped-Jacobi cycle (and differ from the RAS one)."""
+    hm, rng = _mixed_case(n_lev=2)
+    hj, _ = _mixed_case(n_lev=2, smoother="jacobi")
+    hr, _ = _mixed_case(n_lev=2, smoother="ras")
+    f = rng.standard_normal(hm.L[0].shape[0])
+    a = M.vcycle(hm, f, 2, 2, 0.6)
+    assert np.array_equal(a, M.vcycle(hj, f, 2, 2, 0.6))
+    assert not np.allclose(a, M.vcycle(hr, f, 2, 2, 0.6), rtol=1e-6, atol=0)
+
+
+def test_mixed_smoother_is_ras_below_the_finest_level():
+    """A cycle started on level 1 never touches the finest level, so there the "Mixed"
+    configuration must give exactly the RAS-type cycle (and differ from the Jacobi one)."""
+    hm, rng = _mixed_case(n_lev=3)
+    hj, _ = _mixed_case(n_lev=3, smoother="jacobi")
+    hr, _ = _mixed_case(n_lev=3, smoother="ras")
+    f1 = rng.standard_normal(hm.L[1].shape[0])
+    a = M.vcycle(hm, f1, 2, 2, 0.6, level=1)
+    assert np.array_equal(a, M.vcycle(hr, f1, 2, 2, 0.6, level=1))
+    assert not np.allclose(a, M.vcycle(hj, f1, 2, 2, 0.6, level=1), rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "ras", "mixed"])
 def test_vcycle_with_jacobi_smoothers_contracts(smoother):
     g = S.Grid(32, 32)
     rng = np.random.default_rng(43)
