@@ -216,10 +216,11 @@ def accelerator_sample(f, n, steps=3):
 
 
 def marker_sample(n=1024, per_cell=16, reps=5):
-    """Marker <-> grid interpolation (the marker-in-cell step around the solve): 16 markers per cell
-    on 1024^2, uniform random positions; marker -> basic nodes (deterministic bucketed gather) and
-    grid -> markers (bilinear), CUDA events. Minimal traffic: 24 B per marker read (x, y, phi) for
-    the scatter, 24 B per marker (x, y in, phi out) for the gather."""
+    """The marker steps of the marker-in-cell loop around the solve: 16 markers per cell on 1024^2,
+    uniform random positions; marker -> basic nodes (deterministic bucketed gather), grid -> markers
+    (bilinear), and one advection step per scheme, CUDA events. Minimal traffic: 24 B per marker
+    read (x, y, phi) for the scatter, 24 B per marker (x, y in, phi out) for the gather, 32 B per
+    marker for advection."""
     import torch
     import paper_2603_14040_b300 as P
     m = per_cell * n * n
@@ -245,6 +246,29 @@ def marker_sample(n=1024, per_cell=16, reps=5):
             ts.append(e0.elapsed_time(e1))
         ms = float(np.median(ts))
         res[name] = {"ms": ms, "markers_per_s": m / (ms / 1e3), "min_traffic_GBps": 24.0 * m / (ms / 1e3) / 1e9}
+    # advection in a cellular flow u = sin(pi x) cos(pi y), v = -cos(pi x) sin(pi y) sampled on the
+    # staggered velocity lattices, one CFL-0.5 step per call (positions updated in place: 32 B per
+    # marker of minimal traffic, the 2 x 8.4 MB velocity arrays stay in L2)
+    h = 1.0 / n
+    jj = torch.arange(n + 2, dtype=torch.float64, device="cuda")
+    ii = jj.view(-1, 1)
+    vx = torch.sin(np.pi * jj * h) * torch.cos(np.pi * (ii - 0.5) * h)
+    vy = -torch.cos(np.pi * (jj - 0.5) * h) * torch.sin(np.pi * ii * h)
+    dt = mk.max_dt(vx, vy, 0.5)
+    for name, scheme in (("advect_euler", P.ADVECT_EULER), ("advect_heun", P.ADVECT_HEUN), ("advect_rk4", P.ADVECT_RK4),
+                         ("advect_taylor", P.ADVECT_TAYLOR)):
+        mk.advect(xm, ym, vx, vy, dt, scheme=scheme)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            mk.advect(xm, ym, vx, vy, dt, scheme=scheme)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        res[name] = {"ms": ms, "markers_per_s": m / (ms / 1e3), "min_traffic_GBps": 32.0 * m / (ms / 1e3) / 1e9}
     mk.close()
     res["markers"] = m
     res["grid"] = [n, n]

@@ -275,16 +275,29 @@ const char* pyro_strerror(int status);
 /* Library version string. */
 const char* pyro_version(void);
 
-/* ---- marker <-> grid interpolation (the marker-in-cell step that feeds eta and rho to the solve:
- * Sec. "Marker-to-grid interpolation" and "Grid-to-marker interpolation") ---------------------
+/* ---- marker steps of the marker-in-cell loop: marker <-> grid interpolation (the step that feeds
+ * eta and rho to the solve: Sec. "Marker-to-grid interpolation" and "Grid-to-marker
+ * interpolation") and marker advection in the solved velocity (Sec. "Advection of Lagrangian
+ * Markers") ---------------------------------------------------------------------------------
  * Lattices in the padded (ny+2) x (nx+2) layout, row i with y:
  *   PYRO_LATTICE_NODES  basic nodes  x_j = j dx,         y_i = i dy,         i in [0,ny], j in [0,nx]
  *   PYRO_LATTICE_CELLS  cell centres x_j = (j - 1/2) dx, y_i = (i - 1/2) dy, i in [1,ny], j in [1,nx]
+ *   PYRO_LATTICE_VX     vx points    x_j = j dx,         y_i = (i - 1/2) dy, i in [1,ny], j in [0,nx]
+ *   PYRO_LATTICE_VY     vy points    x_j = (j - 1/2) dx, y_i = i dy,         i in [0,ny], j in [1,nx]
  * A marker belongs to the lattice cell whose top-left node lies at or left/above it (clamped into
  * the outermost cell when it lies beyond the lattice). Bilinear weights: that node (1-fx)(1-fy),
  * its right neighbour fx(1-fy), the node below (1-fx)fy, the diagonal fx fy, with fx = r_x/dx,
  * fy = r_y/dy the offsets from the top-left node. */
-typedef enum { PYRO_LATTICE_NODES = 0, PYRO_LATTICE_CELLS = 1 } pyro_lattice;
+typedef enum { PYRO_LATTICE_NODES = 0, PYRO_LATTICE_CELLS = 1, PYRO_LATTICE_VX = 2, PYRO_LATTICE_VY = 3 } pyro_lattice;
+/* Advection schemes (Sec. "Advection of Lagrangian Markers"), per (sub)step of size h:
+ *   EULER   x + h v(x)                                          (eq. euler_advection)
+ *   HEUN    x* = x + h v(x); x + h/2 (v(x) + v(x*))              (eq. heun_method)
+ *   RK4     the classical four-stage Runge-Kutta step            (eq. rk4_method)
+ *   TAYLOR  x + h v0 + h^2/2 J v0 + h^3/6 (H : v0 v0)            (eq. lpi_update)
+ * v(x) is vx interpolated bilinearly on PYRO_LATTICE_VX and vy on PYRO_LATTICE_VY; for TAYLOR, J
+ * and H are the first derivatives and the d2/dxdy term of those interpolants at the marker (zero
+ * across a direction in which the marker lies beyond the lattice). */
+typedef enum { PYRO_ADVECT_EULER = 0, PYRO_ADVECT_HEUN = 1, PYRO_ADVECT_RK4 = 2, PYRO_ADVECT_TAYLOR = 3 } pyro_advect_scheme;
 typedef struct pyro_markers_s* pyro_markers;  /* opaque; owns the bucketing workspace */
 
 /* Workspace for an nx x ny grid of size Lx x Ly and up to max_markers markers (about
@@ -306,6 +319,22 @@ int pyro_markers_to_grid(pyro_markers h, int lattice, long long n, const double*
  * sum to one). Device pointers; stream-ordered, returns after enqueueing. */
 int pyro_grid_to_markers(pyro_markers h, int lattice, long long n, const double* xm, const double* ym,
                          const double* grid, double* phim, void* cuda_stream);
+
+/* Advect n markers in place through a time dt in the frozen velocity (vx, vy: device (ny+2) x
+ * (nx+2) arrays as returned by pyro_stokes_solve), in `substeps` equal steps of `scheme`, each
+ * step's result clamped into [0, Lx] x [0, Ly]. xm, ym: n device doubles (updated). One thread per
+ * marker in FP64; stream-ordered, returns after enqueueing. PYRO_E_INVALID for a null handle,
+ * n < 0, an unknown scheme, substeps < 1, non-finite dt or host pointers. Non-finite positions
+ * stay non-finite. */
+int pyro_markers_advect(pyro_markers h, int scheme, long long n, double* xm, double* ym, const double* vx,
+                        const double* vy, double dt, int substeps, void* cuda_stream);
+
+/* CFL-limited step (the grid-based step limit of Sec. "Advection of Lagrangian Markers"):
+ * *dt_out = cfl * min(dx / max|vx|, dy / max|vy|), maxima over the whole padded arrays, +infinity
+ * (HUGE_VAL) when both are zero everywhere. Synchronises cuda_stream. PYRO_E_INVALID for cfl <= 0,
+ * a null dt_out or host pointers; PYRO_E_NONFINITE if an entry is not finite. */
+int pyro_markers_max_dt(pyro_markers h, const double* vx, const double* vy, double cfl, double* dt_out,
+                        void* cuda_stream);
 
 /* Release the workspace (NULL is a no-op). */
 void pyro_markers_destroy(pyro_markers h);

@@ -1,5 +1,7 @@
-// Marker <-> grid interpolation of the marker-in-cell loop (Sec. "Marker-to-grid interpolation"
-// and "Grid-to-marker interpolation"), the step that feeds eta and rho to the Stokes solve.
+// Marker steps of the marker-in-cell loop: marker <-> grid interpolation (Sec. "Marker-to-grid
+// interpolation" and "Grid-to-marker interpolation"), the step that feeds eta and rho to the
+// Stokes solve, and the advection of the markers in the solved velocity (Sec. "Advection of
+// Lagrangian Markers": forward Euler, Heun, classical RK4, the locally polynomial Taylor update).
 //
 // Marker -> grid is a weighted average over the markers around each lattice node with bilinear
 // weights. The paper accumulates with atomics; floating-point atomics make the result depend on
@@ -7,12 +9,15 @@
 // counts and slots), each bucket is sorted by marker index, and every node gathers from the four
 // cells around it in a fixed order. The result is deterministic and independent of the launch.
 //
-// Lattices: basic nodes (x_j = j dx, y_i = i dy, i in [0, ny], j in [0, nx]) or cell centres
-// (x_j = (j - 1/2) dx, y_i = (i - 1/2) dy, i, j in [1, n]) in the padded (ny+2) x (nx+2) layout;
-// row i goes with y. A marker belongs to the lattice cell whose top-left node is at or left/above
+// Lattices: basic nodes (x_j = j dx, y_i = i dy, i in [0, ny], j in [0, nx]), cell centres
+// (x_j = (j - 1/2) dx, y_i = (i - 1/2) dy, i, j in [1, n]), vx points (x_j = j dx,
+// y_i = (i - 1/2) dy, i in [1, ny], j in [0, nx]) and vy points (x_j = (j - 1/2) dx, y_i = i dy,
+// i in [0, ny], j in [1, nx]) in the padded (ny+2) x (nx+2) layout; row i goes with y. A marker belongs to the lattice cell whose top-left node is at or left/above
 // it (clamped into the outermost cell when it lies beyond the lattice); that node takes the weight
 // (1 - fx)(1 - fy), its right neighbour fx (1 - fy), the one below (1 - fx) fy, the diagonal fx fy.
 #include <cuda_runtime.h>
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <new>
 
@@ -32,6 +37,7 @@ struct pyro_markers_s {
   int* cell = nullptr;     // cell of each marker
   double* frac = nullptr;  // (fx, fy) of each marker
   int* flag = nullptr;
+  double* red = nullptr;   // per-block maxima of the CFL reduction (2 x kRedBlocks)
 };
 
 namespace {
@@ -39,6 +45,7 @@ namespace {
 using namespace pyro;
 constexpr int kMkThreads = 256;
 constexpr int kScanBlock = 1024;
+constexpr int kRedBlocks = 296;
 
 struct Lat {
   double x0, y0, idx, idy;
@@ -53,6 +60,10 @@ Lat make_lat(const pyro_markers_s* h, int kind) {
   L.idy = 1.0 / dy;
   if (kind == PYRO_LATTICE_CELLS) {
     L.x0 = -0.5 * dx; L.y0 = -0.5 * dy; L.ilo = 1; L.ihi = h->ny; L.jlo = 1; L.jhi = h->nx;
+  } else if (kind == PYRO_LATTICE_VX) {
+    L.x0 = 0.0; L.y0 = -0.5 * dy; L.ilo = 1; L.ihi = h->ny; L.jlo = 0; L.jhi = h->nx;
+  } else if (kind == PYRO_LATTICE_VY) {
+    L.x0 = -0.5 * dx; L.y0 = 0.0; L.ilo = 0; L.ihi = h->ny; L.jlo = 1; L.jhi = h->nx;
   } else {
     L.x0 = 0.0; L.y0 = 0.0; L.ilo = 0; L.ihi = h->ny; L.jlo = 0; L.jhi = h->nx;
   }
@@ -177,6 +188,115 @@ __global__ void k_mk_to_markers(Lat L, int ld, long long n, const double* __rest
   }
 }
 
+// ---- advection --------------------------------------------------------------------------------
+// bilinear value of a lattice field at (x, y), the same arithmetic as k_mk_to_markers
+__device__ inline double interp(const Lat& L, int ld, const double* __restrict__ g, double x, double y) {
+  int i, j;
+  double fx, fy;
+  locate(L, x, y, i, j, fx, fy);
+  const size_t o = (size_t)i * ld + j;
+  return (1.0 - fx) * (1.0 - fy) * g[o] + fx * (1.0 - fy) * g[o + 1] + (1.0 - fx) * fy * g[o + ld] +
+         fx * fy * g[o + ld + 1];
+}
+
+// value, d/dx, d/dy and d2/dxdy of the bilinear interpolant at (x, y); a derivative across a
+// direction in which the point lies beyond the lattice is zero (the clamped interpolant is flat)
+__device__ inline void interp_d(const Lat& L, int ld, const double* __restrict__ g, double x, double y, double& val,
+                                double& ddx, double& ddy, double& dxy) {
+  int i, j;
+  double fx, fy;
+  locate(L, x, y, i, j, fx, fy);
+  const double u = (x - L.x0) * L.idx, v = (y - L.y0) * L.idy;
+  const bool inx = u >= L.jlo && u <= L.jhi, iny = v >= L.ilo && v <= L.ihi;
+  const size_t o = (size_t)i * ld + j;
+  const double a00 = g[o], a01 = g[o + 1], a10 = g[o + ld], a11 = g[o + ld + 1];
+  val = (1.0 - fx) * (1.0 - fy) * a00 + fx * (1.0 - fy) * a01 + (1.0 - fx) * fy * a10 + fx * fy * a11;
+  ddx = inx ? ((a01 - a00) * (1.0 - fy) + (a11 - a10) * fy) * L.idx : 0.0;
+  ddy = iny ? ((a10 - a00) * (1.0 - fx) + (a11 - a01) * fx) * L.idy : 0.0;
+  dxy = (inx && iny) ? (a11 - a10 - a01 + a00) * (L.idx * L.idy) : 0.0;
+}
+
+struct VelField {
+  Lat lu, lv;  // vx and vy lattices
+  int ld;
+  const double* vx;
+  const double* vy;
+  __device__ inline void at(double x, double y, double& u, double& v) const {
+    u = interp(lu, ld, vx, x, y);
+    v = interp(lv, ld, vy, x, y);
+  }
+};
+
+// substeps steps of size h of the scheme (Sec. "Advection of Lagrangian Markers"), each result
+// clamped into [0, Lx] x [0, Ly]; one thread per marker, FP64 throughout
+template <int SCHEME>
+__global__ void k_mk_advect(VelField F, long long n, double* __restrict__ xm, double* __restrict__ ym, double h,
+                            int substeps, double Lx, double Ly) {
+  for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (long long)gridDim.x * blockDim.x) {
+    double x = xm[m], y = ym[m];
+    for (int k = 0; k < substeps; ++k) {
+      double xn, yn;
+      if (SCHEME == PYRO_ADVECT_EULER) {            // eq. euler_advection
+        double u, v;
+        F.at(x, y, u, v);
+        xn = x + h * u;
+        yn = y + h * v;
+      } else if (SCHEME == PYRO_ADVECT_HEUN) {      // eq. heun_method
+        double u1, v1, u2, v2;
+        F.at(x, y, u1, v1);
+        F.at(x + h * u1, y + h * v1, u2, v2);
+        xn = x + 0.5 * h * (u1 + u2);
+        yn = y + 0.5 * h * (v1 + v2);
+      } else if (SCHEME == PYRO_ADVECT_RK4) {       // eq. rk4_method
+        double u1, v1, u2, v2, u3, v3, u4, v4;
+        F.at(x, y, u1, v1);
+        F.at(x + 0.5 * h * u1, y + 0.5 * h * v1, u2, v2);
+        F.at(x + 0.5 * h * u2, y + 0.5 * h * v2, u3, v3);
+        F.at(x + h * u3, y + h * v3, u4, v4);
+        xn = x + h / 6.0 * (u1 + 2.0 * u2 + 2.0 * u3 + u4);
+        yn = y + h / 6.0 * (v1 + 2.0 * v2 + 2.0 * v3 + v4);
+      } else {                                       // eq. lpi_update: x + h v0 + h^2/2 J v0 + h^3/6 H:v0 v0
+        double u, ux, uy, uxy, v, vx_, vy_, vxy;
+        interp_d(F.lu, F.ld, F.vx, x, y, u, ux, uy, uxy);
+        interp_d(F.lv, F.ld, F.vy, x, y, v, vx_, vy_, vxy);
+        const double h2 = 0.5 * h * h, h3 = h * h * h / 6.0;
+        xn = x + h * u + h2 * (ux * u + uy * v) + h3 * (2.0 * uxy * u * v);
+        yn = y + h * v + h2 * (vx_ * u + vy_ * v) + h3 * (2.0 * vxy * u * v);
+      }
+      x = fmin(fmax(xn, 0.0), Lx);
+      y = fmin(fmax(yn, 0.0), Ly);
+    }
+    xm[m] = x;
+    ym[m] = y;
+  }
+}
+
+// per-block max |a| and max |b| over n entries (NaN propagates); red[blockIdx.x], red[gridDim.x + blockIdx.x]
+__global__ void k_absmax2(const double* __restrict__ a, const double* __restrict__ b, size_t n, double* __restrict__ red) {
+  __shared__ double sa[kMkThreads / 32], sb[kMkThreads / 32];
+  double ma = 0.0, mb = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const double x = fabs(a[e]), y = fabs(b[e]);
+    ma = (x > ma || isnan(x)) ? x : ma;
+    mb = (y > mb || isnan(y)) ? y : mb;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double x = __shfl_xor_sync(0xffffffffu, ma, o), y = __shfl_xor_sync(0xffffffffu, mb, o);
+    ma = (x > ma || isnan(x)) ? x : ma;
+    mb = (y > mb || isnan(y)) ? y : mb;
+  }
+  if ((threadIdx.x & 31) == 0) { sa[threadIdx.x >> 5] = ma; sb[threadIdx.x >> 5] = mb; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < kMkThreads / 32; ++k) {
+      ma = (sa[k] > ma || isnan(sa[k])) ? sa[k] : ma;
+      mb = (sb[k] > mb || isnan(sb[k])) ? sb[k] : mb;
+    }
+    red[blockIdx.x] = ma;
+    red[gridDim.x + blockIdx.x] = mb;
+  }
+}
+
 bool on_device(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -208,7 +328,8 @@ int pyro_markers_create(int nx, int ny, double Lx, double Ly, long long max_mark
             cudaMalloc(&h->idx, (size_t)max_markers * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->cell, (size_t)max_markers * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->frac, (size_t)max_markers * 2 * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&h->flag, sizeof(int)) == cudaSuccess;
+            cudaMalloc(&h->flag, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&h->red, 2 * kRedBlocks * sizeof(double)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     pyro_markers_destroy(h);
@@ -220,7 +341,7 @@ int pyro_markers_create(int nx, int ny, double Lx, double Ly, long long max_mark
 
 int pyro_markers_to_grid(pyro_markers h, int lattice, long long n, const double* xm, const double* ym,
                          const double* phim, double* grid, double* wsum, void* cuda_stream) {
-  if (!h || n < 0 || n > h->cap || (lattice != PYRO_LATTICE_NODES && lattice != PYRO_LATTICE_CELLS)) return PYRO_E_INVALID;
+  if (!h || n < 0 || n > h->cap || lattice < PYRO_LATTICE_NODES || lattice > PYRO_LATTICE_VY) return PYRO_E_INVALID;
   if (!grid || !on_device(grid) || (wsum && !on_device(wsum))) return PYRO_E_INVALID;
   if (n > 0 && (!on_device(xm) || !on_device(ym) || !on_device(phim))) return PYRO_E_INVALID;
   cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -249,7 +370,7 @@ int pyro_markers_to_grid(pyro_markers h, int lattice, long long n, const double*
 
 int pyro_grid_to_markers(pyro_markers h, int lattice, long long n, const double* xm, const double* ym,
                          const double* grid, double* phim, void* cuda_stream) {
-  if (!h || n < 0 || (lattice != PYRO_LATTICE_NODES && lattice != PYRO_LATTICE_CELLS)) return PYRO_E_INVALID;
+  if (!h || n < 0 || lattice < PYRO_LATTICE_NODES || lattice > PYRO_LATTICE_VY) return PYRO_E_INVALID;
   if (n == 0) return PYRO_OK;
   if (!on_device(grid) || !on_device(xm) || !on_device(ym) || !on_device(phim)) return PYRO_E_INVALID;
   cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -260,11 +381,64 @@ int pyro_grid_to_markers(pyro_markers h, int lattice, long long n, const double*
   return PYRO_OK;
 }
 
+int pyro_markers_advect(pyro_markers h, int scheme, long long n, double* xm, double* ym, const double* vx,
+                        const double* vy, double dt, int substeps, void* cuda_stream) {
+  if (!h || n < 0 || scheme < PYRO_ADVECT_EULER || scheme > PYRO_ADVECT_TAYLOR || substeps < 1 || !isfinite(dt))
+    return PYRO_E_INVALID;
+  if (n == 0) return PYRO_OK;
+  if (!on_device(xm) || !on_device(ym) || !on_device(vx) || !on_device(vy)) return PYRO_E_INVALID;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaSetDevice(h->dev);
+  const VelField F{make_lat(h, PYRO_LATTICE_VX), make_lat(h, PYRO_LATTICE_VY), h->nx + 2, vx, vy};
+  const double step = dt / substeps;
+  const int nb = grid_blocks(n);
+  switch (scheme) {
+    case PYRO_ADVECT_EULER:
+      k_mk_advect<PYRO_ADVECT_EULER><<<nb, kMkThreads, 0, s>>>(F, n, xm, ym, step, substeps, h->Lx, h->Ly);
+      break;
+    case PYRO_ADVECT_HEUN:
+      k_mk_advect<PYRO_ADVECT_HEUN><<<nb, kMkThreads, 0, s>>>(F, n, xm, ym, step, substeps, h->Lx, h->Ly);
+      break;
+    case PYRO_ADVECT_RK4:
+      k_mk_advect<PYRO_ADVECT_RK4><<<nb, kMkThreads, 0, s>>>(F, n, xm, ym, step, substeps, h->Lx, h->Ly);
+      break;
+    default:
+      k_mk_advect<PYRO_ADVECT_TAYLOR><<<nb, kMkThreads, 0, s>>>(F, n, xm, ym, step, substeps, h->Lx, h->Ly);
+      break;
+  }
+  if (cudaGetLastError() != cudaSuccess) return PYRO_E_CUDA;
+  return PYRO_OK;
+}
+
+int pyro_markers_max_dt(pyro_markers h, const double* vx, const double* vy, double cfl, double* dt_out,
+                        void* cuda_stream) {
+  if (!h || !dt_out || !(cfl > 0) || !isfinite(cfl) || !on_device(vx) || !on_device(vy)) return PYRO_E_INVALID;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaSetDevice(h->dev);
+  const size_t P = (size_t)(h->ny + 2) * (h->nx + 2);
+  k_absmax2<<<kRedBlocks, kMkThreads, 0, s>>>(vx, vy, P, h->red);
+  double r[2 * kRedBlocks];
+  if (cudaMemcpyAsync(r, h->red, sizeof(r), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return PYRO_E_CUDA;
+  double mx = 0.0, my = 0.0;
+  for (int b = 0; b < kRedBlocks; ++b) {
+    if (std::isnan(r[b]) || std::isnan(r[kRedBlocks + b])) return PYRO_E_NONFINITE;
+    mx = std::max(mx, r[b]);
+    my = std::max(my, r[kRedBlocks + b]);
+  }
+  if (!std::isfinite(mx) || !std::isfinite(my)) return PYRO_E_NONFINITE;
+  const double tx = mx > 0.0 ? (h->Lx / h->nx) / mx : HUGE_VAL;
+  const double ty = my > 0.0 ? (h->Ly / h->ny) / my : HUGE_VAL;
+  *dt_out = cfl * std::min(tx, ty);
+  return PYRO_OK;
+}
+
 void pyro_markers_destroy(pyro_markers h) {
   if (!h) return;
   std::lock_guard<std::recursive_mutex> lk(pyro::device_sync_lock());
   cudaFree(h->count); cudaFree(h->offset); cudaFree(h->fill); cudaFree(h->bsum);
-  cudaFree(h->idx); cudaFree(h->cell); cudaFree(h->frac); cudaFree(h->flag);
+  cudaFree(h->idx); cudaFree(h->cell); cudaFree(h->frac); cudaFree(h->flag); cudaFree(h->red);
   delete h;
 }
 

@@ -52,7 +52,8 @@ class PyroStats(ctypes.Structure):
 EXPORTED = ["pyro_default_opts", "pyro_stokes_create", "pyro_stokes_footprint", "pyro_stokes_apply",
             "pyro_stokes_solve", "pyro_stokes_precond", "pyro_stokes_set_timing", "pyro_stokes_get_timing",
             "pyro_stokes_residual_noalloc", "pyro_stokes_adjoint", "pyro_stokes_destroy", "pyro_strerror", "pyro_version",
-            "pyro_markers_create", "pyro_markers_to_grid", "pyro_grid_to_markers", "pyro_markers_destroy"]
+            "pyro_markers_create", "pyro_markers_to_grid", "pyro_grid_to_markers", "pyro_markers_advect",
+            "pyro_markers_max_dt", "pyro_markers_destroy"]
 
 
 def load_library(path=_LIB_PATH):
@@ -93,6 +94,10 @@ def load_library(path=_LIB_PATH):
     lib.pyro_markers_to_grid.restype = I
     lib.pyro_grid_to_markers.argtypes = [P, I, ctypes.c_longlong, P, P, P, P, P]
     lib.pyro_grid_to_markers.restype = I
+    lib.pyro_markers_advect.argtypes = [P, I, ctypes.c_longlong, P, P, P, P, D, I, P]
+    lib.pyro_markers_advect.restype = I
+    lib.pyro_markers_max_dt.argtypes = [P, P, P, D, ctypes.POINTER(D), P]
+    lib.pyro_markers_max_dt.restype = I
     lib.pyro_markers_destroy.argtypes = [P]
     lib.pyro_markers_destroy.restype = None
     return lib
@@ -130,6 +135,11 @@ def make_bc(kind=(FREE_SLIP,) * 4, vt=(0.0,) * 4):
         b.kind[k] = int(kind[k])
         b.vt[k] = float(vt[k])
     return b
+
+
+def _count(a):
+    """Element count of a torch tensor or numpy array."""
+    return int(a.numel()) if hasattr(a, "numel") else int(a.size)
 
 
 def _ptr(a, shape=None, writable=False):
@@ -182,11 +192,13 @@ def residual_noalloc(nx, ny, Lx, Ly, bc, eta_n, eta_c, rho, g, vx, vy, p, r_vx, 
                                               _ptr(r_vy, s), _ptr(r_p, s), _ptr(rel_res), _stream_handle(stream))
 
 
-LATTICE_NODES, LATTICE_CELLS = 0, 1
+LATTICE_NODES, LATTICE_CELLS, LATTICE_VX, LATTICE_VY = 0, 1, 2, 3
+ADVECT_EULER, ADVECT_HEUN, ADVECT_RK4, ADVECT_TAYLOR = 0, 1, 2, 3
 
 
 class Markers:
-    """Marker <-> grid interpolation workspace (pyro_markers): CUDA float64 tensors in and out."""
+    """Marker workspace (pyro_markers): marker <-> grid interpolation and marker advection; CUDA
+    float64 tensors in and out."""
 
     def __init__(self, nx, ny, Lx=1.0, Ly=1.0, max_markers=1):
         self.nx, self.ny, self.Lx, self.Ly = int(nx), int(ny), float(Lx), float(Ly)
@@ -198,7 +210,7 @@ class Markers:
         self.shape = (self.ny + 2, self.nx + 2)
 
     def to_grid(self, lattice, xm, ym, phim, grid, wsum=None, stream=None):
-        n = xm.numel()
+        n = _count(xm)
         st = lib().pyro_markers_to_grid(self._h, int(lattice), n, _ptr(xm, (n,)), _ptr(ym, (n,)), _ptr(phim, (n,)),
                                         _ptr(grid, self.shape), _ptr(wsum, self.shape) if wsum is not None else None,
                                         _stream_handle(stream))
@@ -207,12 +219,30 @@ class Markers:
         return st
 
     def to_markers(self, lattice, xm, ym, grid, phim, stream=None):
-        n = xm.numel()
+        n = _count(xm)
         st = lib().pyro_grid_to_markers(self._h, int(lattice), n, _ptr(xm, (n,)), _ptr(ym, (n,)),
                                         _ptr(grid, self.shape), _ptr(phim, (n,)), _stream_handle(stream))
         if st < 0:
             raise PyroError(st, "pyro_grid_to_markers")
         return st
+
+    def advect(self, xm, ym, vx, vy, dt, scheme=ADVECT_RK4, substeps=1, stream=None):
+        """Move the markers (xm, ym updated in place) through dt in the velocity (vx, vy)."""
+        n = _count(xm)
+        st = lib().pyro_markers_advect(self._h, int(scheme), n, _ptr(xm, (n,)), _ptr(ym, (n,)), _ptr(vx, self.shape),
+                                       _ptr(vy, self.shape), float(dt), int(substeps), _stream_handle(stream))
+        if st < 0:
+            raise PyroError(st, "pyro_markers_advect")
+        return st
+
+    def max_dt(self, vx, vy, cfl=0.5, stream=None):
+        """cfl * min(dx / max|vx|, dy / max|vy|) (inf for a zero velocity)."""
+        out = ctypes.c_double(0.0)
+        st = lib().pyro_markers_max_dt(self._h, _ptr(vx, self.shape), _ptr(vy, self.shape), float(cfl),
+                                       ctypes.byref(out), _stream_handle(stream))
+        if st < 0:
+            raise PyroError(st, "pyro_markers_max_dt")
+        return out.value
 
     def close(self):
         if getattr(self, "_h", None):
