@@ -217,9 +217,11 @@ __global__ void k_multidot(const double* __restrict__ V, size_t stride, const in
 // The same partial sums as k_multidot<WEIGHTED> for nvec <= kDotRegs, in a single pass over w and
 // W: each thread keeps one accumulator per vector in registers. The code path is chosen from nvec
 // in steps of 4 (the FP64 pipe, not memory, bounds these passes, so a path sized to the vector
-// count avoids issuing FMAs for absent vectors). Launch with kThreads threads; gridDim.x blocks
-// write partial[k * gridDim.x + blockIdx.x].
+// count avoids issuing FMAs for absent vectors). Launch kDotBlocks blocks of kThreads threads:
+// two resident blocks per SM (up to 128 registers a thread) make one full wave on 148 SMs; block b
+// writes partial[k * gridDim.x + b].
 constexpr int kDotRegs = 32;
+constexpr int kDotBlocks = 2 * 148;
 
 template <int G, bool WEIGHTED>
 __device__ __forceinline__ void multidot_regs(const double* __restrict__ V, size_t stride, int nvec,
@@ -252,7 +254,7 @@ __device__ __forceinline__ void multidot_regs(const double* __restrict__ V, size
 }
 
 template <bool WEIGHTED>
-__global__ void __launch_bounds__(kThreads) k_multidot_r(const double* __restrict__ V, size_t stride,
+__global__ void __launch_bounds__(kThreads, 2) k_multidot_r(const double* __restrict__ V, size_t stride,
                                                          const int* __restrict__ d_j, const double* __restrict__ w,
                                                          const double* __restrict__ W, size_t n,
                                                          double* __restrict__ partial, int off) {

@@ -669,15 +669,18 @@ inline void mark(pyro_stokes_s* h, int k, cudaStream_t s) {
   if (h->timing) CK(cudaEventRecordWithFlags(h->tev[k], s, cudaEventRecordExternal));
 }
 
-// partial[k * kReduceBlocks + b] = block b's share of sum_e (W[e]) w[e] V_k[e], k < *d_cnt + 1 + off:
-// the one-pass register kernel while the basis fits (m + 1 <= kDotRegs), else groups of 8 vectors.
+// partial[k * nblk + b] = block b's share of sum_e (W[e]) w[e] V_k[e], k < *d_cnt + 1 + off: the
+// one-pass register kernel while the basis fits (m + 1 <= kDotRegs), else groups of 8 vectors.
+// Returns nblk, the number of partials per vector (for k_reduce).
 template <bool WEIGHTED>
-void multidot(pyro_stokes_s* h, cudaStream_t s, const double* V, const int* d_cnt, const double* w, int off) {
-  if (h->m + 1 <= kDotRegs)
-    k_multidot_r<WEIGHTED><<<kReduceBlocks, kThreads, 0, s>>>(V, h->n3, d_cnt, w, h->W, h->n3, h->partial, off);
-  else
-    k_multidot<WEIGHTED><<<dim3(kReduceBlocks, (unsigned)h->dot_grid_y), kThreads, 0, s>>>(
-        V, h->n3, d_cnt, 0, w, h->W, h->n3, h->partial, nullptr, nullptr, off);
+int multidot(pyro_stokes_s* h, cudaStream_t s, const double* V, const int* d_cnt, const double* w, int off) {
+  if (h->m + 1 <= kDotRegs) {
+    k_multidot_r<WEIGHTED><<<kDotBlocks, kThreads, 0, s>>>(V, h->n3, d_cnt, w, h->W, h->n3, h->partial, off);
+    return kDotBlocks;
+  }
+  k_multidot<WEIGHTED><<<dim3(kReduceBlocks, (unsigned)h->dot_grid_y), kThreads, 0, s>>>(
+      V, h->n3, d_cnt, 0, w, h->W, h->n3, h->partial, nullptr, nullptr, off);
+  return kReduceBlocks;
 }
 
 // z = M^-1 v with v = in + (*d_idx) in_stride and z = out + (*d_idx) out_stride (device index), and
@@ -716,11 +719,11 @@ void precond_any(pyro_stokes_s* h, cudaStream_t s, const double* in, size_t in_s
 void fgmres_body(pyro_stokes_s* h, cudaStream_t s) {
   precond_any(h, s, h->V, h->n3, (double*)h->Z, h->n3, h->d_j, true);
   // classical Gram-Schmidt with one re-orthogonalisation (CGS2) in the W inner product
-  multidot<true>(h, s, h->V, h->d_j, h->w, 0);
-  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, h->h1, nullptr);
+  int nb = multidot<true>(h, s, h->V, h->d_j, h->w, 0);
+  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, nb, h->d_j, 0, h->h1, nullptr);
   k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h1, h->n3, nullptr, nullptr, nullptr);
-  multidot<true>(h, s, h->V, h->d_j, h->w, 0);
-  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, h->h2, nullptr);
+  nb = multidot<true>(h, s, h->V, h->d_j, h->w, 0);
+  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, nb, h->d_j, 0, h->h2, nullptr);
   k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h2, h->n3, h->W, h->part2, nullptr);
   k_arnoldi_finish<<<1, kThreads, 0, s>>>(h->d_j, h->h1, h->h2, h->part2, 2 * kReduceBlocks, h->hcol, h->inv, h->flag,
                                           nullptr, nullptr);
@@ -739,8 +742,8 @@ void gcr_body(pyro_stokes_s* h, cudaStream_t s) {
   double* Zb = (double*)h->Z;
   for (int pass = 0; pass < 2; ++pass) {
     double* hc = pass == 0 ? h->h1 : h->h2;
-    multidot<true>(h, s, h->V, h->d_j, h->w, -1);
-    k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_j, 0, hc, nullptr, -1);
+    const int nb = multidot<true>(h, s, h->V, h->d_j, h->w, -1);
+    k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, nb, h->d_j, 0, hc, nullptr, -1);
     k_multiaxpy<<<kReduceBlocks, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, hc, h->n3, pass ? h->W : nullptr,
                                                    pass ? h->part2 : nullptr, nullptr, -1);
     k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->zc, Zb, h->n3, h->d_j, hc, h->n3, nullptr, nullptr, nullptr,
@@ -770,8 +773,8 @@ void aa_body(pyro_stokes_s* h, cudaStream_t s) {
   k_sum_pairs<<<1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->ydev);
   precond_any(h, s, h->r, 0, h->zc, 0, h->d_j, false);
   k_aa_store<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, (double*)h->Z, h->n3, h->d_slot, h->x, h->zc, h->n3);
-  multidot<false>(h, s, (double*)h->Z, h->d_cnt, h->zc, -1);
-  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, kReduceBlocks, h->d_cnt, 0, h->h1, nullptr, -1);
+  const int nb = multidot<false>(h, s, (double*)h->Z, h->d_cnt, h->zc, -1);
+  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, nb, h->d_cnt, 0, h->h1, nullptr, -1);
   h->launches += 6;
   mark(h, 6, s);
 }
