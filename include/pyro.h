@@ -99,25 +99,28 @@ typedef enum { PYRO_ACCEL_FGMRES = 0, PYRO_ACCEL_GCR = 1, PYRO_ACCEL_ANDERSON = 
 typedef enum { PYRO_SMOOTH_RBGS = 0, PYRO_SMOOTH_JACOBI = 1, PYRO_SMOOTH_RAS = 2, PYRO_SMOOTH_MIXED = 3 } pyro_smoother;
 typedef enum { PYRO_ETA_ARITH = 0, PYRO_ETA_GEOM = 1 } pyro_eta_coarsening;
 
-/* Solver options. pyro_default_opts() fills the defaults given in brackets. */
+/* Solver options. pyro_default_opts() fills the defaults given in brackets. pyro_stokes_create
+ * returns PYRO_E_INVALID (and pyro_stokes_footprint 0) when an option lies outside the range given
+ * here; nothing is clamped or replaced. */
 typedef struct {
-  int nu1, nu2;          /* pre/post RBGS sweeps per level [2, 2] */
-  double omega_v;        /* RBGS damping (eq. sor_update) [1.0] */
-  double alpha_p;        /* Uzawa pressure relaxation alpha (eq. uzawa_iteration) [1.0] */
+  int nu1, nu2;          /* pre/post smoothing sweeps per level, >= 0 with nu1 + nu2 >= 1 [2, 2] */
+  double omega_v;        /* velocity smoother damping (eq. sor_update), in (0, 2) [1.0] */
+  double alpha_p;        /* Uzawa pressure relaxation alpha (eq. uzawa_iteration), > 0 [1.0] */
   int restart_m;         /* FGMRES / GCR restart length, Anderson depth; 1..256 [30] */
-  int max_iter;          /* total FGMRES iterations before PYRO_W_NOT_CONVERGED [500] */
+  int max_iter;          /* total outer iterations before PYRO_W_NOT_CONVERGED, >= 1 [500] */
   int prec;              /* pyro_precision [PYRO_PREC_MIXED] */
-  int coarsest_min;      /* halve while the short side stays >= this many cells [4] */
+  int coarsest_min;      /* halve while the short side stays >= this many cells, >= 1 [4] */
   int eta_coarsen;       /* pyro_eta_coarsening [PYRO_ETA_ARITH] */
   int warm_start;        /* 1: vx, vy, p passed to solve hold the initial guess [0] */
   int use_graphs;        /* 1: capture the FGMRES iteration into a CUDA graph [1] */
   double timeout_s;      /* wall-clock limit of one solve, <= 0 for none [0] */
-  int kcycle;            /* K-cycle depth: on levels l < kcycle the coarse correction is two
+  int kcycle;            /* K-cycle depth 0..16: on levels l < kcycle the coarse correction is two
                             flexible-CG steps preconditioned by the next level's cycle (recursive
                             Krylov cycle, not in the paper; 0 = the paper's plain V-cycle) [0] */
   int cluster_cells;     /* levels with at most this many cells run their whole cycle inside one
-                            thread-block-cluster launch (8 CTAs, cluster barriers between steps);
-                            <= 0 = never, every step is its own kernel [0] */
+                            thread-block-cluster launch (16 CTAs where the GPU can hold such a
+                            cluster, else 8; cluster barriers between steps); <= 0 = never, every
+                            step is its own kernel [0] */
   int tile_fusion;       /* 1: smoothing sweeps (with the prolongation) and residual+restriction run
                             as shared-memory tile kernels, one launch each per level visit (FP32
                             levels; FP64 levels see tile_fusion64); 2: as 1, but FP32 levels large
@@ -125,29 +128,29 @@ typedef struct {
                             the row-streaming wavefront kernel; 3: as 2 on every FP32 level (for
                             tests and tuning); 4: as 1 with the 64 x 32 colour-split tiles on large
                             levels instead of the warp-per-row tiles; 0: one kernel per colour and
-                            step [1] */
+                            step; 0..4 [1] */
   int tile_sweeps;       /* FP32 tile kernels: sweeps fused per launch, 1 (halo 4, one HBM pass per
                             sweep) or 2 (halo 8, one pass per two sweeps) [2] */
   int tile_fusion64;     /* 1: FP64 levels of up to 65536 cells also smooth and restrict with the
                             tile kernels; 0: every FP64 level runs one kernel per colour and step on
                             precomputed viscosity coefficients (B300's FP64 rate per SM is so low
-                            that one CTA per tile becomes the critical path) [0] */
+                            that one CTA per tile becomes the critical path); 0 or 1 [0] */
   int accel;             /* pyro_accel: outer accelerator [PYRO_ACCEL_FGMRES] */
   double aa_beta;        /* Anderson mixing beta in (0, 1] (the paper suggests 0.5-0.8) [1.0] */
   int smoother;          /* pyro_smoother [PYRO_SMOOTH_RBGS] */
-  int ras_inner;         /* RAS smoother: local Jacobi iterations per tile pass (T_inner) [4] */
+  int ras_inner;         /* RAS smoother: local Jacobi iterations per tile pass (T_inner), >= 1 [4] */
   int litho_guess;       /* 1: start the pressure from the lithostatic column integral of rho g_y
                             (Sec. "Viscosity Rescaling and Initial Guess"; cell pressures going down
                             differ by dy g_y times the vy-node density) when not warm-starting [0] */
   int cont_stages;       /* viscosity-contrast continuation (same section): > 0 runs cont_stages
                             stages with eta_comp = (1 - theta) eta_min + theta eta, theta = k /
                             cont_stages, each cont_iters outer iterations from the previous stage's
-                            iterate, then the full-contrast solve; 0 = off [0] */
-  int cont_iters;        /* outer iterations per continuation stage (the paper: 25) [25] */
+                            iterate, then the full-contrast solve; 0 = off; >= 0 [0] */
+  int cont_iters;        /* outer iterations per continuation stage (the paper: 25), >= 1 [25] */
   int coarse_sweeps;     /* when the coarsest level has more than 1024 velocity unknowns (grids that
                             do not halve down far, e.g. odd sizes), this many smoothing sweeps from
                             zero stand in for its direct solve (Sec. "Multigrid Cycles": direct
-                            method or a few smoothing iterations) [40] */
+                            method or a few smoothing iterations); >= 1 [40] */
   double coarsen_ratio;  /* 2: halve while possible; any other value in [1.5, 8] coarsens every level
                             by that ratio, n_c = ceil(n / ratio) (the paper's arbitrary ratio, e.g.
                             2.5) [2.0] */

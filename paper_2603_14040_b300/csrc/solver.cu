@@ -1238,24 +1238,17 @@ int continuation_solve(pyro_stokes_s* h, double tol, pyro_stats* st, cudaStream_
   return outer_solve(h, tol, st, s);
 }
 
-void validate_opts(pyro_opts& o) {
-  if (o.nu1 < 0) o.nu1 = 0;
-  if (o.nu2 < 0) o.nu2 = 0;
-  if (o.nu1 + o.nu2 == 0) o.nu2 = 1;
-  if (o.restart_m < 1) o.restart_m = 1;
-  if (o.restart_m > kMaxRestart) o.restart_m = kMaxRestart;
-  if (o.max_iter < 1) o.max_iter = 1;
-  if (o.coarsest_min < 1) o.coarsest_min = 1;
-  if (o.kcycle < 0) o.kcycle = 0;
-  if (o.kcycle > 16) o.kcycle = 16;
-  if (o.accel < PYRO_ACCEL_FGMRES || o.accel > PYRO_ACCEL_ANDERSON) o.accel = PYRO_ACCEL_FGMRES;
-  if (!(o.aa_beta > 0.0) || o.aa_beta > 1.0) o.aa_beta = 1.0;
-  if (o.smoother < PYRO_SMOOTH_RBGS || o.smoother > PYRO_SMOOTH_MIXED) o.smoother = PYRO_SMOOTH_RBGS;
-  if (o.ras_inner < 1) o.ras_inner = 1;
-  if (o.cont_stages < 0) o.cont_stages = 0;
-  if (o.cont_iters < 1) o.cont_iters = 1;
-  if (o.coarse_sweeps < 1) o.coarse_sweeps = 1;
-  if (!(o.coarsen_ratio >= 1.5) || o.coarsen_ratio > 8.0) o.coarsen_ratio = 2.0;
+// true when every option lies in the range pyro.h documents (nothing is clamped or replaced)
+bool opts_valid(const pyro_opts& o) {
+  return o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 1 && o.omega_v > 0.0 && o.omega_v < 2.0 &&
+         o.alpha_p > 0.0 && std::isfinite(o.alpha_p) && o.restart_m >= 1 && o.restart_m <= kMaxRestart &&
+         o.max_iter >= 1 && (o.prec == PYRO_PREC_FP64 || o.prec == PYRO_PREC_MIXED) && o.coarsest_min >= 1 &&
+         (o.eta_coarsen == PYRO_ETA_ARITH || o.eta_coarsen == PYRO_ETA_GEOM) && o.kcycle >= 0 && o.kcycle <= 16 &&
+         o.tile_fusion >= 0 && o.tile_fusion <= 4 && (o.tile_sweeps == 1 || o.tile_sweeps == 2) &&
+         (o.tile_fusion64 == 0 || o.tile_fusion64 == 1) && o.accel >= PYRO_ACCEL_FGMRES &&
+         o.accel <= PYRO_ACCEL_ANDERSON && o.aa_beta > 0.0 && o.aa_beta <= 1.0 && o.smoother >= PYRO_SMOOTH_RBGS &&
+         o.smoother <= PYRO_SMOOTH_MIXED && o.ras_inner >= 1 && o.cont_stages >= 0 && o.cont_iters >= 1 &&
+         o.coarse_sweeps >= 1 && o.coarsen_ratio >= 1.5 && o.coarsen_ratio <= 8.0;
 }
 
 std::vector<std::pair<int, int>> sizes_of(int nx, int ny, const pyro_opts& o) {
@@ -1346,7 +1339,7 @@ size_t pyro_stokes_footprint(int nx, int ny, const pyro_opts* opts) {
   pyro_opts o;
   pyro_default_opts(&o);
   if (opts) o = *opts;
-  validate_opts(o);
+  if (!opts_valid(o)) return 0;
   const int L = check_size(nx, ny, o);
   if (L < 1) return 0;
   return footprint_bytes(nx, ny, o, L);
@@ -1361,7 +1354,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
   pyro_opts o;
   pyro_default_opts(&o);
   if (opts) o = *opts;
-  validate_opts(o);
+  if (!opts_valid(o)) return PYRO_E_INVALID;
   pyro_bc b{};
   for (int k = 0; k < 4; ++k) { b.kind[k] = PYRO_BC_FREE_SLIP; b.vt[k] = 0.0; }
   if (bc) b = *bc;

@@ -46,6 +46,20 @@ def test_host_logic_without_gpu():
     assert P.footprint(1024, 1024, o10) < f2
 
 
+@pytest.mark.parametrize("kw", [dict(smoother=9), dict(accel=-1), dict(prec=5), dict(eta_coarsen=2), dict(restart_m=0),
+                                dict(restart_m=257), dict(nu1=0, nu2=0), dict(nu1=-1), dict(omega_v=0.0),
+                                dict(omega_v=2.0), dict(alpha_p=0.0), dict(aa_beta=0.0), dict(aa_beta=1.5),
+                                dict(kcycle=17), dict(tile_fusion=5), dict(tile_sweeps=3), dict(tile_fusion64=2),
+                                dict(ras_inner=0), dict(max_iter=0), dict(coarsen_ratio=1.2), dict(coarse_sweeps=0),
+                                dict(cont_iters=0), dict(coarsest_min=0)])
+def test_options_outside_their_range_are_rejected_not_clamped(kw):
+    """pyro_stokes_footprint (host logic, no GPU) answers 0 for an option outside its documented
+    range, as pyro_stokes_create answers PYRO_E_INVALID; the same options in range are served."""
+    import paper_2603_14040_b300 as P
+    assert P.footprint(64, 64, P.default_opts()) > 0
+    assert P.footprint(64, 64, P.default_opts(**kw)) == 0
+
+
 def test_product_path_has_no_oracle_dependency():
     pkg = os.path.join(ROOT, "paper_2603_14040_b300")
     for dirpath, _, files in os.walk(pkg):
