@@ -55,7 +55,7 @@ def _precond_case(nx, ny, Lx, Ly, bc, prec, seed, kcycle=0, cluster_cells=0, til
     z = M.uzawa_precond(h_or, r, ec, alpha=1.0, nu1=2, nu2=2, omega=omega, kcycle=kcycle)
     zx, zy, zp = S.vector_to_fields(g, z, fill_ghosts=False)
     h = P.Stokes(nx, ny, Lx, Ly, bc=P.make_bc(kind, vt), prec=prec, kcycle=kcycle, cluster_cells=cluster_cells,
-                 tile_fusion=tile_fusion, tile_fusion64=tile_fusion, eta_coarsen=eta_coarsen, coarsest_min=2,
+                 tile_fusion=tile_fusion, tile_fusion64=1 if tile_fusion else 0, eta_coarsen=eta_coarsen, coarsest_min=2,
                  smoother=smoother, ras_inner=ras_inner, omega_v=omega, coarsen_general=coarsen_general,
                  coarsen_ratio=coarsen_ratio)
     Zx, Zy, Zp = zeros(ny, nx), zeros(ny, nx), zeros(ny, nx)
