@@ -304,11 +304,13 @@ def sinker_e1_sample():
     return res
 
 
-def serving_sample(n_req=48, slots=4, max_iter=3000, restart_m=200, seed=4):
+def serving_sample(n_req=48, slots=4, max_iter=3000, restart_m=200, seed=4, nu=8):
     """Continuous batching on a bounded sample of the serving workload: requests with n in
     {128, 256, 512}, aspect in {1, 2, 4}, 16 inclusions of contrast 10^U[2,6], tol 1e-8, Poisson
     arrivals at 0.8 x the measured single-slot service rate; mixed precision, FGMRES with the
-    longest restart (<= 200) whose handle fits a quarter of the device budget."""
+    longest restart (<= 200) whose handle fits a quarter of the device budget, V(nu, nu) cycles
+    (on these sharp-inclusion requests 8 sweeps per level halve the total solve time of V(2, 2):
+    fewer iterations of the long-restart FGMRES outweigh the cheaper cycles)."""
     import torch
     from synth import serving_request
     from paper_2603_14040_b300.serving import SolveServer, Request, PyroBackend, latency_stats, poisson_arrivals
@@ -318,7 +320,7 @@ def serving_sample(n_req=48, slots=4, max_iter=3000, restart_m=200, seed=4):
         f, C = serving_request(k, base_seed=seed, sizes=(128, 256, 512))
         reqs.append((Request(rid=k, nx=f.nx, ny=f.ny, Lx=f.Lx, Ly=f.Ly, eta_n=dev(f.eta_n), eta_c=dev(f.eta_c),
                              rho=dev(f.rho), g=(0.0, 1.0), tol=1e-8), C))
-    be = PyroBackend(opts_kw={"max_iter": max_iter, "prec": 1},
+    be = PyroBackend(opts_kw={"max_iter": max_iter, "prec": 1, "nu1": nu, "nu2": nu},
                      restart_choices=tuple(m for m in (restart_m, 100, 50, 30) if m <= restart_m))
     # service rate from a sequential pass over the first requests (also warms the handle pool)
     srv = SolveServer(be, max_slots=1)
@@ -345,7 +347,7 @@ def serving_sample(n_req=48, slots=4, max_iter=3000, restart_m=200, seed=4):
     conv = sum(1 for r in done if r.status == 0)
     st.update({"requests": n_req, "slots": slots, "arrival_rate_per_s": rate, "mean_single_service_ms":
                mean_service * 1e3, "converged_to_tol": conv, "not_converged_at_max_iter": n_req - conv,
-               "max_iter": max_iter, "max_concurrent": srv.max_concurrent,
+               "max_iter": max_iter, "cycle": f"V({nu},{nu})", "max_concurrent": srv.max_concurrent,
                "mean_iters": float(np.mean([r.iters for r in done]))})
     return st
 
