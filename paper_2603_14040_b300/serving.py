@@ -239,13 +239,18 @@ class PyroBackend:
     grids still admit several concurrent solves while small ones keep long Krylov cycles (the
     high-contrast requests need them)."""
 
+    # V(8, 8) cycles unless the caller says otherwise: on sharp high-contrast inclusions (the
+    # serving workload) eight sweeps per level about halve the total solve time of V(2, 2)
+    DEFAULT_OPTS = {"nu1": 8, "nu2": 8}
+
     def __init__(self, opts_kw=None, device=0, restart_choices=None, per_handle_bytes=None):
         import torch
         from . import pyro as P
         self.P = P
         self.torch = torch
         self.device = device
-        self.opts_kw = dict(opts_kw or {})
+        self.opts_kw = dict(self.DEFAULT_OPTS)
+        self.opts_kw.update(opts_kw or {})
         self.restart_choices = tuple(restart_choices) if restart_choices else None
         self.per_handle_bytes = per_handle_bytes
         self._fp = {}
