@@ -467,12 +467,18 @@ def main():
     ap.add_argument("--smoother", type=int, default=0, help="pyro_opts.smoother of the --profile solve")
     ap.add_argument("--omega", type=float, default=1.0, help="pyro_opts.omega_v of the --profile solve")
     ap.add_argument("--accel", type=int, default=0, help="pyro_opts.accel of the --profile solve")
+    ap.add_argument("--markers", action="store_true",
+                    help="only the marker sample (16.8 M markers on 1024^2: interpolation both ways and one "
+                         "advection step per scheme), for ncu captures")
     args = ap.parse_args()
     rank, world, local = env_rank()
     import torch
     import torch.distributed as dist
     if args.profile:
         return profile_solve(args)
+    if args.markers:
+        print(json.dumps({"markers": marker_sample(reps=1)}))
+        return
     if world > 1 and not dist.is_initialized():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     if args.impl == "reference":

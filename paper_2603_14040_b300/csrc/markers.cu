@@ -49,6 +49,7 @@ constexpr int kRedBlocks = 296;
 
 struct Lat {
   double x0, y0, idx, idy;
+  double ox, oy;           // -x0 idx, -y0 idy: lattice coordinate u = x idx + ox
   int ilo, ihi, jlo, jhi;  // lattice index range (inclusive)
   int ncx, ncy;            // lattice cells per row / column
 };
@@ -69,14 +70,18 @@ Lat make_lat(const pyro_markers_s* h, int kind) {
   }
   L.ncx = L.jhi - L.jlo;
   L.ncy = L.ihi - L.ilo;
+  L.ox = -L.x0 * L.idx;
+  L.oy = -L.y0 * L.idy;
   return L;
 }
 
+// lattice cell (i, j) and fractions of (x, y); a coordinate beyond the lattice (or not finite)
+// lands in the outermost cell (NaN: the first) with its fraction clamped to [0, 1]
 __device__ inline void locate(const Lat& L, double x, double y, int& i, int& j, double& fx, double& fy) {
-  const double u = (x - L.x0) * L.idx, v = (y - L.y0) * L.idy;
+  const double u = fma(x, L.idx, L.ox), v = fma(y, L.idy, L.oy);
   const double fu = floor(u), fv = floor(v);
-  j = (int)fmin(fmax(fu, (double)L.jlo), (double)(L.jhi - 1));
-  i = (int)fmin(fmax(fv, (double)L.ilo), (double)(L.ihi - 1));
+  j = !(fu >= L.jlo) ? L.jlo : (fu >= L.jhi - 1 ? L.jhi - 1 : (int)fu);
+  i = !(fv >= L.ilo) ? L.ilo : (fv >= L.ihi - 1 ? L.ihi - 1 : (int)fv);
   fx = fmin(fmax(u - j, 0.0), 1.0);
   fy = fmin(fmax(v - i, 0.0), 1.0);
 }
@@ -206,7 +211,7 @@ __device__ inline void interp_d(const Lat& L, int ld, const double* __restrict__
   int i, j;
   double fx, fy;
   locate(L, x, y, i, j, fx, fy);
-  const double u = (x - L.x0) * L.idx, v = (y - L.y0) * L.idy;
+  const double u = fma(x, L.idx, L.ox), v = fma(y, L.idy, L.oy);
   const bool inx = u >= L.jlo && u <= L.jhi, iny = v >= L.ilo && v <= L.ihi;
   const size_t o = (size_t)i * ld + j;
   const double a00 = g[o], a01 = g[o + 1], a10 = g[o + ld], a11 = g[o + ld + 1];
