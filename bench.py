@@ -164,15 +164,22 @@ def vcycle_rooflines(peaks):
                                 launches=2, smoother=1, omega_v=0.6)
     main["traffic"] = 525.78e6
     main["traffic_source"] = "ncu dram__bytes_read+write of one launch (profiles/k_jacobi_fp32_4096_level0.md)"
+    main["sweeps_per_launch"] = 1
     main["variants"] = {}
-    for key, label, launches, opts in [
-            ("rbgs_tiles_2_sweeps_default", "k_rbgs_tile_cs<2,64,32> (2 RBGS sweeps per launch, the default)", 1,
+    # sweeps: smoothing sweeps (RBGS) or local Jacobi iterations (RAS) one launch performs for its
+    # one HBM pass; effective = sweeps x algorithmic bytes of one sweep / launch time
+    for key, label, launches, sweeps, opts in [
+            ("rbgs_tiles_2_sweeps_default", "k_rbgs_tile_w<2,32> (2 RBGS sweeps per launch, the default)", 1, 2,
              dict(tile_sweeps=2)),
-            ("rbgs_tiles_1_sweep", "k_rbgs_tile_cs<1,64,32> (1 RBGS sweep per launch)", 2, dict(tile_sweeps=1)),
-            ("ras_inner_2", "k_ras_tile<float,32,32> (RAS pass of 2 local Jacobi iterations)", 1,
-             dict(smoother=2, ras_inner=2, omega_v=0.6))]:
+            ("rbgs_tiles_1_sweep", "k_rbgs_tile_w<1,32> (1 RBGS sweep per launch)", 2, 1, dict(tile_sweeps=1)),
+            ("ras_inner_2", "k_ras_tile<float,32,32> (RAS pass of 2 local Jacobi iterations)", 1, 2,
+             dict(smoother=2, ras_inner=2, omega_v=0.6)),
+            ("ras_inner_4", "k_ras_tile<float,32,32> (RAS pass of 4 local Jacobi iterations, the paper's T_inner)",
+             1, 4, dict(smoother=2, ras_inner=4, omega_v=0.6))]:
         v = vcycle_roofline_4096(peaks, label=label, launches=launches, **opts)
         main["variants"][key] = {k: v[k] for k in ("kernel", "achieved", "frac", "launch_ms", "vcycle_ms_per_iter")}
+        main["variants"][key].update({"sweeps_per_launch": sweeps, "effective_sweep_GBps": sweeps * v["achieved"],
+                                      "effective_frac": sweeps * v["frac"]})
     return main
 
 
