@@ -28,7 +28,8 @@ constexpr int kMaxCoarse = 1024;
 constexpr int kStreamMinRows = 96;  // shortest row chunk worth a streaming pass
 constexpr int kRasTile = 32;        // RAS-type Jacobi tile edge (cells), the paper's 32 x 32
 constexpr long long kSmallTileCells = 65536;  // FP32 levels up to 256^2 smooth with 32 x 16 tiles
-constexpr int kWTileY2 = 32;        // owned rows of the two-sweep warp-per-row tile
+constexpr int kWTileY2 = 48;        // owned rows of the two-sweep warp-per-row tile (2 CTAs per SM)
+constexpr int kWTileY1 = 48;        // owned rows of the one-sweep warp-per-row tile
 
 struct CudaError {
   cudaError_t e;
@@ -374,9 +375,9 @@ struct MG {
             k_rbgs_tile_w<2, kWTileY2><<<gr, kTileThreads, Tl::smem_bytes(), s>>>(
                 L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, gc, cvx, cvy);
           } else {
-            using Tl = SweepTileW<1, 32>;
-            const dim3 gr((L.g.nx + 2 + Tl::TX - 1) / Tl::TX, (L.g.ny + 2 + 31) / 32);
-            k_rbgs_tile_w<1, 32><<<gr, kTileThreads, Tl::smem_bytes(), s>>>(
+            using Tl = SweepTileW<1, kWTileY1>;
+            const dim3 gr((L.g.nx + 2 + Tl::TX - 1) / Tl::TX, (L.g.ny + 2 + kWTileY1 - 1) / kWTileY1);
+            k_rbgs_tile_w<1, kWTileY1><<<gr, kTileThreads, Tl::smem_bytes(), s>>>(
                 L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, gc, cvx, cvy);
           }
         } else if ((long long)L.g.nx * L.g.ny > kSmallTileCells) {
@@ -462,8 +463,8 @@ struct MG {
                               (int)SweepTileCS<1, 64, 32>::smem_bytes()));
       CK(cudaFuncSetAttribute(k_rbgs_tile_w<2, kWTileY2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)SweepTileW<2, kWTileY2>::smem_bytes()));
-      CK(cudaFuncSetAttribute(k_rbgs_tile_w<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)SweepTileW<1, 32>::smem_bytes()));
+      CK(cudaFuncSetAttribute(k_rbgs_tile_w<1, kWTileY1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)SweepTileW<1, kWTileY1>::smem_bytes()));
       CK(cudaFuncSetAttribute(k_rbgs_tile_cs<2, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)SweepTileCS<2, 32, 16>::smem_bytes()));
       CK(cudaFuncSetAttribute(k_rbgs_tile_cs<1, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
