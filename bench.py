@@ -486,16 +486,19 @@ def main():
     if args.markers:
         print(json.dumps({"markers": marker_sample(reps=1)}))
         return
-    if world > 1 and not dist.is_initialized():
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     if args.impl == "reference":
+        # the oracle runs on rank 0's host cores; the other ranks exit without work
         run_reference(args, rank, world)
-        if world > 1:
-            dist.barrier()
         return
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    if world > 1 and not dist.is_initialized():
+        if torch.cuda.is_available():
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
 
     import paper_2603_14040_b300 as P
-    torch.cuda.set_device(local)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     f = make_fields(1024)
     n = 1024
