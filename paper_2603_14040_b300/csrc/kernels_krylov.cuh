@@ -185,21 +185,15 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
 template <bool WEIGHTED>
 __global__ void k_multidot(const double* __restrict__ V, size_t stride, const int* __restrict__ d_j, int nfix,
                            const double* __restrict__ w, const double* __restrict__ W, size_t n,
-                           double* __restrict__ partial, const int* __restrict__ d_run, double* __restrict__ part_ww,
-                           int off = 0) {
+                           double* __restrict__ partial, int off = 0) {
   __shared__ double sh[32];
-  if (d_run && *d_run == 0) return;  // optional device-side switch
   const int nvec = d_j ? (*d_j + 1 + off) : nfix;
   const int k0 = blockIdx.y * 8;
   if (k0 >= nvec) return;
   const int kn = min(8, nvec - k0);
-  const bool ww = part_ww && blockIdx.y == 0;
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  double aww = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const double we = w[e];
-    const double t = WEIGHTED ? W[e] * we : we;
-    if (ww) aww += t * we;
+    const double t = WEIGHTED ? W[e] * w[e] : w[e];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
       if (q < kn) acc[q] += t * V[(size_t)(k0 + q) * stride + e];
@@ -207,10 +201,6 @@ __global__ void k_multidot(const double* __restrict__ V, size_t stride, const in
   for (int q = 0; q < kn; ++q) {
     const double s = block_sum(acc[q], sh);
     if (threadIdx.x == 0) partial[(size_t)(k0 + q) * gridDim.x + blockIdx.x] = s;
-  }
-  if (ww) {
-    const double s = block_sum(aww, sh);
-    if (threadIdx.x == 0) part_ww[blockIdx.x] = s;
   }
 }
 
@@ -275,9 +265,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_multidot_r(const double* __rest
 
 // out[k] = sum_b partial[k * nblk + b] for k < nvec (one block per k, fixed order)
 __global__ void k_reduce(const double* __restrict__ partial, int nblk, const int* __restrict__ d_j, int nfix,
-                         double* __restrict__ out, const int* __restrict__ d_run, int off = 0) {
+                         double* __restrict__ out, int off = 0) {
   __shared__ double sh[32];
-  if (d_run && *d_run == 0) return;
   const int nvec = d_j ? (*d_j + 1 + off) : nfix;
   const int k = blockIdx.x;
   if (k >= nvec) return;
@@ -290,11 +279,9 @@ __global__ void k_reduce(const double* __restrict__ partial, int nblk, const int
 // w -= sum_{k<nvec} h[k] V_k; if part != null also per-block sum(W w^2) into part[blockIdx.x]
 __global__ void k_multiaxpy(double* __restrict__ w, const double* __restrict__ V, size_t stride,
                             const int* __restrict__ d_j, const double* __restrict__ h, size_t n,
-                            const double* __restrict__ W, double* __restrict__ part, const int* __restrict__ d_run,
-                            int off = 0) {
+                            const double* __restrict__ W, double* __restrict__ part, int off = 0) {
   __shared__ double sh[32];
   __shared__ double hs[kMaxRestart + 2];
-  if (d_run && *d_run == 0) return;
   const int nvec = *d_j + 1 + off;
   for (int k = threadIdx.x; k < nvec; k += blockDim.x) hs[k] = h[k];
   __syncthreads();
@@ -311,23 +298,19 @@ __global__ void k_multiaxpy(double* __restrict__ w, const double* __restrict__ V
   }
 }
 
-// Finish one Arnoldi step (single thread): column j of the Hessenberg matrix
+// Finish one Arnoldi step (one block; thread 0 writes): column j of the Hessenberg matrix
 // hcol[k] = h1[k] + h2[k] (k <= j), hcol[j+1] = ||w||_W; inv = 1/||w||_W.
 __global__ void k_arnoldi_finish(const int* __restrict__ d_j, const double* __restrict__ h1,
                                  const double* __restrict__ h2, const double* __restrict__ part, int nblk,
-                                 double* __restrict__ hcol, double* __restrict__ inv, int* __restrict__ flag,
-                                 const int* __restrict__ d_run, const double* __restrict__ nrm2_after1) {
+                                 double* __restrict__ hcol, double* __restrict__ inv, int* __restrict__ flag) {
   __shared__ double sh[32];
-  const bool second = d_run == nullptr || *d_run != 0;
   double s = 0.0;
-  if (second)
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[b];
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[b];
   s = block_sum(s, sh);
   if (threadIdx.x != 0) return;
-  if (!second) s = *nrm2_after1;
   const int j = *d_j;
   double* col = hcol + (size_t)j * kHcolStride;
-  for (int k = 0; k <= j; ++k) col[k] = h1[k] + (second ? h2[k] : 0.0);
+  for (int k = 0; k <= j; ++k) col[k] = h1[k] + h2[k];
   const double nrm = sqrt(s);
   col[j + 1] = nrm;
   if (!isfinite(nrm)) atomicOr(flag, FLAG_NONFINITE);

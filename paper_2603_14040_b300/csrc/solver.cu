@@ -680,7 +680,7 @@ int multidot(pyro_stokes_s* h, cudaStream_t s, const double* V, const int* d_cnt
     return kDotBlocks;
   }
   k_multidot<WEIGHTED><<<dim3(kReduceBlocks, (unsigned)h->dot_grid_y), kThreads, 0, s>>>(
-      V, h->n3, d_cnt, 0, w, h->W, h->n3, h->partial, nullptr, nullptr, off);
+      V, h->n3, d_cnt, 0, w, h->W, h->n3, h->partial, off);
   return kReduceBlocks;
 }
 
@@ -721,13 +721,13 @@ void fgmres_body(pyro_stokes_s* h, cudaStream_t s) {
   precond_any(h, s, h->V, h->n3, (double*)h->Z, h->n3, h->d_j, true);
   // classical Gram-Schmidt with one re-orthogonalisation (CGS2) in the W inner product
   int nb = multidot<true>(h, s, h->V, h->d_j, h->w, 0);
-  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, nb, h->d_j, 0, h->h1, nullptr);
-  k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h1, h->n3, nullptr, nullptr, nullptr);
+  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, nb, h->d_j, 0, h->h1);
+  k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h1, h->n3, nullptr, nullptr);
   nb = multidot<true>(h, s, h->V, h->d_j, h->w, 0);
-  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, nb, h->d_j, 0, h->h2, nullptr);
-  k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h2, h->n3, h->W, h->part2, nullptr);
-  k_arnoldi_finish<<<1, kThreads, 0, s>>>(h->d_j, h->h1, h->h2, h->part2, 2 * kReduceBlocks, h->hcol, h->inv, h->flag,
-                                          nullptr, nullptr);
+  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, nb, h->d_j, 0, h->h2);
+  k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, h->h2, h->n3, h->W, h->part2);
+  k_arnoldi_finish<<<1, kThreads, 0, s>>>(h->d_j, h->h1, h->h2, h->part2, 2 * kReduceBlocks, h->hcol, h->inv,
+                                          h->flag);
   k_scale_next<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, h->n3, h->d_j, h->w, h->inv, h->n3);
   k_inc<<<1, 1, 0, s>>>(h->d_j);
   h->launches += 9;
@@ -744,22 +744,20 @@ void gcr_body(pyro_stokes_s* h, cudaStream_t s) {
   for (int pass = 0; pass < 2; ++pass) {
     double* hc = pass == 0 ? h->h1 : h->h2;
     const int nb = multidot<true>(h, s, h->V, h->d_j, h->w, -1);
-    k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, nb, h->d_j, 0, hc, nullptr, -1);
+    k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, nb, h->d_j, 0, hc, -1);
     k_multiaxpy<<<kReduceBlocks, kThreads, 0, s>>>(h->w, h->V, h->n3, h->d_j, hc, h->n3, pass ? h->W : nullptr,
-                                                   pass ? h->part2 : nullptr, nullptr, -1);
-    k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->zc, Zb, h->n3, h->d_j, hc, h->n3, nullptr, nullptr, nullptr,
-                                                       -1);
+                                                   pass ? h->part2 : nullptr, -1);
+    k_multiaxpy<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->zc, Zb, h->n3, h->d_j, hc, h->n3, nullptr, nullptr, -1);
   }
   // ||w||_W: the second pass left its per-block partials in part2 (also when j = 0 and no vector is
   // subtracted); the Hessenberg column it also writes is not used by GCR
-  k_arnoldi_finish<<<1, kThreads, 0, s>>>(h->d_j, h->h1, h->h2, h->part2, kReduceBlocks, h->hcol, h->inv, h->flag,
-                                          nullptr, nullptr);
+  k_arnoldi_finish<<<1, kThreads, 0, s>>>(h->d_j, h->h1, h->h2, h->part2, kReduceBlocks, h->hcol, h->inv, h->flag);
   k_gcr_scale<<<kReduceBlocks, kThreads, 0, s>>>(h->V, Zb, h->n3, h->d_j, h->w, h->zc, h->inv, h->r, h->W, h->n3,
                                                  h->partial);
-  k_reduce<<<1, kThreads, 0, s>>>(h->partial, kReduceBlocks, nullptr, 1, h->ydev, nullptr);
+  k_reduce<<<1, kThreads, 0, s>>>(h->partial, kReduceBlocks, nullptr, 1, h->ydev);
   k_gcr_update<<<kReduceBlocks, kThreads, 0, s>>>(h->x, h->r, h->V, Zb, h->n3, h->d_j, h->ydev, h->W, h->n3,
                                                   h->part2);
-  k_reduce<<<1, kThreads, 0, s>>>(h->part2, kReduceBlocks, nullptr, 1, h->ydev + 1, nullptr);
+  k_reduce<<<1, kThreads, 0, s>>>(h->part2, kReduceBlocks, nullptr, 1, h->ydev + 1);
   k_inc<<<1, 1, 0, s>>>(h->d_j);
   h->launches += 15;
   mark(h, 6, s);
@@ -775,7 +773,7 @@ void aa_body(pyro_stokes_s* h, cudaStream_t s) {
   precond_any(h, s, h->r, 0, h->zc, 0, h->d_j, false);
   k_aa_store<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, (double*)h->Z, h->n3, h->d_slot, h->x, h->zc, h->n3);
   const int nb = multidot<false>(h, s, (double*)h->Z, h->d_cnt, h->zc, -1);
-  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, nb, h->d_cnt, 0, h->h1, nullptr, -1);
+  k_reduce<<<h->m + 1, kThreads, 0, s>>>(h->partial, nb, h->d_cnt, 0, h->h1, -1);
   h->launches += 6;
   mark(h, 6, s);
 }
@@ -855,7 +853,7 @@ std::pair<double, double> residual_norms(pyro_stokes_s* h, const double* b, cons
 }
 
 double weighted_norm2(pyro_stokes_s* h, const double* v, cudaStream_t s) {
-  k_multidot<true><<<dim3(kReduceBlocks, 1), kThreads, 0, s>>>(v, 0, nullptr, 1, v, h->W, h->n3, h->partial, nullptr, nullptr);
+  k_multidot<true><<<dim3(kReduceBlocks, 1), kThreads, 0, s>>>(v, 0, nullptr, 1, v, h->W, h->n3, h->partial);
   h->launches += 1;
   CK(cudaMemcpyAsync(h->hbuf, h->partial, kReduceBlocks * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
