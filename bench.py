@@ -518,7 +518,6 @@ def main():
 
     for _ in range(args.warmup):
         one_solve(h)
-    h.set_timing(True)
     clocks = ClockSampler(local)
     clocks.start()
     if world > 1:
@@ -537,15 +536,23 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
+    value, total_ms = job_throughput(float(np.sum(step_ms)), args.steps, world, "cuda")
+    # phase breakdown (CUDA events at the phase boundaries inside the captured iteration) from one
+    # more solve outside the timed region, so the timed solves carry no timing events
+    h.set_timing(True)
+    one_solve(h)     # captures the iteration graph with the timing events
+    h.set_timing(True)
+    one_solve(h)
+    torch.cuda.synchronize()
     phases, counts = h.get_timing()
     h.set_timing(False)
-    value, total_ms = job_throughput(float(np.sum(step_ms)), args.steps, world, "cuda")
 
     # end to end through the public API with host (pinned) buffers: H2D of the inputs and D2H of
     # the solution happen inside the C-ABI call
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_en, h_ec, h_rho = pin(f.eta_n), pin(f.eta_c), pin(f.rho)
     h_out = [torch.zeros((n + 2, n + 2), dtype=torch.float64).pin_memory() for _ in range(3)]
+    h.solve(h_en, h_ec, h_rho, g_vec, tol, *h_out)     # warm-up (re-captures the graph without timing)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_steps = max(2, args.steps // 2)
