@@ -285,7 +285,9 @@ def marker_sample(n=1024, per_cell=16, reps=5):
 def sinker_e1_sample():
     """The robustness sinker at the paper's grid (501 x 601 nodes = 500 x 600 cells, box 1 x 1.2,
     contrast 1e8, density contrast 1.03125), mixed precision, lithostatic start, tol 1e-8: the
-    default hierarchy (halving, then ratio-2 general coarsening) and the paper's ratio 2.5."""
+    default hierarchy (halving, then ratio-2 general coarsening) and the paper's ratio 2.5; then the
+    paper's four smoother configurations (RBGS, damped Jacobi, RAS-type with T_inner 4, and "Mixed")
+    at its relaxation factors omega_v = 0.3, omega_p (alpha_p) = 0.6, inside FGMRES(30)."""
     import torch
     import paper_2603_14040_b300 as P
     from synth import sinker
@@ -295,8 +297,13 @@ def sinker_e1_sample():
     en, ec, rho = dev(f.eta_n), dev(f.eta_c), dev(f.rho)
     outs = [torch.zeros((ny + 2, nx + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
     res = {}
+    relax = {"omega_v": 0.3, "alpha_p": 0.6, "ras_inner": 4}
     for name, kw in (("ratio2_default", {}), ("ratio2.5", {"coarsen_ratio": 2.5}),
-                     ("ratio2.5_restart100", {"coarsen_ratio": 2.5, "restart_m": 100})):
+                     ("ratio2.5_restart100", {"coarsen_ratio": 2.5, "restart_m": 100}),
+                     ("paper_relaxation_rbgs", dict(relax, smoother=P.SMOOTH_RBGS)),
+                     ("paper_relaxation_jacobi", dict(relax, smoother=P.SMOOTH_JACOBI)),
+                     ("paper_relaxation_ras4", dict(relax, smoother=P.SMOOTH_RAS)),
+                     ("paper_relaxation_mixed", dict(relax, smoother=P.SMOOTH_MIXED))):
         h = P.Stokes(nx, ny, 1.0, 1.2, prec=P.PREC_MIXED, max_iter=3000, litho_guess=1, **kw)
         h.solve(en, ec, rho, (0.0, 1.0), 1e-8, *outs)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
