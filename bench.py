@@ -162,7 +162,7 @@ def vcycle_rooflines(peaks):
     sweep) heads the object; the default RBGS tile kernels and the RAS-type pass are variants."""
     main = vcycle_roofline_4096(peaks, label="k_jacobi<float> (damped Jacobi sweep, smoother=JACOBI, omega 0.6)",
                                 launches=2, smoother=1, omega_v=0.6)
-    main["traffic"] = 525.78e6
+    main["traffic"] = 518.10e6
     main["traffic_source"] = "ncu dram__bytes_read+write of one launch (profiles/k_jacobi_fp32_4096_level0.md)"
     main["sweeps_per_launch"] = 1
     main["variants"] = {}
