@@ -150,12 +150,26 @@ __global__ void __launch_bounds__(256)
     EC[t] = in ? ec[o] : T(0);
   }
   __syncthreads();
+  // every owned cell interior (2 <= i <= ny-2, 2 <= j <= nx-2): no masks needed (block-uniform)
+  const bool interior = i0 >= 2 && i0 + TI - 1 <= g.ny - 2 && j0 >= 2 && j0 + TJ - 1 <= g.nx - 2;
   int cur = 0;
   for (int it = 0; it < inner; ++it) {
     const T* xs = sm + cur * N;
     const T* ys = sm + (2 + cur) * N;
     T* xd = sm + (cur ^ 1) * N;
     T* yd = sm + (2 + (cur ^ 1)) * N;
+    if (interior) {
+      for (int t = threadIdx.x; t < TI * TJ; t += blockDim.x) {
+        const size_t c = (size_t)(1 + t / TJ) * RW + 1 + t % TJ;
+        T a, b;
+        jacobi_interior<T>(g, c, RW, xs, ys, FX, FY, EN, EC, omega, a, b);
+        xd[c] = a;
+        yd[c] = b;
+      }
+      __syncthreads();
+      cur ^= 1;
+      continue;
+    }
     for (int t = threadIdx.x; t < TI * TJ; t += blockDim.x) {
       const int a = 1 + t / TJ, b = 1 + t % TJ;
       const int gi = i0 - 1 + a, gj = j0 - 1 + b;
