@@ -46,6 +46,31 @@ __device__ inline void stokes_point(const GeomT<double>& g, int i, int j, const 
          (ldvy<double>(yv, g.ld, g.ny, i, j) - ldvy<double>(yv, g.ld, g.ny, i - 1, j)) * g.idy;
 }
 
+// The three Stokes rows at an interior point (2 <= i <= ny-2, 2 <= j <= nx-2) with precomputed
+// coefficients: every neighbour is an unknown, so the masks of lx_coef / ly_coef / the
+// divergence drop out (same arithmetic as stokes_point).
+template <typename TV>
+__device__ inline void stokes_point_interior(const GeomT<double>& g, size_t c, const TV* xv, const TV* yv,
+                                             const TV* pv, const Coef<double>& k, double& ox, double& oy,
+                                             double& op) {
+  const int ld = g.ld;
+  {
+    const double vc = xv[c], vw = xv[c - 1], ve = xv[c + 1], vn = xv[c - ld], vs = xv[c + ld];
+    const double yA = yv[c - ld], yB = yv[c - ld + 1], yC = yv[c], yD = yv[c + 1];
+    ox = (k.cxx[c + 1] * (ve - vc) - k.cxx[c] * (vc - vw) + k.nyy[c] * (vs - vc) + k.nxy[c] * (yD - yC) -
+          k.nyy[c - ld] * (vc - vn) - k.nxy[c - ld] * (yB - yA)) -
+         ((double)pv[c + 1] - (double)pv[c]) * g.idx;
+  }
+  {
+    const double vc = yv[c], vn = yv[c - ld], vs = yv[c + ld], vw = yv[c - 1], ve = yv[c + 1];
+    const double xA = xv[c - 1], xB = xv[c + ld - 1], xC = xv[c], xD = xv[c + ld];
+    oy = (k.cyy[c + ld] * (vs - vc) - k.cyy[c] * (vc - vn) + k.nxx[c] * (ve - vc) + k.nxy[c] * (xD - xC) -
+          k.nxx[c - 1] * (vc - vw) - k.nxy[c - 1] * (xB - xA)) -
+         ((double)pv[c + ld] - (double)pv[c]) * g.idy;
+  }
+  op = ((double)xv[c] - (double)xv[c - 1]) * g.idx + ((double)yv[c] - (double)yv[c - ld]) * g.idy;
+}
+
 // y = A x_k, x_k = X + (*d_k) * stride (d_k may be null: k = 0)
 template <typename TV>
 __global__ void k_apply(GeomT<double> g, const double* __restrict__ en, const double* __restrict__ ec,
@@ -57,8 +82,11 @@ __global__ void k_apply(GeomT<double> g, const double* __restrict__ en, const do
   const size_t P = (size_t)(g.ny + 2) * g.ld;
   const TV* x = X + (d_k ? (size_t)(*d_k) * stride : 0);
   double ox, oy, op;
-  stokes_point<TV>(g, i, j, en, ec, x, x + P, x + 2 * P, ox, oy, op, kc);
   const size_t c = (size_t)i * g.ld + j;
+  if (kc.cxx && i >= 2 && i <= g.ny - 2 && j >= 2 && j <= g.nx - 2)
+    stokes_point_interior<TV>(g, c, x, x + P, x + 2 * P, kc, ox, oy, op);
+  else
+    stokes_point<TV>(g, i, j, en, ec, x, x + P, x + 2 * P, ox, oy, op, kc);
   y[c] = ox;
   y[P + c] = oy;
   y[2 * P + c] = op;
