@@ -624,14 +624,16 @@ def main():
                                    "rel_energy_res": sm.rel_energy_res, "rel_diff_vs_fp64_v": errv,
                                    "rel_diff_vs_fp64_p": errp, "p50_ms": float(np.percentile(ms, 50)),
                                    "p99_ms": float(np.percentile(ms, 99))}
-    if rank == 0 and not args.no_extras:
+    # single-GPU samples and the CPU baseline: at N = 1 only (at N > 1 they would hold every GPU of
+    # the job while rank 0 alone works)
+    if rank == 0 and world == 1 and not args.no_extras:
         line["vcycle_roofline"] = vcycle_rooflines(peaks)
         line["accelerators"] = accelerator_sample(f, n)
         line["markers"] = marker_sample()
         line["sinker_1e8_500x600"] = sinker_e1_sample()
         line["serving"] = serving_sample()
         line["adjoint"] = adjoint_sample()
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
