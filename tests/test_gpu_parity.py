@@ -283,6 +283,23 @@ def test_nonfinite_input_is_rejected():
     assert e.value.status == -4
 
 
+@pytest.mark.parametrize("accel", [P.ACCEL_FGMRES, P.ACCEL_GCR, P.ACCEL_ANDERSON])
+def test_wall_clock_limit_ends_the_solve_with_timeout(accel):
+    """timeout_s: a solve that cannot finish within the limit returns PYRO_E_TIMEOUT (-5); the
+    handle stays usable and the same solve without the limit converges."""
+    f = sinker(64, 64, eta_inc=1e6)
+    args = (dev(f.eta_n), dev(f.eta_c), dev(f.rho), (0.0, 1.0), 1e-12)
+    h = P.Stokes(64, 64, accel=accel, max_iter=3000, timeout_s=1e-9)
+    with pytest.raises(P.PyroError) as e:
+        h.solve(*args, zeros(64, 64), zeros(64, 64), zeros(64, 64))
+    assert e.value.status == -5
+    h.close()
+    h = P.Stokes(64, 64, accel=accel, max_iter=3000)
+    st = h.solve(*args, zeros(64, 64), zeros(64, 64), zeros(64, 64))
+    assert st.status == 0
+    h.close()
+
+
 def test_not_converged_warning_returns_best_iterate():
     f = sinker(32, 32, eta_inc=1e4)
     out, st = _solve_gpu(f, (0.0, 1.0), 1e-12, P.PREC_MIXED, max_iter=3)
