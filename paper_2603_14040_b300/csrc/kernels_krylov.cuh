@@ -355,6 +355,89 @@ __global__ void k_scale_next(double* __restrict__ V, size_t stride, const int* _
 }
 __global__ void k_inc(int* d_j) { *d_j += 1; }
 
+// ---- modified Gram-Schmidt in the W inner product, one fused step per basis vector ----------
+// The basis is stored scaled by W^(1/2) (sw), so <u, v>_W is the plain dot product of the scaled
+// vectors and each step costs two FP64 operations per element. Step k of column j (nvec = *d_j + 1
+// basis vectors): step 0 scales w by sw; with k >= 1, h_{k-1} = sum of the previous step's
+// per-block partials (fixed order, every block forms the same value; block 0 stores it in
+// h[k-1]) and w -= h_{k-1} v_{k-1}; then the per-block partial of v_k . w (k < nvec) or of w . w
+// (k == nvec) goes to part_out. Steps k > nvec return at once, so one captured chain of m + 1
+// steps serves every j. part_in / part_out alternate between two buffers from step to step.
+__global__ void k_mgs_step(const double* __restrict__ V, size_t stride, const int* __restrict__ d_j, int k,
+                           double* __restrict__ w, const double* __restrict__ sw, size_t n,
+                           const double* __restrict__ part_in, double* __restrict__ part_out,
+                           double* __restrict__ h) {
+  __shared__ double sh[32];
+  __shared__ double hprev_s;
+  const int nvec = *d_j + 1;
+  if (k > nvec) return;
+  double hp = 0.0;
+  if (k >= 1) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += part_in[b];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+      hprev_s = s;
+      if (blockIdx.x == 0) h[k - 1] = s;
+    }
+    __syncthreads();
+    hp = hprev_s;
+  }
+  const double* vp = V + (size_t)(k >= 1 ? k - 1 : 0) * stride;
+  const double* vk = V + (size_t)(k < nvec ? k : 0) * stride;
+  double acc = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double x;
+    if (k == 0) {
+      x = w[e] * sw[e];
+      w[e] = x;
+    } else {
+      x = w[e] - hp * vp[e];
+      w[e] = x;
+    }
+    acc += x * (k < nvec ? vk[e] : x);
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) part_out[blockIdx.x] = s;
+}
+
+// sw = W^(1/2), isw = W^(-1/2) (0 where W = 0: entries that are not unknowns)
+__global__ void k_sqrt_weights(const double* __restrict__ W, double* __restrict__ sw, double* __restrict__ isw,
+                               size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const double r = sqrt(W[e]);
+    sw[e] = r;
+    isw[e] = r > 0.0 ? 1.0 / r : 0.0;
+  }
+}
+
+// dst = src * sw * a (the first basis vector in the scaled space)
+__global__ void k_scale_sw(double* __restrict__ dst, const double* __restrict__ src, const double* __restrict__ sw,
+                           double a, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = src[e] * sw[e] * a;
+}
+
+// end of a modified Gram-Schmidt column j: ||w||_W from the last step's partials (buffer
+// (nvec % 2)), Hessenberg column j = h[0..j] with ||w||_W below the diagonal, inv = 1/||w||_W
+__global__ void k_mgs_finish(const int* __restrict__ d_j, const double* __restrict__ h,
+                             const double* __restrict__ part2buf, int nblk, double* __restrict__ hcol,
+                             double* __restrict__ inv, int* __restrict__ flag) {
+  __shared__ double sh[32];
+  const int j = *d_j, nvec = j + 1;
+  const double* part = part2buf + (size_t)(nvec & 1) * nblk;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[b];
+  s = block_sum(s, sh);
+  if (threadIdx.x != 0) return;
+  double* col = hcol + (size_t)j * kHcolStride;
+  for (int q = 0; q <= j; ++q) col[q] = h[q];
+  const double nrm = sqrt(s);
+  col[j + 1] = nrm;
+  if (!isfinite(nrm)) atomicOr(flag, FLAG_NONFINITE);
+  *inv = (nrm > 0.0 && isfinite(nrm)) ? 1.0 / nrm : 0.0;
+}
+
 // dst = src * a (host scalar)
 __global__ void k_scale(double* __restrict__ dst, const double* __restrict__ src, double a, size_t n) {
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
@@ -376,14 +459,16 @@ __global__ void k_update_x(double* __restrict__ x, const TZ* __restrict__ Z, siz
 }
 
 // ---- preconditioner input / output ---------------------------------------------------------
-// fx, fy (level 0, type T) <- velocity planes of V_j; level-0 iterate zeroed.
+// fx, fy (level 0, type T) <- velocity planes of V_j (times isw, when given: the basis is stored
+// scaled by W^(1/2)); level-0 iterate zeroed.
 template <typename T>
 __global__ void k_precond_in(size_t P, const double* __restrict__ V, size_t stride, const int* __restrict__ d_j,
-                             T* __restrict__ fx, T* __restrict__ fy, T* __restrict__ vx, T* __restrict__ vy) {
+                             T* __restrict__ fx, T* __restrict__ fy, T* __restrict__ vx, T* __restrict__ vy,
+                             const double* __restrict__ isw) {
   const double* v = V + (size_t)(*d_j) * stride;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    fx[e] = (T)v[e];
-    fy[e] = (T)v[P + e];
+    fx[e] = (T)(isw ? v[e] * isw[e] : v[e]);
+    fy[e] = (T)(isw ? v[P + e] * isw[P + e] : v[P + e]);
     vx[e] = T(0);
     vy[e] = T(0);
   }
@@ -395,7 +480,7 @@ template <typename T, typename TZ>
 __global__ void k_precond_out(GeomT<double> g, const T* __restrict__ vx, const T* __restrict__ vy,
                               const double* __restrict__ V, size_t vstride, TZ* __restrict__ Z, size_t stride,
                               const int* __restrict__ d_j, const double* __restrict__ ec, double alpha,
-                              double* __restrict__ part) {
+                              double* __restrict__ part, const double* __restrict__ isw) {
   __shared__ double sh[32];
   const size_t P = (size_t)(g.ny + 2) * g.ld;
   const double* v = V + (size_t)(*d_j) * vstride;
@@ -416,7 +501,8 @@ __global__ void k_precond_out(GeomT<double> g, const T* __restrict__ vx, const T
       const double uy = (i <= g.ny - 1) ? (double)(TZ)vy[e] : 0.0;
       const double uyn = (i - 1 >= 1) ? (double)(TZ)vy[e - g.ld] : 0.0;
       const double div = (ux - uxw) * g.idx + (uy - uyn) * g.idy;
-      zp = (double)(TZ)(alpha * ec[e] * (v[2 * P + e] - div));
+      const double rp = isw ? v[2 * P + e] * isw[2 * P + e] : v[2 * P + e];
+      zp = (double)(TZ)(alpha * ec[e] * (rp - div));
       acc += zp;
     }
     z[2 * P + e] = (TZ)zp;
@@ -680,15 +766,16 @@ template __global__ void k_apply<double>(GeomT<double>, const double*, const dou
                                          const int*, double*, Coef<double>);
 template __global__ void k_update_x<double>(double*, const double*, size_t, int, const double*, size_t);
 template __global__ void k_update_x<float>(double*, const float*, size_t, int, const double*, size_t);
-template __global__ void k_precond_in<float>(size_t, const double*, size_t, const int*, float*, float*, float*, float*);
+template __global__ void k_precond_in<float>(size_t, const double*, size_t, const int*, float*, float*, float*, float*,
+                                             const double*);
 template __global__ void k_precond_in<double>(size_t, const double*, size_t, const int*, double*, double*, double*,
-                                              double*);
+                                              double*, const double*);
 template __global__ void k_precond_out<float, double>(GeomT<double>, const float*, const float*, const double*,
                                                       size_t, double*, size_t, const int*, const double*, double,
-                                                      double*);
+                                                      double*, const double*);
 template __global__ void k_precond_out<double, double>(GeomT<double>, const double*, const double*, const double*,
                                                        size_t, double*, size_t, const int*, const double*, double,
-                                                       double*);
+                                                       double*, const double*);
 template __global__ void k_sub_mean<float>(GeomT<double>, float*, size_t, const int*, const double*, int);
 template __global__ void k_sub_mean<double>(GeomT<double>, double*, size_t, const int*, const double*, int);
 

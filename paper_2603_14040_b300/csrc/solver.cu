@@ -641,6 +641,7 @@ struct pyro_stokes_s {
   double *h1 = nullptr, *h2 = nullptr, *partial = nullptr, *part2 = nullptr, *hcol = nullptr, *inv = nullptr,
          *ydev = nullptr;
   int *d_j = nullptr, *flag = nullptr;
+  double *sw = nullptr, *isw = nullptr;    // W^(1/2), W^(-1/2) (modified Gram-Schmidt basis scaling)
   double* zc = nullptr;                    // GCR / Anderson: the current preconditioned residual
   double *en_full = nullptr, *ec_full = nullptr;  // continuation: the full-contrast viscosity
   int *d_slot = nullptr, *d_cnt = nullptr;  // Anderson: history slot of this step, pairs stored
@@ -688,10 +689,10 @@ int multidot(pyro_stokes_s* h, cudaStream_t s, const double* V, const int* d_cnt
 // optionally w = A z.
 template <typename T, typename TZ>
 void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s, const double* in, size_t in_stride, TZ* out,
-                  size_t out_stride, const int* d_idx, bool with_apply) {
+                  size_t out_stride, const int* d_idx, bool with_apply, const double* isw) {
   Level<T>& L0 = mg.lv[0];
   mark(h, 0, s);
-  k_precond_in<T><<<kReduceBlocks, kThreads, 0, s>>>(h->P, in, in_stride, d_idx, L0.fx, L0.fy, L0.vx, L0.vy);
+  k_precond_in<T><<<kReduceBlocks, kThreads, 0, s>>>(h->P, in, in_stride, d_idx, L0.fx, L0.fy, L0.vx, L0.vy, isw);
   mark(h, 1, s);
   mg.hooks = h->timing ? h->tev : nullptr;
   mg.nlaunch = &h->launches;
@@ -699,7 +700,7 @@ void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s, const double* in,
   mg.hooks = nullptr;
   h->launches += 3;
   k_precond_out<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), in, in_stride, out, out_stride, d_idx,
-                                                           h->ec, h->o.alpha_p, h->part2);
+                                                           h->ec, h->o.alpha_p, h->part2, isw);
   k_sub_mean<TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, out + 2 * h->P, out_stride, d_idx, h->part2, kReduceBlocks);
   if (with_apply) {
     k_apply<TZ><<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->ec, (const TZ*)out, out_stride, d_idx,
@@ -709,10 +710,11 @@ void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s, const double* in,
   mark(h, 5, s);
 }
 
+// isw (optional): the input is stored scaled by W^(1/2) and is unscaled on the way in
 void precond_any(pyro_stokes_s* h, cudaStream_t s, const double* in, size_t in_stride, double* out,
-                 size_t out_stride, const int* d_idx, bool with_apply) {
-  if (h->mixed) precond_body<float, double>(h, h->mgf, s, in, in_stride, out, out_stride, d_idx, with_apply);
-  else precond_body<double, double>(h, h->mgd, s, in, in_stride, out, out_stride, d_idx, with_apply);
+                 size_t out_stride, const int* d_idx, bool with_apply, const double* isw = nullptr) {
+  if (h->mixed) precond_body<float, double>(h, h->mgf, s, in, in_stride, out, out_stride, d_idx, with_apply, isw);
+  else precond_body<double, double>(h, h->mgd, s, in, in_stride, out, out_stride, d_idx, with_apply, isw);
 }
 
 // one Arnoldi step j (j read on the device): z_j = M^-1 v_j, w = A z_j, CGS2 against v_0..v_j,
@@ -731,6 +733,27 @@ void fgmres_body(pyro_stokes_s* h, cudaStream_t s) {
   k_scale_next<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, h->n3, h->d_j, h->w, h->inv, h->n3);
   k_inc<<<1, 1, 0, s>>>(h->d_j);
   h->launches += 9;
+  mark(h, 6, s);
+}
+
+constexpr int kMgsBlocks = 592;   // blocks of one modified Gram-Schmidt step (4 per SM)
+
+// One Arnoldi step j with modified Gram-Schmidt (option gram_schmidt = 1), the basis stored scaled
+// by W^(1/2) so that the W inner product is a plain dot product: z_j = M^-1 (W^(-1/2) v_j),
+// w = A z_j, then the m + 1 fused steps of k_mgs_step (those beyond column j's j + 2 return at
+// once), each subtracting the previous basis vector's component and forming the next inner
+// product, then the column's norm.
+void fgmres_body_mgs(pyro_stokes_s* h, cudaStream_t s) {
+  precond_any(h, s, h->V, h->n3, (double*)h->Z, h->n3, h->d_j, true, h->isw);
+  double* pb = h->partial;   // two alternating partial buffers of kReduceBlocks
+  for (int k = 0; k <= h->m; ++k)
+    k_mgs_step<<<kMgsBlocks, kThreads, 0, s>>>(h->V, h->n3, h->d_j, k, h->w, h->sw, h->n3,
+                                               pb + (size_t)((k + 1) & 1) * kMgsBlocks,
+                                               pb + (size_t)(k & 1) * kMgsBlocks, h->h1);
+  k_mgs_finish<<<1, kThreads, 0, s>>>(h->d_j, h->h1, pb, kMgsBlocks, h->hcol, h->inv, h->flag);
+  k_scale_next<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, h->n3, h->d_j, h->w, h->inv, h->n3);
+  k_inc<<<1, 1, 0, s>>>(h->d_j);
+  h->launches += h->m + 4;
   mark(h, 6, s);
 }
 
@@ -781,6 +804,7 @@ void aa_body(pyro_stokes_s* h, cudaStream_t s) {
 void iteration_body(pyro_stokes_s* h, cudaStream_t s) {
   if (h->o.accel == PYRO_ACCEL_GCR) gcr_body(h, s);
   else if (h->o.accel == PYRO_ACCEL_ANDERSON) aa_body(h, s);
+  else if (h->sw) fgmres_body_mgs(h, s);
   else fgmres_body(h, s);
 }
 
@@ -921,6 +945,10 @@ void setup_eta(pyro_stokes_s* h, cudaStream_t s) {
     h->mgd.setup(s, h->flag);
   }
   k_weights<<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->ec, h->W);
+  if (h->sw) {
+    k_sqrt_weights<<<kReduceBlocks, kThreads, 0, s>>>(h->W, h->sw, h->isw, h->n3);
+    h->launches += 1;
+  }
   h->launches += 1;
 }
 
@@ -984,7 +1012,10 @@ int fgmres(pyro_stokes_s* h, double tol, pyro_stats* st, cudaStream_t s) {
       const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       if (el > h->o.timeout_s) { status = PYRO_E_TIMEOUT; break; }
     }
-    k_scale<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, h->r, 1.0 / beta, h->n3);
+    if (h->sw)
+      k_scale_sw<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, h->r, h->sw, 1.0 / beta, h->n3);
+    else
+      k_scale<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, h->r, 1.0 / beta, h->n3);
     h->launches += 1;
     CK(cudaMemsetAsync(h->d_j, 0, sizeof(int), s));
     gv.start(beta);
@@ -1237,6 +1268,17 @@ int continuation_solve(pyro_stokes_s* h, double tol, pyro_stats* st, cudaStream_
   return outer_solve(h, tol, st, s);
 }
 
+// FGMRES orthogonalisation: modified Gram-Schmidt when asked, or (gram_schmidt 2) when the basis
+// is short enough for the register multi-dot and the grid large enough that each step's FP64
+// arithmetic outweighs its launch (measured crossover between 512^2, where CGS2 is 6% faster, and
+// 1024^2, where MGS is 9-15% faster)
+constexpr long long kMgsMinCells = 1LL << 19;
+bool use_mgs(const pyro_opts& o, int nx, int ny) {
+  if (o.accel != PYRO_ACCEL_FGMRES) return false;
+  if (o.gram_schmidt == 1) return true;
+  return o.gram_schmidt == 2 && o.restart_m + 1 <= kDotRegs && (long long)nx * ny >= kMgsMinCells;
+}
+
 // true when every option lies in the range pyro.h documents (nothing is clamped or replaced)
 bool opts_valid(const pyro_opts& o) {
   return o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 >= 1 && o.omega_v > 0.0 && o.omega_v < 2.0 &&
@@ -1247,7 +1289,8 @@ bool opts_valid(const pyro_opts& o) {
          (o.tile_fusion64 == 0 || o.tile_fusion64 == 1) && o.accel >= PYRO_ACCEL_FGMRES &&
          o.accel <= PYRO_ACCEL_ANDERSON && o.aa_beta > 0.0 && o.aa_beta <= 1.0 && o.smoother >= PYRO_SMOOTH_RBGS &&
          o.smoother <= PYRO_SMOOTH_MIXED && o.ras_inner >= 1 && o.cont_stages >= 0 && o.cont_iters >= 1 &&
-         o.coarse_sweeps >= 1 && o.coarsen_ratio >= 1.5 && o.coarsen_ratio <= 8.0;
+         o.coarse_sweeps >= 1 && o.coarsen_ratio >= 1.5 && o.coarsen_ratio <= 8.0 &&
+         o.gram_schmidt >= 0 && o.gram_schmidt <= 2;
 }
 
 std::vector<std::pair<int, int>> sizes_of(int nx, int ny, const pyro_opts& o) {
@@ -1273,6 +1316,7 @@ size_t footprint_bytes(int nx, int ny, const pyro_opts& o, int L) {
   b += (m + 1) * n3 * 8;           // V
   b += (m + 1) * n3 * 8;           // Z (preconditioned vectors; FP32-valued velocities in mixed mode)
   b += n3 * 8 + 16;                // GCR / Anderson current direction, Anderson slot indices
+  if (use_mgs(o, nx, ny)) b += 2 * n3 * 8;   // W^(1/2), W^(-1/2)
   if (o.cont_stages > 0) b += 2 * P * 8;   // full-contrast viscosity kept during continuation
   (void)L;
   const auto sz = sizes_of(nx, ny, o);
@@ -1316,6 +1360,7 @@ void pyro_default_opts(pyro_opts* o) {
   o->coarse_sweeps = 40;
   o->coarsen_ratio = 2.0;
   o->coarsen_general = 1;
+  o->gram_schmidt = 2;
 }
 
 const char* pyro_version(void) { return "pyro-b300 0.1 (sm_103a)"; }
@@ -1400,6 +1445,10 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
     h->ydev = A.get<double>(kMaxRestart + 2);
     h->d_j = A.get<int>(1);
     h->flag = A.get<int>(1);
+    if (use_mgs(o, nx, ny)) {
+      h->sw = A.get<double>(h->n3);
+      h->isw = A.get<double>(h->n3);
+    }
     if (h->mixed) {
       h->mgf.nu1 = o.nu1; h->mgf.nu2 = o.nu2; h->mgf.omega = (float)o.omega_v; h->mgf.eta_mode = o.eta_coarsen;
       h->mgf.coarse_sweeps = o.coarse_sweeps;
@@ -1467,21 +1516,23 @@ int pyro_stokes_precond(pyro_stokes h, const double* eta_n, const double* eta_c,
     CK(cudaMemsetAsync(h->d_j, 0, sizeof(int), s));
     if (h->mixed) {
       Level<float>& L0 = h->mgf.lv[0];
-      k_precond_in<float><<<kReduceBlocks, kThreads, 0, s>>>(h->P, h->V, h->n3, h->d_j, L0.fx, L0.fy, L0.vx, L0.vy);
+      k_precond_in<float><<<kReduceBlocks, kThreads, 0, s>>>(h->P, h->V, h->n3, h->d_j, L0.fx, L0.fy, L0.vx, L0.vy,
+                                                             nullptr);
       h->mgf.cycle(0, s);
       k_precond_out<float, double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->V, h->n3,
                                                                        (double*)h->Z, h->n3, h->d_j, h->ec,
-                                                                       h->o.alpha_p, h->part2);
+                                                                       h->o.alpha_p, h->part2, nullptr);
       k_sub_mean<double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, (double*)h->Z + 2 * h->P, h->n3, h->d_j, h->part2,
                                                            kReduceBlocks);
       CK(cudaMemcpyAsync(h->w, h->Z, h->n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     } else {
       Level<double>& L0 = h->mgd.lv[0];
-      k_precond_in<double><<<kReduceBlocks, kThreads, 0, s>>>(h->P, h->V, h->n3, h->d_j, L0.fx, L0.fy, L0.vx, L0.vy);
+      k_precond_in<double><<<kReduceBlocks, kThreads, 0, s>>>(h->P, h->V, h->n3, h->d_j, L0.fx, L0.fy, L0.vx, L0.vy,
+                                                              nullptr);
       h->mgd.cycle(0, s);
       k_precond_out<double, double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->V, h->n3,
                                                                         (double*)h->Z, h->n3, h->d_j, h->ec,
-                                                                        h->o.alpha_p, h->part2);
+                                                                        h->o.alpha_p, h->part2, nullptr);
       k_sub_mean<double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, (double*)h->Z + 2 * h->P, h->n3, h->d_j, h->part2,
                                                            kReduceBlocks);
       CK(cudaMemcpyAsync(h->w, h->Z, h->n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));

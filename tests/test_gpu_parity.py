@@ -283,6 +283,29 @@ def test_nonfinite_input_is_rejected():
     assert e.value.status == -4
 
 
+@pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
+@pytest.mark.parametrize("case", ["sinker", "random", "odd"])
+def test_modified_gram_schmidt_matches_direct_oracle(prec, case):
+    """FGMRES with modified Gram-Schmidt on the W^(1/2)-scaled basis (gram_schmidt 1; the default
+    on large grids) against the direct oracle, and against the CGS2 run of the same problem: same
+    iteration count, same solution to the convergence tolerance."""
+    if case == "sinker":
+        f, Lx, Ly = sinker(64, 64, eta_inc=1e4), 1.0, 1.0
+    elif case == "random":
+        f, Lx, Ly = grf_config(96, 64, seed=5, Lx=1.5, Ly=1.0), 1.5, 1.0
+    else:
+        f, Lx, Ly = sinker(45, 33, 1.0, 33 / 45), 1.0, 33 / 45
+    # the random field's 4-decade contrast amplifies the residual into the velocity error by about
+    # 2e3 (1.8e-8 at 1e-11), so it is solved to 1e-12 like the other random-field parity cases
+    tol = 1e-12 if case == "random" else 1e-11
+    out, st = _solve_gpu(f, (0.0, 1.0), tol, prec, Lx=Lx, Ly=Ly, gram_schmidt=1, max_iter=3000)
+    _check_against_direct(f, out, st, Lx=Lx, Ly=Ly, tol=tol, tol_err=1e-8)
+    out2, st2 = _solve_gpu(f, (0.0, 1.0), tol, prec, Lx=Lx, Ly=Ly, gram_schmidt=0, max_iter=3000)
+    assert abs(st.iters - st2.iters) <= 2, (st.iters, st2.iters)
+    for a, b in zip(out, out2):
+        assert rel(a, b) <= 1e-8
+
+
 @pytest.mark.parametrize("accel", [P.ACCEL_FGMRES, P.ACCEL_GCR, P.ACCEL_ANDERSON])
 def test_wall_clock_limit_ends_the_solve_with_timeout(accel):
     """timeout_s: a solve that cannot finish within the limit returns PYRO_E_TIMEOUT (-5); the
