@@ -650,7 +650,9 @@ struct pyro_stokes_s {
   int* hflag = nullptr;
   MG<float> mgf;
   MG<double> mgd;
-  cudaGraphExec_t graph = nullptr;
+  std::vector<cudaGraphExec_t> graphs;       // captured iteration graphs (per Krylov column with MGS)
+  std::vector<long long> graph_kernel_counts;
+  int cur_j = 0;                              // Krylov column of the step being launched or captured
   cudaEvent_t ev[4]{};
   bool have_solution = false;
   double last_gx = 0, last_gy = 0;
@@ -746,14 +748,15 @@ constexpr int kMgsBlocks = 592;   // blocks of one modified Gram-Schmidt step (4
 void fgmres_body_mgs(pyro_stokes_s* h, cudaStream_t s) {
   precond_any(h, s, h->V, h->n3, (double*)h->Z, h->n3, h->d_j, true, h->isw);
   double* pb = h->partial;   // two alternating partial buffers of kReduceBlocks
-  for (int k = 0; k <= h->m; ++k)
+  const int nsteps = std::min(h->cur_j + 2, h->m + 1);   // steps 0 .. j + 1 of column j
+  for (int k = 0; k < nsteps; ++k)
     k_mgs_step<<<kMgsBlocks, kThreads, 0, s>>>(h->V, h->n3, h->d_j, k, h->w, h->sw, h->n3,
                                                pb + (size_t)((k + 1) & 1) * kMgsBlocks,
                                                pb + (size_t)(k & 1) * kMgsBlocks, h->h1);
   k_mgs_finish<<<1, kThreads, 0, s>>>(h->d_j, h->h1, pb, kMgsBlocks, h->hcol, h->inv, h->flag);
   k_scale_next<<<kReduceBlocks * 2, kThreads, 0, s>>>(h->V, h->n3, h->d_j, h->w, h->inv, h->n3);
   k_inc<<<1, 1, 0, s>>>(h->d_j);
-  h->launches += h->m + 4;
+  h->launches += nsteps + 3;
   mark(h, 6, s);
 }
 
@@ -825,13 +828,19 @@ void collect_timing(pyro_stokes_s* h) {
   h->tcount[1] += h->o.nu1 + h->o.nu2;
 }
 
-void launch_iteration(pyro_stokes_s* h, cudaStream_t s) {
+// j: the Krylov column of this step (host side); the modified Gram-Schmidt iteration captures one
+// graph per column (exactly j + 2 orthogonalisation steps), every other iteration one graph
+void launch_iteration(pyro_stokes_s* h, cudaStream_t s, int j = 0) {
   if (h->o.use_graphs) {
-    if (h->graph && h->graph_timing != h->timing) {
-      cudaGraphExecDestroy(h->graph);
-      h->graph = nullptr;
+    const size_t slot = h->sw ? (size_t)j : 0;
+    if (h->graphs.size() <= slot) h->graphs.resize(slot + 1, nullptr);
+    if (h->graph_timing != h->timing) {
+      for (auto& g : h->graphs)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     }
-    if (!h->graph) {
+    cudaGraphExec_t& graph = h->graphs[slot];
+    h->cur_j = j;
+    if (!graph) {
       std::lock_guard<std::recursive_mutex> lk(device_sync_lock());
       const long long saved = h->launches;  // capture records kernels, it does not launch them
       h->graph_timing = h->timing;
@@ -853,14 +862,17 @@ void launch_iteration(pyro_stokes_s* h, cudaStream_t s) {
           if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++h->graph_kernels;
         }
       }
-      e = cudaGraphInstantiate(&h->graph, gr, 0);
+      e = cudaGraphInstantiate(&graph, gr, 0);
       cudaGraphDestroy(gr);
       h->launches = saved;
       CK(e);
+      if (h->graph_kernel_counts.size() <= slot) h->graph_kernel_counts.resize(slot + 1, 0);
+      h->graph_kernel_counts[slot] = h->graph_kernels;
     }
-    CK(cudaGraphLaunch(h->graph, s));
-    h->launches += h->graph_kernels;
+    CK(cudaGraphLaunch(graph, s));
+    h->launches += h->graph_kernel_counts[slot];
   } else {
+    h->cur_j = j;
     iteration_body(h, s);
   }
 }
@@ -1022,7 +1034,7 @@ int fgmres(pyro_stokes_s* h, double tol, pyro_stats* st, cudaStream_t s) {
     int k = 0;
     bool stop_inner = false;
     for (int j = 0; j < h->m; ++j) {
-      launch_iteration(h, s);
+      launch_iteration(h, s, j);
       CK(cudaMemcpyAsync(h->hbuf, h->hcol + (size_t)j * kHcolStride, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(h->hflag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
@@ -1571,7 +1583,8 @@ void pyro_stokes_destroy(pyro_stokes h) {
   if (!h) return;
   std::lock_guard<std::recursive_mutex> lk(device_sync_lock());
   cudaSetDevice(h->dev);
-  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (auto g : h->graphs)
+    if (g) cudaGraphExecDestroy(g);
   for (int k = 0; k < 4; ++k)
     if (h->ev[k]) cudaEventDestroy(h->ev[k]);
   for (int k = 0; k < 7; ++k)
