@@ -1282,8 +1282,8 @@ int continuation_solve(pyro_stokes_s* h, double tol, pyro_stats* st, cudaStream_
 
 // FGMRES orthogonalisation: modified Gram-Schmidt when asked, or (gram_schmidt 2) when the basis
 // is short enough for the register multi-dot and the grid large enough that each step's FP64
-// arithmetic outweighs its launch (measured crossover between 512^2, where CGS2 is 6% faster, and
-// 1024^2, where MGS is 9-15% faster)
+// arithmetic outweighs its launch (measured crossover between 512^2, where CGS2 is 1-2% faster, and
+// 1024^2, where MGS is 10-17% faster)
 constexpr long long kMgsMinCells = 1LL << 19;
 bool use_mgs(const pyro_opts& o, int nx, int ny) {
   if (o.accel != PYRO_ACCEL_FGMRES) return false;
