@@ -588,9 +588,9 @@ def main():
     fp64_peak = 1.25  # TFLOP/s nominal B300 FP64 (about 2 FMA per clock per SM at 2.03 GHz); a probe measured 1.13
     roof = {"kernel": "k_rbgs<double> finest level (one sweep = 4 launches)", "bound": "alu",
             "achieved": achieved_flops, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved_flops / fp64_peak,
-            "traffic": 4 * 59.674e6, "traffic_unit": "B per sweep",
-            "traffic_source": "ncu dram__bytes_read+write of the level-0 vx-red launch (59.67 MB, profiles/k_rbgs_fp64_1024_level0.md) x 4 half-sweeps",
-            "fp64_pipe_active_pct_ncu": 77.6,
+            "traffic": 4 * 59.579e6, "traffic_unit": "B per sweep",
+            "traffic_source": "ncu dram__bytes_read+write of the level-0 vx-red launch (59.58 MB, profiles/k_rbgs_fp64_1024_level0.md) x 4 half-sweeps",
+            "fp64_pipe_active_pct_ncu": 78.1,
             "peak_source": "nominal B300 FP64 rate 1.25 TFLOP/s (148 SMs x ~2.08 FMA/clk x 2 flop x 2.03 GHz); not in MEASURED_PEAKS.json",
             "flop_per_cell_sweep": 30,
             "hbm_equiv_GBps": bytes_per_sweep / (sweep_ms / 1e3) / 1e9, "hbm_peak_measured": peaks.get("hbm_gbs"),

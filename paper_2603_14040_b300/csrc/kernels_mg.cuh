@@ -81,6 +81,23 @@ __global__ void k_invdiag(GeomT<T> g, const T* __restrict__ en, const T* __restr
   idgy[c] = oy;
 }
 
+// Coefficient-form update of rbgs_point with the undamped case (omega = 1) fixed at compile time,
+// so the damped form's extra multiplies and the read of the old value are not computed there.
+template <typename T, bool UNDAMPED>
+__device__ inline void rbgs_coef_point(const GeomT<T>& g, int i, int j, int field, T omega, T* vx, T* vy,
+                                       const T* fx, const T* fy, const T* idgx, const T* idgy, const Coef<T>& kc) {
+  const size_t c = (size_t)i * g.ld + j;
+  if (field == 0) {
+    if (!is_vx(g.nx, g.ny, i, j)) return;
+    const T t = idgx[c] * (fx[c] - lx_off<T>(g, i, j, vx, vy, kc));
+    vx[c] = UNDAMPED ? t : (T(1) - omega) * vx[c] + omega * t;
+  } else {
+    if (!is_vy(g.nx, g.ny, i, j)) return;
+    const T t = idgy[c] * (fy[c] - ly_off<T>(g, i, j, vx, vy, kc));
+    vy[c] = UNDAMPED ? t : (T(1) - omega) * vy[c] + omega * t;
+  }
+}
+
 template <typename T>
 __global__ void k_rbgs(GeomT<T> g, T* __restrict__ vx, T* __restrict__ vy, const T* __restrict__ fx,
                        const T* __restrict__ fy, const T* __restrict__ en, const T* __restrict__ ec,
@@ -90,6 +107,11 @@ __global__ void k_rbgs(GeomT<T> g, T* __restrict__ vx, T* __restrict__ vy, const
   const int jh = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = 2 * jh + ((i + colour) & 1);
   if (i > g.ny + 1 || j > g.nx + 1) return;
+  if (kc.cxx && idgx) {   // launch-uniform branches
+    if (omega == T(1)) rbgs_coef_point<T, true>(g, i, j, field, omega, vx, vy, fx, fy, idgx, idgy, kc);
+    else rbgs_coef_point<T, false>(g, i, j, field, omega, vx, vy, fx, fy, idgx, idgy, kc);
+    return;
+  }
   rbgs_point<T>(g, i, j, field, omega, vx, vy, fx, fy, en, ec, idgx, idgy, kc);
 }
 
