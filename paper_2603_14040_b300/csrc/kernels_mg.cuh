@@ -152,7 +152,8 @@ __global__ void k_vresidual(GeomT<T> g, const T* __restrict__ vx, const T* __res
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (i > g.ny + 1 || j > g.nx + 1) return;
-  vresid_point<T>(g, i, j, vx, vy, fx, fy, en, ec, rx, ry, kc);
+  if (kc.cxx) vresid_point<T>(g, i, j, vx, vy, fx, fy, en, ec, rx, ry, kc);   // launch-uniform
+  else vresid_point<T>(g, i, j, vx, vy, fx, fy, en, ec, rx, ry, Coef<T>{});
 }
 
 template <typename T>
@@ -162,34 +163,55 @@ __device__ inline void restrict_point(const GeomT<T>& gf, const GeomT<T>& gc, in
   const T w4[4] = {T(1), T(3), T(3), T(1)};
   const T w3[3] = {T(1), T(2), T(1)};
   T ox = T(0), oy = T(0);
+  // FP64 levels: away from the walls all twelve taps are present and the weights sum to 32, so
+  // the same sum in the same order is scaled by 1/32 (exact, equal to the division by the summed
+  // weights) without the weight sum and the FP64 division (B300's FP64 rate is low).
   if (is_vx(gc.nx, gc.ny, I, J)) {
     // rows 2I-2 .. 2I+1 (cell-centred direction), columns 2J-1 .. 2J+1 (node direction)
-    T s = T(0), ws = T(0);
-    for (int a = 0; a < 4; ++a) {
-      const int i = 2 * I - 2 + a;
-      if (i < 1 || i > gf.ny) continue;
-      for (int b = 0; b < 3; ++b) {
-        const int j = 2 * J - 1 + b;
-        const T w = w4[a] * w3[b];
-        s += w * rx[(size_t)i * gf.ld + j];
-        ws += w;
+    T s = T(0);
+    if (sizeof(T) == 8 && 2 * I - 2 >= 1 && 2 * I + 1 <= gf.ny) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) s += w4[a] * w3[b] * rx[(size_t)(2 * I - 2 + a) * gf.ld + 2 * J - 1 + b];
+      ox = s * T(0.03125);
+    } else {
+      T ws = T(0);
+      for (int a = 0; a < 4; ++a) {
+        const int i = 2 * I - 2 + a;
+        if (i < 1 || i > gf.ny) continue;
+        for (int b = 0; b < 3; ++b) {
+          const int j = 2 * J - 1 + b;
+          const T w = w4[a] * w3[b];
+          s += w * rx[(size_t)i * gf.ld + j];
+          ws += w;
+        }
       }
+      ox = s / ws;
     }
-    ox = s / ws;
   }
   if (is_vy(gc.nx, gc.ny, I, J)) {
-    T s = T(0), ws = T(0);
-    for (int a = 0; a < 3; ++a) {
-      const int i = 2 * I - 1 + a;
-      for (int b = 0; b < 4; ++b) {
-        const int j = 2 * J - 2 + b;
-        if (j < 1 || j > gf.nx) continue;
-        const T w = w3[a] * w4[b];
-        s += w * ry[(size_t)i * gf.ld + j];
-        ws += w;
+    T s = T(0);
+    if (sizeof(T) == 8 && 2 * J - 2 >= 1 && 2 * J + 1 <= gf.nx) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) s += w3[a] * w4[b] * ry[(size_t)(2 * I - 1 + a) * gf.ld + 2 * J - 2 + b];
+      oy = s * T(0.03125);
+    } else {
+      T ws = T(0);
+      for (int a = 0; a < 3; ++a) {
+        const int i = 2 * I - 1 + a;
+        for (int b = 0; b < 4; ++b) {
+          const int j = 2 * J - 2 + b;
+          if (j < 1 || j > gf.nx) continue;
+          const T w = w3[a] * w4[b];
+          s += w * ry[(size_t)i * gf.ld + j];
+          ws += w;
+        }
       }
+      oy = s / ws;
     }
-    oy = s / ws;
   }
   fxc[C] = ox;
   fyc[C] = oy;
