@@ -249,33 +249,30 @@ __device__ inline T coarse_vy(const GeomT<T>& gc, const T* vyc, int I, int J) {
 }
 
 // bilinear coarse-to-fine increments at a fine vx / vy unknown (rows and columns follow the
-// node-centred or cell-centred direction of each component)
+// node-centred or cell-centred direction of each component). Branch-free in the node-centred
+// direction: a fine node between two coarse nodes takes the mean of the two coarse blends, one
+// on a coarse node takes the mean of that blend with itself (exactly the blend), so a warp does
+// not run both forms (B300's FP64 pipe makes such divergence expensive).
 template <typename T>
 __device__ inline T prolong_vx_inc(const GeomT<T>& gc, int i, int j, const T* vxc) {
-  const int I0 = (i & 1) ? (i - 1) / 2 : i / 2;
+  const int I0 = i >> 1;                         // (i - 1) / 2 for odd i, i / 2 for even i
   const T wy0 = (i & 1) ? T(0.25) : T(0.75);
   const T wy1 = T(1) - wy0;
-  if (j & 1) {
-    const int J0 = (j - 1) / 2;
-    return T(0.5) * (wy0 * coarse_vx(gc, vxc, I0, J0) + wy1 * coarse_vx(gc, vxc, I0 + 1, J0) +
-                     wy0 * coarse_vx(gc, vxc, I0, J0 + 1) + wy1 * coarse_vx(gc, vxc, I0 + 1, J0 + 1));
-  }
-  const int J = j / 2;
-  return wy0 * coarse_vx(gc, vxc, I0, J) + wy1 * coarse_vx(gc, vxc, I0 + 1, J);
+  const int Ja = j >> 1, Jb = Ja + (j & 1);
+  const T a = wy0 * coarse_vx(gc, vxc, I0, Ja) + wy1 * coarse_vx(gc, vxc, I0 + 1, Ja);
+  const T b = wy0 * coarse_vx(gc, vxc, I0, Jb) + wy1 * coarse_vx(gc, vxc, I0 + 1, Jb);
+  return T(0.5) * (a + b);
 }
 
 template <typename T>
 __device__ inline T prolong_vy_inc(const GeomT<T>& gc, int i, int j, const T* vyc) {
-  const int J0 = (j & 1) ? (j - 1) / 2 : j / 2;
+  const int J0 = j >> 1;
   const T wx0 = (j & 1) ? T(0.25) : T(0.75);
   const T wx1 = T(1) - wx0;
-  if (i & 1) {
-    const int I0 = (i - 1) / 2;
-    return T(0.5) * (wx0 * coarse_vy(gc, vyc, I0, J0) + wx1 * coarse_vy(gc, vyc, I0, J0 + 1) +
-                     wx0 * coarse_vy(gc, vyc, I0 + 1, J0) + wx1 * coarse_vy(gc, vyc, I0 + 1, J0 + 1));
-  }
-  const int I = i / 2;
-  return wx0 * coarse_vy(gc, vyc, I, J0) + wx1 * coarse_vy(gc, vyc, I, J0 + 1);
+  const int Ia = i >> 1, Ib = Ia + (i & 1);
+  const T a = wx0 * coarse_vy(gc, vyc, Ia, J0) + wx1 * coarse_vy(gc, vyc, Ia, J0 + 1);
+  const T b = wx0 * coarse_vy(gc, vyc, Ib, J0) + wx1 * coarse_vy(gc, vyc, Ib, J0 + 1);
+  return T(0.5) * (a + b);
 }
 
 template <typename T>
