@@ -108,6 +108,17 @@ def test_preconditioner_jacobi_smoothers_match_oracle(nx, ny, Lx, Ly, smoother, 
         assert rel(a, b) <= (1e-11 if prec == P.PREC_FP64 else 2e-4), (rel(a, b), nlev)
 
 
+@pytest.mark.parametrize("omega", [0.7, 1.3])
+@pytest.mark.parametrize("prec,tf", [(P.PREC_FP64, 0), (P.PREC_MIXED, 0), (P.PREC_MIXED, 1)])
+def test_damped_rbgs_preconditioner_matches_oracle(prec, tf, omega):
+    """Red-black Gauss-Seidel with damping (omega_v < 1) and over-relaxation (omega_v > 1) inside the
+    V-cycle, step by step against the oracle; the FP64 per-colour kernel compiles the undamped
+    update (the default omega_v = 1) as a separate path, so the damped form is checked here."""
+    gpu, ora, nlev = _precond_case(96, 64, 1.5, 1.0, "free", prec, 23, omega=omega, tile_fusion=tf)
+    for a, b in zip(gpu, ora):
+        assert rel(a, b) <= (1e-11 if prec == P.PREC_FP64 else 2e-4), (rel(a, b), nlev)
+
+
 @pytest.mark.parametrize("smoother,inner", [(P.SMOOTH_JACOBI, 1), (P.SMOOTH_RAS, 2), (P.SMOOTH_MIXED, 4)])
 @pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
 def test_sinker_with_jacobi_smoothers_matches_direct_oracle(smoother, inner, prec):
