@@ -287,7 +287,11 @@ def sinker_e1_sample():
     contrast 1e8, density contrast 1.03125), mixed precision, lithostatic start, tol 1e-8: the
     default hierarchy (halving, then ratio-2 general coarsening) and the paper's ratio 2.5; then the
     paper's four smoother configurations (RBGS, damped Jacobi, RAS-type with T_inner 4, and "Mixed")
-    at its relaxation factors omega_v = 0.3, omega_p (alpha_p) = 0.6, inside FGMRES(30)."""
+    at its relaxation factors omega_v = 0.3, omega_p (alpha_p) = 0.6, inside FGMRES(30); and the
+    viscosity-contrast continuation (4 stages of 25 outer iterations at eta_comp = (1 - theta)
+    eta_min + theta eta before the full-contrast solve) with the default and the paper's smoother
+    settings (iters and levels describe the final full-contrast solve; the stages add at most
+    4 x 25 outer iterations, and ms covers the whole call)."""
     import torch
     import paper_2603_14040_b300 as P
     from synth import sinker
@@ -303,7 +307,10 @@ def sinker_e1_sample():
                      ("paper_relaxation_rbgs", dict(relax, smoother=P.SMOOTH_RBGS)),
                      ("paper_relaxation_jacobi", dict(relax, smoother=P.SMOOTH_JACOBI)),
                      ("paper_relaxation_ras4", dict(relax, smoother=P.SMOOTH_RAS)),
-                     ("paper_relaxation_mixed", dict(relax, smoother=P.SMOOTH_MIXED))):
+                     ("paper_relaxation_mixed", dict(relax, smoother=P.SMOOTH_MIXED)),
+                     ("continuation_4x25", {"cont_stages": 4, "cont_iters": 25}),
+                     ("continuation_4x25_paper_relaxation_rbgs", dict(relax, smoother=P.SMOOTH_RBGS,
+                                                                       cont_stages=4, cont_iters=25))):
         h = P.Stokes(nx, ny, 1.0, 1.2, prec=P.PREC_MIXED, max_iter=3000, litho_guess=1, **kw)
         h.solve(en, ec, rho, (0.0, 1.0), 1e-8, *outs)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
