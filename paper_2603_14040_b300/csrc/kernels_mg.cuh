@@ -530,6 +530,32 @@ __global__ void k_coarse_invert(double* __restrict__ A, int n, int* __restrict__
   }
 }
 
+// One Gauss-Jordan step k of the same inversion, spread over the whole GPU (one row per
+// blockIdx.y, columns over blockIdx.x / threads), out of place (B from A) so that no row is read
+// after another CTA has rewritten it; same per-element arithmetic as k_coarse_invert. A single
+// CTA does n^3 FP64 operations at one SM's FP64 rate (about 50 ms at n = 573), n such launches
+// take a few microseconds each.
+__global__ void k_coarse_invert_step(const double* __restrict__ A, double* __restrict__ B, int n, int k,
+                                     int* __restrict__ flag) {
+  const int i = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double piv = A[(size_t)k * n + k];
+  if (!(piv > 0.0)) {  // not SPD or non-finite: report (the host fails the solve)
+    if (i == 0 && j == 0) atomicOr(flag, FLAG_BREAKDOWN);
+    B[(size_t)i * n + j] = A[(size_t)i * n + j];
+    return;
+  }
+  const double ip = 1.0 / piv;
+  const double skj = (j == k) ? ip : A[(size_t)k * n + j] * ip;   // row k after scaling
+  if (i == k) {
+    B[(size_t)i * n + j] = skj;
+    return;
+  }
+  const double f = A[(size_t)i * n + k];
+  B[(size_t)i * n + j] = (j == k) ? -f * ip : A[(size_t)i * n + j] - f * skj;
+}
+
 // x = L^-1 f = -(-L)^-1 f on the coarsest level (FP64 whatever T is). One warp per row of the
 // inverse (coalesced row reads, fixed-order shuffle reduction), kCoarseRows rows per CTA, so the
 // matvec spreads over ceil(n / kCoarseRows) SMs (one SM's FP64 rate would make it the critical path).

@@ -25,6 +25,7 @@ using namespace pyro;
 namespace {
 
 constexpr int kMaxCoarse = 1024;
+constexpr int kCoarseInvertMulti = 128;   // larger coarsest systems invert with one launch per pivot
 constexpr int kStreamMinRows = 96;  // shortest row chunk worth a streaming pass
 constexpr int kRasTile = 32;        // RAS-type Jacobi tile edge (cells), the paper's 32 x 32
 constexpr long long kSmallTileCells = 65536;  // FP32 levels up to 256^2 smooth with 32 x 16 tiles
@@ -133,6 +134,7 @@ struct MG {
   std::vector<Level<T>> lv;
   std::vector<char> f2;    // f2[l]: level l+1 is level l halved (factor-2 kernels), else any ratio
   double* Ainv = nullptr;  // coarsest (-L)^-1, dense FP64 (when coarse_direct)
+  double* Atmp = nullptr;  // second buffer of the multi-launch inversion (nc > kCoarseInvertMulti)
   bool coarse_direct = true;  // coarsest level solved by the dense inverse, else by smoothing
   int coarse_sweeps = 40;     // smoothing sweeps on a coarsest level too large for the inverse
   int nc = 0;              // coarse unknowns
@@ -170,7 +172,8 @@ struct MG {
       if (kc_level(l, nlev, kcycle)) b += (size_t)6 * P * sizeof(T) + 5 * 296 * 8 + 64;
     }
     const size_t nc = (size_t)velocity_unknowns(sz.back().first, sz.back().second);
-    return b + (nc <= (size_t)kMaxCoarse ? nc * nc * sizeof(double) : 0);
+    if (nc > (size_t)kMaxCoarse) return b;
+    return b + (nc > (size_t)kCoarseInvertMulti ? 2 : 1) * nc * nc * sizeof(double);
   }
 
   void alloc(DevAlloc& A, const Geom& g0, double Lx, double Ly, const std::vector<std::pair<int, int>>& sz,
@@ -213,6 +216,7 @@ struct MG {
     nc = gc.ny * (gc.nx - 1) + (gc.ny - 1) * gc.nx;
     coarse_direct = nc <= kMaxCoarse;
     if (coarse_direct) Ainv = A.get<double>((size_t)nc * nc);
+    if (coarse_direct && nc > kCoarseInvertMulti) Atmp = A.get<double>((size_t)nc * nc);
   }
 
   // choose the first level of the cluster sub-cycle and fill its launch arguments
@@ -316,8 +320,19 @@ struct MG {
     if (!coarse_direct) return;
     CK(cudaMemsetAsync(Ainv, 0, (size_t)nc * nc * sizeof(double), s));
     k_coarse_assemble<T><<<(nc + 127) / 128, 128, 0, s>>>(C.g, C.en, C.ec, Ainv, nc);
-    k_coarse_invert<<<1, 1024, nc * sizeof(double), s>>>(Ainv, nc, flag);
-    count((long long)lv.size() - 1 + 2);
+    if (nc > kCoarseInvertMulti) {
+      double *a = Ainv, *b = Atmp;
+      const dim3 gg((nc + 255) / 256, nc);
+      for (int k = 0; k < nc; ++k) {
+        k_coarse_invert_step<<<gg, 256, 0, s>>>(a, b, nc, k, flag);
+        std::swap(a, b);
+      }
+      if (a != Ainv) CK(cudaMemcpyAsync(Ainv, a, (size_t)nc * nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      count((long long)lv.size() - 1 + 1 + nc);
+    } else {
+      k_coarse_invert<<<1, 1024, nc * sizeof(double), s>>>(Ainv, nc, flag);
+      count((long long)lv.size() - 1 + 2);
+    }
   }
 
   bool fused(int l) const {
