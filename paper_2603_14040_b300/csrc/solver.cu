@@ -25,7 +25,9 @@ using namespace pyro;
 namespace {
 
 constexpr int kMaxCoarse = 1024;
-constexpr int kCoarseInvertMulti = 128;   // larger coarsest systems invert with one launch per pivot
+constexpr int kCoarseInvertMulti = 80;    // larger coarsest systems invert with one launch per pivot
+                                          // (one CTA: about n^3 / 2 clocks of one SM plus a barrier
+                                          // per pivot; one launch per pivot: a few us each)
 constexpr int kStreamMinRows = 96;  // shortest row chunk worth a streaming pass
 constexpr int kRasTile = 32;        // RAS-type Jacobi tile edge (cells), the paper's 32 x 32
 constexpr long long kSmallTileCells = 65536;  // FP32 levels up to 256^2 smooth with 32 x 16 tiles
