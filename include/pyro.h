@@ -163,8 +163,8 @@ typedef struct {
                             multi-axpy passes over the basis); 1 modified Gram-Schmidt on the basis
                             stored scaled by W^(1/2) (one fused subtract-and-dot step per basis
                             vector, half the FP64 arithmetic of CGS2, j + 2 dependent steps for
-                            column j); 2 modified when restart_m <= 31 and nx ny >= 2^19 cells,
-                            else classical (the faster of the two on B300 either side); 0..2 [2] */
+                            column j); 2 modified when nx ny >= 2^19 cells, else classical (the
+                            faster of the two on B300 either side); 0..2 [2] */
 } pyro_opts;
 
 typedef struct {
