@@ -495,10 +495,12 @@ __global__ void k_precond_out(GeomT<double> g, const T* __restrict__ vx, const T
     z[P + e] = zy;
     double zp = 0.0;
     if (is_p(g.nx, g.ny, i, j)) {
-      // D z_v from the stored (rounded) velocity values, walls masked
-      const double ux = (j <= g.nx - 1) ? (double)(TZ)vx[e] : 0.0;
+      // D z_v from the stored (rounded) velocity values, walls masked; at a cell the east and
+      // south faces are the point's own vx and vy, already in zx and zy (0 on the walls j = nx
+      // and i = ny, where they are not unknowns)
+      const double ux = (double)zx;
       const double uxw = (j - 1 >= 1) ? (double)(TZ)vx[e - 1] : 0.0;
-      const double uy = (i <= g.ny - 1) ? (double)(TZ)vy[e] : 0.0;
+      const double uy = (double)zy;
       const double uyn = (i - 1 >= 1) ? (double)(TZ)vy[e - g.ld] : 0.0;
       const double div = (ux - uxw) * g.idx + (uy - uyn) * g.idy;
       const double rp = isw ? v[2 * P + e] * isw[2 * P + e] : v[2 * P + e];
