@@ -108,6 +108,18 @@ def test_preconditioner_jacobi_smoothers_match_oracle(nx, ny, Lx, Ly, smoother, 
         assert rel(a, b) <= (1e-11 if prec == P.PREC_FP64 else 2e-4), (rel(a, b), nlev)
 
 
+@pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
+def test_preconditioner_with_large_coarsest_block_matches_oracle(prec):
+    """120 x 90 cells halve once and then coarsen by 2 with the general transfer operators down to
+    15 x 12 cells (333 velocity unknowns), so the coarsest block is inverted with one launch per
+    Gauss-Jordan pivot over the whole GPU (the form used above 80 unknowns); one Uzawa sweep step by
+    step against the oracle, whose coarsest solve is a sparse LU factorisation."""
+    gpu, ora, nlev = _precond_case(120, 90, 1.2, 0.9, "free", prec, 29)
+    assert nlev == 4
+    for a, b in zip(gpu, ora):
+        assert rel(a, b) <= (1e-11 if prec == P.PREC_FP64 else 2e-4), (rel(a, b), nlev)
+
+
 @pytest.mark.parametrize("omega", [0.7, 1.3])
 @pytest.mark.parametrize("prec,tf", [(P.PREC_FP64, 0), (P.PREC_MIXED, 0), (P.PREC_MIXED, 1)])
 def test_damped_rbgs_preconditioner_matches_oracle(prec, tf, omega):
