@@ -329,6 +329,21 @@ def test_modified_gram_schmidt_matches_direct_oracle(prec, case):
         assert rel(a, b) <= 1e-8
 
 
+@pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
+def test_modified_gram_schmidt_with_long_restart_matches_oracle(prec):
+    """Modified Gram-Schmidt with FGMRES(80) (the default on large grids at any restart length, as
+    in the solve server): Krylov columns beyond 31, each with its own captured graph of j + 2 steps,
+    against the direct oracle and against CGS2 on the same problem."""
+    f = grf_config(96, 64, seed=5, Lx=1.5, Ly=1.0)
+    out, st = _solve_gpu(f, (0.0, 1.0), 1e-12, prec, Lx=1.5, Ly=1.0, gram_schmidt=1, restart_m=80, max_iter=3000)
+    assert st.iters > 40, st.iters
+    _check_against_direct(f, out, st, Lx=1.5, Ly=1.0, tol=1e-12, tol_err=1e-8)
+    out2, st2 = _solve_gpu(f, (0.0, 1.0), 1e-12, prec, Lx=1.5, Ly=1.0, gram_schmidt=0, restart_m=80, max_iter=3000)
+    assert abs(st.iters - st2.iters) <= 2, (st.iters, st2.iters)
+    for a, b in zip(out, out2):
+        assert rel(a, b) <= 1e-8
+
+
 @pytest.mark.parametrize("accel", [P.ACCEL_FGMRES, P.ACCEL_GCR, P.ACCEL_ANDERSON])
 def test_wall_clock_limit_ends_the_solve_with_timeout(accel):
     """timeout_s: a solve that cannot finish within the limit returns PYRO_E_TIMEOUT (-5); the
