@@ -36,6 +36,7 @@ struct pyro_markers_s {
   int* idx = nullptr;      // marker indices bucketed by cell
   int* cell = nullptr;     // cell of each marker
   double* frac = nullptr;  // (fx, fy) of each marker
+  double* csum = nullptr;  // per-cell corner sums: 4 planes of sum w phi, 4 of sum w (TL, TR, BL, BR)
   int* flag = nullptr;
   double* red = nullptr;   // per-block maxima of the CFL reduction (2 x kRedBlocks)
 };
@@ -154,11 +155,32 @@ __global__ void k_mk_sort(int ncell, const int* __restrict__ offset, int* __rest
   }
 }
 
-// phi(i, j) = sum w phi_m / sum w over the markers of the four cells around node (i, j), cells in
-// the order (i-1, j-1), (i-1, j), (i, j-1), (i, j), markers in index order within a cell
-__global__ void k_mk_gather(Lat L, int ld, const int* __restrict__ offset, const int* __restrict__ idx,
-                            const double* __restrict__ frac, const double* __restrict__ phim,
-                            double* __restrict__ grid, double* __restrict__ wsum) {
+// Per-cell corner sums: for the markers of lattice cell c in index order, sum w phi and sum w for
+// each corner node of the cell (top-left, top-right, bottom-left, bottom-right), w the bilinear
+// weight of the marker at that corner. Each marker is read once (the node pass below adds up
+// four cells' sums instead of re-reading their markers).
+__global__ void k_mk_cell_sums(int ncell, const int* __restrict__ offset, const int* __restrict__ idx,
+                               const double* __restrict__ frac, const double* __restrict__ phim,
+                               double* __restrict__ cs) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  double n0 = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0, d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+  for (int k = offset[c]; k < offset[c + 1]; ++k) {
+    const int m = idx[k];
+    const double fx = frac[2 * m], fy = frac[2 * m + 1], p = phim[m];
+    const double w0 = (1.0 - fx) * (1.0 - fy), w1 = fx * (1.0 - fy), w2 = (1.0 - fx) * fy, w3 = fx * fy;
+    n0 += w0 * p; n1 += w1 * p; n2 += w2 * p; n3 += w3 * p;
+    d0 += w0; d1 += w1; d2 += w2; d3 += w3;
+  }
+  cs[c] = n0; cs[(size_t)ncell + c] = n1; cs[2 * (size_t)ncell + c] = n2; cs[3 * (size_t)ncell + c] = n3;
+  cs[4 * (size_t)ncell + c] = d0; cs[5 * (size_t)ncell + c] = d1; cs[6 * (size_t)ncell + c] = d2;
+  cs[7 * (size_t)ncell + c] = d3;
+}
+
+// phi(i, j) = sum w phi_m / sum w over the markers of the four cells around node (i, j): the cells'
+// corner sums for this node, cells in the order (i-1, j-1), (i-1, j), (i, j-1), (i, j)
+__global__ void k_mk_node_sums(Lat L, int ld, const double* __restrict__ cs, int ncell,
+                               double* __restrict__ grid, double* __restrict__ wsum) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x + L.jlo;
   const int i = blockIdx.y * blockDim.y + threadIdx.y + L.ilo;
   if (i > L.ihi || j > L.jhi) return;
@@ -167,14 +189,9 @@ __global__ void k_mk_gather(Lat L, int ld, const int* __restrict__ offset, const
     const int ci = i - 1 + (q >> 1), cj = j - 1 + (q & 1);     // cell with top-left node (ci, cj)
     if (ci < L.ilo || ci > L.ihi - 1 || cj < L.jlo || cj > L.jhi - 1) continue;
     const int c = (ci - L.ilo) * L.ncx + (cj - L.jlo);
-    const bool right = cj < j, below = ci < i;                   // this node is the cell's right / lower corner
-    for (int k = offset[c]; k < offset[c + 1]; ++k) {
-      const int m = idx[k];
-      const double fx = frac[2 * m], fy = frac[2 * m + 1];
-      const double w = (right ? fx : 1.0 - fx) * (below ? fy : 1.0 - fy);
-      num += w * phim[m];
-      den += w;
-    }
+    const int corner = (ci < i ? 2 : 0) + (cj < j ? 1 : 0);     // this node is the cell's corner
+    num += cs[(size_t)corner * ncell + c];
+    den += cs[(size_t)(4 + corner) * ncell + c];
   }
   const size_t o = (size_t)i * ld + j;
   if (den > 0.0) grid[o] = num / den;
@@ -333,6 +350,7 @@ int pyro_markers_create(int nx, int ny, double Lx, double Ly, long long max_mark
             cudaMalloc(&h->idx, (size_t)max_markers * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->cell, (size_t)max_markers * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->frac, (size_t)max_markers * 2 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&h->csum, 8 * ncell * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&h->flag, sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->red, 2 * kRedBlocks * sizeof(double)) == cudaSuccess;
   if (!ok) {
@@ -363,8 +381,11 @@ int pyro_markers_to_grid(pyro_markers h, int lattice, long long n, const double*
   k_scan_add<<<nb, kScanBlock, 0, s>>>(h->offset, ncell, h->bsum);
   if (n > 0) k_mk_scatter<<<grid_blocks(n), kMkThreads, 0, s>>>(n, h->cell, h->offset, h->fill, h->idx);
   k_mk_sort<<<(ncell + kMkThreads - 1) / kMkThreads, kMkThreads, 0, s>>>(ncell, h->offset, h->idx);
+  // with n = 0 every cell is empty and phim is never read
+  k_mk_cell_sums<<<(ncell + kMkThreads - 1) / kMkThreads, kMkThreads, 0, s>>>(ncell, h->offset, h->idx, h->frac,
+                                                                              phim, h->csum);
   const dim3 b(32, 8), gr((L.jhi - L.jlo + 1 + 31) / 32, (L.ihi - L.ilo + 1 + 7) / 8);
-  k_mk_gather<<<gr, b, 0, s>>>(L, h->nx + 2, h->offset, h->idx, h->frac, n > 0 ? phim : nullptr, grid, wsum);
+  k_mk_node_sums<<<gr, b, 0, s>>>(L, h->nx + 2, h->csum, ncell, grid, wsum);
   int flag = 0;
   if (cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
@@ -443,7 +464,7 @@ void pyro_markers_destroy(pyro_markers h) {
   if (!h) return;
   std::lock_guard<std::recursive_mutex> lk(pyro::device_sync_lock());
   cudaFree(h->count); cudaFree(h->offset); cudaFree(h->fill); cudaFree(h->bsum);
-  cudaFree(h->idx); cudaFree(h->cell); cudaFree(h->frac); cudaFree(h->flag); cudaFree(h->red);
+  cudaFree(h->idx); cudaFree(h->cell); cudaFree(h->frac); cudaFree(h->csum); cudaFree(h->flag); cudaFree(h->red);
   delete h;
 }
 
