@@ -311,15 +311,16 @@ typedef enum { PYRO_ADVECT_EULER = 0, PYRO_ADVECT_HEUN = 1, PYRO_ADVECT_RK4 = 2,
 typedef struct pyro_markers_s* pyro_markers;  /* opaque; owns the bucketing workspace */
 
 /* Workspace for an nx x ny grid of size Lx x Ly and up to max_markers markers (about
- * 24 B x max_markers + 12 B x cells of device memory). PYRO_E_INVALID on bad sizes,
+ * 24 B x max_markers + 76 B x cells of device memory). PYRO_E_INVALID on bad sizes,
  * PYRO_E_NOMEM if allocation fails. */
 int pyro_markers_create(int nx, int ny, double Lx, double Ly, long long max_markers, pyro_markers* out);
 
 /* Marker -> grid weighted average: grid(i,j) = sum_m w_m(i,j) phi_m / sum_m w_m(i,j) over the
  * markers of the four lattice cells around the node; nodes no marker reaches keep their input
  * value; wsum (optional) receives the weight sums (0 where no marker reaches). Deterministic: the
- * markers are bucketed by cell with integer atomics, each bucket sorted by marker index, and each
- * node sums its four cells in a fixed order. xm, ym, phim: n device doubles; grid, wsum: device
+ * markers are bucketed by cell with integer atomics, each bucket sorted by marker index and summed
+ * in that order into per-cell corner sums, and each node adds its four cells' sums in a fixed
+ * order. xm, ym, phim: n device doubles; grid, wsum: device
  * (ny+2) x (nx+2) arrays. Synchronises cuda_stream before it returns. PYRO_E_INVALID for host
  * pointers, n > max_markers or an unknown lattice; PYRO_E_NONFINITE if a position is not finite. */
 int pyro_markers_to_grid(pyro_markers h, int lattice, long long n, const double* xm, const double* ym,
