@@ -28,7 +28,9 @@
  * POINTERS
  *   Field pointers may be device pointers or host pointers (pageable or pinned); the library
  *   detects which with cudaPointerGetAttributes. Host buffers are staged through the handle's own
- *   device workspace with copies ordered on `cuda_stream`. The caller owns every buffer.
+ *   device workspace with copies ordered on `cuda_stream`. A device pointer must belong to the
+ *   handle's device (the current device for calls without a handle) or be managed memory; memory
+ *   of another GPU is rejected with PYRO_E_INVALID. The caller owns every buffer.
  *   `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
  *
  * STATUS CODES: 0 = success; > 0 warning with a valid best-effort result; < 0 error (outputs
@@ -261,12 +263,14 @@ int pyro_stokes_get_timing(pyro_stokes h, double* ms, long long* counts);
  * b = -rho g plus the boundary constants (exactly the residual of pyro_stokes_solve) for the
  * fields vx, vy, p, writes r_vx, r_vy, r_p (residual at unknowns, 0 elsewhere) and
  * rel_res[0] = relative energy residual, rel_res[1] = relative l2 residual (rel_res may be a
- * host or device pointer; every field pointer must be a device pointer). Its only scratch is a
- * fixed 128 KiB array in device global memory (16384 doubles: one 4-value partial per block of 4
- * grid rows), held by every GPU that loads the library until the process exits; hence ny + 2 must
- * not exceed 16380 rows (else PYRO_E_INVALID, as for host pointers or a periodic boundary). The
- * first call on a device looks up the array's device address (once per device, with that device
- * current); make that first call before any stream capture. All calls share the array and it keeps
+ * host or device pointer; every field pointer must be a device pointer of the current device). Its
+ * only scratch is a fixed 128 KiB array in device global memory (16384 doubles: one 4-value
+ * partial per block of 4 grid rows), held by every GPU that loads the library until the process
+ * exits; hence ny + 2 must not exceed 16380 rows (else PYRO_E_INVALID, as for host pointers, other
+ * GPUs' memory or a periodic boundary). Every call looks up the array's device address in the
+ * current device's context (a lookup allocates nothing); the first lookup in a context may load the
+ * library's device code, so make the first call on a device before any stream capture. All calls
+ * share the array and it keeps
  * the last call's contents (every slot read is written first in the same call, so nothing needs to
  * start at zero); calls that overlap on the GPU, on any streams, race on it. Returns after
  * completion on cuda_stream. */

@@ -24,6 +24,31 @@ inline std::recursive_mutex& device_sync_lock() {
   return m;
 }
 
+// Host side. Where a caller's pointer lives, seen from the current device:
+//   PTR_HOST   host memory (pageable or pinned): staged through device buffers;
+//   PTR_HERE   device memory of the current device, or managed memory: read / written in place;
+//   PTR_OTHER  device memory of another GPU, or a null / unreadable pointer: rejected
+//              (PYRO_E_INVALID), since a kernel here would read peer memory or fault.
+enum PtrPlace { PTR_OTHER = -1, PTR_HOST = 0, PTR_HERE = 1 };
+inline PtrPlace ptr_place(const void* p) {
+  if (!p) return PTR_OTHER;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return PTR_OTHER;
+  }
+  if (a.type == cudaMemoryTypeManaged) return PTR_HERE;
+  if (a.type == cudaMemoryTypeDevice) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+      cudaGetLastError();
+      return PTR_OTHER;
+    }
+    return a.device == cur ? PTR_HERE : PTR_OTHER;
+  }
+  return PTR_HOST;
+}
+
 struct Geom {
   int nx, ny;      // cell counts
   int ld;          // row stride (nx + 2)

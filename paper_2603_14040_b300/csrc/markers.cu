@@ -319,12 +319,9 @@ __global__ void k_absmax2(const double* __restrict__ a, const double* __restrict
   }
 }
 
-bool on_device(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+// device memory of the current device (or managed memory); host pointers and other GPUs' memory
+// are rejected by the callers
+bool on_device(const void* p) { return pyro::ptr_place(p) == pyro::PTR_HERE; }
 
 int grid_blocks(long long n) { return (int)((n + kMkThreads - 1) / kMkThreads < 4 * 148 * 8 ? (n + kMkThreads - 1) / kMkThreads : 4 * 148 * 8); }
 

@@ -14,7 +14,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "../../include/pyro.h"
 #include "common.cuh"
@@ -172,33 +171,24 @@ __global__ void k_finish_noalloc(double* __restrict__ scratch, int nblk) {
   }
 }
 
-// Device address of g_noalloc_scratch, looked up once per device (with that device current).
-std::mutex g_lookup_mutex;
-void* g_scratch_addr[128] = {};
-
-int scratch_address(int dev, double** out) {
-  if (dev < 0 || dev >= 128) return PYRO_E_INVALID;
-  std::lock_guard<std::mutex> lock(g_lookup_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
-      cudaGetLastError();
-      return PYRO_E_CUDA;
-    }
-    g_scratch_addr[dev] = ptr;
+// Device address of g_noalloc_scratch in the current device's context. Looked up on every call:
+// the lookup allocates nothing, and an address kept from an earlier call would be stale after the
+// context that held it was destroyed (cudaDeviceReset, or a primary context released and made
+// again). The first lookup in a context may load the library's device code, which is why the first
+// call on a device should come before any stream capture.
+int scratch_address(double** out) {
+  void* ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+    cudaGetLastError();
+    return PYRO_E_CUDA;
   }
-  *out = (double*)g_scratch_addr[dev];
+  *out = (double*)ptr;
   return PYRO_OK;
 }
 
-bool on_device(const void* p) {
-  cudaPointerAttributes a;
-  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+// device memory of the current device (or managed memory); host pointers and other GPUs' memory
+// are rejected
+bool on_device(const void* p) { return ptr_place(p) == PTR_HERE; }
 
 }  // namespace
 
@@ -216,16 +206,16 @@ extern "C" int pyro_stokes_residual_noalloc(int nx, int ny, double Lx, double Ly
     if (!on_device(a)) return PYRO_E_INVALID;
   for (double* a : outs)
     if (!on_device(a)) return PYRO_E_INVALID;
+  const PtrPlace res_place = ptr_place(rel_res);
+  if (res_place == PTR_OTHER) return PYRO_E_INVALID;
   pyro_bc b{};
   for (int k = 0; k < 4; ++k) { b.kind[k] = PYRO_BC_FREE_SLIP; b.vt[k] = 0.0; }
   if (bc) b = *bc;
   for (int k = 0; k < 4; ++k)
     if (b.kind[k] != PYRO_BC_FREE_SLIP && b.kind[k] != PYRO_BC_NO_SLIP && b.kind[k] != PYRO_BC_VELOCITY)
       return PYRO_E_INVALID;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return PYRO_E_CUDA;
   double* scratch = nullptr;
-  const int st = scratch_address(dev, &scratch);
+  const int st = scratch_address(&scratch);
   if (st != PYRO_OK) return st;
   Geom g0;
   g0.nx = nx; g0.ny = ny; g0.ld = nx + 2; g0.dx = Lx / nx; g0.dy = Ly / ny;
@@ -237,7 +227,7 @@ extern "C" int pyro_stokes_residual_noalloc(int nx, int ny, double Lx, double Ly
   k_residual_noalloc<<<nblk, 256, 0, s>>>(g, eta_n, eta_c, rho, gx, gy, c_of(2), c_of(3), c_of(0), c_of(1), vx, vy,
                                           p, r_vx, r_vy, r_p, scratch);
   k_finish_noalloc<<<1, 256, 0, s>>>(scratch, nblk);
-  const bool dev_out = on_device(rel_res);
+  const bool dev_out = res_place == PTR_HERE;
   if (cudaMemcpyAsync(rel_res, scratch + 4 * kNoAllocMaxBlocks, 2 * sizeof(double),
                       dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s) != cudaSuccess) {
     cudaGetLastError();

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <utility>
 #include <vector>
@@ -47,14 +48,15 @@ inline dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + 2 + b.x - 1) / b.x
 inline dim3 grid_rb(int nx, int ny, dim3 b) { return dim3(((nx + 2) / 2 + 1 + b.x - 1) / b.x, (ny + 2 + b.y - 1) / b.y); }
 const dim3 kBlk2(32, 8);
 
-bool is_device_ptr(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+// true for memory the current device reads in place; host pointers are staged. Entry points reject
+// other GPUs' memory up front (places_ok), so everything that is not PTR_HERE here is host memory.
+bool is_device_ptr(const void* p) { return ptr_place(p) == PTR_HERE; }
+
+// every non-null caller pointer is host memory or memory of the handle's device
+bool places_ok(std::initializer_list<const void*> ptrs) {
+  for (const void* p : ptrs)
+    if (p && ptr_place(p) == PTR_OTHER) return false;
+  return true;
 }
 
 struct DevAlloc {
@@ -1532,6 +1534,8 @@ int pyro_stokes_precond(pyro_stokes h, const double* eta_n, const double* eta_c,
                         const double* r_vy, const double* r_p, double* z_vx, double* z_vy, double* z_p,
                         void* cuda_stream) {
   if (!h || !eta_n || !eta_c || !r_vx || !r_vy || !r_p || !z_vx || !z_vy || !z_p) return PYRO_E_INVALID;
+  if (cudaSetDevice(h->dev) != cudaSuccess) return PYRO_E_CUDA;
+  if (!places_ok({eta_n, eta_c, r_vx, r_vy, r_p, z_vx, z_vy, z_p})) return PYRO_E_INVALID;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   try {
     CK(cudaSetDevice(h->dev));
@@ -1616,6 +1620,8 @@ void pyro_stokes_destroy(pyro_stokes h) {
 int pyro_stokes_apply(pyro_stokes h, const double* eta_n, const double* eta_c, const double* vx, const double* vy,
                       const double* p, double* Ax, double* Ay, double* Ap, void* cuda_stream) {
   if (!h || !eta_n || !eta_c || !vx || !vy || !p || !Ax || !Ay || !Ap) return PYRO_E_INVALID;
+  if (cudaSetDevice(h->dev) != cudaSuccess) return PYRO_E_CUDA;
+  if (!places_ok({eta_n, eta_c, vx, vy, p, Ax, Ay, Ap})) return PYRO_E_INVALID;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   try {
     CK(cudaSetDevice(h->dev));
@@ -1645,6 +1651,8 @@ int pyro_stokes_solve(pyro_stokes h, const double* eta_n, const double* eta_c, c
                       double tol, double* vx, double* vy, double* p, pyro_stats* stats, void* cuda_stream) {
   if (!h || !eta_n || !eta_c || !rho || !vx || !vy || !p) return PYRO_E_INVALID;
   if (!(tol > 0) || !std::isfinite(gx) || !std::isfinite(gy)) return PYRO_E_INVALID;
+  if (cudaSetDevice(h->dev) != cudaSuccess) return PYRO_E_CUDA;
+  if (!places_ok({eta_n, eta_c, rho, vx, vy, p})) return PYRO_E_INVALID;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   pyro_stats st{};
   st.levels = h->nlev;
@@ -1713,6 +1721,8 @@ int pyro_stokes_adjoint(pyro_stokes h, const double* dJ_dvx, const double* dJ_dv
                         double* dJ_deta_n, double* dJ_deta_c, double* dJ_drho, pyro_stats* stats, void* cuda_stream) {
   if (!h || !dJ_dvx || !dJ_dvy || !dJ_dp || !dJ_deta_n || !dJ_deta_c || !(tol > 0)) return PYRO_E_INVALID;
   if (!h->have_solution) return PYRO_E_INVALID;
+  if (cudaSetDevice(h->dev) != cudaSuccess) return PYRO_E_CUDA;
+  if (!places_ok({dJ_dvx, dJ_dvy, dJ_dp, dJ_deta_n, dJ_deta_c, dJ_drho})) return PYRO_E_INVALID;
   for (int k = 0; k < 4; ++k)
     if (h->bc.kind[k] == PYRO_BC_VELOCITY) return PYRO_E_INVALID;
   cudaStream_t s = (cudaStream_t)cuda_stream;

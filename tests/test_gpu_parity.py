@@ -366,3 +366,17 @@ def test_not_converged_warning_returns_best_iterate():
     out, st = _solve_gpu(f, (0.0, 1.0), 1e-12, P.PREC_MIXED, max_iter=3)
     assert st.status == P.PYRO_W_NOT_CONVERGED and st.iters == 3
     assert 0 < st.rel_energy_res < 1.0
+
+
+@pytest.mark.skipif(torch.cuda.device_count() < 2, reason="needs memory of a second GPU")
+def test_memory_of_another_gpu_is_rejected():
+    # the check runs on the host before any kernel: a field on GPU 1 given to a handle on GPU 0
+    n = 8
+    h = P.Stokes(n, n)
+    ok = [zeros(n, n) for _ in range(5)]
+    other = torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda:1")
+    out = [zeros(n, n) for _ in range(3)]
+    with pytest.raises(P.PyroError) as err:
+        h.apply(ok[0], ok[1], ok[2], ok[3], other, *out)
+    assert err.value.status == P.PYRO_E_INVALID
+    h.close()
