@@ -167,6 +167,14 @@ typedef struct {
                             vector, half the FP64 arithmetic of CGS2, j + 2 dependent steps for
                             column j); 2 modified when nx ny >= 2^19 cells, else classical (the
                             faster of the two on B300 either side); 0..2 [2] */
+  int schur;             /* pressure block of the Uzawa preconditioner: 0 the paper's diagonal viscosity
+                            surrogate, z_p = alpha_p eta_c (r_p - D z_v); 1 the weighted BFBt
+                            approximation of the Schur complement (not in the paper; for viscosity
+                            that jumps by many orders of magnitude), z_p = alpha_p K^-1 (D W^-1 (-L)
+                            W^-1 G) K^-1 (r_p - D z_v) with K = D W^-1 G, W = diag(-L)^(1/2), each K^-1
+                            one V-cycle of a smoothed-aggregation multigrid on the cell grid (2 x 2
+                            aggregates, Galerkin coarse operators in a 5 x 5-box stencil, damped Jacobi
+                            smoothing, dense coarsest inverse); 0 or 1 [0] */
 } pyro_opts;
 
 typedef struct {
@@ -282,6 +290,14 @@ int pyro_stokes_residual_noalloc(int nx, int ny, double Lx, double Ly, const pyr
 
 /* Release every device allocation of h (NULL is a no-op). */
 void pyro_stokes_destroy(pyro_stokes h);
+
+/* Diagnostic (no counterpart in the paper): the FP64 fused multiply-add rate of the current GPU in
+ * TFLOP/s (2 flop per FMA), timed with CUDA events on one launch of independent FMA chains
+ * (8 chains x iters FMAs per thread, 8 blocks of 256 threads per SM) after one warm-up launch.
+ * The library's FP64 stencils and Krylov passes are bound by this rate on B300, so it is the
+ * denominator of their roofline. Allocates and frees one double. Synchronises cuda_stream.
+ * PYRO_E_INVALID for iters < 1 or a null tflops. */
+int pyro_fp64_fma_rate(int iters, double* tflops, void* cuda_stream);
 
 /* Static description of a status code. */
 const char* pyro_strerror(int status);

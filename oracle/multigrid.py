@@ -399,14 +399,127 @@ def divergence(grid, zv):
     return (vx[i, j] - vx[i, jm]) / grid.dx + (vy[i, j] - vy[i - 1, j]) / grid.dy
 
 
-def uzawa_precond(h, r, eta_c, alpha=0.6, nu1=2, nu2=2, omega=1.0, literal_sign=False, kcycle=0):
-    """z = M^-1 r for one Uzawa sweep: z_v = V-cycle(L, r_v), z_p = alpha eta_c (r_p - D z_v),
-    then the mean of z_p is removed (Eq. pressure_normalization). `literal_sign` flips to the
+def uzawa_precond(h, r, eta_c, alpha=0.6, nu1=2, nu2=2, omega=1.0, literal_sign=False, kcycle=0, schur=None):
+    """z = M^-1 r for one Uzawa sweep: z_v = V-cycle(L, r_v), z_p = alpha S~^-1 (r_p - D z_v), then
+    the mean of z_p is removed (Eq. pressure_normalization). S~^-1 is eta_c (the paper's diagonal
+    viscosity surrogate) unless `schur` (a WeightedBFBt) is given. `literal_sign` flips to the
     paper's printed sign alpha eta_c (D z_v - r_p) (used only to demonstrate the reading)."""
     g = h.grids[0]
     zv = vcycle(h, r[:g.n_v], nu1, nu2, omega, kcycle=kcycle)
-    e = g.eta_c_at(eta_c, g.p_i, g.p_j)
     dz = divergence(g, zv)
-    zp = alpha * e * ((dz - r[g.n_v:]) if literal_sign else (r[g.n_v:] - dz))
+    if schur is not None:
+        zp = alpha * schur.apply(r[g.n_v:] - dz)
+    else:
+        e = g.eta_c_at(eta_c, g.p_i, g.p_j)
+        zp = alpha * e * ((dz - r[g.n_v:]) if literal_sign else (r[g.n_v:] - dz))
     zp -= zp.mean()
     return np.concatenate([zv, zp])
+
+
+# ---- weighted BFBt Schur-complement surrogate (not in the paper) ------------------------------
+# The paper's pressure block uses the diagonal viscosity surrogate eta_c. Where the viscosity jumps
+# by many orders of magnitude over short distances (a stiff lid over a weak mantle with weak and
+# strong inclusions) that surrogate misses whole families of pressure modes and the outer Krylov
+# method stalls. The weighted BFBt approximation of the Schur complement S = D (-L)^-1 G (Elman,
+# SIAM J. Sci. Comput. 20 (1999) 1299-1316; the square-root-diagonal weighting of Rudi, Stadler and
+# Ghattas, SIAM J. Sci. Comput. 39 (2017) S272-S297) is
+#     S~^-1 = K^-1 (D W^-1 (-L) W^-1 G) K^-1,   K = D W^-1 G,   W = diag(-L)^(1/2),
+# with both Poisson-type solves K^-1 replaced by one V-cycle of a smoothed-aggregation multigrid
+# (PressureAMG below), so the surrogate is a fixed linear operator.
+def aggregation_matrix(nx, ny):
+    """P0: cell (i, j) of an nx x ny cell grid (compact row-major) -> aggregate (i // 2, j // 2) of the
+    ceil(ny / 2) x ceil(nx / 2) coarse grid (2 x 2 aggregates, 1-wide ones at odd edges)."""
+    nxc, nyc = (nx + 1) // 2, (ny + 1) // 2
+    k = np.arange(nx * ny)
+    i, j = np.divmod(k, nx)
+    return sp.csr_matrix((np.ones(nx * ny), (k, (i // 2) * nxc + j // 2)), shape=(nx * ny, nxc * nyc))
+
+
+def near_part(K, nx):
+    """The part of K that couples cells at most one apart in both directions (a 3 x 3 box), with
+    every dropped entry added to its row's diagonal, so row sums (and the constant null space) are
+    unchanged."""
+    C = K.tocoo()
+    ri, rj = np.divmod(C.row, nx)
+    ci, cj = np.divmod(C.col, nx)
+    near = (np.abs(ri - ci) <= 1) & (np.abs(rj - cj) <= 1)
+    lump = np.bincount(C.row[~near], weights=C.data[~near], minlength=K.shape[0])
+    Kn = sp.csr_matrix((C.data[near], (C.row[near], C.col[near])), shape=K.shape)
+    return (Kn + sp.diags(lump.astype(np.float64))).tocsr()
+
+
+class PressureAMG:
+    """Smoothed-aggregation multigrid for a symmetric cell-centred operator K with the constant null
+    space (here K = D W^-1 G with the walls' zero-flux condition), on structured 2 x 2 aggregates.
+
+    Level l -> l + 1: P = (I - omega_p diag(K)^-1 K_near) P0 with P0 the aggregation matrix and K_near
+    the 3 x 3-box part of K (dropped couplings lumped on the diagonal), R = P^T, K_{l+1} = P^T K P
+    (Galerkin). Smoothing the tentative prolongator with only the near part keeps every coarse
+    operator within a 5 x 5 box stencil. Coarsening stops when a level has <= max_coarse cells; the
+    coarsest level is solved exactly with the zero-mean gauge. The cycle: nu damped Jacobi sweeps
+    x += omega_s (f - K x) / diag(K), residual, restriction, recursion from zero, prolongation,
+    nu damped Jacobi sweeps."""
+
+    def __init__(self, K, nx, ny, omega_p=2.0 / 3.0, omega_s=0.8, nu=2, max_coarse=256):
+        self.omega_s, self.nu = omega_s, nu
+        self.K, self.P, self.shape = [K.tocsr()], [], [(nx, ny)]
+        while nx * ny > max_coarse:
+            P0 = aggregation_matrix(nx, ny)
+            Kl = self.K[-1]
+            Kn = near_part(Kl, nx)
+            P = (P0 - omega_p * (sp.diags(1.0 / Kl.diagonal()) @ (Kn @ P0))).tocsr()
+            self.P.append(P)
+            self.K.append((P.T @ Kl @ P).tocsr())
+            nx, ny = (nx + 1) // 2, (ny + 1) // 2
+            self.shape.append((nx, ny))
+        Kc = self.K[-1]
+        one = np.ones(Kc.shape[0])
+        self.coarse_lu = spla.splu(sp.bmat([[Kc, sp.csr_matrix(one[:, None])],
+                                            [sp.csr_matrix(one[None, :]), None]], format="csc"))
+
+    @property
+    def nlev(self):
+        return len(self.K)
+
+    def vcycle(self, f, level=0):
+        if level == self.nlev - 1:
+            return self.coarse_lu.solve(np.concatenate([f - f.mean(), [0.0]]))[:-1]
+        K = self.K[level]
+        d = K.diagonal()
+        x = np.zeros_like(f)
+        for _ in range(self.nu):
+            x = x + self.omega_s * (f - K @ x) / d
+        ec = self.vcycle(self.P[level].T @ (f - K @ x), level + 1)
+        x = x + self.P[level] @ ec
+        for _ in range(self.nu):
+            x = x + self.omega_s * (f - K @ x) / d
+        return x
+
+
+class WeightedBFBt:
+    """S~^-1 y = K^-1 (D W^-1 (-L) W^-1 G) K^-1 y on the pressure unknowns of the finest grid, with
+    W = diag(-L)^(1/2) and each K^-1 one PressureAMG V-cycle (exact=True: sparse LU instead, used by
+    the tests to separate the surrogate from its multigrid)."""
+
+    def __init__(self, sysm, weight_exp=0.5, exact=False, **amg):
+        g = sysm.grid
+        A = sysm.A.tocsr()
+        nv = g.n_v
+        self.L = A[:nv, :nv].tocsr()
+        self.G = A[:nv, nv:].tocsr()
+        self.D = A[nv:, :nv].tocsr()
+        self.W = (-self.L.diagonal()) ** weight_exp
+        self.Kmat = (self.D @ sp.diags(1.0 / self.W) @ self.G).tocsr()
+        if exact:
+            one = np.ones(g.n_p)
+            lu = spla.splu(sp.bmat([[self.Kmat, sp.csr_matrix(one[:, None])],
+                                    [sp.csr_matrix(one[None, :]), None]], format="csc"))
+            self.Kinv = lambda y: lu.solve(np.concatenate([y - y.mean(), [0.0]]))[:-1]
+        else:
+            self.amg = PressureAMG(self.Kmat, g.nx, g.ny, **amg)
+            self.Kinv = self.amg.vcycle
+
+    def apply(self, y):
+        t1 = self.Kinv(y)
+        t2 = self.D @ ((-(self.L @ ((self.G @ t1) / self.W))) / self.W)
+        return self.Kinv(t2)

@@ -20,6 +20,7 @@
 #include "kernels_tile.cuh"
 #include "kernels_stream.cuh"
 #include "kernels_jacobi.cuh"
+#include "kernels_schur.cuh"
 
 using namespace pyro;
 
@@ -639,6 +640,126 @@ struct MG {
 
 }  // namespace
 
+// ---- pressure multigrid of the weighted BFBt Schur surrogate ----------------------------------
+// Levels of the pressure grid (compact nx * ny cells): level 0 holds the face conductances, each
+// coarser level (ceil halves, 2 x 2 aggregates) a 5 x 5-box Galerkin stencil; the coarsest level
+// (<= kSchurMaxCoarse cells) a dense inverse. One V-cycle: nu damped Jacobi sweeps from zero,
+// residual, restriction P^T r, the coarse cycle, x += P e, nu damped Jacobi sweeps.
+template <typename T>
+struct SchurMG {
+  struct Lv {
+    int nx = 0, ny = 0;
+    size_t n = 0;
+    T *cx = nullptr, *cy = nullptr, *box = nullptr, *diag = nullptr;
+    T *x = nullptr, *x2 = nullptr, *f = nullptr, *r = nullptr, *pw = nullptr;
+    int cur = 0;
+    T* X() const { return cur ? x2 : x; }
+    T* Xo() const { return cur ? x : x2; }
+  };
+  std::vector<Lv> lv;
+  T *wix = nullptr, *wiy = nullptr;  // W^-1 at the velocity unknowns of the finest grid (padded)
+  double* Ainv = nullptr;
+  int nc = 0;
+  int nu = 2;
+  T omega_s = T(0.8), omega_p = T(2.0 / 3.0);
+  long long* nlaunch = nullptr;
+  void count(long long k) const { if (nlaunch) *nlaunch += k; }
+
+  static std::vector<std::pair<int, int>> sizes(int nx, int ny) {
+    std::vector<std::pair<int, int>> v{{nx, ny}};
+    while ((long long)nx * ny > kSchurMaxCoarse) {
+      nx = (nx + 1) / 2;
+      ny = (ny + 1) / 2;
+      v.push_back({nx, ny});
+    }
+    return v;
+  }
+  static size_t bytes(int nx, int ny, size_t P) {
+    const auto sz = sizes(nx, ny);
+    size_t b = 2 * P * sizeof(T);
+    for (size_t l = 0; l < sz.size(); ++l) {
+      const size_t n = (size_t)sz[l].first * sz[l].second;
+      b += (4 + 1) * n * sizeof(T);                                    // x, x2, f, r, diag
+      b += (l == 0 ? 2 : kSchurBox) * n * sizeof(T);                   // conductances / box stencil
+      if (l + 1 < sz.size()) b += 4 * n * sizeof(T);                   // prolongator rows
+      b += 5 * 256;                                                    // allocation rounding
+    }
+    const size_t ncl = (size_t)sz.back().first * sz.back().second;
+    return b + ncl * ncl * sizeof(double);
+  }
+  void alloc(DevAlloc& A, int nx, int ny, size_t P) {
+    const auto sz = sizes(nx, ny);
+    wix = A.get<T>(P);
+    wiy = A.get<T>(P);
+    for (size_t l = 0; l < sz.size(); ++l) {
+      Lv L;
+      L.nx = sz[l].first; L.ny = sz[l].second;
+      L.n = (size_t)L.nx * L.ny;
+      if (l == 0) { L.cx = A.get<T>(L.n); L.cy = A.get<T>(L.n); }
+      else L.box = A.get<T>((size_t)kSchurBox * L.n);
+      L.diag = A.get<T>(L.n);
+      L.x = A.get<T>(L.n); L.x2 = A.get<T>(L.n); L.f = A.get<T>(L.n); L.r = A.get<T>(L.n);
+      if (l + 1 < sz.size()) L.pw = A.get<T>(4 * L.n);
+      lv.push_back(L);
+    }
+    nc = (int)lv.back().n;
+    Ainv = A.get<double>((size_t)nc * nc);
+  }
+  PLev<T> plev(int l) const {
+    const Lv& L = lv[l];
+    return PLev<T>{L.nx, L.ny, L.cx, L.cy, L.box, L.diag};
+  }
+  static unsigned nb(size_t n) { return (unsigned)((n + 255) / 256); }
+
+  // conductances from the finest level's viscosity, prolongators and Galerkin coarse operators,
+  // dense coarsest inverse
+  void setup(const GeomT<T>& g, const T* en, const T* ec, cudaStream_t s, int* flag) {
+    k_schur_weights<T, T><<<grid2(g.nx, g.ny, kBlk2), kBlk2, 0, s>>>(g, en, ec, wix, wiy, lv[0].cx, lv[0].cy,
+                                                                     lv[0].diag);
+    for (size_t l = 0; l + 1 < lv.size(); ++l) {
+      const Lv& F = lv[l];
+      Lv& C = lv[l + 1];
+      k_schur_prow<T><<<nb(F.n), 256, 0, s>>>(plev((int)l), C.nx, C.ny, omega_p, F.pw);
+      k_schur_rap<T><<<nb(C.n), 256, 0, s>>>(plev((int)l), F.pw, C.nx, C.ny, C.box, C.diag);
+    }
+    k_schur_coarse_assemble<T><<<1, 1024, 0, s>>>(plev((int)lv.size() - 1), Ainv);
+    k_coarse_invert<<<1, 1024, nc * sizeof(double), s>>>(Ainv, nc, flag);
+    count(1 + 2 * ((long long)lv.size() - 1) + 2);
+  }
+
+  void jacobi(int l, bool from_zero, cudaStream_t s) {
+    Lv& L = lv[l];
+    if (from_zero) {
+      k_schur_jacobi<T><<<nb(L.n), 256, 0, s>>>(plev(l), nullptr, L.x, L.f, omega_s);
+      L.cur = 0;
+    } else {
+      k_schur_jacobi<T><<<nb(L.n), 256, 0, s>>>(plev(l), L.X(), L.Xo(), L.f, omega_s);
+      L.cur ^= 1;
+    }
+    count(1);
+  }
+
+  // one V-cycle on level l for K x = lv[l].f from zero; the result is lv[l].X()
+  void cycle(int l, cudaStream_t s) {
+    Lv& L = lv[l];
+    if (l == (int)lv.size() - 1) {
+      k_schur_coarse_solve<T><<<1, 256, 0, s>>>(Ainv, nc, L.f, L.x);
+      L.cur = 0;
+      count(1);
+      return;
+    }
+    Lv& C = lv[l + 1];
+    for (int k = 0; k < nu; ++k) jacobi(l, k == 0, s);
+    k_schur_resid<T><<<nb(L.n), 256, 0, s>>>(plev(l), L.X(), L.f, L.r);
+    k_schur_restrict<T><<<nb(C.n), 256, 0, s>>>(L.nx, L.ny, L.pw, L.r, C.nx, C.ny, C.f);
+    count(2);
+    cycle(l + 1, s);
+    k_schur_prolong<T><<<nb(L.n), 256, 0, s>>>(L.nx, L.ny, L.pw, C.X(), C.nx, C.ny, L.X());
+    count(1);
+    for (int k = 0; k < nu; ++k) jacobi(l, false, s);
+  }
+};
+
 // ---- the handle -----------------------------------------------------------------------------
 struct pyro_stokes_s {
   int dev = 0;
@@ -669,6 +790,8 @@ struct pyro_stokes_s {
   int* hflag = nullptr;
   MG<float> mgf;
   MG<double> mgd;
+  SchurMG<float> smf;                        // weighted BFBt pressure block (option schur = 1)
+  SchurMG<double> smd;
   std::vector<cudaGraphExec_t> graphs;       // captured iteration graphs (per Krylov column with MGS)
   std::vector<long long> graph_kernel_counts;
   int cur_j = 0;                              // Krylov column of the step being launched or captured
@@ -706,6 +829,13 @@ int multidot(pyro_stokes_s* h, cudaStream_t s, const double* V, const int* d_cnt
   return kReduceBlocks;
 }
 
+template <typename T>
+SchurMG<T>& schur_of(pyro_stokes_s* h);
+template <>
+SchurMG<float>& schur_of<float>(pyro_stokes_s* h) { return h->smf; }
+template <>
+SchurMG<double>& schur_of<double>(pyro_stokes_s* h) { return h->smd; }
+
 // z = M^-1 v with v = in + (*d_idx) in_stride and z = out + (*d_idx) out_stride (device index), and
 // optionally w = A z.
 template <typename T, typename TZ>
@@ -720,8 +850,26 @@ void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s, const double* in,
   mg.cycle(0, s);
   mg.hooks = nullptr;
   h->launches += 3;
-  k_precond_out<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), in, in_stride, out, out_stride, d_idx,
-                                                           h->ec, h->o.alpha_p, h->part2, isw);
+  if (h->o.schur) {
+    // weighted BFBt pressure block: z_p = alpha K^-1 (D W^-1 (-L) W^-1 G) K^-1 (r_p - D z_v)
+    SchurMG<T>& sm = schur_of<T>(h);
+    auto& F0 = sm.lv[0];
+    sm.nlaunch = &h->launches;
+    k_precond_out_schur<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), in, in_stride, out,
+                                                                   out_stride, d_idx, F0.f, isw);
+    sm.cycle(0, s);
+    const dim3 g2 = grid2(h->nx, h->ny, kBlk2);
+    k_schur_grad<T><<<g2, kBlk2, 0, s>>>(L0.gt, F0.X(), sm.wix, sm.wiy, L0.rx, L0.ry);
+    k_schur_lw<T, T><<<g2, kBlk2, 0, s>>>(L0.gt, L0.rx, L0.ry, L0.en, L0.ec, sm.wix, sm.wiy, L0.fx, L0.fy);
+    k_schur_div<T><<<SchurMG<T>::nb(F0.n), 256, 0, s>>>(L0.gt, L0.fx, L0.fy, F0.f);
+    sm.cycle(0, s);
+    k_schur_out<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, F0.X(), h->o.alpha_p, out, out_stride, d_idx,
+                                                           h->part2);
+    h->launches += 4;
+  } else {
+    k_precond_out<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), in, in_stride, out, out_stride,
+                                                             d_idx, h->ec, h->o.alpha_p, h->part2, isw);
+  }
   k_sub_mean<TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, out + 2 * h->P, out_stride, d_idx, h->part2, kReduceBlocks);
   if (with_apply) {
     k_apply<TZ><<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->ec, (const TZ*)out, out_stride, d_idx,
@@ -971,9 +1119,18 @@ void setup_eta(pyro_stokes_s* h, cudaStream_t s) {
     h->launches += 2;
     h->mgf.nlaunch = &h->launches;
     h->mgf.setup(s, h->flag);
+    if (h->o.schur) {
+      h->smf.nlaunch = &h->launches;
+      h->smf.setup(L0.gt, L0.en, L0.ec, s, h->flag);
+    }
   } else {
     h->mgd.nlaunch = &h->launches;
     h->mgd.setup(s, h->flag);
+    if (h->o.schur) {
+      const Level<double>& D0 = h->mgd.lv[0];
+      h->smd.nlaunch = &h->launches;
+      h->smd.setup(D0.gt, D0.en, D0.ec, s, h->flag);
+    }
   }
   k_weights<<<grid2(h->nx, h->ny, kBlk2), kBlk2, 0, s>>>(h->g64, h->en, h->ec, h->W);
   if (h->sw) {
@@ -1322,7 +1479,7 @@ bool opts_valid(const pyro_opts& o) {
          o.accel <= PYRO_ACCEL_ANDERSON && o.aa_beta > 0.0 && o.aa_beta <= 1.0 && o.smoother >= PYRO_SMOOTH_RBGS &&
          o.smoother <= PYRO_SMOOTH_MIXED && o.ras_inner >= 1 && o.cont_stages >= 0 && o.cont_iters >= 1 &&
          o.coarse_sweeps >= 1 && o.coarsen_ratio >= 1.5 && o.coarsen_ratio <= 8.0 &&
-         o.gram_schmidt >= 0 && o.gram_schmidt <= 2;
+         o.gram_schmidt >= 0 && o.gram_schmidt <= 2 && (o.schur == 0 || o.schur == 1);
 }
 
 std::vector<std::pair<int, int>> sizes_of(int nx, int ny, const pyro_opts& o) {
@@ -1354,6 +1511,7 @@ size_t footprint_bytes(int nx, int ny, const pyro_opts& o, int L) {
   const auto sz = sizes_of(nx, ny, o);
   b += mixed ? MG<float>::bytes(sz, o.kcycle) : MG<double>::bytes(sz, o.kcycle) - 2 * P * 8;
   b += 2 * kSubClusterMax * 4 * 8;
+  if (o.schur) b += mixed ? SchurMG<float>::bytes(nx, ny, P) : SchurMG<double>::bytes(nx, ny, P);
   b += 2 * (kMaxRestart + 2) * 8 + 2 * (size_t)kReduceBlocks * (kMaxRestart + 1) * 8 + 4 * kReduceBlocks * 8 +
        (size_t)kMaxRestart * kHcolStride * 8 + 64;
   return b;
@@ -1393,6 +1551,7 @@ void pyro_default_opts(pyro_opts* o) {
   o->coarsen_ratio = 2.0;
   o->coarsen_general = 1;
   o->gram_schmidt = 2;
+  o->schur = 0;
 }
 
 const char* pyro_version(void) { return "pyro-b300 0.1 (sm_103a)"; }
@@ -1496,6 +1655,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       CK(cudaDeviceSynchronize());
       h->mgf.alloc(A, h->g, Lx, Ly, sizes_of(nx, ny, o), false);
       h->mgf.setup_sub(A, o.cluster_cells);
+      if (o.schur) h->smf.alloc(A, nx, ny, h->P);
     } else {
       h->mgd.nu1 = o.nu1; h->mgd.nu2 = o.nu2; h->mgd.omega = o.omega_v; h->mgd.eta_mode = o.eta_coarsen;
       h->mgd.coarse_sweeps = o.coarse_sweeps;
@@ -1510,6 +1670,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->mgd.lv[0].ec = h->ec;
       if (!h->mgd.fused(0)) h->mgd.lv[0].kc = h->okc;  // FP64 level 0 shares the outer coefficients
       h->mgd.setup_sub(A, o.cluster_cells);
+      if (o.schur) h->smd.alloc(A, nx, ny, h->P);
     }
     CK(cudaMallocHost(&h->hbuf, 4 * kReduceBlocks * sizeof(double) + 1024));
     CK(cudaMallocHost(&h->hflag, sizeof(int)));
@@ -1548,29 +1709,9 @@ int pyro_stokes_precond(pyro_stokes h, const double* eta_n, const double* eta_c,
     ingest(h, r_p, h->V + 2 * h->P, 2, s);
     setup_eta(h, s);
     CK(cudaMemsetAsync(h->d_j, 0, sizeof(int), s));
-    if (h->mixed) {
-      Level<float>& L0 = h->mgf.lv[0];
-      k_precond_in<float><<<kReduceBlocks, kThreads, 0, s>>>(h->P, h->V, h->n3, h->d_j, L0.fx, L0.fy, L0.vx, L0.vy,
-                                                             nullptr);
-      h->mgf.cycle(0, s);
-      k_precond_out<float, double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->V, h->n3,
-                                                                       (double*)h->Z, h->n3, h->d_j, h->ec,
-                                                                       h->o.alpha_p, h->part2, nullptr);
-      k_sub_mean<double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, (double*)h->Z + 2 * h->P, h->n3, h->d_j, h->part2,
-                                                           kReduceBlocks);
-      CK(cudaMemcpyAsync(h->w, h->Z, h->n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    } else {
-      Level<double>& L0 = h->mgd.lv[0];
-      k_precond_in<double><<<kReduceBlocks, kThreads, 0, s>>>(h->P, h->V, h->n3, h->d_j, L0.fx, L0.fy, L0.vx, L0.vy,
-                                                              nullptr);
-      h->mgd.cycle(0, s);
-      k_precond_out<double, double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->V, h->n3,
-                                                                        (double*)h->Z, h->n3, h->d_j, h->ec,
-                                                                        h->o.alpha_p, h->part2, nullptr);
-      k_sub_mean<double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, (double*)h->Z + 2 * h->P, h->n3, h->d_j, h->part2,
-                                                           kReduceBlocks);
-      CK(cudaMemcpyAsync(h->w, h->Z, h->n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    }
+    // the same preconditioner body the Krylov iteration runs (V-cycle, pressure block, mean removal)
+    precond_any(h, s, h->V, h->n3, (double*)h->Z, h->n3, h->d_j, false);
+    CK(cudaMemcpyAsync(h->w, h->Z, h->n3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     double* outs[3] = {z_vx, z_vy, z_p};
     for (int k = 0; k < 3; ++k)
       CK(cudaMemcpyAsync(outs[k], h->w + k * h->P, h->P * sizeof(double),

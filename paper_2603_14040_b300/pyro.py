@@ -36,7 +36,7 @@ class PyroOpts(ctypes.Structure):
                 ("aa_beta", ctypes.c_double), ("smoother", ctypes.c_int), ("ras_inner", ctypes.c_int),
                 ("litho_guess", ctypes.c_int), ("cont_stages", ctypes.c_int), ("cont_iters", ctypes.c_int),
                 ("coarse_sweeps", ctypes.c_int), ("coarsen_ratio", ctypes.c_double),
-                ("coarsen_general", ctypes.c_int), ("gram_schmidt", ctypes.c_int)]
+                ("coarsen_general", ctypes.c_int), ("gram_schmidt", ctypes.c_int), ("schur", ctypes.c_int)]
 
 
 class PyroStats(ctypes.Structure):
@@ -100,6 +100,8 @@ def load_library(path=_LIB_PATH):
     lib.pyro_markers_max_dt.restype = I
     lib.pyro_markers_destroy.argtypes = [P]
     lib.pyro_markers_destroy.restype = None
+    lib.pyro_fp64_fma_rate.argtypes = [I, ctypes.POINTER(D), P]
+    lib.pyro_fp64_fma_rate.restype = I
     return lib
 
 
@@ -178,6 +180,15 @@ def _stream_handle(stream):
 
 def footprint(nx, ny, opts=None):
     return int(lib().pyro_stokes_footprint(nx, ny, ctypes.byref(opts) if opts is not None else None))
+
+
+def fp64_fma_rate(iters=4096, stream=None):
+    """pyro_fp64_fma_rate: measured FP64 FMA rate of the current GPU in TFLOP/s."""
+    out = ctypes.c_double(0.0)
+    st = lib().pyro_fp64_fma_rate(int(iters), ctypes.byref(out), _stream_handle(stream))
+    if st < 0:
+        raise PyroError(st, "pyro_fp64_fma_rate")
+    return out.value
 
 
 def residual_noalloc(nx, ny, Lx, Ly, bc, eta_n, eta_c, rho, g, vx, vy, p, r_vx, r_vy, r_p, rel_res, stream=None):
