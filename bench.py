@@ -92,28 +92,40 @@ def make_fields(n=1024):
     return grf_config(n, n, seed=2)
 
 
-def oracle_baseline(seconds_budget=20.0, sample_n=128):
-    """The FP64 CPU oracle (sparse direct solve) as it stands, on a bounded sample of the same
-    workload generator; returns solves/s scaled to the full grid by the cell ratio."""
+def oracle_baseline(workload, target_cells, sizes=(48, 64, 96), budget_s=25.0):
+    """The FP64 CPU oracle (sparse direct solve of the assembled system) as it stands, timed on a
+    bounded sample of the same generator at three sizes; the per-solve time is fitted as
+    t = a N^b (N = cells) and extrapolated to the workload's cell count. SuperLU factorises on one
+    thread; the fit exponent is reported (about 1.5-2 for these saddle-point systems)."""
     from oracle import stokes as S
-    from synth import grf_config
-    f = grf_config(sample_n, sample_n, seed=2)
-    t0 = time.perf_counter()
-    n_done = 0
-    while True:
-        S.solve_fields(sample_n, sample_n, 1.0, 1.0, f.eta_n, f.eta_c, f.rho, (0.0, 1.0))
-        n_done += 1
-        if time.perf_counter() - t0 > seconds_budget or n_done >= 50:
+    gen = {"layered": lambda n: __import__("synth").layered_config(n, n, seed=3),
+           "grf": lambda n: __import__("synth").grf_config(n, n, seed=2)}[workload]
+    rows = []
+    t_all = time.perf_counter()
+    for n in sizes:
+        f = gen(n)
+        ts = []
+        while True:
+            t0 = time.perf_counter()
+            S.solve_fields(n, n, 1.0, 1.0, f.eta_n, f.eta_c, f.rho, (0.0, 1.0))
+            ts.append(time.perf_counter() - t0)
+            if sum(ts) > budget_s / (2 * len(sizes)) or len(ts) >= 5:
+                break
+        rows.append((n * n, float(np.median(ts)), len(ts)))
+        if time.perf_counter() - t_all > budget_s:
             break
-    dt = (time.perf_counter() - t0) / n_done
-    scale = (sample_n * sample_n) / (1024.0 * 1024.0)
-    threads = os.environ.get("OMP_NUM_THREADS") or str(len(os.sched_getaffinity(0)))
-    return {"value": (1.0 / dt) * scale, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{n_done} direct solves (SuperLU, COLAMD, 2 refinement steps) of the same random-field "
-                       f"generator at {sample_n}x{sample_n}, {dt:.2f} s each; value = sample rate x "
-                       f"({sample_n}^2/1024^2) cell ratio (generous: the direct solve grows faster than linearly); "
-                       f"SuperLU factorisation is single-threaded; host affinity {threads} threads"),
-            "sample_seconds_per_solve": dt}
+    N = np.array([r[0] for r in rows], dtype=float)
+    T = np.array([r[1] for r in rows])
+    b, loga = np.polyfit(np.log(N), np.log(T), 1) if len(rows) >= 2 else (1.0, np.log(T[0] / N[0]))
+    t_target = float(np.exp(loga) * target_cells ** b)
+    threads = len(os.sched_getaffinity(0))
+    return {"value": 1.0 / t_target, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"direct FP64 solves (SuperLU, COLAMD, 2 refinement steps) of the same {workload} generator at "
+                       + ", ".join(f"{int(round(np.sqrt(r[0])))}^2 ({r[1]:.3f} s, median of {r[2]})" for r in rows)
+                       + f"; fitted t = a N^{b:.2f} over cells N and extrapolated to {target_cells} cells; SuperLU "
+                       f"factorises on one thread (host affinity {threads} threads)"),
+            "fit_exponent": float(b), "sample_seconds": [r[1] for r in rows], "sample_cells": [r[0] for r in rows],
+            "extrapolated_seconds_per_solve": t_target, "host_threads": threads}
 
 
 def vcycle_roofline_4096(peaks, iters=6, label="", launches=1, **opts):

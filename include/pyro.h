@@ -175,6 +175,14 @@ typedef struct {
                             one V-cycle of a smoothed-aggregation multigrid on the cell grid (2 x 2
                             aggregates, Galerkin coarse operators in a 5 x 5-box stencil, damped Jacobi
                             smoothing, dense coarsest inverse); 0 or 1 [0] */
+  int galerkin;          /* 1: every coarse level reached by halving takes the Galerkin operator R L P of
+                            the level above it (the V-cycle's own restriction and prolongation; a
+                            31-point stencil per velocity unknown) instead of the re-discretised
+                            operator of the transferred viscosity, and is smoothed by damped Jacobi
+                            (omega 0.6; red-black ordering does not decouple that stencil); the
+                            finest level keeps its smoother. Not in the paper: for viscosity that
+                            jumps by orders of magnitude within a coarse cell. Requires kcycle = 0
+                            and cluster_cells <= 0; 0 or 1 [0] */
 } pyro_opts;
 
 typedef struct {

@@ -42,6 +42,7 @@ from .stokes import Grid, assemble
 
 ETA_ARITH, ETA_GEOM = 0, 1
 MAX_COARSE = 1024
+GAL_OMEGA = 0.6   # damped-Jacobi smoothing on Galerkin levels
 
 
 def coarsen_grid(g, nxc=None, nyc=None):
@@ -294,8 +295,13 @@ def level_smoother(smoother, level):
 
 def smooth(h, level, f, x, nu, omega, phase):
     """nu smoothing steps on `level` with the level's smoother: damped RBGS sweeps (default),
-    damped Jacobi sweeps, or ceil(nu / inner) RAS passes of `inner` local Jacobi iterations."""
+    damped Jacobi sweeps, or ceil(nu / inner) RAS passes of `inner` local Jacobi iterations; a
+    Galerkin level is always smoothed by damped Jacobi with GAL_OMEGA."""
     L = h.L[level]
+    if h.gal[level]:
+        for _ in range(nu):
+            x = jacobi_sweep(L, f, x, GAL_OMEGA)
+        return x
     kind = level_smoother(h.smoother, level)
     if kind == "rbgs":
         for _ in range(nu):
@@ -315,7 +321,8 @@ def smooth(h, level, f, x, nu, omega, phase):
 # ---- hierarchy and V-cycle ---------------------------------------------------------------------
 class Hierarchy:
     def __init__(self, grid, eta_n, eta_c, coarsest_min=4, eta_mode=ETA_ARITH, n_lev=None, smoother="rbgs",
-                 ras_inner=4, ras_tile=32, coarse_sweeps=40, coarsen_ratio=2.0, coarsen_general=True):
+                 ras_inner=4, ras_tile=32, coarse_sweeps=40, coarsen_ratio=2.0, coarsen_general=True,
+                 galerkin=False):
         self.smoother, self.ras_inner, self.ras_tile = smoother, ras_inner, ras_tile
         self.coarse_sweeps = coarse_sweeps
         sizes = level_sizes(grid.nx, grid.ny, coarsest_min, coarsen_ratio, coarsen_general)
@@ -332,6 +339,16 @@ class Hierarchy:
         for f, c in zip(self.grids[:-1], self.grids[1:]):
             self.R.append(sp.block_diag([restriction_matrix(f, c, "vx"), restriction_matrix(f, c, "vy")]).tocsr())
             self.P.append(sp.block_diag([prolongation_matrix(f, c, "vx"), prolongation_matrix(f, c, "vy")]).tocsr())
+        # Galerkin coarse operators (not in the paper): a level reached by halving from a chain of
+        # halvings takes L_l = R_{l-1} L_{l-1} P_{l-1} with the cycle's own transfer operators
+        self.gal = [False] * len(self.grids)
+        if galerkin:
+            for l in range(1, len(self.grids)):
+                f, c = self.grids[l - 1], self.grids[l]
+                if not (c.nx * 2 == f.nx and c.ny * 2 == f.ny and (l == 1 or self.gal[l - 1])):
+                    break
+                self.L[l] = (self.R[l - 1] @ self.L[l - 1] @ self.P[l - 1]).tocsr()
+                self.gal[l] = True
         # the coarsest level is solved directly when it is small (<= MAX_COARSE velocity unknowns),
         # else by coarse_sweeps smoothing steps from zero (Sec. "Multigrid Cycles": a direct
         # method or a few smoothing iterations on the coarsest level)

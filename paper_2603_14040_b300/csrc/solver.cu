@@ -21,6 +21,7 @@
 #include "kernels_stream.cuh"
 #include "kernels_jacobi.cuh"
 #include "kernels_schur.cuh"
+#include "kernels_galerkin.cuh"
 
 using namespace pyro;
 
@@ -132,6 +133,7 @@ struct Level {
   T* Y() const { return cur ? vy2 : vy; }
   double *kpart = nullptr, *ks = nullptr;
   int kblocks = 0;
+  T* gal = nullptr;                    // Galerkin coarse operator R L P (2 x kGalSlots planes), else null
 };
 
 template <typename T>
@@ -152,6 +154,7 @@ struct MG {
   int smoother = PYRO_SMOOTH_RBGS;          // velocity smoother (MIXED: Jacobi on level 0, RAS below)
   int ras_inner = 4;                        // RAS-type Jacobi: local iterations per tile pass
   int tile_sweeps = 2;                      // FP32: sweeps fused per tile launch
+  int galerkin = 0;                         // 1: factor-2 coarse levels take R L P (damped-Jacobi smoothed)
   static constexpr long long kFuse64Cells = 65536;
   SubArgs<T> sub{};
   int sub_ncta = 8;  // CTAs of the sub-cycle cluster
@@ -168,12 +171,21 @@ struct MG {
 
   static bool kc_level(int l, int nlev, int kcycle) { return l >= 1 && l - 1 < kcycle && l < nlev - 1; }
 
-  static size_t bytes(const std::vector<std::pair<int, int>>& sz, int kcycle = 0) {
+  // level l takes a Galerkin operator when every level above it halves its predecessor
+  static bool gal_level(const std::vector<std::pair<int, int>>& sz, int l, int galerkin) {
+    if (!galerkin || l < 1) return false;
+    for (int k = 1; k <= l; ++k)
+      if (sz[k].first * 2 != sz[k - 1].first || sz[k].second * 2 != sz[k - 1].second) return false;
+    return true;
+  }
+
+  static size_t bytes(const std::vector<std::pair<int, int>>& sz, int kcycle = 0, int galerkin = 0) {
     size_t b = 0;
     const int nlev = (int)sz.size();
     for (int l = 0; l < nlev; ++l) {
       const size_t P = (size_t)(sz[l].second + 2) * (sz[l].first + 2);
       b += (size_t)(sizeof(T) == 8 ? 17 : 10) * P * sizeof(T);
+      if (gal_level(sz, l, galerkin)) b += (size_t)2 * kGalSlots * P * sizeof(T) + 256;
       if (kc_level(l, nlev, kcycle)) b += (size_t)6 * P * sizeof(T) + 5 * 296 * 8 + 64;
     }
     const size_t nc = (size_t)velocity_unknowns(sz.back().first, sz.back().second);
@@ -203,7 +215,8 @@ struct MG {
         L.kc = Coef<T>{k5, k5 + L.P, k5 + 2 * L.P, k5 + 3 * L.P, k5 + 4 * L.P};
         L.own_kc = true;
       }
-      if (tiles || smoother != PYRO_SMOOTH_RBGS) {
+      if (gal_level(sz, l, galerkin)) L.gal = A.get<T>((size_t)2 * kGalSlots * L.P);
+      if (tiles || smoother != PYRO_SMOOTH_RBGS || L.gal) {
         L.vx2 = A.get<T>(L.P); L.vy2 = A.get<T>(L.P);
         CK(cudaMemset(L.vx2, 0, L.P * sizeof(T)));
         CK(cudaMemset(L.vy2, 0, L.P * sizeof(T)));
@@ -228,7 +241,7 @@ struct MG {
   void setup_sub(DevAlloc& A, int cluster_cells) {
     ls = -1;
     if (cluster_cells <= 0 || (int)lv.size() > kSubMaxLevels || lv.size() < 2 || smoother != PYRO_SMOOTH_RBGS ||
-        !coarse_direct)
+        !coarse_direct || galerkin)
       return;
     for (size_t l = 0; l + 1 < lv.size(); ++l)
       if (!f2[l]) return;
@@ -321,10 +334,21 @@ struct MG {
         k_invdiag<T><<<grid2(L.g.nx, L.g.ny, kBlk2), kBlk2, 0, s>>>(L.gt, L.en, L.ec, L.idgx, L.idgy);
         count(1);
       }
+    for (size_t l = 1; l < lv.size(); ++l)
+      if (lv[l].gal) {
+        const Level<T>& F = lv[l - 1];
+        Level<T>& G = lv[l];
+        const GalSrc<T> src{F.gt, F.gal ? nullptr : F.en, F.gal ? nullptr : F.ec, F.gal, F.P};
+        k_gal_rap<T><<<grid2(G.g.nx, G.g.ny, kBlk2), kBlk2, 0, s>>>(src, G.gt, G.gal, G.P, flag);
+        count(1);
+      }
     const Level<T>& C = lv.back();
     if (!coarse_direct) return;
     CK(cudaMemsetAsync(Ainv, 0, (size_t)nc * nc * sizeof(double), s));
-    k_coarse_assemble<T><<<(nc + 127) / 128, 128, 0, s>>>(C.g, C.en, C.ec, Ainv, nc);
+    if (C.gal)
+      k_gal_coarse_assemble<T><<<(nc + 127) / 128, 128, 0, s>>>(C.gt, C.gal, C.P, Ainv, nc);
+    else
+      k_coarse_assemble<T><<<(nc + 127) / 128, 128, 0, s>>>(C.g, C.en, C.ec, Ainv, nc);
     if (nc > kCoarseInvertMulti) {
       double *a = Ainv, *b = Atmp;
       const dim3 gg((nc + 255) / 256, nc);
@@ -341,6 +365,7 @@ struct MG {
   }
 
   bool fused(int l) const {
+    if (lv[l].gal) return false;
     return tiles && (sizeof(T) == 4 || (long long)lv[l].g.nx * lv[l].g.ny <= kFuse64Cells);
   }
 
@@ -523,6 +548,18 @@ struct MG {
       k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, C->gt, L.X(), L.Y(), C->X(), C->Y());
       count(1);
     }
+    if (L.gal) {
+      // Galerkin level: damped Jacobi on the stored stencil (red-black ordering is not a Gauss-Seidel
+      // ordering of its couplings)
+      for (int k = 0; k < nsweeps; ++k) {
+        k_gal_jacobi<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, L.gal, L.P, L.X(), L.Y(),
+                                                                         L.cur ? L.vx : L.vx2, L.cur ? L.vy : L.vy2,
+                                                                         L.fx, L.fy, T(kGalOmega));
+        L.cur ^= 1;
+      }
+      count(nsweeps);
+      return;
+    }
     if (sm == PYRO_SMOOTH_RBGS) {
       for (int k = 0; k < nsweeps; ++k) sweep(l, s);
       return;
@@ -593,15 +630,23 @@ struct MG {
     if (fz && f2[l]) {
       resrestrict_tiles(l, s);  // also zeroes the coarse iterate
     } else if (!f2[l]) {
-      k_vresidual<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, L.rx,
-                                                                       L.ry, L.kc);
+      if (L.gal)
+        k_gal_resid<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, L.gal, L.P, L.X(), L.Y(), L.fx, L.fy,
+                                                                         L.rx, L.ry);
+      else
+        k_vresidual<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec,
+                                                                         L.rx, L.ry, L.kc);
       k_restrict_gen<T><<<grid2(C.g.nx, C.g.ny, blk(C)), blk(C), 0, s>>>(L.g, C.g, L.gt, L.rx, L.ry, C.fx, C.fy, C.vx,
                                                                           C.vy);
       count(2);
       C.cur = 0;
     } else {
-      k_vresidual<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec, L.rx,
-                                                                       L.ry, L.kc);
+      if (L.gal)
+        k_gal_resid<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, L.gal, L.P, L.X(), L.Y(), L.fx, L.fy,
+                                                                         L.rx, L.ry);
+      else
+        k_vresidual<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, L.X(), L.Y(), L.fx, L.fy, L.en, L.ec,
+                                                                         L.rx, L.ry, L.kc);
       k_restrict<T><<<grid2(C.g.nx, C.g.ny, blk(C)), blk(C), 0, s>>>(L.gt, C.gt, L.rx, L.ry, C.fx, C.fy, C.vx,
                                                                        C.vy);   // also zeroes the coarse iterate
       count(2);
@@ -1479,7 +1524,8 @@ bool opts_valid(const pyro_opts& o) {
          o.accel <= PYRO_ACCEL_ANDERSON && o.aa_beta > 0.0 && o.aa_beta <= 1.0 && o.smoother >= PYRO_SMOOTH_RBGS &&
          o.smoother <= PYRO_SMOOTH_MIXED && o.ras_inner >= 1 && o.cont_stages >= 0 && o.cont_iters >= 1 &&
          o.coarse_sweeps >= 1 && o.coarsen_ratio >= 1.5 && o.coarsen_ratio <= 8.0 &&
-         o.gram_schmidt >= 0 && o.gram_schmidt <= 2 && (o.schur == 0 || o.schur == 1);
+         o.gram_schmidt >= 0 && o.gram_schmidt <= 2 && (o.schur == 0 || o.schur == 1) &&
+         (o.galerkin == 0 || (o.galerkin == 1 && o.kcycle == 0 && o.cluster_cells <= 0));
 }
 
 std::vector<std::pair<int, int>> sizes_of(int nx, int ny, const pyro_opts& o) {
@@ -1509,7 +1555,7 @@ size_t footprint_bytes(int nx, int ny, const pyro_opts& o, int L) {
   if (o.cont_stages > 0) b += 2 * P * 8;   // full-contrast viscosity kept during continuation
   (void)L;
   const auto sz = sizes_of(nx, ny, o);
-  b += mixed ? MG<float>::bytes(sz, o.kcycle) : MG<double>::bytes(sz, o.kcycle) - 2 * P * 8;
+  b += mixed ? MG<float>::bytes(sz, o.kcycle, o.galerkin) : MG<double>::bytes(sz, o.kcycle, o.galerkin) - 2 * P * 8;
   b += 2 * kSubClusterMax * 4 * 8;
   if (o.schur) b += mixed ? SchurMG<float>::bytes(nx, ny, P) : SchurMG<double>::bytes(nx, ny, P);
   b += 2 * (kMaxRestart + 2) * 8 + 2 * (size_t)kReduceBlocks * (kMaxRestart + 1) * 8 + 4 * kReduceBlocks * 8 +
@@ -1552,6 +1598,7 @@ void pyro_default_opts(pyro_opts* o) {
   o->coarsen_general = 1;
   o->gram_schmidt = 2;
   o->schur = 0;
+  o->galerkin = 0;
 }
 
 const char* pyro_version(void) { return "pyro-b300 0.1 (sm_103a)"; }
@@ -1651,6 +1698,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->mgf.stream = (o.tile_fusion == 2 || o.tile_fusion == 3) ? o.tile_fusion - 1 : 0;
       h->mgf.tile_form = o.tile_fusion == 4 ? 1 : 0;
       h->mgf.tile_sweeps = o.tile_sweeps;
+      h->mgf.galerkin = o.galerkin;
       if (h->mgf.tiles) MG<float>::enable_tiles();
       CK(cudaDeviceSynchronize());
       h->mgf.alloc(A, h->g, Lx, Ly, sizes_of(nx, ny, o), false);
@@ -1664,6 +1712,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->mgd.ras_inner = o.ras_inner;
       if (o.smoother == PYRO_SMOOTH_RAS || o.smoother == PYRO_SMOOTH_MIXED) MG<double>::enable_ras();
       h->mgd.tiles = o.tile_fusion64 != 0;
+      h->mgd.galerkin = o.galerkin;
       if (h->mgd.tiles) MG<double>::enable_tiles();
       h->mgd.alloc(A, h->g, Lx, Ly, sizes_of(nx, ny, o), true);
       h->mgd.lv[0].en = h->en;

@@ -36,7 +36,8 @@ class PyroOpts(ctypes.Structure):
                 ("aa_beta", ctypes.c_double), ("smoother", ctypes.c_int), ("ras_inner", ctypes.c_int),
                 ("litho_guess", ctypes.c_int), ("cont_stages", ctypes.c_int), ("cont_iters", ctypes.c_int),
                 ("coarse_sweeps", ctypes.c_int), ("coarsen_ratio", ctypes.c_double),
-                ("coarsen_general", ctypes.c_int), ("gram_schmidt", ctypes.c_int), ("schur", ctypes.c_int)]
+                ("coarsen_general", ctypes.c_int), ("gram_schmidt", ctypes.c_int), ("schur", ctypes.c_int),
+                ("galerkin", ctypes.c_int)]
 
 
 class PyroStats(ctypes.Structure):
