@@ -656,7 +656,7 @@ def main():
         line["serving"] = serving_sample()
         line["adjoint"] = adjoint_sample()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_baseline()
+        line["cpu_baseline"] = oracle_baseline("grf", n * n)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
