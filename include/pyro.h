@@ -183,6 +183,12 @@ typedef struct {
                             finest level keeps its smoother. Not in the paper: for viscosity that
                             jumps by orders of magnitude within a coarse cell. Requires kcycle = 0
                             and cluster_cells <= 0; 0 or 1 [0] */
+  int inner_cg;          /* velocity block of the preconditioner: 0 one V-cycle (the paper); k >= 1: k
+                            steps of flexible conjugate gradients on L z_v = r_v from zero, each
+                            preconditioned by one V-cycle (one-term flexible recurrence, dot products
+                            reduced on the device). Not in the paper: on viscosity that jumps by orders
+                            of magnitude a single cycle leaves most of the velocity error, and each
+                            outer Krylov iteration saved also saves its orthogonalisation; 0..16 [0] */
 } pyro_opts;
 
 typedef struct {

@@ -416,13 +416,41 @@ def divergence(grid, zv):
     return (vx[i, j] - vx[i, jm]) / grid.dx + (vy[i, j] - vy[i - 1, j]) / grid.dy
 
 
-def uzawa_precond(h, r, eta_c, alpha=0.6, nu1=2, nu2=2, omega=1.0, literal_sign=False, kcycle=0, schur=None):
-    """z = M^-1 r for one Uzawa sweep: z_v = V-cycle(L, r_v), z_p = alpha S~^-1 (r_p - D z_v), then
+def velocity_fcg(h, f, steps, nu1=2, nu2=2, omega=1.0, kcycle=0):
+    """`steps` steps of flexible conjugate gradients on L x = f from x = 0, each preconditioned by
+    one V-cycle, with the one-term flexible recurrence (each direction L-conjugate to the previous
+    one; Notay, SIAM J. Sci. Comput. 22 (2000)). Not part of the paper, whose Uzawa sweep applies a
+    single V-cycle to the velocity block."""
+    L = h.L[0]
+    x = np.zeros_like(f)
+    r = f.copy()
+    d = q = None
+    for _ in range(steps):
+        z = vcycle(h, r, nu1, nu2, omega, kcycle=kcycle)
+        w = L @ z
+        if d is not None:
+            beta = (z @ q) / (d @ q)
+            z = z - beta * d
+            w = w - beta * q
+        alpha = (r @ z) / (z @ w)
+        x = x + alpha * z
+        r = r - alpha * w
+        d, q = z, w
+    return x
+
+
+def uzawa_precond(h, r, eta_c, alpha=0.6, nu1=2, nu2=2, omega=1.0, literal_sign=False, kcycle=0, schur=None,
+                  inner_cg=0):
+    """z = M^-1 r for one Uzawa sweep: z_v = V-cycle(L, r_v) (or `inner_cg` flexible-CG steps with that
+    cycle as preconditioner), z_p = alpha S~^-1 (r_p - D z_v), then
     the mean of z_p is removed (Eq. pressure_normalization). S~^-1 is eta_c (the paper's diagonal
     viscosity surrogate) unless `schur` (a WeightedBFBt) is given. `literal_sign` flips to the
     paper's printed sign alpha eta_c (D z_v - r_p) (used only to demonstrate the reading)."""
     g = h.grids[0]
-    zv = vcycle(h, r[:g.n_v], nu1, nu2, omega, kcycle=kcycle)
+    if inner_cg > 0:
+        zv = velocity_fcg(h, r[:g.n_v], inner_cg, nu1, nu2, omega, kcycle=kcycle)
+    else:
+        zv = vcycle(h, r[:g.n_v], nu1, nu2, omega, kcycle=kcycle)
     dz = divergence(g, zv)
     if schur is not None:
         zp = alpha * schur.apply(r[g.n_v:] - dz)

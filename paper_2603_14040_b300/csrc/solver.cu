@@ -22,6 +22,7 @@
 #include "kernels_jacobi.cuh"
 #include "kernels_schur.cuh"
 #include "kernels_galerkin.cuh"
+#include "kernels_fcg.cuh"
 
 using namespace pyro;
 
@@ -805,6 +806,25 @@ struct SchurMG {
   }
 };
 
+// ---- inner flexible CG on the finest velocity level (option inner_cg) -------------------------
+template <typename T>
+struct InnerCG {
+  T *xx = nullptr, *xy = nullptr, *wx = nullptr, *wy = nullptr, *dx = nullptr, *dy = nullptr, *qx = nullptr,
+    *qy = nullptr;
+  double *part = nullptr, *scal = nullptr;
+  static size_t bytes(size_t P) { return 8 * P * sizeof(T) + (2 * kReduceBlocks + 3) * sizeof(double) + 10 * 256; }
+  void alloc(DevAlloc& A, size_t P) {
+    T** arr[8] = {&xx, &xy, &wx, &wy, &dx, &dy, &qx, &qy};
+    for (T** a : arr) {
+      *a = A.get<T>(P);
+      CK(cudaMemset(*a, 0, P * sizeof(T)));
+    }
+    part = A.get<double>(2 * kReduceBlocks);
+    scal = A.get<double>(3);
+    CK(cudaMemset(scal, 0, 3 * sizeof(double)));
+  }
+};
+
 // ---- the handle -----------------------------------------------------------------------------
 struct pyro_stokes_s {
   int dev = 0;
@@ -837,6 +857,8 @@ struct pyro_stokes_s {
   MG<double> mgd;
   SchurMG<float> smf;                        // weighted BFBt pressure block (option schur = 1)
   SchurMG<double> smd;
+  InnerCG<float> icf;                         // inner flexible CG on the finest velocity level
+  InnerCG<double> icd;
   std::vector<cudaGraphExec_t> graphs;       // captured iteration graphs (per Krylov column with MGS)
   std::vector<long long> graph_kernel_counts;
   int cur_j = 0;                              // Krylov column of the step being launched or captured
@@ -875,6 +897,13 @@ int multidot(pyro_stokes_s* h, cudaStream_t s, const double* V, const int* d_cnt
 }
 
 template <typename T>
+InnerCG<T>& inner_of(pyro_stokes_s* h);
+template <>
+InnerCG<float>& inner_of<float>(pyro_stokes_s* h) { return h->icf; }
+template <>
+InnerCG<double>& inner_of<double>(pyro_stokes_s* h) { return h->icd; }
+
+template <typename T>
 SchurMG<T>& schur_of(pyro_stokes_s* h);
 template <>
 SchurMG<float>& schur_of<float>(pyro_stokes_s* h) { return h->smf; }
@@ -892,7 +921,33 @@ void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s, const double* in,
   mark(h, 1, s);
   mg.hooks = h->timing ? h->tev : nullptr;
   mg.nlaunch = &h->launches;
-  mg.cycle(0, s);
+  const T* zvx = nullptr;
+  const T* zvy = nullptr;
+  if (h->o.inner_cg > 0) {
+    // inner flexible CG on L z_v = r_v (the residual lives in the level-0 right-hand side), each step
+    // preconditioned by one V-cycle; the phase events time the first cycle only
+    InnerCG<T>& ic = inner_of<T>(h);
+    for (int k = 0; k < h->o.inner_cg; ++k) {
+      const int first = k == 0;
+      mg.cycle(0, s);
+      mg.hooks = nullptr;
+      k_fcg_apply<T><<<kReduceBlocks, kThreads, 0, s>>>(L0.gt, L0.X(), L0.Y(), L0.en, L0.ec, ic.qx, ic.qy, ic.wx,
+                                                        ic.wy, first, ic.part);
+      k_fcg_beta<<<1, kThreads, 0, s>>>(ic.part, kReduceBlocks, first, ic.scal);
+      k_fcg_orth<T><<<kReduceBlocks, kThreads, 0, s>>>(L0.gt, L0.X(), L0.Y(), ic.wx, ic.wy, L0.fx, L0.fy, ic.dx,
+                                                       ic.dy, ic.qx, ic.qy, ic.scal, first, ic.part);
+      k_fcg_alpha<<<1, kThreads, 0, s>>>(ic.part, kReduceBlocks, ic.scal);
+      k_fcg_update<T><<<kReduceBlocks, kThreads, 0, s>>>(L0.P, ic.dx, ic.dy, ic.qx, ic.qy, ic.xx, ic.xy, L0.fx,
+                                                         L0.fy, L0.vx, L0.vy, ic.scal, first);
+      h->launches += 5;
+    }
+    zvx = ic.xx;
+    zvy = ic.xy;
+  } else {
+    mg.cycle(0, s);
+    zvx = L0.X();
+    zvy = L0.Y();
+  }
   mg.hooks = nullptr;
   h->launches += 3;
   if (h->o.schur) {
@@ -900,7 +955,7 @@ void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s, const double* in,
     SchurMG<T>& sm = schur_of<T>(h);
     auto& F0 = sm.lv[0];
     sm.nlaunch = &h->launches;
-    k_precond_out_schur<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), in, in_stride, out,
+    k_precond_out_schur<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, zvx, zvy, in, in_stride, out,
                                                                    out_stride, d_idx, F0.f, isw);
     sm.cycle(0, s);
     const dim3 g2 = grid2(h->nx, h->ny, kBlk2);
@@ -912,7 +967,7 @@ void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s, const double* in,
                                                            h->part2);
     h->launches += 4;
   } else {
-    k_precond_out<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), in, in_stride, out, out_stride,
+    k_precond_out<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, zvx, zvy, in, in_stride, out, out_stride,
                                                              d_idx, h->ec, h->o.alpha_p, h->part2, isw);
   }
   k_sub_mean<TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, out + 2 * h->P, out_stride, d_idx, h->part2, kReduceBlocks);
@@ -1525,7 +1580,8 @@ bool opts_valid(const pyro_opts& o) {
          o.smoother <= PYRO_SMOOTH_MIXED && o.ras_inner >= 1 && o.cont_stages >= 0 && o.cont_iters >= 1 &&
          o.coarse_sweeps >= 1 && o.coarsen_ratio >= 1.5 && o.coarsen_ratio <= 8.0 &&
          o.gram_schmidt >= 0 && o.gram_schmidt <= 2 && (o.schur == 0 || o.schur == 1) &&
-         (o.galerkin == 0 || (o.galerkin == 1 && o.kcycle == 0 && o.cluster_cells <= 0));
+         (o.galerkin == 0 || (o.galerkin == 1 && o.kcycle == 0 && o.cluster_cells <= 0)) && o.inner_cg >= 0 &&
+         o.inner_cg <= 16;
 }
 
 std::vector<std::pair<int, int>> sizes_of(int nx, int ny, const pyro_opts& o) {
@@ -1558,6 +1614,7 @@ size_t footprint_bytes(int nx, int ny, const pyro_opts& o, int L) {
   b += mixed ? MG<float>::bytes(sz, o.kcycle, o.galerkin) : MG<double>::bytes(sz, o.kcycle, o.galerkin) - 2 * P * 8;
   b += 2 * kSubClusterMax * 4 * 8;
   if (o.schur) b += mixed ? SchurMG<float>::bytes(nx, ny, P) : SchurMG<double>::bytes(nx, ny, P);
+  if (o.inner_cg) b += mixed ? InnerCG<float>::bytes(P) : InnerCG<double>::bytes(P);
   b += 2 * (kMaxRestart + 2) * 8 + 2 * (size_t)kReduceBlocks * (kMaxRestart + 1) * 8 + 4 * kReduceBlocks * 8 +
        (size_t)kMaxRestart * kHcolStride * 8 + 64;
   return b;
@@ -1599,6 +1656,7 @@ void pyro_default_opts(pyro_opts* o) {
   o->gram_schmidt = 2;
   o->schur = 0;
   o->galerkin = 0;
+  o->inner_cg = 0;
 }
 
 const char* pyro_version(void) { return "pyro-b300 0.1 (sm_103a)"; }
@@ -1704,6 +1762,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->mgf.alloc(A, h->g, Lx, Ly, sizes_of(nx, ny, o), false);
       h->mgf.setup_sub(A, o.cluster_cells);
       if (o.schur) h->smf.alloc(A, nx, ny, h->P);
+      if (o.inner_cg) h->icf.alloc(A, h->P);
     } else {
       h->mgd.nu1 = o.nu1; h->mgd.nu2 = o.nu2; h->mgd.omega = o.omega_v; h->mgd.eta_mode = o.eta_coarsen;
       h->mgd.coarse_sweeps = o.coarse_sweeps;
@@ -1720,6 +1779,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       if (!h->mgd.fused(0)) h->mgd.lv[0].kc = h->okc;  // FP64 level 0 shares the outer coefficients
       h->mgd.setup_sub(A, o.cluster_cells);
       if (o.schur) h->smd.alloc(A, nx, ny, h->P);
+      if (o.inner_cg) h->icd.alloc(A, h->P);
     }
     CK(cudaMallocHost(&h->hbuf, 4 * kReduceBlocks * sizeof(double) + 1024));
     CK(cudaMallocHost(&h->hflag, sizeof(int)));

@@ -43,7 +43,7 @@ def test_apply_matches_oracle(nx, ny, Lx, Ly, bc):
 
 def _precond_case(nx, ny, Lx, Ly, bc, prec, seed, kcycle=0, cluster_cells=0, tile_fusion=1, eta_coarsen=0,
                   eta=None, smoother=0, ras_inner=4, omega=1.0, coarsen_general=1, coarsen_ratio=2.0, schur=0,
-                  galerkin=0):
+                  galerkin=0, inner_cg=0):
     kind, vt = BCS[bc]
     g = S.Grid(nx, ny, Lx, Ly, S.BC(kind, vt))
     en, ec = rand_eta(nx, ny, seed, -1, 1) if eta is None else eta
@@ -54,12 +54,13 @@ def _precond_case(nx, ny, Lx, Ly, bc, prec, seed, kcycle=0, cluster_cells=0, til
                        ras_inner=ras_inner, ras_tile=32, coarsen_ratio=coarsen_ratio,
                        coarsen_general=bool(coarsen_general), galerkin=bool(galerkin))
     sch = M.WeightedBFBt(S.assemble(g, en, ec)) if schur else None
-    z = M.uzawa_precond(h_or, r, ec, alpha=1.0, nu1=2, nu2=2, omega=omega, kcycle=kcycle, schur=sch)
+    z = M.uzawa_precond(h_or, r, ec, alpha=1.0, nu1=2, nu2=2, omega=omega, kcycle=kcycle, schur=sch,
+                        inner_cg=inner_cg)
     zx, zy, zp = S.vector_to_fields(g, z, fill_ghosts=False)
     h = P.Stokes(nx, ny, Lx, Ly, bc=P.make_bc(kind, vt), prec=prec, kcycle=kcycle, cluster_cells=cluster_cells,
                  tile_fusion=tile_fusion, tile_fusion64=1 if tile_fusion else 0, eta_coarsen=eta_coarsen, coarsest_min=2,
                  smoother=smoother, ras_inner=ras_inner, omega_v=omega, coarsen_general=coarsen_general,
-                 coarsen_ratio=coarsen_ratio, schur=schur, galerkin=galerkin)
+                 coarsen_ratio=coarsen_ratio, schur=schur, galerkin=galerkin, inner_cg=inner_cg)
     Zx, Zy, Zp = zeros(ny, nx), zeros(ny, nx), zeros(ny, nx)
     h.precond(dev(en), dev(ec), dev(rx), dev(ry), dev(rp), Zx, Zy, Zp)
     torch.cuda.synchronize()
@@ -475,3 +476,17 @@ def test_galerkin_bfbt_solve_of_the_layered_field_matches_direct_oracle(prec):
     # (at a viscosity contrast of 1e9 the residual is amplified up to 1e4-fold into p); the bounds
     # allow a stop anywhere below tol
     assert rel(x[:nv], xd[:nv]) <= 1e-6 and rel(x[nv:], xd[nv:]) <= 5e-6
+
+
+
+@pytest.mark.parametrize("nx,ny,Lx,Ly", [(16, 16, 1, 1), (48, 80, 0.6, 1.0), (256, 128, 2, 1)])
+@pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
+@pytest.mark.parametrize("steps,schur,galerkin,tf", [(1, 0, 0, 1), (3, 0, 0, 1), (3, 1, 0, 0), (4, 1, 1, 1)])
+def test_preconditioner_inner_flexible_cg_matches_oracle(nx, ny, Lx, Ly, prec, steps, schur, galerkin, tf):
+    """Inner flexible CG on the finest velocity level (V-cycle preconditioned, device-side dot
+    products), alone and with the weighted BFBt block and Galerkin coarse levels, step by step against
+    the oracle's plain recurrence."""
+    gpu, ora, nlev = _precond_case(nx, ny, Lx, Ly, "mixed", prec, 43, schur=schur, galerkin=galerkin,
+                                   inner_cg=steps, tile_fusion=tf)
+    for a, b in zip(gpu, ora):
+        assert rel(a, b) <= (1e-10 if prec == P.PREC_FP64 else 1e-3), (rel(a, b), nlev)
