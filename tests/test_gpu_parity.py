@@ -232,6 +232,17 @@ def _solve_gpu(f, g_vec, tol, prec, bc=None, Lx=1.0, Ly=1.0, host_ptrs=False, **
     return (host(vx), host(vy), host(p)), st
 
 
+def _record(key, value):
+    # optional log of the achieved errors (the tests assert their bounds either way)
+    import json
+    import os
+    out = os.environ.get("PYRO_PARITY_OUT")
+    if out:
+        d = json.load(open(out)) if os.path.exists(out) else {}
+        d[key] = {k: float(v) for k, v in value.items()}
+        json.dump(d, open(out, "w"), indent=1)
+
+
 def _check_against_direct(f, out, st, bc=S.BC(), Lx=1.0, Ly=1.0, g_vec=(0.0, 1.0), tol=1e-10, tol_err=1e-8):
     """Element-wise comparison with the oracle's direct solve; returns (velocity, pressure) errors.
     The oracle also recomputes the energy residual of the GPU iterate from its own assembly."""
@@ -261,9 +272,11 @@ def test_sinker_64_matches_direct_oracle(prec):
     f = sinker(64, 64)
     out, st = _solve_gpu(f, (0.0, 1.0), 1e-10, prec)
     ev, ep = _check_against_direct(f, out, st, tol=1e-10, tol_err=None)
+    _record(f"sinker64_{prec}_tol1e-10", {"du": ev, "dp": ep, "iters": st.iters, "rel_energy": st.rel_energy_res})
     assert ev <= 1e-7 and ep <= 1e-7
     out, st = _solve_gpu(f, (0.0, 1.0), 1e-12, prec)
-    _check_against_direct(f, out, st, tol=1e-12, tol_err=1e-8)
+    ev, ep = _check_against_direct(f, out, st, tol=1e-12, tol_err=1e-8)
+    _record(f"sinker64_{prec}_tol1e-12", {"du": ev, "dp": ep, "iters": st.iters, "rel_energy": st.rel_energy_res})
 
 
 @pytest.mark.parametrize("bc", ["noslip", "mixed"])
