@@ -234,6 +234,43 @@ def accelerator_sample(f, n, steps=3):
     return res
 
 
+def layered_sample(n=1024, steps=3):
+    """The layered workload's recipe (stiff lid 1e6, mantle 1 +- 50 %, 64 inclusions 10^U[-3,3]) at
+    n x n, solved to 1e-10 with the options that converge on it: weighted BFBt pressure block, 5
+    inner flexible-CG steps per preconditioner application, FGMRES(200), V(4,4); mixed and FP64."""
+    import torch
+    import paper_2603_14040_b300 as P
+    from synth import layered_config
+    f = layered_config(n, n, seed=3)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    en, ec, rho = dev(f.eta_n), dev(f.eta_c), dev(f.rho)
+    outs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
+    res = {"grid": [n, n], "options": "schur=1 (weighted BFBt), inner_cg=5, restart_m=200, V(4,4), tol 1e-10"}
+    sols = {}
+    for prec, name in ((P.PREC_MIXED, "mixed"), (P.PREC_FP64, "fp64")):
+        h = P.Stokes(n, n, prec=prec, schur=1, inner_cg=5, restart_m=200, nu1=4, nu2=4, max_iter=3000)
+        h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
+        ts = []
+        for _ in range(steps if name == "mixed" else 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            st = h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        sols[name] = [o.clone() for o in outs]
+        res[name] = {"ms": float(np.median(ts)), "solves_per_s": 1e3 / float(np.median(ts)), "iters": st.iters,
+                     "status": st.status, "rel_energy_res": st.rel_energy_res}
+        h.close()
+    a, b = sols["mixed"], sols["fp64"]
+    res["rel_diff_mixed_vs_fp64_v"] = float(torch.linalg.norm(torch.cat([a[0].flatten(), a[1].flatten()]) -
+                                                              torch.cat([b[0].flatten(), b[1].flatten()])) /
+                                            torch.linalg.norm(torch.cat([b[0].flatten(), b[1].flatten()])))
+    res["rel_diff_mixed_vs_fp64_p"] = float(torch.linalg.norm(a[2] - b[2]) / torch.linalg.norm(b[2]))
+    return res
+
+
 def marker_sample(n=1024, per_cell=16, reps=5):
     """The marker steps of the marker-in-cell loop around the solve: 16 markers per cell on 1024^2,
     uniform random positions; marker -> basic nodes (deterministic bucketed gather), grid -> markers
@@ -385,45 +422,157 @@ def serving_sample(n_req=48, slots=4, max_iter=3000, restart_m=200, seed=4, nu=8
     return st
 
 
-def adjoint_sample(members=64, n=512):
-    """The adjoint batch: 64 members on 512^2, forward solve + adjoint (dJ/dlog eta through
-    autograd) per member; the observation solve of each member is outside the timed region."""
+def serving_sweep(n_req=40, slots=4, sizes=(128, 256, 512, 1024), seed=4, nu=8, max_iter=3000):
+    """Serving on the config-4 request distribution (ny = n, nx = a n, a in {1, 2, 4}, 16 inclusions of
+    contrast 10^U[2,6], tol 1e-8), n restricted to `sizes` (the 2048 rows of the distribution need
+    handles of up to 170 GB each, more than a 4-slot share of the device). Measures: the
+    single-slot service capacity (sequential pass, warm handle pool); saturation throughput with all
+    requests submitted at once on 1 slot and on `slots` slots (the device overlap of concurrent
+    solves); and p50 / p99 latency and throughput for Poisson arrivals at 0.5, 0.8, 1.0 and 1.2 x
+    the single-slot capacity."""
+    import torch
+    from synth import serving_request
+    from paper_2603_14040_b300.serving import SolveServer, Request, PyroBackend, latency_stats, poisson_arrivals
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    src = []
+    for k in range(n_req):
+        f, C = serving_request(k, base_seed=seed, sizes=sizes)
+        src.append((f, C))
+
+    def fresh():
+        return [Request(rid=k, nx=f.nx, ny=f.ny, Lx=f.Lx, Ly=f.Ly, eta_n=dev(f.eta_n), eta_c=dev(f.eta_c),
+                        rho=dev(f.rho), g=(0.0, 1.0), tol=1e-8) for k, (f, C) in enumerate(src)]
+
+    be = PyroBackend(opts_kw={"max_iter": max_iter, "prec": 1, "nu1": nu, "nu2": nu},
+                     restart_choices=(200, 100, 50, 30))
+    out = {"requests": n_req, "sizes": list(sizes), "aspects": [1, 2, 4], "cycle": f"V({nu},{nu})",
+           "cells_total": int(sum(f.nx * f.ny for f, _ in src))}
+    # warm pass (creates and captures every shape's handle), then the timed sequential pass
+    for label, nslots in (("warm", 1), ("sequential", 1)):
+        srv = SolveServer(be, max_slots=nslots)
+        reqs = fresh()
+        t0 = time.perf_counter()
+        for r in reqs:
+            srv.submit(r)
+            srv.drain(timeout=3600)
+        dt = time.perf_counter() - t0
+        srv.close()
+        if label == "sequential":
+            out["single_slot_capacity_per_s"] = n_req / dt
+            out["converged"] = sum(1 for r in reqs if r.status == 0)
+            out["mean_iters"] = float(np.mean([r.iters for r in reqs]))
+    cap = out["single_slot_capacity_per_s"]
+    for nslots in (1, slots):
+        srv = SolveServer(be, max_slots=nslots)
+        reqs = fresh()
+        t0 = time.perf_counter()
+        for r in reqs:
+            srv.submit(r)
+        srv.drain(timeout=3600)
+        dt = time.perf_counter() - t0
+        srv.close()
+        out[f"saturation_{nslots}_slots"] = {"throughput_per_s": n_req / dt, "max_concurrent": srv.max_concurrent}
+    out["overlap_speedup"] = (out[f"saturation_{slots}_slots"]["throughput_per_s"] /
+                              out["saturation_1_slots"]["throughput_per_s"])
+    out["arrival_sweep"] = {}
+    for frac in (0.5, 0.8, 1.0, 1.2):
+        rate = frac * cap
+        arr = poisson_arrivals(n_req, rate, seed)
+        srv = SolveServer(be, max_slots=slots)
+        reqs = fresh()
+        t_start = time.perf_counter()
+        for r, a in zip(reqs, arr):
+            while time.perf_counter() - t_start < a:
+                time.sleep(0.0005)
+            r.arrival = 0.0
+            srv.submit(r)
+        done = srv.drain(timeout=3600)
+        srv.close()
+        st = latency_stats(done)
+        st.update({"arrival_rate_per_s": rate, "max_concurrent": srv.max_concurrent,
+                   "converged": sum(1 for r in done if r.status == 0)})
+        out["arrival_sweep"][f"{frac}x"] = st
+    return out
+
+
+def adjoint_sample(members=64, n=512, slots=4):
+    """The adjoint batch: 64 members on 512^2 (log10 eta random fields, seeds 500..563), each a forward
+    solve, J = 1/2 |vx(top row) - vx_obs|^2, an adjoint solve and the strain-rate products, chained to
+    dJ/dlog(eta) (dJ/dlog eta = eta dJ/deta; the same arithmetic as the torch.autograd.Function, called
+    directly so that members on different handles run concurrently instead of queueing behind the
+    autograd engine's device thread). Members are spread over `slots` handles, each on its own host
+    thread and CUDA stream; the batch is also run on one slot. The observation solves (eta perturbed
+    by 10^(0.1 xi)) are outside the timed region. Mixed precision, tol 1e-10."""
+    import threading
     import torch
     import paper_2603_14040_b300 as P
     from synth import adjoint_member
-    from paper_2603_14040_b300.autograd import stokes_solve, surface_misfit
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=3000)
-    hp = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=3000)
-    times, norms = [], []
-    # warm-up (captures the iteration graph of both handles outside the timed region)
-    base, pert = adjoint_member(0, n, n)
-    warm = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
-    for hh in (h, hp):
-        hh.solve(dev(base.eta_n), dev(base.eta_c), dev(base.rho), (0.0, 1.0), 1e-10, *warm)
+    data = []
+    hobs = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=3000)
     for b in range(members):
         base, pert = adjoint_member(b, n, n)
         obs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
-        hp.solve(dev(pert.eta_n), dev(pert.eta_c), dev(pert.rho), (0.0, 1.0), 1e-10, *obs)
-        vx_obs = obs[0][1].clone()
-        log_ec = dev(np.log(np.where(base.eta_c > 0, base.eta_c, 1.0))).requires_grad_(True)
-        log_en = dev(np.log(np.where(base.eta_n > 0, base.eta_n, 1.0))).requires_grad_(True)
+        hobs.solve(dev(pert.eta_n), dev(pert.eta_c), dev(pert.rho), (0.0, 1.0), 1e-10, *obs)
+        data.append((dev(base.eta_n), dev(base.eta_c), dev(base.rho), obs[0][1].clone()))
+    hobs.close()
+    torch.cuda.synchronize()
+
+    def member(h, stream, b, rec):
+        en, ec, rho, vx_obs = data[b]
+        with torch.cuda.stream(stream):
+            t0 = time.perf_counter()
+            out = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
+            sf = h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *out, stream=stream)
+            d = torch.zeros_like(out[0])
+            d[1, 1:n] = out[0][1, 1:n] - vx_obs[1:n]
+            zero = torch.zeros_like(d)
+            gn, gc = torch.zeros_like(d), torch.zeros_like(d)
+            sa = h.adjoint(d, zero, zero, 1e-10, gn, gc, None, stream=stream)
+            glog_c = gc * ec
+            glog_n = gn * en
+            gnorm = float(torch.linalg.norm(glog_c))
+            stream.synchronize()
+            rec[b] = {"ms": (time.perf_counter() - t0) * 1e3, "fwd_iters": sf.iters, "adj_iters": sa.iters,
+                      "grad_norm": gnorm, "grad_n_norm": float(torch.linalg.norm(glog_n))}
+
+    def run(nslots):
+        hs = [P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=3000) for _ in range(nslots)]
+        ss = [torch.cuda.Stream() for _ in range(nslots)]
+        rec = {}
+        for k in range(nslots):       # warm-up: capture each handle's iteration graph
+            member(hs[k], ss[k], k, {})
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        mask_c = torch.zeros_like(log_ec); mask_c[1:n + 1, 1:n + 1] = 1
-        mask_n = torch.zeros_like(log_en); mask_n[:n + 1, :n + 1] = 1
-        vx, vy, p = stokes_solve(torch.exp(log_en) * mask_n, torch.exp(log_ec) * mask_c, dev(base.rho), h,
-                                 (0.0, 1.0), 1e-10)
-        J = surface_misfit(vx, vx_obs)
-        J.backward()
-        torch.cuda.synchronize()
-        times.append(time.perf_counter() - t0)
-        norms.append(float(torch.linalg.norm(log_ec.grad)))
-    ms = np.array(times) * 1e3
-    return {"members": members, "grid": n, "ms_per_member_forward_plus_adjoint": float(ms.mean()),
-            "batch_s": float(ms.sum() / 1e3), "ms_p50": float(np.percentile(ms, 50)),
-            "ms_max": float(ms.max()), "grad_norm_log_eta_c_range": [float(min(norms)), float(max(norms))],
-            "note": "graphs captured before timing"}
+
+        def worker(k):
+            for b in range(k, members, nslots):
+                member(hs[k], ss[k], b, rec)
+        th = [threading.Thread(target=worker, args=(k,)) for k in range(nslots)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        wall = time.perf_counter() - t0
+        for h in hs:
+            h.close()
+        return wall, rec
+
+    wall1, rec1 = run(1)
+    wallk, reck = run(slots)
+    ms = np.array([reck[b]["ms"] for b in range(members)])
+    its = np.array([reck[b]["fwd_iters"] + reck[b]["adj_iters"] for b in range(members)])
+    slow = int(np.argmax([rec1[b]["ms"] for b in range(members)]))
+    return {"members": members, "grid": n, "slots": slots, "batch_s": wallk, "batch_s_one_slot": wall1,
+            "overlap_speedup": wall1 / wallk, "members_per_s": members / wallk,
+            "ms_per_member_one_slot": {"p50": float(np.percentile([rec1[b]["ms"] for b in range(members)], 50)),
+                                       "max": float(max(rec1[b]["ms"] for b in range(members)))},
+            "iters_fwd_plus_adj": {"min": int(its.min()), "p50": float(np.median(its)), "max": int(its.max())},
+            "slowest_member_one_slot": {"member": slow, **rec1[slow]},
+            "ms_in_mix": {"p50": float(np.percentile(ms, 50)), "max": float(ms.max())},
+            "grad_norm_log_eta_c_range": [float(min(r["grad_norm"] for r in reck.values())),
+                                          float(max(r["grad_norm"] for r in reck.values()))],
+            "note": "graphs captured before timing; observation solves outside the timed region"}
 
 
 def profile_solve(args):
@@ -447,26 +596,41 @@ def profile_solve(args):
 
 
 def run_reference(args, rank, world):
+    """The reference arm of this workload: the FP64 CPU oracle as it stands (direct solve of the
+    assembled system) on rank 0's host cores. Each step is one direct solve of the same generator at
+    96^2; the power-law exponent of the solve time over the cell count is fitted once from solves at
+    48^2 and 64^2 (untimed), and the step time is extrapolated to the workload's cell count with it."""
     if rank != 0:
         return
-    times = []
     from oracle import stokes as S
     from synth import grf_config
-    n = 128
+    calib = []
+    for m in (48, 64):
+        f = grf_config(m, m, seed=2)
+        t0 = time.perf_counter()
+        S.solve_fields(m, m, 1.0, 1.0, f.eta_n, f.eta_c, f.rho, (0.0, 1.0))
+        calib.append((m * m, time.perf_counter() - t0))
+    n = 96
     f = grf_config(n, n, seed=2)
+    times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         S.solve_fields(n, n, 1.0, 1.0, f.eta_n, f.eta_c, f.rho, (0.0, 1.0))
         if k >= args.warmup:
             times.append(time.perf_counter() - t0)
     dt = float(np.mean(times))
-    value = (1.0 / dt) * (n * n) / (1024.0 * 1024.0)
+    pts = calib + [(n * n, float(np.median(times)))]
+    b = float(np.polyfit(np.log([p[0] for p in pts]), np.log([p[1] for p in pts]), 1)[0])
+    target = WORKLOAD["nx"] * WORKLOAD["ny"]
+    t_target = dt * (target / (n * n)) ** b
+    value = 1.0 / t_target
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_target * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": WORKLOAD,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step one direct FP64 solve of the same generator at {n}x{n}; "
-                                       f"value scaled by the cell ratio to 1024x1024"},
+                             "sample": (f"each step one direct FP64 solve (SuperLU, one thread) of the same generator at "
+                                        f"{n}x{n} ({dt:.3f} s mean); time extrapolated to {target} cells with the "
+                                        f"fitted exponent {b:.2f} (from 48^2, 64^2, 96^2)")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -503,6 +667,9 @@ def main():
     ap.add_argument("--smoother", type=int, default=0, help="pyro_opts.smoother of the --profile solve")
     ap.add_argument("--omega", type=float, default=1.0, help="pyro_opts.omega_v of the --profile solve")
     ap.add_argument("--accel", type=int, default=0, help="pyro_opts.accel of the --profile solve")
+    ap.add_argument("--serving-sweep", action="store_true",
+                    help="only the serving measurement on the config-4 request distribution (n <= 1024): capacity, "
+                         "1-slot vs 4-slot saturation, arrival-rate sweep")
     ap.add_argument("--markers", action="store_true",
                     help="only the marker sample (16.8 M markers on 1024^2: interpolation both ways and one "
                          "advection step per scheme), for ncu captures")
@@ -514,6 +681,9 @@ def main():
         return profile_solve(args)
     if args.markers:
         print(json.dumps({"markers": marker_sample(reps=1)}))
+        return
+    if args.serving_sweep:
+        print(json.dumps({"serving_sweep": serving_sweep()}))
         return
     if args.impl == "reference":
         # the oracle runs on rank 0's host cores; the other ranks exit without work
@@ -594,25 +764,28 @@ def main():
            "api": "pyro_stokes_solve with host pointers (library stages the copies)"}
 
     # roofline of the dominant kernel: finest-level RBGS sweep (4 launches vx-red, vx-black, vy-red,
-    # vy-black). Algorithmic per cell and sweep: read eta_n, eta_c, fx, fy, vx, vy + write vx, vy.
+    # vy-black), FP64. Algorithmic per cell and sweep: read eta_n, eta_c, fx, fy, vx, vy + write vx,
+    # vy = 64 B; arithmetic: per velocity point the off-diagonal sum on precomputed
+    # coefficients (6 products, 2 differences, 5 sums) and the update (2) = 15 flop, 30 per cell.
+    # B300's FP64 rate binds it, so the bound is the FP64 rate measured in this run.
     peaks = load_peaks()
     sweeps = max(counts["l0_sweeps"], 1)
     sweep_ms = (phases["l0_pre_smooth"] + phases["l0_post_smooth"]) / sweeps
     cells = n * n
-    bytes_per_sweep = 8 * 8 * cells
-    # per velocity point: off-diagonal sum on precomputed coefficients (6 products, 2 differences,
-    # 5 sums) and the update (f - sum) / diag (2): 15 flop
-    flops_per_sweep = 2 * 15 * cells
+    bytes_per_sweep = 64 * cells
+    flops_per_sweep = 30 * cells
     achieved_flops = flops_per_sweep / (sweep_ms / 1e3) / 1e12
-    fp64_peak = 1.25  # TFLOP/s nominal B300 FP64 (about 2 FMA per clock per SM at 2.03 GHz); a probe measured 1.13
+    fp64_peak = P.fp64_fma_rate()
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    hbm_achieved = bytes_per_sweep / (sweep_ms / 1e3) / 1e9
     roof = {"kernel": "k_rbgs<double> finest level (one sweep = 4 launches)", "bound": "alu",
             "achieved": achieved_flops, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved_flops / fp64_peak,
+            "peak_source": "FP64 FMA rate measured in this run (pyro_fp64_fma_rate: FMA chains, CUDA events), of measured",
             "traffic": 4 * 59.579e6, "traffic_unit": "B per sweep",
             "traffic_source": "ncu dram__bytes_read+write of the level-0 vx-red launch (59.58 MB, profiles/k_rbgs_fp64_1024_level0.md) x 4 half-sweeps",
-            "fp64_pipe_active_pct_ncu": 78.1,
-            "peak_source": "nominal B300 FP64 rate 1.25 TFLOP/s (148 SMs x ~2.08 FMA/clk x 2 flop x 2.03 GHz); not in MEASURED_PEAKS.json",
-            "flop_per_cell_sweep": 30,
-            "hbm_equiv_GBps": bytes_per_sweep / (sweep_ms / 1e3) / 1e9, "hbm_peak_measured": peaks.get("hbm_gbs"),
+            "fp64_pipe_active_pct_ncu": 78.1, "flop_per_cell_sweep": 30, "alg_bytes_per_cell_sweep": 64,
+            "hbm": {"achieved_GBps": hbm_achieved, "peak_GBps": hbm_peak, "frac": hbm_achieved / hbm_peak,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6400 GB/s"},
             "sweep_ms": sweep_ms, "phase_ms_per_iter": {k: v / max(counts["iterations"], 1) for k, v in phases.items()}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -649,6 +822,7 @@ def main():
     # single-GPU samples and the CPU baseline: at N = 1 only (at N > 1 they would hold every GPU of
     # the job while rank 0 alone works)
     if rank == 0 and world == 1 and not args.no_extras:
+        line["layered_1024"] = layered_sample()
         line["vcycle_roofline"] = vcycle_rooflines(peaks)
         line["accelerators"] = accelerator_sample(f, n)
         line["markers"] = marker_sample()
