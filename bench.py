@@ -576,23 +576,24 @@ def adjoint_sample(members=64, n=512, slots=4):
 
 
 def profile_solve(args):
-    """One solve (for ncu captures): random-viscosity workload at N x N, given precision, restart
-    length and iteration cap; prints a one-line summary."""
+    """One solve (for ncu captures): the random-viscosity or layered workload at N x N, given
+    precision, restart length, iteration cap and preconditioner options; prints a one-line summary."""
     import torch
     import paper_2603_14040_b300 as P
-    from synth import grf_config
+    from synth import grf_config, layered_config
     n = args.profile
-    f = grf_config(n, n, seed=2)
+    f = layered_config(n, n, seed=3) if args.workload == "layered" else grf_config(n, n, seed=2)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     en, ec, rho = dev(f.eta_n), dev(f.eta_c), dev(f.rho)
     outs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
     prec = P.PREC_MIXED if args.prec == "mixed" else P.PREC_FP64
     h = P.Stokes(n, n, prec=prec, max_iter=args.max_iter, restart_m=args.restart, tile_fusion=args.tile_fusion,
-                 tile_sweeps=args.tile_sweeps, smoother=args.smoother, omega_v=args.omega, accel=args.accel)
+                 tile_sweeps=args.tile_sweeps, smoother=args.smoother, omega_v=args.omega, accel=args.accel,
+                 schur=args.schur, inner_cg=args.inner_cg, nu1=args.nu, nu2=args.nu)
     st = h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_solve": n, "prec": args.prec, "iters": st.iters, "status": st.status,
-                      "kernel_launches": st.kernel_launches}))
+    print(json.dumps({"profile_solve": n, "workload": args.workload, "prec": args.prec, "iters": st.iters,
+                      "status": st.status, "kernel_launches": st.kernel_launches}))
 
 
 def run_reference(args, rank, world):
@@ -667,6 +668,10 @@ def main():
     ap.add_argument("--smoother", type=int, default=0, help="pyro_opts.smoother of the --profile solve")
     ap.add_argument("--omega", type=float, default=1.0, help="pyro_opts.omega_v of the --profile solve")
     ap.add_argument("--accel", type=int, default=0, help="pyro_opts.accel of the --profile solve")
+    ap.add_argument("--workload", default="grf", choices=["grf", "layered"], help="field of the --profile solve")
+    ap.add_argument("--schur", type=int, default=0, help="pyro_opts.schur of the --profile solve")
+    ap.add_argument("--inner-cg", type=int, default=0, help="pyro_opts.inner_cg of the --profile solve")
+    ap.add_argument("--nu", type=int, default=2, help="pre/post smoothing sweeps of the --profile solve")
     ap.add_argument("--serving-sweep", action="store_true",
                     help="only the serving measurement on the config-4 request distribution (n <= 1024): capacity, "
                          "1-slot vs 4-slot saturation, arrival-rate sweep")
