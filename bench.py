@@ -663,7 +663,7 @@ def main():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--max-iter", type=int, default=3000)
     ap.add_argument("--restart", type=int, default=30)
-    ap.add_argument("--tile-fusion", type=int, default=2, help="pyro_opts.tile_fusion of the --profile solve")
+    ap.add_argument("--tile-fusion", type=int, default=1, help="pyro_opts.tile_fusion of the --profile solve")
     ap.add_argument("--tile-sweeps", type=int, default=2, help="pyro_opts.tile_sweeps of the --profile solve")
     ap.add_argument("--smoother", type=int, default=0, help="pyro_opts.smoother of the --profile solve")
     ap.add_argument("--omega", type=float, default=1.0, help="pyro_opts.omega_v of the --profile solve")

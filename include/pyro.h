@@ -119,18 +119,15 @@ typedef struct {
   int kcycle;            /* K-cycle depth 0..16: on levels l < kcycle the coarse correction is two
                             flexible-CG steps preconditioned by the next level's cycle (recursive
                             Krylov cycle, not in the paper; 0 = the paper's plain V-cycle) [0] */
-  int cluster_cells;     /* levels with at most this many cells run their whole cycle inside one
-                            thread-block-cluster launch (16 CTAs where the GPU can hold such a
-                            cluster, else 8; cluster barriers between steps); <= 0 = never, every
-                            step is its own kernel [0] */
+  int cluster_cells;     /* reserved, must be <= 0: a sub-cycle running the small levels inside one
+                            thread-block-cluster launch was measured to save nothing against the
+                            graph-launched per-level kernels and was removed [0] */
   int tile_fusion;       /* 1: smoothing sweeps (with the prolongation) and residual+restriction run
                             as shared-memory tile kernels, one launch each per level visit (FP32
-                            levels; FP64 levels see tile_fusion64); 2: as 1, but FP32 levels large
-                            enough for it (row chunks of >= 96 rows at two CTAs per SM) smooth with
-                            the row-streaming wavefront kernel; 3: as 2 on every FP32 level (for
-                            tests and tuning); 4: as 1 with the 64 x 32 colour-split tiles on large
-                            levels instead of the warp-per-row tiles; 0: one kernel per colour and
-                            step; 0..4 [1] */
+                            levels; FP64 levels see tile_fusion64); 4: as 1 with the 64 x 32
+                            colour-split tiles on large levels instead of the warp-per-row tiles; 0:
+                            one kernel per colour and step; 0, 1 or 4 [1] (a row-streaming wavefront
+                            variant measured no faster than the tiles and was removed) */
   int tile_sweeps;       /* FP32 tile kernels: sweeps fused per launch, 1 (halo 4, one HBM pass per
                             sweep) or 2 (halo 8, one pass per two sweeps) [2] */
   int tile_fusion64;     /* 1: FP64 levels of up to 65536 cells also smooth and restrict with the

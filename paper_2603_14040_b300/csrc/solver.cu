@@ -16,9 +16,7 @@
 
 #include "kernels_mg.cuh"
 #include "kernels_krylov.cuh"
-#include "kernels_sub.cuh"
 #include "kernels_tile.cuh"
-#include "kernels_stream.cuh"
 #include "kernels_jacobi.cuh"
 #include "kernels_schur.cuh"
 #include "kernels_galerkin.cuh"
@@ -32,7 +30,6 @@ constexpr int kMaxCoarse = 1024;
 constexpr int kCoarseInvertMulti = 80;    // larger coarsest systems invert with one launch per pivot
                                           // (one CTA: about n^3 / 2 clocks of one SM plus a barrier
                                           // per pivot; one launch per pivot: a few us each)
-constexpr int kStreamMinRows = 96;  // shortest row chunk worth a streaming pass
 constexpr int kRasTile = 32;        // RAS-type Jacobi tile edge (cells), the paper's 32 x 32
 constexpr long long kSmallTileCells = 65536;  // FP32 levels up to 256^2 smooth with 32 x 16 tiles
 constexpr int kWTileY2 = 48;        // owned rows of the two-sweep warp-per-row tile (2 CTAs per SM)
@@ -148,18 +145,13 @@ struct MG {
   int nc = 0;              // coarse unknowns
   int nu1 = 2, nu2 = 2, eta_mode = 0;
   int kcycle = 0;  // levels l < kcycle get their coarse correction from two flexible-CG steps
-  int ls = -1;     // first level run by the cluster sub-cycle kernel (-1: none)
   bool tiles = true;                        // tile-fused smoothing / residual+restriction
-  int stream = 0;                           // FP32 row-streaming sweeps: 0 never, 1 large levels, 2 all
   int tile_form = 0;                        // FP32 large levels: 0 warp-per-row tiles, 1 64 x 32 colour-split
   int smoother = PYRO_SMOOTH_RBGS;          // velocity smoother (MIXED: Jacobi on level 0, RAS below)
   int ras_inner = 4;                        // RAS-type Jacobi: local iterations per tile pass
   int tile_sweeps = 2;                      // FP32: sweeps fused per tile launch
   int galerkin = 0;                         // 1: factor-2 coarse levels take R L P (damped-Jacobi smoothed)
   static constexpr long long kFuse64Cells = 65536;
-  SubArgs<T> sub{};
-  int sub_ncta = 8;  // CTAs of the sub-cycle cluster
-  double* red = nullptr;
   T omega = T(1);
   const cudaEvent_t* hooks = nullptr;  // level-0 phase events (timing mode), else null
   long long* nlaunch = nullptr;        // kernel-launch counter of the owning handle
@@ -238,79 +230,6 @@ struct MG {
     if (coarse_direct && nc > kCoarseInvertMulti) Atmp = A.get<double>((size_t)nc * nc);
   }
 
-  // choose the first level of the cluster sub-cycle and fill its launch arguments
-  void setup_sub(DevAlloc& A, int cluster_cells) {
-    ls = -1;
-    if (cluster_cells <= 0 || (int)lv.size() > kSubMaxLevels || lv.size() < 2 || smoother != PYRO_SMOOTH_RBGS ||
-        !coarse_direct || galerkin)
-      return;
-    for (size_t l = 0; l + 1 < lv.size(); ++l)
-      if (!f2[l]) return;
-    for (int l = 0; l < (int)lv.size(); ++l)
-      if ((long long)lv[l].g.nx * lv[l].g.ny <= cluster_cells) { ls = l; break; }
-    if (ls < 0 || ls == (int)lv.size() - 1) { ls = -1; return; }
-    red = A.get<double>(2 * kSubClusterMax * 4);
-    sub_ncta = sub_cluster_size();
-    sub.solo_points = sizeof(T) == 4 ? 4096 : 324;
-    sub.nlev = (int)lv.size();
-    sub.nu1 = nu1; sub.nu2 = nu2; sub.kcycle = kcycle; sub.omega = omega;
-    sub.gc = lv.back().g;
-    sub.Ainv = Ainv;
-    sub.nc = nc;
-    sub.red = red;
-    for (size_t l = 0; l < lv.size(); ++l) {
-      const Level<T>& L = lv[l];
-      SubLevel<T>& S = sub.L[l];
-      S.gt = L.gt;
-      S.vx = L.vx; S.vy = L.vy; S.fx = L.fx; S.fy = L.fy; S.rx = L.rx; S.ry = L.ry; S.en = L.en; S.ec = L.ec;
-      S.d1x = L.d1x; S.d1y = L.d1y; S.q1x = L.q1x; S.q1y = L.q1y; S.ex = L.ex; S.ey = L.ey;
-      S.idgx = L.idgx; S.idgy = L.idgy;
-      S.kc = L.kc;
-    }
-  }
-
-  // 16 CTAs if a cluster of 16 (non-portable size) with kSubThreads threads each can be resident,
-  // else the portable 8
-  static int sub_cluster_size() {
-    static int n = 0;
-    if (n) return n;
-    n = 8;
-    if (cudaFuncSetAttribute(k_subcycle<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-      cudaGetLastError();
-      return n;
-    }
-    cudaLaunchConfig_t cfg{};
-    cudaLaunchAttribute at{};
-    at.id = cudaLaunchAttributeClusterDimension;
-    at.val.clusterDim.x = kSubClusterMax;
-    at.val.clusterDim.y = 1;
-    at.val.clusterDim.z = 1;
-    cfg.gridDim = dim3(kSubClusterMax);
-    cfg.blockDim = dim3(kSubThreads);
-    cfg.attrs = &at;
-    cfg.numAttrs = 1;
-    int active = 0;
-    if (cudaOccupancyMaxActiveClusters(&active, k_subcycle<T>, &cfg) == cudaSuccess && active > 0) n = kSubClusterMax;
-    cudaGetLastError();
-    return n;
-  }
-
-  void launch_sub(int l, cudaStream_t s) {
-    cudaLaunchConfig_t cfg{};
-    cudaLaunchAttribute at{};
-    at.id = cudaLaunchAttributeClusterDimension;
-    at.val.clusterDim.x = (unsigned)sub_ncta;
-    at.val.clusterDim.y = 1;
-    at.val.clusterDim.z = 1;
-    cfg.gridDim = dim3((unsigned)sub_ncta);
-    cfg.blockDim = dim3(kSubThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cfg.attrs = &at;
-    cfg.numAttrs = 1;
-    CK(cudaLaunchKernelEx(&cfg, k_subcycle<T>, sub, l));
-  }
-
   // viscosity on every level + coarse inverse (eta of level 0 must already be in place)
   void setup(cudaStream_t s, int* flag) {
     for (size_t l = 1; l < lv.size(); ++l) {
@@ -382,32 +301,6 @@ struct MG {
       count(1);
       return;
     }
-    if constexpr (sizeof(T) == 4) {
-      if (stream_level(l)) {
-        if (C) {
-          k_prolong_add<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(L.gt, C->gt, L.X(), L.Y(), C->X(), C->Y());
-          count(1);
-        }
-        while (nsweeps > 0) {
-          float* ox = L.cur ? L.vx : L.vx2;
-          float* oy = L.cur ? L.vy : L.vy2;
-          if (nsweeps >= 2 && tile_sweeps >= 2) {
-            const dim3 gr = stream_grid<2>(L);
-            k_rbgs_stream<2, 2><<<gr, StreamCfg<2, 2>::THREADS, StreamCfg<2, 2>::smem_bytes(), s>>>(
-                L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, stream_rows(L, gr.y));
-            nsweeps -= 2;
-          } else {
-            const dim3 gr = stream_grid<1>(L);
-            k_rbgs_stream<1, 2><<<gr, StreamCfg<1, 2>::THREADS, StreamCfg<1, 2>::smem_bytes(), s>>>(
-                L.gt, L.X(), L.Y(), ox, oy, L.fx, L.fy, L.en, L.ec, omega, stream_rows(L, gr.y));
-            nsweeps -= 1;
-          }
-          count(1);
-          L.cur ^= 1;
-        }
-        return;
-      }
-    }
     while (nsweeps > 0) {
       if constexpr (sizeof(T) == 4) {
         float* ox = L.cur ? L.vx : L.vx2;
@@ -462,32 +355,6 @@ struct MG {
     }
   }
 
-  // streaming-sweep launch shape: strips of W columns, row chunks sized so the grid fills the
-  // GPU's SMs (two CTAs each) in one wave
-  static int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-      int d = 0;
-      CK(cudaGetDevice(&d));
-      CK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d));
-    }
-    return n;
-  }
-  template <int NS>
-  static dim3 stream_grid(const Level<T>& L) {
-    const int strips = (L.g.nx + 2 + StreamCfg<NS, 2>::W - 1) / StreamCfg<NS, 2>::W;
-    const int chunks = std::max(1, 2 * sm_count() / strips);
-    const int H = (L.g.ny + 2 + chunks - 1) / chunks;
-    return dim3(strips, (L.g.ny + 2 + H - 1) / H);
-  }
-  static int stream_rows(const Level<T>& L, unsigned chunks) { return (L.g.ny + 2 + (int)chunks - 1) / (int)chunks; }
-  bool stream_level(int l) const {
-    const Level<T>& L = lv[l];
-    if (stream == 0 || L.g.nx % 2 != 0) return false;
-    if (stream == 2) return true;
-    const dim3 gr = stream_grid<2>(L);
-    return stream_rows(L, gr.y) >= kStreamMinRows && (int)(gr.x * gr.y) >= sm_count();
-  }
 
   void resrestrict_tiles(int l, cudaStream_t s) {
     Level<T>& L = lv[l];
@@ -517,10 +384,6 @@ struct MG {
                               (int)SweepTileCS<1, 32, 16>::smem_bytes()));
       CK(cudaFuncSetAttribute(k_resrestrict_tile<T, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)ResTile<T, 32, 16>::smem_bytes()));
-      CK(cudaFuncSetAttribute(k_rbgs_stream<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)StreamCfg<2, 2>::smem_bytes()));
-      CK(cudaFuncSetAttribute(k_rbgs_stream<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)StreamCfg<1, 2>::smem_bytes()));
     } else {
       CK(cudaFuncSetAttribute(k_rbgs_tile<T, 1, 64, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)SweepTile<T, 1, 64, 16>::smem_bytes(true)));
@@ -607,11 +470,6 @@ struct MG {
     Level<T>& L = lv[l];
     // entry: the iterate is zero in the first buffer
     L.cur = 0;
-    if (l == ls) {
-      launch_sub(l, s);
-      count(1);
-      return;
-    }
     if (l == (int)lv.size() - 1) {
       if (coarse_direct) {
         k_coarse_solve<T><<<(nc + kCoarseRows - 1) / kCoarseRows, 32 * kCoarseRows, nc * sizeof(double), s>>>(
@@ -705,6 +563,7 @@ struct SchurMG {
   std::vector<Lv> lv;
   T *wix = nullptr, *wiy = nullptr;  // W^-1 at the velocity unknowns of the finest grid (padded)
   double* Ainv = nullptr;
+  double* Atmp = nullptr;            // second buffer of the one-launch-per-pivot inversion (nc > 80)
   int nc = 0;
   int nu = 2;
   T omega_s = T(0.8), omega_p = T(2.0 / 3.0);
@@ -731,7 +590,7 @@ struct SchurMG {
       b += 5 * 256;                                                    // allocation rounding
     }
     const size_t ncl = (size_t)sz.back().first * sz.back().second;
-    return b + ncl * ncl * sizeof(double);
+    return b + (ncl > (size_t)kCoarseInvertMulti ? 2 : 1) * ncl * ncl * sizeof(double);
   }
   void alloc(DevAlloc& A, int nx, int ny, size_t P) {
     const auto sz = sizes(nx, ny);
@@ -750,6 +609,7 @@ struct SchurMG {
     }
     nc = (int)lv.back().n;
     Ainv = A.get<double>((size_t)nc * nc);
+    if (nc > kCoarseInvertMulti) Atmp = A.get<double>((size_t)nc * nc);
   }
   PLev<T> plev(int l) const {
     const Lv& L = lv[l];
@@ -769,8 +629,20 @@ struct SchurMG {
       k_schur_rap<T><<<nb(C.n), 256, 0, s>>>(plev((int)l), F.pw, C.nx, C.ny, C.box, C.diag);
     }
     k_schur_coarse_assemble<T><<<1, 1024, 0, s>>>(plev((int)lv.size() - 1), Ainv);
-    k_coarse_invert<<<1, 1024, nc * sizeof(double), s>>>(Ainv, nc, flag);
-    count(1 + 2 * ((long long)lv.size() - 1) + 2);
+    if (nc > kCoarseInvertMulti) {
+      // one launch per Gauss-Jordan pivot over the whole GPU (a single CTA would take milliseconds)
+      double *a = Ainv, *b = Atmp;
+      const dim3 gg((nc + 255) / 256, nc);
+      for (int k = 0; k < nc; ++k) {
+        k_coarse_invert_step<<<gg, 256, 0, s>>>(a, b, nc, k, flag);
+        std::swap(a, b);
+      }
+      if (a != Ainv) CK(cudaMemcpyAsync(Ainv, a, (size_t)nc * nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      count(1 + 2 * ((long long)lv.size() - 1) + 1 + nc);
+    } else {
+      k_coarse_invert<<<1, 1024, nc * sizeof(double), s>>>(Ainv, nc, flag);
+      count(1 + 2 * ((long long)lv.size() - 1) + 2);
+    }
   }
 
   void jacobi(int l, bool from_zero, cudaStream_t s) {
@@ -1574,7 +1446,8 @@ bool opts_valid(const pyro_opts& o) {
          o.alpha_p > 0.0 && std::isfinite(o.alpha_p) && o.restart_m >= 1 && o.restart_m <= kMaxRestart &&
          o.max_iter >= 1 && (o.prec == PYRO_PREC_FP64 || o.prec == PYRO_PREC_MIXED) && o.coarsest_min >= 1 &&
          (o.eta_coarsen == PYRO_ETA_ARITH || o.eta_coarsen == PYRO_ETA_GEOM) && o.kcycle >= 0 && o.kcycle <= 16 &&
-         o.tile_fusion >= 0 && o.tile_fusion <= 4 && (o.tile_sweeps == 1 || o.tile_sweeps == 2) &&
+         (o.tile_fusion == 0 || o.tile_fusion == 1 || o.tile_fusion == 4) && o.cluster_cells <= 0 &&
+         (o.tile_sweeps == 1 || o.tile_sweeps == 2) &&
          (o.tile_fusion64 == 0 || o.tile_fusion64 == 1) && o.accel >= PYRO_ACCEL_FGMRES &&
          o.accel <= PYRO_ACCEL_ANDERSON && o.aa_beta > 0.0 && o.aa_beta <= 1.0 && o.smoother >= PYRO_SMOOTH_RBGS &&
          o.smoother <= PYRO_SMOOTH_MIXED && o.ras_inner >= 1 && o.cont_stages >= 0 && o.cont_iters >= 1 &&
@@ -1612,7 +1485,6 @@ size_t footprint_bytes(int nx, int ny, const pyro_opts& o, int L) {
   (void)L;
   const auto sz = sizes_of(nx, ny, o);
   b += mixed ? MG<float>::bytes(sz, o.kcycle, o.galerkin) : MG<double>::bytes(sz, o.kcycle, o.galerkin) - 2 * P * 8;
-  b += 2 * kSubClusterMax * 4 * 8;
   if (o.schur) b += mixed ? SchurMG<float>::bytes(nx, ny, P) : SchurMG<double>::bytes(nx, ny, P);
   if (o.inner_cg) b += mixed ? InnerCG<float>::bytes(P) : InnerCG<double>::bytes(P);
   b += 2 * (kMaxRestart + 2) * 8 + 2 * (size_t)kReduceBlocks * (kMaxRestart + 1) * 8 + 4 * kReduceBlocks * 8 +
@@ -1753,14 +1625,12 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->mgf.ras_inner = o.ras_inner;
       if (o.smoother == PYRO_SMOOTH_RAS || o.smoother == PYRO_SMOOTH_MIXED) MG<float>::enable_ras();
       h->mgf.tiles = o.tile_fusion != 0;
-      h->mgf.stream = (o.tile_fusion == 2 || o.tile_fusion == 3) ? o.tile_fusion - 1 : 0;
       h->mgf.tile_form = o.tile_fusion == 4 ? 1 : 0;
       h->mgf.tile_sweeps = o.tile_sweeps;
       h->mgf.galerkin = o.galerkin;
       if (h->mgf.tiles) MG<float>::enable_tiles();
       CK(cudaDeviceSynchronize());
       h->mgf.alloc(A, h->g, Lx, Ly, sizes_of(nx, ny, o), false);
-      h->mgf.setup_sub(A, o.cluster_cells);
       if (o.schur) h->smf.alloc(A, nx, ny, h->P);
       if (o.inner_cg) h->icf.alloc(A, h->P);
     } else {
@@ -1777,7 +1647,6 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->mgd.lv[0].en = h->en;
       h->mgd.lv[0].ec = h->ec;
       if (!h->mgd.fused(0)) h->mgd.lv[0].kc = h->okc;  // FP64 level 0 shares the outer coefficients
-      h->mgd.setup_sub(A, o.cluster_cells);
       if (o.schur) h->smd.alloc(A, nx, ny, h->P);
       if (o.inner_cg) h->icd.alloc(A, h->P);
     }

@@ -69,18 +69,17 @@ def _precond_case(nx, ny, Lx, Ly, bc, prec, seed, kcycle=0, cluster_cells=0, til
 
 @pytest.mark.parametrize("nx,ny,Lx,Ly", [(2, 2, 1, 1), (16, 16, 1, 1), (48, 80, 0.6, 1.0), (64, 16, 4, 1), (256, 128, 2, 1)])
 @pytest.mark.parametrize("bc", list(BCS))
-@pytest.mark.parametrize("cc,tf", [(0, 0), (0, 1), (4096, 1), (1 << 20, 0)])
+@pytest.mark.parametrize("cc,tf", [(0, 0), (0, 1)])
 def test_preconditioner_fp64_matches_oracle(nx, ny, Lx, Ly, bc, cc, tf):
     """One Uzawa sweep with an FP64 V-cycle (RBGS, residual, restriction, eta coarsening, coarse
     direct solve, prolongation, pressure update, mean removal) equals the oracle's step by step,
-    with one kernel per step, with tile-fused kernels, with the smallest levels in the cluster kernel,
-    and with all levels in the cluster kernel."""
+    with one kernel per step and with tile-fused kernels."""
     gpu, ora, nlev = _precond_case(nx, ny, Lx, Ly, bc, P.PREC_FP64, 11, cluster_cells=cc, tile_fusion=tf)
     for a, b in zip(gpu, ora):
         assert rel(a, b) <= 1e-11, (rel(a, b), nlev)
 
 
-@pytest.mark.parametrize("prec,tf", [(P.PREC_FP64, 0), (P.PREC_FP64, 1), (P.PREC_MIXED, 1), (P.PREC_MIXED, 3)])
+@pytest.mark.parametrize("prec,tf", [(P.PREC_FP64, 0), (P.PREC_FP64, 1), (P.PREC_MIXED, 1), (P.PREC_MIXED, 4)])
 @pytest.mark.parametrize("field", ["random", "layered"])
 def test_preconditioner_geometric_eta_coarsening_matches_oracle(prec, tf, field):
     """Viscosity coarsened on log(eta) (the geometric-mean option of the eta-coarsening reading),
@@ -175,7 +174,7 @@ def test_odd_size_sinker_matches_direct_oracle(prec):
 
 @pytest.mark.parametrize("nx,ny,Lx,Ly", [(32, 32, 1, 1), (48, 80, 0.6, 1.0)])
 @pytest.mark.parametrize("kc", [1, 2, 8])
-@pytest.mark.parametrize("cc,tf", [(0, 0), (0, 1), (4096, 1), (1 << 20, 0)])
+@pytest.mark.parametrize("cc,tf", [(0, 0), (0, 1)])
 def test_preconditioner_kcycle_fp64_matches_oracle(nx, ny, Lx, Ly, kc, cc, tf):
     """The K-cycle variant (two flexible-CG steps per coarse correction on the top kc levels)."""
     gpu, ora, nlev = _precond_case(nx, ny, Lx, Ly, "free", P.PREC_FP64, 13, kcycle=kc, cluster_cells=cc,
@@ -185,7 +184,7 @@ def test_preconditioner_kcycle_fp64_matches_oracle(nx, ny, Lx, Ly, kc, cc, tf):
 
 
 @pytest.mark.parametrize("nx,ny", [(16, 16), (48, 80), (320, 192), (512, 386)])
-@pytest.mark.parametrize("tf", [0, 1, 3, 4])
+@pytest.mark.parametrize("tf", [0, 1, 4])
 def test_preconditioner_fp32_close_to_oracle(nx, ny, tf):
     gpu, ora, _ = _precond_case(nx, ny, 1.0, 1.0, "free", P.PREC_MIXED, 5, tile_fusion=tf)
     for a, b in zip(gpu, ora):
@@ -195,18 +194,17 @@ def test_preconditioner_fp32_close_to_oracle(nx, ny, tf):
 @pytest.mark.parametrize("nx,ny,kc", [(16, 16, 0), (48, 80, 2), (320, 192, 3), (1024, 256, 2), (2048, 2048, 0),
                                       (1152, 704, 0)])
 def test_fp32_tile_fusion_matches_unfused(nx, ny, kc):
-    """The tile kernels (halo recomputation), the row-streaming wavefront kernel (forced on every
-    level, and on the large levels only) reproduce the one-kernel-per-colour FP32 cycle to FP32
-    rounding (the same point operations; only the compiler's multiply-add contraction may differ
-    between the kernels). 2048^2 takes the streaming kernel on its finest level by default;
-    1152 x 704 (forced) has ragged strips and row chunks on every level."""
+    """The tile kernels (halo recomputation; warp-per-row and colour-split forms) reproduce the
+    one-kernel-per-colour FP32 cycle to FP32 rounding (the same point operations; only the
+    compiler's multiply-add contraction may differ between the kernels), on grids with ragged tiles
+    on every level."""
     g = S.Grid(nx, ny)
     en, ec = rand_eta(nx, ny, 21, -1, 1)
     rng = np.random.default_rng(22)
     r = rng.standard_normal(g.n)
     rx, ry, rp = S.vector_to_fields(g, r, fill_ghosts=False)
     outs = []
-    for tf in (0, 1, 2, 3, 4):
+    for tf in (0, 1, 4):
         h = P.Stokes(nx, ny, prec=P.PREC_MIXED, kcycle=kc, tile_fusion=tf)
         Z = [zeros(ny, nx) for _ in range(3)]
         h.precond(dev(en), dev(ec), dev(rx), dev(ry), dev(rp), *Z)
