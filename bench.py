@@ -271,6 +271,37 @@ def layered_sample(n=1024, steps=3):
     return res
 
 
+def config3_sample(n=4096, max_iter=3000, restart_m=200):
+    """Config 3 itself: the 4096^2 layered workload (lid 1e6 over a mantle with 64 inclusions of
+    10^U[-3,3]), mixed precision, to relative energy residual 1e-10, with the options that converge
+    on it (weighted BFBt pressure block, 5 inner flexible-CG steps with an FP64 recurrence,
+    FGMRES(restart_m), V(4,4)). One timed solve after one untimed one (graph capture); about 170 GB
+    of Krylov basis on the device."""
+    import torch
+    import paper_2603_14040_b300 as P
+    from synth import layered_config
+    f = layered_config(n, n, seed=3)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    en, ec, rho = dev(f.eta_n), dev(f.eta_c), dev(f.rho)
+    del f
+    outs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
+    h = P.Stokes(n, n, prec=P.PREC_MIXED, schur=1, inner_cg=5, restart_m=restart_m, nu1=4, nu2=4, max_iter=max_iter)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    st = h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
+    e1.record()
+    torch.cuda.synchronize()
+    res = {"grid": [n, n], "options": f"mixed, schur=1, inner_cg=5, restart_m={restart_m}, V(4,4), tol 1e-10",
+           "ms": e0.elapsed_time(e1), "iters": st.iters, "restarts": st.restarts, "status": st.status,
+           "rel_energy_res": st.rel_energy_res, "rel_l2_res": st.rel_l2_res,
+           "footprint_GB": P.footprint(n, n, h.opts) / 1e9, "note": "first solve (includes the graph captures)"}
+    h.close()
+    del outs, en, ec, rho
+    torch.cuda.empty_cache()
+    return res
+
+
 def marker_sample(n=1024, per_cell=16, reps=5):
     """The marker steps of the marker-in-cell loop around the solve: 16 markers per cell on 1024^2,
     uniform random positions; marker -> basic nodes (deterministic bucketed gather), grid -> markers
@@ -675,6 +706,8 @@ def main():
     ap.add_argument("--serving-sweep", action="store_true",
                     help="only the serving measurement on the config-4 request distribution (n <= 1024): capacity, "
                          "1-slot vs 4-slot saturation, arrival-rate sweep")
+    ap.add_argument("--config3", action="store_true",
+                    help="only config 3 (4096^2 layered, mixed, weighted BFBt + inner CG): one solve, about 170 GB")
     ap.add_argument("--markers", action="store_true",
                     help="only the marker sample (16.8 M markers on 1024^2: interpolation both ways and one "
                          "advection step per scheme), for ncu captures")
@@ -686,6 +719,9 @@ def main():
         return profile_solve(args)
     if args.markers:
         print(json.dumps({"markers": marker_sample(reps=1)}))
+        return
+    if args.config3:
+        print(json.dumps({"config3": config3_sample()}))
         return
     if args.serving_sweep:
         print(json.dumps({"serving_sweep": serving_sweep()}))

@@ -182,8 +182,10 @@ typedef struct {
                             and cluster_cells <= 0; 0 or 1 [0] */
   int inner_cg;          /* velocity block of the preconditioner: 0 one V-cycle (the paper); k >= 1: k
                             steps of flexible conjugate gradients on L z_v = r_v from zero, each
-                            preconditioned by one V-cycle (one-term flexible recurrence, dot products
-                            reduced on the device). Not in the paper: on viscosity that jumps by orders
+                            preconditioned by one V-cycle (one-term flexible recurrence; the recurrence,
+                            the operator and the dot products in FP64 in both precision modes, only the
+                            V-cycle in FP32 in mixed mode; reduced on the device). Not in the paper: on
+                            viscosity that jumps by orders
                             of magnitude a single cycle leaves most of the velocity error, and each
                             outer Krylov iteration saved also saves its orthogonalisation; 0..16 [0] */
 } pyro_opts;

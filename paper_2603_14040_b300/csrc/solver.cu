@@ -678,18 +678,17 @@ struct SchurMG {
   }
 };
 
-// ---- inner flexible CG on the finest velocity level (option inner_cg) -------------------------
-template <typename T>
+// ---- inner flexible CG on the finest velocity level (option inner_cg): FP64 recurrence -------
 struct InnerCG {
-  T *xx = nullptr, *xy = nullptr, *wx = nullptr, *wy = nullptr, *dx = nullptr, *dy = nullptr, *qx = nullptr,
-    *qy = nullptr;
+  double *xx = nullptr, *xy = nullptr, *wx = nullptr, *wy = nullptr, *dx = nullptr, *dy = nullptr, *qx = nullptr,
+         *qy = nullptr, *rx = nullptr, *ry = nullptr;
   double *part = nullptr, *scal = nullptr;
-  static size_t bytes(size_t P) { return 8 * P * sizeof(T) + (2 * kReduceBlocks + 3) * sizeof(double) + 10 * 256; }
+  static size_t bytes(size_t P) { return 10 * P * sizeof(double) + (2 * kReduceBlocks + 3) * sizeof(double) + 12 * 256; }
   void alloc(DevAlloc& A, size_t P) {
-    T** arr[8] = {&xx, &xy, &wx, &wy, &dx, &dy, &qx, &qy};
-    for (T** a : arr) {
-      *a = A.get<T>(P);
-      CK(cudaMemset(*a, 0, P * sizeof(T)));
+    double** arr[10] = {&xx, &xy, &wx, &wy, &dx, &dy, &qx, &qy, &rx, &ry};
+    for (double** a : arr) {
+      *a = A.get<double>(P);
+      CK(cudaMemset(*a, 0, P * sizeof(double)));
     }
     part = A.get<double>(2 * kReduceBlocks);
     scal = A.get<double>(3);
@@ -729,8 +728,7 @@ struct pyro_stokes_s {
   MG<double> mgd;
   SchurMG<float> smf;                        // weighted BFBt pressure block (option schur = 1)
   SchurMG<double> smd;
-  InnerCG<float> icf;                         // inner flexible CG on the finest velocity level
-  InnerCG<double> icd;
+  InnerCG ic;                                 // inner flexible CG on the finest velocity level
   std::vector<cudaGraphExec_t> graphs;       // captured iteration graphs (per Krylov column with MGS)
   std::vector<long long> graph_kernel_counts;
   int cur_j = 0;                              // Krylov column of the step being launched or captured
@@ -769,13 +767,6 @@ int multidot(pyro_stokes_s* h, cudaStream_t s, const double* V, const int* d_cnt
 }
 
 template <typename T>
-InnerCG<T>& inner_of(pyro_stokes_s* h);
-template <>
-InnerCG<float>& inner_of<float>(pyro_stokes_s* h) { return h->icf; }
-template <>
-InnerCG<double>& inner_of<double>(pyro_stokes_s* h) { return h->icd; }
-
-template <typename T>
 SchurMG<T>& schur_of(pyro_stokes_s* h);
 template <>
 SchurMG<float>& schur_of<float>(pyro_stokes_s* h) { return h->smf; }
@@ -798,23 +789,29 @@ void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s, const double* in,
   if (h->o.inner_cg > 0) {
     // inner flexible CG on L z_v = r_v (the residual lives in the level-0 right-hand side), each step
     // preconditioned by one V-cycle; the phase events time the first cycle only
-    InnerCG<T>& ic = inner_of<T>(h);
+    InnerCG& ic = h->ic;
+    k_fcg_init<<<kReduceBlocks, kThreads, 0, s>>>(h->P, in, in_stride, d_idx, isw, ic.rx, ic.ry);
     for (int k = 0; k < h->o.inner_cg; ++k) {
       const int first = k == 0;
+      // step 0's right-hand side and zero iterate were set by k_precond_in
+      if (!first) k_fcg_load<T><<<kReduceBlocks, kThreads, 0, s>>>(L0.P, ic.rx, ic.ry, L0.fx, L0.fy, L0.vx, L0.vy);
       mg.cycle(0, s);
       mg.hooks = nullptr;
-      k_fcg_apply<T><<<kReduceBlocks, kThreads, 0, s>>>(L0.gt, L0.X(), L0.Y(), L0.en, L0.ec, ic.qx, ic.qy, ic.wx,
+      k_fcg_apply<T><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->en, h->ec, ic.qx, ic.qy, ic.wx,
                                                         ic.wy, first, ic.part);
       k_fcg_beta<<<1, kThreads, 0, s>>>(ic.part, kReduceBlocks, first, ic.scal);
-      k_fcg_orth<T><<<kReduceBlocks, kThreads, 0, s>>>(L0.gt, L0.X(), L0.Y(), ic.wx, ic.wy, L0.fx, L0.fy, ic.dx,
+      k_fcg_orth<T><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), ic.wx, ic.wy, ic.rx, ic.ry, ic.dx,
                                                        ic.dy, ic.qx, ic.qy, ic.scal, first, ic.part);
       k_fcg_alpha<<<1, kThreads, 0, s>>>(ic.part, kReduceBlocks, ic.scal);
-      k_fcg_update<T><<<kReduceBlocks, kThreads, 0, s>>>(L0.P, ic.dx, ic.dy, ic.qx, ic.qy, ic.xx, ic.xy, L0.fx,
-                                                         L0.fy, L0.vx, L0.vy, ic.scal, first);
-      h->launches += 5;
+      k_fcg_update<<<kReduceBlocks, kThreads, 0, s>>>(h->P, ic.dx, ic.dy, ic.qx, ic.qy, ic.xx, ic.xy, ic.rx, ic.ry,
+                                                      ic.scal, first);
+      h->launches += first ? 5 : 6;
     }
-    zvx = ic.xx;
-    zvy = ic.xy;
+    k_fcg_store<T><<<kReduceBlocks, kThreads, 0, s>>>(L0.P, ic.xx, ic.xy, L0.vx, L0.vy);
+    L0.cur = 0;
+    h->launches += 2;
+    zvx = L0.vx;
+    zvy = L0.vy;
   } else {
     mg.cycle(0, s);
     zvx = L0.X();
@@ -1486,7 +1483,7 @@ size_t footprint_bytes(int nx, int ny, const pyro_opts& o, int L) {
   const auto sz = sizes_of(nx, ny, o);
   b += mixed ? MG<float>::bytes(sz, o.kcycle, o.galerkin) : MG<double>::bytes(sz, o.kcycle, o.galerkin) - 2 * P * 8;
   if (o.schur) b += mixed ? SchurMG<float>::bytes(nx, ny, P) : SchurMG<double>::bytes(nx, ny, P);
-  if (o.inner_cg) b += mixed ? InnerCG<float>::bytes(P) : InnerCG<double>::bytes(P);
+  if (o.inner_cg) b += InnerCG::bytes(P);
   b += 2 * (kMaxRestart + 2) * 8 + 2 * (size_t)kReduceBlocks * (kMaxRestart + 1) * 8 + 4 * kReduceBlocks * 8 +
        (size_t)kMaxRestart * kHcolStride * 8 + 64;
   return b;
@@ -1632,7 +1629,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       CK(cudaDeviceSynchronize());
       h->mgf.alloc(A, h->g, Lx, Ly, sizes_of(nx, ny, o), false);
       if (o.schur) h->smf.alloc(A, nx, ny, h->P);
-      if (o.inner_cg) h->icf.alloc(A, h->P);
+      if (o.inner_cg) h->ic.alloc(A, h->P);
     } else {
       h->mgd.nu1 = o.nu1; h->mgd.nu2 = o.nu2; h->mgd.omega = o.omega_v; h->mgd.eta_mode = o.eta_coarsen;
       h->mgd.coarse_sweeps = o.coarse_sweeps;
@@ -1648,7 +1645,7 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       h->mgd.lv[0].ec = h->ec;
       if (!h->mgd.fused(0)) h->mgd.lv[0].kc = h->okc;  // FP64 level 0 shares the outer coefficients
       if (o.schur) h->smd.alloc(A, nx, ny, h->P);
-      if (o.inner_cg) h->icd.alloc(A, h->P);
+      if (o.inner_cg) h->ic.alloc(A, h->P);
     }
     CK(cudaMallocHost(&h->hbuf, 4 * kReduceBlocks * sizeof(double) + 1024));
     CK(cudaMallocHost(&h->hflag, sizeof(int)));
