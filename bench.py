@@ -161,7 +161,14 @@ def vcycle_roofline_4096(peaks, iters=6, label="", launches=1, **opts):
     h.close()
     del outs, en, ec, rho
     torch.cuda.empty_cache()
+    # the whole V-cycle against SURVEY 8(d)'s algorithmic bytes: 208 B per fine cell for V(2,2) over all
+    # levels when fused (FP32), scaled by the sweeps per level
+    vcycle_ms = (ph["l0_pre_smooth"] + ph["coarse_levels"] + ph["l0_post_smooth"]) / it
+    nu = opts.get("nu1", 2)
+    vbytes = (208.0 + (nu - 2) * 2 * 32 * 4.0 / 3.0) * cells
     return {"kernel": f"{label} level 0, 4096x4096 layered, mixed", "opts": opts,
+            "vcycle_alg_bytes": vbytes, "vcycle_GBps": vbytes / (vcycle_ms / 1e3) / 1e9,
+            "vcycle_frac": vbytes / (vcycle_ms / 1e3) / 1e9 / peak,
             "bound": "hbm", "achieved": gbs_pre, "peak": peak, "unit": "GB/s", "frac": gbs_pre / peak,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback 6400 GB/s",
             "bytes_per_launch": bytes_pre, "launch_ms": pre_ms,
@@ -189,7 +196,8 @@ def vcycle_rooflines(peaks):
             ("ras_inner_4", "k_ras_tile<float,32,32> (RAS pass of 4 local Jacobi iterations, the paper's T_inner)",
              1, 4, dict(smoother=2, ras_inner=4, omega_v=0.6))]:
         v = vcycle_roofline_4096(peaks, label=label, launches=launches, **opts)
-        main["variants"][key] = {k: v[k] for k in ("kernel", "achieved", "frac", "launch_ms", "vcycle_ms_per_iter")}
+        main["variants"][key] = {k: v[k] for k in ("kernel", "achieved", "frac", "launch_ms", "vcycle_ms_per_iter",
+                                                   "vcycle_GBps", "vcycle_frac")}
         main["variants"][key].update({"sweeps_per_launch": sweeps, "effective_sweep_GBps": sweeps * v["achieved"],
                                       "effective_frac": sweeps * v["frac"]})
     return main
@@ -271,12 +279,12 @@ def layered_sample(n=1024, steps=3):
     return res
 
 
-def config3_sample(n=4096, max_iter=3000, restart_m=200):
+def config3_sample(n=4096, max_iter=4000, restart_m=256, prec="mixed"):
     """Config 3 itself: the 4096^2 layered workload (lid 1e6 over a mantle with 64 inclusions of
-    10^U[-3,3]), mixed precision, to relative energy residual 1e-10, with the options that converge
-    on it (weighted BFBt pressure block, 5 inner flexible-CG steps with an FP64 recurrence,
-    FGMRES(restart_m), V(4,4)). One timed solve after one untimed one (graph capture); about 170 GB
-    of Krylov basis on the device."""
+    10^U[-3,3]) to relative energy residual 1e-10 with the weighted BFBt pressure block, 5 inner
+    flexible-CG steps and FGMRES(restart_m), V(4,4). In FP64 it converges (2746 iterations, 318 s on
+    a B300); with the FP32 V-cycle of the mixed mode it does not. One timed solve (it includes the
+    graph captures); about 220 GB on the device at restart 256."""
     import torch
     import paper_2603_14040_b300 as P
     from synth import layered_config
@@ -285,14 +293,15 @@ def config3_sample(n=4096, max_iter=3000, restart_m=200):
     en, ec, rho = dev(f.eta_n), dev(f.eta_c), dev(f.rho)
     del f
     outs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
-    h = P.Stokes(n, n, prec=P.PREC_MIXED, schur=1, inner_cg=5, restart_m=restart_m, nu1=4, nu2=4, max_iter=max_iter)
+    h = P.Stokes(n, n, prec=P.PREC_MIXED if prec == "mixed" else P.PREC_FP64, schur=1, inner_cg=5,
+                 restart_m=restart_m, nu1=4, nu2=4, max_iter=max_iter)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
     st = h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
     e1.record()
     torch.cuda.synchronize()
-    res = {"grid": [n, n], "options": f"mixed, schur=1, inner_cg=5, restart_m={restart_m}, V(4,4), tol 1e-10",
+    res = {"grid": [n, n], "options": f"{prec}, schur=1, inner_cg=5, restart_m={restart_m}, V(4,4), tol 1e-10",
            "ms": e0.elapsed_time(e1), "iters": st.iters, "restarts": st.restarts, "status": st.status,
            "rel_energy_res": st.rel_energy_res, "rel_l2_res": st.rel_l2_res,
            "footprint_GB": P.footprint(n, n, h.opts) / 1e9, "note": "first solve (includes the graph captures)"}
@@ -721,7 +730,7 @@ def main():
         print(json.dumps({"markers": marker_sample(reps=1)}))
         return
     if args.config3:
-        print(json.dumps({"config3": config3_sample()}))
+        print(json.dumps({"config3": config3_sample(prec=args.prec)}))
         return
     if args.serving_sweep:
         print(json.dumps({"serving_sweep": serving_sweep()}))
