@@ -63,3 +63,22 @@ def test_energy_weights_follow_the_paper_norm():
     r = sysm.b - sysm.A @ x
     den = np.sum(W[:g.n_v] * sysm.b[:g.n_v] ** 2)
     assert np.sqrt(np.sum(W * r * r) / den) == pytest.approx(S.energy_residual(sysm, f.eta_c, x)[0], rel=1e-12)
+
+
+
+def test_bfbt_preconditioned_reference_equals_direct_solve_on_the_layered_field():
+    """The reference form used for the layered workload (exact velocity LU, weighted BFBt pressure
+    block) reaches the direct solution of a lid + inclusions field with viscosity from 1e-3 to 1e6."""
+    from oracle import multigrid as M
+    from synth import layered_config
+    n = 64
+    f = layered_config(n, n, seed=3)
+    g = S.Grid(n, n)
+    sysm = S.assemble(g, f.eta_n, f.eta_c, f.rho, (0.0, 1.0))
+    res = I.solve_reference(sysm, f.eta_c, tol=1e-13, m=200, schur=M.WeightedBFBt(sysm))
+    assert res.rel_energy <= 1e-13
+    xd = S.remove_pressure_mean(g, S.solve_direct(sysm))
+    nv = g.n_v
+    dv = np.linalg.norm(res.x[:nv] - xd[:nv]) / np.linalg.norm(xd[:nv])
+    dp = np.linalg.norm(res.x[nv:] - xd[nv:]) / np.linalg.norm(xd[nv:])
+    assert dv <= 1e-9 and dp <= 1e-9, (dv, dp)
