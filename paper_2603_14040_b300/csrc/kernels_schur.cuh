@@ -42,11 +42,12 @@ __device__ inline T negdiag_vy(const GeomT<T>& g, int i, int j, const SE* en, co
 }
 
 // W^-1 = diag(-L)^(-1/2) at the velocity unknowns (padded layout, 0 elsewhere) and, per cell of the
-// finest pressure grid, the conductances of its east face cx and south face cy (0 on walls) and the
-// diagonal of K (sum of the four face conductances).
+// finest pressure grid, the conductances of its east face cx and south face cy (0 on walls), the
+// diagonal of K (sum of the four face conductances) and its inverse.
 template <typename T, typename SE>
 __global__ void k_schur_weights(GeomT<T> g, const SE* __restrict__ en, const SE* __restrict__ ec, T* __restrict__ wix,
-                                T* __restrict__ wiy, T* __restrict__ cx, T* __restrict__ cy, T* __restrict__ diag) {
+                                T* __restrict__ wiy, T* __restrict__ cx, T* __restrict__ cy, T* __restrict__ diag,
+                                T* __restrict__ idg) {
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (i > g.ny + 1 || j > g.nx + 1) return;
@@ -62,7 +63,9 @@ __global__ void k_schur_weights(GeomT<T> g, const SE* __restrict__ en, const SE*
   const T cn = (i - 1 >= 1) ? g.idy2 / sqrt(negdiag_vy<T>(g, i - 1, j, en, ec)) : T(0);
   cx[k] = ce;
   cy[k] = cs;
-  diag[k] = ce + cw + cs + cn;
+  const T d = ce + cw + cs + cn;
+  diag[k] = d;
+  idg[k] = d > T(0) ? one / d : T(0);
 }
 
 // One level of the pressure hierarchy as seen by the kernels.
@@ -73,6 +76,7 @@ struct PLev {
   const T* cy;    // finest level: south-face conductances
   const T* box;   // coarse levels: 25 planes of nx*ny coefficients (else null)
   const T* diag;  // diagonal of K
+  const T* idg;   // 1 / diagonal (0 where the diagonal is 0)
 };
 
 // K(k, k + di nx + dj) for |di|, |dj| <= 2 (0 outside the stencil or the grid)
@@ -91,29 +95,36 @@ __device__ inline T pcoef(const PLev<T>& L, int i, int j, int di, int dj) {
   return T(0);
 }
 
-// (K x)_k
+// (K x)_k, without branches around the loads so that all of them are in flight at once: the
+// coefficient of every coupling that leaves the grid is 0 (walls carry no conductance, and the
+// Galerkin boxes hold 0 there), so the neighbour index is only clamped into the array and the
+// product adds an exact 0; the finest level's west / north couplings of the first column / row,
+// whose stored conductance belongs to another cell, are masked. Same terms in the same order as
+// the plain sum over the couplings inside the grid.
 template <typename T>
 __device__ inline T papply(const PLev<T>& L, int i, int j, const T* __restrict__ x) {
-  const size_t k = (size_t)i * L.nx + j;
+  const int n = L.nx * L.ny;
+  const int k = i * L.nx + j;
   if (!L.box) {
+    const T cE = L.cx[k], cS = L.cy[k];
+    const T cWr = L.cx[max(k - 1, 0)], cNr = L.cy[max(k - L.nx, 0)];
+    const T cW = j >= 1 ? cWr : T(0), cN = i >= 1 ? cNr : T(0);
+    const T xE = x[min(k + 1, n - 1)], xW = x[max(k - 1, 0)];
+    const T xS = x[min(k + L.nx, n - 1)], xN = x[max(k - L.nx, 0)];
     T s = L.diag[k] * x[k];
-    if (j + 1 < L.nx) s -= L.cx[k] * x[k + 1];
-    if (j >= 1) s -= L.cx[k - 1] * x[k - 1];
-    if (i + 1 < L.ny) s -= L.cy[k] * x[k + L.nx];
-    if (i >= 1) s -= L.cy[k - L.nx] * x[k - L.nx];
+    s -= cE * xE;
+    s -= cW * xW;
+    s -= cS * xS;
+    s -= cN * xN;
     return s;
   }
-  const size_t n = (size_t)L.nx * L.ny;
   T s = T(0);
 #pragma unroll
   for (int di = -2; di <= 2; ++di) {
-    const int ii = i + di;
-    if (ii < 0 || ii >= L.ny) continue;
 #pragma unroll
     for (int dj = -2; dj <= 2; ++dj) {
-      const int jj = j + dj;
-      if (jj < 0 || jj >= L.nx) continue;
-      s += L.box[(size_t)((di + 2) * 5 + (dj + 2)) * n + k] * x[(size_t)ii * L.nx + jj];
+      const int kk = min(max(k + di * L.nx + dj, 0), n - 1);
+      s += L.box[(size_t)((di + 2) * 5 + (dj + 2)) * n + k] * x[kk];
     }
   }
   return s;
@@ -162,7 +173,7 @@ __global__ void k_schur_prow(PLev<T> L, int nxc, int nyc, T omega_p, T* __restri
 // Galerkin coarse operator K_c = P^T K P, one coarse cell per thread, into 25 planes (+ diagonal)
 template <typename T>
 __global__ void k_schur_rap(PLev<T> L, const T* __restrict__ pw, int nxc, int nyc, T* __restrict__ box,
-                            T* __restrict__ cdiag) {
+                            T* __restrict__ cdiag, T* __restrict__ cidg) {
   const int K0 = blockIdx.x * blockDim.x + threadIdx.x;
   const int nc = nxc * nyc;
   if (K0 >= nc) return;
@@ -199,68 +210,131 @@ __global__ void k_schur_rap(PLev<T> L, const T* __restrict__ pw, int nxc, int ny
 #pragma unroll
   for (int q = 0; q < kSchurBox; ++q) box[(size_t)q * nc + K0] = acc[q];
   cdiag[K0] = acc[12];
+  cidg[K0] = acc[12] > T(0) ? T(1) / acc[12] : T(0);
 }
 
-// One damped Jacobi sweep x_out = x_in + omega (f - K x_in) / diag (x_in null: from zero)
+// One damped Jacobi sweep x_out = x_in + omega (f - K x_in) / diag (the sweep from zero, omega f /
+// diag, is formed by whoever writes f)
 template <typename T>
 __global__ void k_schur_jacobi(PLev<T> L, const T* __restrict__ x_in, T* __restrict__ x_out, const T* __restrict__ f,
                                T omega) {
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (k0 >= L.nx * L.ny) return;
-  const int i = k0 / L.nx, j = k0 % L.nx;
-  if (!x_in) { x_out[k0] = omega * f[k0] / L.diag[k0]; return; }
-  x_out[k0] = x_in[k0] + omega * (f[k0] - papply<T>(L, i, j, x_in)) / L.diag[k0];
+  const int i = k0 / L.nx, j = k0 - i * L.nx;
+  x_out[k0] = x_in[k0] + omega * (f[k0] - papply<T>(L, i, j, x_in)) * L.idg[k0];
 }
 
-// r = f - K x
-template <typename T>
-__global__ void k_schur_resid(PLev<T> L, const T* __restrict__ x, const T* __restrict__ f, T* __restrict__ r) {
-  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k0 >= L.nx * L.ny) return;
-  r[k0] = f[k0] - papply<T>(L, k0 / L.nx, k0 % L.nx, x);
-}
+// ---- fused steps of the pressure cycle (same arithmetic, fewer dependent launches) ----------
+constexpr int kSchurCT = 16;   // coarse cells per tile side of k_schur_resrestrict
+constexpr int kSchurTS = 16;   // fine cells per tile side of k_schur_prolong_jacobi
 
-// f_c = P^T r
+// Residual and restriction in one launch: a block computes r = f - K x on the fine cells its
+// 16 x 16 coarse cells restrict from (a (2 * 16 + 2)^2 region, kept in shared memory; cells
+// outside the grid hold 0), then f_c = P^T r for each coarse cell exactly as k_schur_restrict
+// sums it. With xc given (the coarse level is not the coarsest) the coarse level's first Jacobi
+// sweep from zero is written too: xc = omega f_c / diag_c, as k_schur_jacobi forms it.
 template <typename T>
-__global__ void k_schur_restrict(int nx, int ny, const T* __restrict__ pw, const T* __restrict__ r, int nxc, int nyc,
-                                 T* __restrict__ fc) {
-  const int K0 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (K0 >= nxc * nyc) return;
-  const int I = K0 / nxc, J = K0 % nxc;
-  const size_t n = (size_t)nx * ny;
-  T s = T(0);
-  for (int ai = 2 * I - 1; ai <= 2 * I + 2; ++ai) {
-    if (ai < 0 || ai >= ny) continue;
-    const int si = I - pwin(ai);
-    if (si < 0 || si > 1) continue;
-    for (int aj = 2 * J - 1; aj <= 2 * J + 2; ++aj) {
-      if (aj < 0 || aj >= nx) continue;
-      const int sj = J - pwin(aj);
-      if (sj < 0 || sj > 1) continue;
-      const size_t a = (size_t)ai * nx + aj;
-      s += pw[(size_t)(si * 2 + sj) * n + a] * r[a];
+__global__ void __launch_bounds__(256) k_schur_resrestrict(PLev<T> L, const T* __restrict__ x,
+                                                           const T* __restrict__ f, const T* __restrict__ pw,
+                                                           int nxc, int nyc, T* __restrict__ fc,
+                                                           const T* __restrict__ idgc, T omega, T* __restrict__ xc) {
+  constexpr int RW = 2 * kSchurCT + 2;
+  __shared__ T rs[RW * RW];
+  const int I0 = blockIdx.y * kSchurCT, J0 = blockIdx.x * kSchurCT;
+  const int fi0 = 2 * I0 - 1, fj0 = 2 * J0 - 1;
+  for (int t = threadIdx.x; t < RW * RW; t += blockDim.x) {
+    const int ai = fi0 + t / RW, aj = fj0 + t % RW;
+    T v = T(0);
+    if (ai >= 0 && ai < L.ny && aj >= 0 && aj < L.nx) {
+      const int k = ai * L.nx + aj;
+      v = f[k] - papply<T>(L, ai, aj, x);
     }
+    rs[t] = v;
   }
-  fc[K0] = s;
-}
-
-// x += P e_c
-template <typename T>
-__global__ void k_schur_prolong(int nx, int ny, const T* __restrict__ pw, const T* __restrict__ ec, int nxc, int nyc,
-                                T* __restrict__ x) {
-  const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t n = (size_t)nx * ny;
-  if (k0 >= (int)n) return;
-  const int i = k0 / nx, j = k0 % nx;
-  const int oi = pwin(i), oj = pwin(j);
+  __syncthreads();
+  const int I = I0 + (int)threadIdx.x / kSchurCT, J = J0 + (int)threadIdx.x % kSchurCT;
+  if (threadIdx.x >= kSchurCT * kSchurCT || I >= nyc || J >= nxc) return;
+  const size_t n = (size_t)L.nx * L.ny;
+  const int li = 2 * (I - I0), lj = 2 * (J - J0);   // local origin of the cell's 4 x 4 window
   T s = T(0);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int Ji = oi + (q >> 1), Jj = oj + (q & 1);
-    if (Ji < 0 || Ji >= nyc || Jj < 0 || Jj >= nxc) continue;
-    s += pw[(size_t)q * n + k0] * ec[(size_t)Ji * nxc + Jj];
+  for (int a = 0; a < 4; ++a) {
+    const int ai = 2 * I - 1 + a;
+    const bool okr = ai >= 0 && ai < L.ny;
+    const size_t row = (size_t)min(max(ai, 0), L.ny - 1) * L.nx;
+    const int si = a < 2 ? 1 : 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int aj = 2 * J - 1 + b;
+      const bool ok = okr && aj >= 0 && aj < L.nx;
+      const size_t idx = row + min(max(aj, 0), L.nx - 1);
+      const int sj = b < 2 ? 1 : 0;
+      const T w = pw[(size_t)(si * 2 + sj) * n + idx];
+      const T rv = rs[(li + a) * RW + (lj + b)];
+      s += ok ? w * rv : T(0);
+    }
   }
-  x[k0] += s;
+  const int K0 = I * nxc + J;
+  fc[K0] = s;
+  if (xc) xc[K0] = omega * s * idgc[K0];
+}
+
+// Prolongation and the first post-smoothing Jacobi sweep in one launch: a block forms
+// x + P e_c on its 16 x 16 fine cells and a halo of 2 (shared memory; 0 outside the grid), then
+// x_out = x_p + omega (f - K x_p) / diag on its own cells. Same sums, in the same order, as
+// k_schur_prolong followed by k_schur_jacobi.
+template <typename T>
+__global__ void __launch_bounds__(256) k_schur_prolong_jacobi(PLev<T> L, const T* __restrict__ x,
+                                                              const T* __restrict__ pw, const T* __restrict__ ec,
+                                                              int nxc, int nyc, const T* __restrict__ f, T omega,
+                                                              T* __restrict__ x_out) {
+  constexpr int H = 2, RW = kSchurTS + 2 * H;
+  __shared__ T xs[RW * RW];
+  const int i0 = blockIdx.y * kSchurTS - H, j0 = blockIdx.x * kSchurTS - H;
+  const size_t n = (size_t)L.nx * L.ny;
+  for (int t = threadIdx.x; t < RW * RW; t += blockDim.x) {
+    const int i = i0 + t / RW, j = j0 + t % RW;
+    T v = T(0);
+    if (i >= 0 && i < L.ny && j >= 0 && j < L.nx) {
+      const size_t k = (size_t)i * L.nx + j;
+      const int oi = pwin(i), oj = pwin(j);
+      T sp = T(0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int Ji = oi + (q >> 1), Jj = oj + (q & 1);
+        if (Ji < 0 || Ji >= nyc || Jj < 0 || Jj >= nxc) continue;
+        sp += pw[(size_t)q * n + k] * ec[(size_t)Ji * nxc + Jj];
+      }
+      v = x[k] + sp;
+    }
+    xs[t] = v;
+  }
+  __syncthreads();
+  const int li = H + (int)threadIdx.x / kSchurTS, lj = H + (int)threadIdx.x % kSchurTS;
+  const int i = i0 + li, j = j0 + lj;
+  if (threadIdx.x >= kSchurTS * kSchurTS || i >= L.ny || j >= L.nx) return;
+  const int k = i * L.nx + j;
+  const T xc = xs[li * RW + lj];
+  T kx;
+  if (!L.box) {
+    const T cE = L.cx[k], cS = L.cy[k];
+    const T cWr = L.cx[max(k - 1, 0)], cNr = L.cy[max(k - L.nx, 0)];
+    const T cW = j >= 1 ? cWr : T(0), cN = i >= 1 ? cNr : T(0);
+    kx = L.diag[k] * xc;
+    kx -= cE * xs[li * RW + lj + 1];
+    kx -= cW * xs[li * RW + lj - 1];
+    kx -= cS * xs[(li + 1) * RW + lj];
+    kx -= cN * xs[(li - 1) * RW + lj];
+  } else {
+    kx = T(0);
+#pragma unroll
+    for (int di = -2; di <= 2; ++di) {
+#pragma unroll
+      for (int dj = -2; dj <= 2; ++dj)
+        kx += L.box[(size_t)((di + 2) * 5 + (dj + 2)) * n + k] * xs[(li + di) * RW + (lj + dj)];
+    }
+  }
+  x_out[k] = xc + omega * (f[k] - kx) * L.idg[k];
 }
 
 // Dense coarsest matrix K_c + s 1 1^T with s = trace(K_c) / nc^2 (symmetric positive definite for
@@ -291,28 +365,34 @@ __global__ void k_schur_coarse_assemble(PLev<T> L, double* __restrict__ A) {
   }
 }
 
-// x = (K_c + s 1 1^T)^-1 (f - mean f), one block, FP64 arithmetic
+// x = (K_c + s 1 1^T)^-1 (f - mean f), FP64 arithmetic, one warp per row of the inverse (coalesced
+// row reads, spread over (nc + 7) / 8 blocks of 256 threads: FP64 work on a single SM is slow on this
+// part). Every block forms the mean itself, in the same fixed order.
 template <typename T>
 __global__ void k_schur_coarse_solve(const double* __restrict__ Ainv, int nc, const T* __restrict__ f,
                                      T* __restrict__ x) {
   __shared__ double fv[kSchurMaxCoarse];
-  __shared__ double mean;
-  for (int k = threadIdx.x; k < nc; k += blockDim.x) fv[k] = (double)f[k];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int k = 0; k < nc; ++k) s += fv[k];
-    mean = s / nc;
+  __shared__ double sh[32];
+  double t = 0.0;
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    const double v = (double)f[k];
+    fv[k] = v;
+    t += v;
   }
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = t;
   __syncthreads();
-  for (int k = threadIdx.x; k < nc; k += blockDim.x) fv[k] -= mean;
-  __syncthreads();
-  for (int r = threadIdx.x; r < nc; r += blockDim.x) {
-    double s = 0.0;
-    const double* a = Ainv + (size_t)r * nc;
-    for (int c = 0; c < nc; ++c) s += a[c] * fv[c];
-    x[r] = (T)s;
-  }
+  double tot = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+  const double mean = tot / nc;
+  const int r = blockIdx.x * (int)(blockDim.x >> 5) + warp;
+  if (r >= nc) return;
+  const double* a = Ainv + (size_t)r * nc;
+  double s = 0.0;
+  for (int c = lane; c < nc; c += 32) s += a[c] * (fv[c] - mean);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) x[r] = (T)s;
 }
 
 // ---- the BFBt pieces around the two pressure cycles (finest grid) ---------------------------
@@ -354,9 +434,10 @@ __global__ void k_schur_lw(GeomT<T> g, const T* __restrict__ ux, const T* __rest
   wy[c] = oy;
 }
 
-// t = D w (compact), walls 0
+// t = D w (compact), walls 0; x0 = omega t / diag_0, the pressure cycle's first Jacobi sweep from zero
 template <typename T>
-__global__ void k_schur_div(GeomT<T> g, const T* __restrict__ wx, const T* __restrict__ wy, T* __restrict__ t) {
+__global__ void k_schur_div(GeomT<T> g, const T* __restrict__ wx, const T* __restrict__ wy, T* __restrict__ t,
+                            const T* __restrict__ idg0, T omega, T* __restrict__ x0) {
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (k0 >= g.nx * g.ny) return;
   const int i = k0 / g.nx + 1, j = k0 % g.nx + 1;
@@ -365,7 +446,9 @@ __global__ void k_schur_div(GeomT<T> g, const T* __restrict__ wx, const T* __res
   const T w = (j - 1 >= 1) ? wx[c - 1] : T(0);
   const T s = (i <= g.ny - 1) ? wy[c] : T(0);
   const T nn = (i - 1 >= 1) ? wy[c - g.ld] : T(0);
-  t[k0] = (e - w) * g.idx + (s - nn) * g.idy;
+  const T v = (e - w) * g.idx + (s - nn) * g.idy;
+  t[k0] = v;
+  x0[k0] = omega * v * idg0[k0];
 }
 
 }  // namespace pyro
@@ -373,12 +456,13 @@ __global__ void k_schur_div(GeomT<T> g, const T* __restrict__ wx, const T* __res
 namespace pyro {
 
 // As k_precond_out for the velocity planes of Z_j; instead of the diagonal surrogate, y = r_p - D z_v
-// goes to the finest pressure grid (compact) for the Schur surrogate, and Z_j's pressure plane is
-// left for k_schur_out.
+// goes to the finest pressure grid (compact) for the Schur surrogate, with the pressure cycle's first
+// Jacobi sweep from zero x0 = omega y / diag_0, and Z_j's pressure plane is left for k_schur_out.
 template <typename T, typename TZ>
 __global__ void k_precond_out_schur(GeomT<double> g, const T* __restrict__ vx, const T* __restrict__ vy,
                                     const double* __restrict__ V, size_t vstride, TZ* __restrict__ Z, size_t stride,
-                                    const int* __restrict__ d_j, T* __restrict__ y, const double* __restrict__ isw) {
+                                    const int* __restrict__ d_j, T* __restrict__ y, const double* __restrict__ isw,
+                                    const T* __restrict__ idg0, T omega, T* __restrict__ x0) {
   const size_t P = (size_t)(g.ny + 2) * g.ld;
   const double* v = V + (size_t)(*d_j) * vstride;
   TZ* z = Z + (size_t)(*d_j) * stride;
@@ -396,7 +480,10 @@ __global__ void k_precond_out_schur(GeomT<double> g, const T* __restrict__ vx, c
       const double uyn = (i - 1 >= 1) ? (double)(TZ)vy[e - g.ld] : 0.0;
       const double div = (ux - uxw) * g.idx + (uy - uyn) * g.idy;
       const double rp = isw ? v[2 * P + e] * isw[2 * P + e] : v[2 * P + e];
-      y[(size_t)(i - 1) * g.nx + (j - 1)] = (T)(rp - div);
+      const size_t k = (size_t)(i - 1) * g.nx + (j - 1);
+      const T yk = (T)(rp - div);
+      y[k] = yk;
+      x0[k] = omega * yk * idg0[k];
     }
   }
 }

@@ -554,8 +554,8 @@ struct SchurMG {
   struct Lv {
     int nx = 0, ny = 0;
     size_t n = 0;
-    T *cx = nullptr, *cy = nullptr, *box = nullptr, *diag = nullptr;
-    T *x = nullptr, *x2 = nullptr, *f = nullptr, *r = nullptr, *pw = nullptr;
+    T *cx = nullptr, *cy = nullptr, *box = nullptr, *diag = nullptr, *idg = nullptr;
+    T *x = nullptr, *x2 = nullptr, *f = nullptr, *pw = nullptr;
     int cur = 0;
     T* X() const { return cur ? x2 : x; }
     T* Xo() const { return cur ? x : x2; }
@@ -584,7 +584,7 @@ struct SchurMG {
     size_t b = 2 * P * sizeof(T);
     for (size_t l = 0; l < sz.size(); ++l) {
       const size_t n = (size_t)sz[l].first * sz[l].second;
-      b += (4 + 1) * n * sizeof(T);                                    // x, x2, f, r, diag
+      b += (3 + 2) * n * sizeof(T);                                    // x, x2, f, diag, 1/diag
       b += (l == 0 ? 2 : kSchurBox) * n * sizeof(T);                   // conductances / box stencil
       if (l + 1 < sz.size()) b += 4 * n * sizeof(T);                   // prolongator rows
       b += 5 * 256;                                                    // allocation rounding
@@ -603,7 +603,8 @@ struct SchurMG {
       if (l == 0) { L.cx = A.get<T>(L.n); L.cy = A.get<T>(L.n); }
       else L.box = A.get<T>((size_t)kSchurBox * L.n);
       L.diag = A.get<T>(L.n);
-      L.x = A.get<T>(L.n); L.x2 = A.get<T>(L.n); L.f = A.get<T>(L.n); L.r = A.get<T>(L.n);
+      L.idg = A.get<T>(L.n);
+      L.x = A.get<T>(L.n); L.x2 = A.get<T>(L.n); L.f = A.get<T>(L.n);
       if (l + 1 < sz.size()) L.pw = A.get<T>(4 * L.n);
       lv.push_back(L);
     }
@@ -613,7 +614,7 @@ struct SchurMG {
   }
   PLev<T> plev(int l) const {
     const Lv& L = lv[l];
-    return PLev<T>{L.nx, L.ny, L.cx, L.cy, L.box, L.diag};
+    return PLev<T>{L.nx, L.ny, L.cx, L.cy, L.box, L.diag, L.idg};
   }
   static unsigned nb(size_t n) { return (unsigned)((n + 255) / 256); }
 
@@ -621,12 +622,12 @@ struct SchurMG {
   // dense coarsest inverse
   void setup(const GeomT<T>& g, const T* en, const T* ec, cudaStream_t s, int* flag) {
     k_schur_weights<T, T><<<grid2(g.nx, g.ny, kBlk2), kBlk2, 0, s>>>(g, en, ec, wix, wiy, lv[0].cx, lv[0].cy,
-                                                                     lv[0].diag);
+                                                                     lv[0].diag, lv[0].idg);
     for (size_t l = 0; l + 1 < lv.size(); ++l) {
       const Lv& F = lv[l];
       Lv& C = lv[l + 1];
       k_schur_prow<T><<<nb(F.n), 256, 0, s>>>(plev((int)l), C.nx, C.ny, omega_p, F.pw);
-      k_schur_rap<T><<<nb(C.n), 256, 0, s>>>(plev((int)l), F.pw, C.nx, C.ny, C.box, C.diag);
+      k_schur_rap<T><<<nb(C.n), 256, 0, s>>>(plev((int)l), F.pw, C.nx, C.ny, C.box, C.diag, C.idg);
     }
     k_schur_coarse_assemble<T><<<1, 1024, 0, s>>>(plev((int)lv.size() - 1), Ainv);
     if (nc > kCoarseInvertMulti) {
@@ -645,36 +646,43 @@ struct SchurMG {
     }
   }
 
-  void jacobi(int l, bool from_zero, cudaStream_t s) {
+  // one damped Jacobi sweep X() -> Xo()
+  void jacobi(int l, cudaStream_t s) {
     Lv& L = lv[l];
-    if (from_zero) {
-      k_schur_jacobi<T><<<nb(L.n), 256, 0, s>>>(plev(l), nullptr, L.x, L.f, omega_s);
-      L.cur = 0;
-    } else {
-      k_schur_jacobi<T><<<nb(L.n), 256, 0, s>>>(plev(l), L.X(), L.Xo(), L.f, omega_s);
-      L.cur ^= 1;
-    }
+    k_schur_jacobi<T><<<nb(L.n), 256, 0, s>>>(plev(l), L.X(), L.Xo(), L.f, omega_s);
+    L.cur ^= 1;
     count(1);
   }
 
-  // one V-cycle on level l for K x = lv[l].f from zero; the result is lv[l].X()
+  // one V-cycle on level l for K x = lv[l].f from zero; the result is lv[l].X(). On entry lv[l].x
+  // already holds the first Jacobi sweep from zero (omega f / diag): whoever writes a level's
+  // right-hand side writes it too (k_precond_out_schur and k_schur_div on the finest level, the
+  // fused residual-restriction below), which saves one launch per level and visit. The residual
+  // and the restriction run as one tile kernel, and so do the prolongation and the first
+  // post-smoothing sweep: 4 launches per level and visit instead of 7, same arithmetic.
   void cycle(int l, cudaStream_t s) {
     Lv& L = lv[l];
-    if (l == (int)lv.size() - 1) {
-      k_schur_coarse_solve<T><<<1, 256, 0, s>>>(Ainv, nc, L.f, L.x);
+    const int last = (int)lv.size() - 1;
+    if (l == last) {
+      k_schur_coarse_solve<T><<<(nc + 7) / 8, 256, 0, s>>>(Ainv, nc, L.f, L.x);
       L.cur = 0;
       count(1);
       return;
     }
     Lv& C = lv[l + 1];
-    for (int k = 0; k < nu; ++k) jacobi(l, k == 0, s);
-    k_schur_resid<T><<<nb(L.n), 256, 0, s>>>(plev(l), L.X(), L.f, L.r);
-    k_schur_restrict<T><<<nb(C.n), 256, 0, s>>>(L.nx, L.ny, L.pw, L.r, C.nx, C.ny, C.f);
-    count(2);
-    cycle(l + 1, s);
-    k_schur_prolong<T><<<nb(L.n), 256, 0, s>>>(L.nx, L.ny, L.pw, C.X(), C.nx, C.ny, L.X());
+    L.cur = 0;
+    for (int k = 1; k < nu; ++k) jacobi(l, s);
+    const dim3 gr((C.nx + kSchurCT - 1) / kSchurCT, (C.ny + kSchurCT - 1) / kSchurCT);
+    const bool coarse_smoothed = l + 1 < last;
+    k_schur_resrestrict<T><<<gr, 256, 0, s>>>(plev(l), L.X(), L.f, L.pw, C.nx, C.ny, C.f, C.idg, omega_s,
+                                              coarse_smoothed ? C.x : nullptr);
     count(1);
-    for (int k = 0; k < nu; ++k) jacobi(l, false, s);
+    cycle(l + 1, s);
+    const dim3 gp((L.nx + kSchurTS - 1) / kSchurTS, (L.ny + kSchurTS - 1) / kSchurTS);
+    k_schur_prolong_jacobi<T><<<gp, 256, 0, s>>>(plev(l), L.X(), L.pw, C.X(), C.nx, C.ny, L.f, omega_s, L.Xo());
+    L.cur ^= 1;
+    count(1);
+    for (int k = 1; k < nu; ++k) jacobi(l, s);
   }
 };
 
@@ -825,12 +833,13 @@ void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s, const double* in,
     auto& F0 = sm.lv[0];
     sm.nlaunch = &h->launches;
     k_precond_out_schur<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, zvx, zvy, in, in_stride, out,
-                                                                   out_stride, d_idx, F0.f, isw);
+                                                                   out_stride, d_idx, F0.f, isw, F0.idg, sm.omega_s,
+                                                                   F0.x);
     sm.cycle(0, s);
     const dim3 g2 = grid2(h->nx, h->ny, kBlk2);
     k_schur_grad<T><<<g2, kBlk2, 0, s>>>(L0.gt, F0.X(), sm.wix, sm.wiy, L0.rx, L0.ry);
     k_schur_lw<T, T><<<g2, kBlk2, 0, s>>>(L0.gt, L0.rx, L0.ry, L0.en, L0.ec, sm.wix, sm.wiy, L0.fx, L0.fy);
-    k_schur_div<T><<<SchurMG<T>::nb(F0.n), 256, 0, s>>>(L0.gt, L0.fx, L0.fy, F0.f);
+    k_schur_div<T><<<SchurMG<T>::nb(F0.n), 256, 0, s>>>(L0.gt, L0.fx, L0.fy, F0.f, F0.idg, sm.omega_s, F0.x);
     sm.cycle(0, s);
     k_schur_out<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, F0.X(), h->o.alpha_p, out, out_stride, d_idx,
                                                            h->part2);
