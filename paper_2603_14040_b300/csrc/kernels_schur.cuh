@@ -170,26 +170,28 @@ __global__ void k_schur_prow(PLev<T> L, int nxc, int nyc, T omega_p, T* __restri
   }
 }
 
-// Galerkin coarse operator K_c = P^T K P, one coarse cell per thread, into 25 planes (+ diagonal)
+// Galerkin coarse operator K_c = P^T K P into 25 planes (+ the diagonal and its inverse). Sixteen
+// threads per coarse cell, one per fine cell of its 4 x 4 window, each summing that fine cell's
+// contributions P(a, K) K(a, b) P(b, J); then a fixed-order shuffle sum over the sixteen (half a
+// warp). One thread per coarse cell left the small levels of the set-up latency-bound on a few SMs.
 template <typename T>
-__global__ void k_schur_rap(PLev<T> L, const T* __restrict__ pw, int nxc, int nyc, T* __restrict__ box,
-                            T* __restrict__ cdiag, T* __restrict__ cidg) {
-  const int K0 = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_schur_rap(PLev<T> L, const T* __restrict__ pw, int nxc, int nyc,
+                                                   T* __restrict__ box, T* __restrict__ cdiag, T* __restrict__ cidg) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int K0 = gt >> 4, sub = gt & 15;
   const int nc = nxc * nyc;
-  if (K0 >= nc) return;
-  const int I = K0 / nxc, J = K0 % nxc;
+  const bool active = K0 < nc;   // the sixteen threads of a coarse cell form one half-warp
+  const int I = active ? K0 / nxc : 0, J = active ? K0 % nxc : 0;
   const int n = L.nx * L.ny;
   T acc[kSchurBox];
 #pragma unroll
   for (int q = 0; q < kSchurBox; ++q) acc[q] = T(0);
-  for (int ai = 2 * I - 1; ai <= 2 * I + 2; ++ai) {
-    if (ai < 0 || ai >= L.ny) continue;
-    for (int aj = 2 * J - 1; aj <= 2 * J + 2; ++aj) {
-      if (aj < 0 || aj >= L.nx) continue;
-      const int sa_i = I - pwin(ai), sa_j = J - pwin(aj);
-      if (sa_i < 0 || sa_i > 1 || sa_j < 0 || sa_j > 1) continue;
-      const T pa = pw[(size_t)(sa_i * 2 + sa_j) * n + (size_t)ai * L.nx + aj];
-      if (pa == T(0)) continue;
+  const int ai = 2 * I - 1 + (sub >> 2), aj = 2 * J - 1 + (sub & 3);
+  if (active && ai >= 0 && ai < L.ny && aj >= 0 && aj < L.nx) {
+    const int sa_i = I - pwin(ai), sa_j = J - pwin(aj);
+    const T pa = (sa_i >= 0 && sa_i <= 1 && sa_j >= 0 && sa_j <= 1)
+                     ? pw[(size_t)(sa_i * 2 + sa_j) * n + (size_t)ai * L.nx + aj] : T(0);
+    if (pa != T(0)) {
       const int r = L.box ? 2 : 1;
       for (int di = -r; di <= r; ++di)
         for (int dj = -r; dj <= r; ++dj) {
@@ -208,6 +210,10 @@ __global__ void k_schur_rap(PLev<T> L, const T* __restrict__ pw, int nxc, int ny
     }
   }
 #pragma unroll
+  for (int q = 0; q < kSchurBox; ++q)
+    for (int o = 8; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+  if (!active || sub != 0) return;
+#pragma unroll
   for (int q = 0; q < kSchurBox; ++q) box[(size_t)q * nc + K0] = acc[q];
   cdiag[K0] = acc[12];
   cidg[K0] = acc[12] > T(0) ? T(1) / acc[12] : T(0);
@@ -225,22 +231,29 @@ __global__ void k_schur_jacobi(PLev<T> L, const T* __restrict__ x_in, T* __restr
 }
 
 // ---- fused steps of the pressure cycle (same arithmetic, fewer dependent launches) ----------
-constexpr int kSchurCT = 16;   // coarse cells per tile side of k_schur_resrestrict
 constexpr int kSchurTS = 16;   // fine cells per tile side of k_schur_prolong_jacobi
 
 // Residual and restriction in one launch: a block computes r = f - K x on the fine cells its
-// 16 x 16 coarse cells restrict from (a (2 * 16 + 2)^2 region, kept in shared memory; cells
-// outside the grid hold 0), then f_c = P^T r for each coarse cell exactly as k_schur_restrict
-// sums it. With xc given (the coarse level is not the coarsest) the coarse level's first Jacobi
-// sweep from zero is written too: xc = omega f_c / diag_c, as k_schur_jacobi forms it.
-template <typename T>
-__global__ void __launch_bounds__(256) k_schur_resrestrict(PLev<T> L, const T* __restrict__ x,
+// CT x CT coarse cells restrict from (a (2 CT + 2)^2 region, kept in shared memory; cells outside
+// the grid hold 0), then f_c = P^T r for each coarse cell exactly as a separate restriction would
+// sum it. With xc given (the coarse level is not the coarsest) the coarse level's first Jacobi
+// sweep from zero is written too: xc = omega f_c / diag_c, as k_schur_jacobi would form it.
+// CT is 16, 8 or 4 by level size (schur_tile_ct) so that small levels still spread their residuals
+// over many SMs, one or two per thread: a single block doing a whole small level serially is
+// latency- (and in FP64 arithmetic-) bound.
+template <int CT>
+constexpr int schur_rr_threads() { return CT == 16 ? 256 : (CT == 8 ? 352 : 128); }
+inline int schur_tile_ct(long long coarse_cells) {
+  return coarse_cells >= 148LL * 256 ? 16 : (coarse_cells >= 148LL * 64 ? 8 : 4);
+}
+template <typename T, int CT>
+__global__ void __launch_bounds__(512) k_schur_resrestrict(PLev<T> L, const T* __restrict__ x,
                                                            const T* __restrict__ f, const T* __restrict__ pw,
                                                            int nxc, int nyc, T* __restrict__ fc,
                                                            const T* __restrict__ idgc, T omega, T* __restrict__ xc) {
-  constexpr int RW = 2 * kSchurCT + 2;
+  constexpr int RW = 2 * CT + 2;
   __shared__ T rs[RW * RW];
-  const int I0 = blockIdx.y * kSchurCT, J0 = blockIdx.x * kSchurCT;
+  const int I0 = blockIdx.y * CT, J0 = blockIdx.x * CT;
   const int fi0 = 2 * I0 - 1, fj0 = 2 * J0 - 1;
   for (int t = threadIdx.x; t < RW * RW; t += blockDim.x) {
     const int ai = fi0 + t / RW, aj = fj0 + t % RW;
@@ -252,8 +265,8 @@ __global__ void __launch_bounds__(256) k_schur_resrestrict(PLev<T> L, const T* _
     rs[t] = v;
   }
   __syncthreads();
-  const int I = I0 + (int)threadIdx.x / kSchurCT, J = J0 + (int)threadIdx.x % kSchurCT;
-  if (threadIdx.x >= kSchurCT * kSchurCT || I >= nyc || J >= nxc) return;
+  const int I = I0 + (int)threadIdx.x / CT, J = J0 + (int)threadIdx.x % CT;
+  if (threadIdx.x >= CT * CT || I >= nyc || J >= nxc) return;
   const size_t n = (size_t)L.nx * L.ny;
   const int li = 2 * (I - I0), lj = 2 * (J - J0);   // local origin of the cell's 4 x 4 window
   T s = T(0);
@@ -280,15 +293,16 @@ __global__ void __launch_bounds__(256) k_schur_resrestrict(PLev<T> L, const T* _
 }
 
 // Prolongation and the first post-smoothing Jacobi sweep in one launch: a block forms
-// x + P e_c on its 16 x 16 fine cells and a halo of 2 (shared memory; 0 outside the grid), then
+// x + P e_c on its 16 x 16 fine cells and a halo of H (2 for the 5 x 5 boxes, 1 for the finest
+// level's 5-point operator; shared memory, 0 outside the grid), then
 // x_out = x_p + omega (f - K x_p) / diag on its own cells. Same sums, in the same order, as
 // k_schur_prolong followed by k_schur_jacobi.
-template <typename T>
+template <typename T, int H>
 __global__ void __launch_bounds__(256) k_schur_prolong_jacobi(PLev<T> L, const T* __restrict__ x,
                                                               const T* __restrict__ pw, const T* __restrict__ ec,
                                                               int nxc, int nyc, const T* __restrict__ f, T omega,
                                                               T* __restrict__ x_out) {
-  constexpr int H = 2, RW = kSchurTS + 2 * H;
+  constexpr int RW = kSchurTS + 2 * H;
   __shared__ T xs[RW * RW];
   const int i0 = blockIdx.y * kSchurTS - H, j0 = blockIdx.x * kSchurTS - H;
   const size_t n = (size_t)L.nx * L.ny;
@@ -315,7 +329,7 @@ __global__ void __launch_bounds__(256) k_schur_prolong_jacobi(PLev<T> L, const T
   if (threadIdx.x >= kSchurTS * kSchurTS || i >= L.ny || j >= L.nx) return;
   const int k = i * L.nx + j;
   const T xc = xs[li * RW + lj];
-  T kx;
+  T kx = T(0);
   if (!L.box) {
     const T cE = L.cx[k], cS = L.cy[k];
     const T cWr = L.cx[max(k - 1, 0)], cNr = L.cy[max(k - L.nx, 0)];
@@ -325,8 +339,7 @@ __global__ void __launch_bounds__(256) k_schur_prolong_jacobi(PLev<T> L, const T
     kx -= cW * xs[li * RW + lj - 1];
     kx -= cS * xs[(li + 1) * RW + lj];
     kx -= cN * xs[(li - 1) * RW + lj];
-  } else {
-    kx = T(0);
+  } else if constexpr (H >= 2) {
 #pragma unroll
     for (int di = -2; di <= 2; ++di) {
 #pragma unroll

@@ -627,7 +627,7 @@ struct SchurMG {
       const Lv& F = lv[l];
       Lv& C = lv[l + 1];
       k_schur_prow<T><<<nb(F.n), 256, 0, s>>>(plev((int)l), C.nx, C.ny, omega_p, F.pw);
-      k_schur_rap<T><<<nb(C.n), 256, 0, s>>>(plev((int)l), F.pw, C.nx, C.ny, C.box, C.diag, C.idg);
+      k_schur_rap<T><<<nb(16 * C.n), 256, 0, s>>>(plev((int)l), F.pw, C.nx, C.ny, C.box, C.diag, C.idg);
     }
     k_schur_coarse_assemble<T><<<1, 1024, 0, s>>>(plev((int)lv.size() - 1), Ainv);
     if (nc > kCoarseInvertMulti) {
@@ -644,6 +644,23 @@ struct SchurMG {
       k_coarse_invert<<<1, 1024, nc * sizeof(double), s>>>(Ainv, nc, flag);
       count(1 + 2 * ((long long)lv.size() - 1) + 2);
     }
+  }
+
+  // residual of level l restricted to level l + 1 (and, if smoothed, its first sweep from zero)
+  template <int CT>
+  void resrestrict_ct(int l, bool coarse_smoothed, cudaStream_t s) {
+    Lv& L = lv[l];
+    Lv& C = lv[l + 1];
+    const dim3 gr((C.nx + CT - 1) / CT, (C.ny + CT - 1) / CT);
+    k_schur_resrestrict<T, CT><<<gr, schur_rr_threads<CT>(), 0, s>>>(plev(l), L.X(), L.f, L.pw, C.nx, C.ny, C.f,
+                                                                     C.idg, omega_s, coarse_smoothed ? C.x : nullptr);
+    count(1);
+  }
+  void resrestrict(int l, bool coarse_smoothed, cudaStream_t s) {
+    const int ct = schur_tile_ct((long long)lv[l + 1].n);
+    if (ct == 16) resrestrict_ct<16>(l, coarse_smoothed, s);
+    else if (ct == 8) resrestrict_ct<8>(l, coarse_smoothed, s);
+    else resrestrict_ct<4>(l, coarse_smoothed, s);
   }
 
   // one damped Jacobi sweep X() -> Xo()
@@ -672,14 +689,13 @@ struct SchurMG {
     Lv& C = lv[l + 1];
     L.cur = 0;
     for (int k = 1; k < nu; ++k) jacobi(l, s);
-    const dim3 gr((C.nx + kSchurCT - 1) / kSchurCT, (C.ny + kSchurCT - 1) / kSchurCT);
-    const bool coarse_smoothed = l + 1 < last;
-    k_schur_resrestrict<T><<<gr, 256, 0, s>>>(plev(l), L.X(), L.f, L.pw, C.nx, C.ny, C.f, C.idg, omega_s,
-                                              coarse_smoothed ? C.x : nullptr);
-    count(1);
+    resrestrict(l, l + 1 < last, s);
     cycle(l + 1, s);
     const dim3 gp((L.nx + kSchurTS - 1) / kSchurTS, (L.ny + kSchurTS - 1) / kSchurTS);
-    k_schur_prolong_jacobi<T><<<gp, 256, 0, s>>>(plev(l), L.X(), L.pw, C.X(), C.nx, C.ny, L.f, omega_s, L.Xo());
+    if (l == 0)
+      k_schur_prolong_jacobi<T, 1><<<gp, 256, 0, s>>>(plev(l), L.X(), L.pw, C.X(), C.nx, C.ny, L.f, omega_s, L.Xo());
+    else
+      k_schur_prolong_jacobi<T, 2><<<gp, 256, 0, s>>>(plev(l), L.X(), L.pw, C.X(), C.nx, C.ny, L.f, omega_s, L.Xo());
     L.cur ^= 1;
     count(1);
     for (int k = 1; k < nu; ++k) jacobi(l, s);
