@@ -847,7 +847,7 @@ def main():
     e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 3 * plane, "d2h_bytes_per_step": 3 * plane,
            "api": "pyro_stokes_solve with host pointers (library stages the copies)"}
 
-    # roofline of the dominant kernel: finest-level RBGS sweep (4 launches vx-red, vx-black, vy-red,
+    # roofline of the FP64 smoother (the largest share after the Gram-Schmidt step): finest-level RBGS sweep (4 launches vx-red, vx-black, vy-red,
     # vy-black), FP64. Algorithmic per cell and sweep: read eta_n, eta_c, fx, fy, vx, vy + write vx,
     # vy = 64 B; arithmetic: per velocity point the off-diagonal sum on precomputed
     # coefficients (6 products, 2 differences, 5 sums) and the update (2) = 15 flop, 30 per cell.
@@ -864,7 +864,8 @@ def main():
     fp64_derived = 148 * 2.08 * 2 * sm_mhz * 1e6 / 1e12
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     hbm_achieved = bytes_per_sweep / (sweep_ms / 1e3) / 1e9
-    roof = {"kernel": "k_rbgs<double> finest level (one sweep = 4 launches)", "bound": "alu",
+    roof = {"kernel": "k_rbgs<double> finest level (one sweep = 4 launches; the largest share after k_mgs_step)",
+            "bound": "alu",
             "achieved": achieved_flops, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved_flops / fp64_peak,
             "peak_source": "FP64 FMA rate measured in this run (pyro_fp64_fma_rate: FMA chains, CUDA events), of measured",
             "traffic": 4 * 59.579e6, "traffic_unit": "B per sweep",
@@ -876,6 +877,36 @@ def main():
             "hbm": {"achieved_GBps": hbm_achieved, "peak_GBps": hbm_peak, "frac": hbm_achieved / hbm_peak,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6400 GB/s"},
             "sweep_ms": sweep_ms, "phase_ms_per_iter": {k: v / max(counts["iterations"], 1) for k, v in phases.items()}}
+
+    # dominant kernel of the headline solve: the modified Gram-Schmidt step k_mgs_step (ncu launch list
+    # of the whole solve, profiles/launches_grf1024_bfbt_fp64.md). One step reads w, v_{k-1}, v_k and
+    # writes w: 4 vectors of n3 = 3 (ny + 2)(nx + 2) doubles (algorithmic; w and v_{k-1} may be served
+    # from L2, so DRAM traffic can be lower); 2 FP64 FMA per entry. Column j of a restart cycle
+    # takes min(j + 2, m + 1) steps; the column's closing k_scale_next moves 2 more vectors.
+    it_t = max(counts["iterations"], 1)
+    m_r = HEADLINE_OPTS["restart_m"]
+    cols = [m_r] * (it_t // m_r) + ([it_t % m_r] if it_t % m_r else [])
+    mgs_steps = sum(min(j + 2, m_r + 1) for c in cols for j in range(c))
+    n3 = 3 * (n + 2) * (n + 2)
+    orth_ms = phases["orthogonalise"]
+    mgs_bytes = (4 * mgs_steps + 2 * it_t) * n3 * 8.0
+    mgs_gbs = mgs_bytes / (orth_ms / 1e3) / 1e9
+    mgs_tflops = 2 * 2 * mgs_steps * n3 / (orth_ms / 1e3) / 1e12
+    roof_smoother = roof
+    roof = {"kernel": "k_mgs_step (modified Gram-Schmidt step of FGMRES(80) on the W^(1/2)-scaled basis)",
+            "bound": "hbm", "achieved": mgs_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": mgs_gbs / hbm_peak,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback 6400 GB/s",
+            "traffic": 75.81e6 + 1.96e6,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one step at 1024^2 under ncu's "
+                               "cold caches (profiles/k_mgs_step_fp64_1024.md); in the solve w and v_{k-1} are "
+                               "partly served from L2"),
+            "alg_bytes_per_step": 4 * n3 * 8, "steps_per_iteration": mgs_steps / it_t,
+            "ms_per_step": orth_ms / mgs_steps,
+            "timing": ("CUDA events around the orthogonalisation phase of each captured iteration (all MGS steps of "
+                       "the column plus its k_mgs_finish and k_scale_next), one solve after the timed ones"),
+            "fp64": {"achieved_TFLOPs": mgs_tflops, "peak": fp64_peak, "frac": mgs_tflops / fp64_peak,
+                     "source": "2 FMA per entry and step against the FP64 FMA rate measured in this run (of measured)"},
+            "fp64_smoother": roof_smoother}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
