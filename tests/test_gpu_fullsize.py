@@ -189,24 +189,25 @@ def test_random_viscosity_1024_matches_iterative_reference_elementwise(prec, tol
 
 
 @pytest.mark.parametrize("tol", [1e-10, 1e-12])
-@pytest.mark.parametrize("prec,restart", [("fp64", 80), ("mixed", 60)])
-def test_random_viscosity_1024_bfbt_matches_iterative_reference_elementwise(prec, restart, tol):
-    """The benchmark's own configuration (weighted BFBt pressure block, FGMRES(80) in FP64 and
-    FGMRES(60) mixed): with the stronger pressure block the forward error at tol 1e-10 is already
-    below 1e-8 (measured on a B300: du 8.8e-9 FP64, 3.1e-9 mixed), so the 1e-8 bar is asserted at
-    both tolerances."""
+@pytest.mark.parametrize("prec,restart,alpha,coarsest", [("fp64", 80, 1.0, 4), ("mixed", 60, 1.0, 4),
+                                                         ("fp64", 80, 0.8, 16), ("mixed", 60, 0.8, 16)])
+def test_random_viscosity_1024_bfbt_matches_iterative_reference_elementwise(prec, restart, alpha, coarsest, tol):
+    """The benchmark's own configuration (weighted BFBt pressure block scaled by 0.8, a 16 x 16
+    coarsest velocity level, FGMRES(80) in FP64 and FGMRES(60) mixed) and the same block unscaled
+    on the default hierarchy: with the stronger pressure block the forward error at tol 1e-10 is
+    already below 1e-8, so the 1e-8 bar is asserted at both tolerances."""
     n = 1024
     f = grf_config(n, n, seed=2)
     g = S.Grid(n, n)
     xref, eref = _reference("grf1024")
     assert eref <= 1e-13
     out, st = _solve(f, n, tol, prec=P.PREC_FP64 if prec == "fp64" else P.PREC_MIXED, max_iter=3000, schur=1,
-                     restart_m=restart)
+                     restart_m=restart, alpha_p=alpha, coarsest_min=coarsest)
     assert st.status == P.PYRO_OK, st.as_dict()
     x = S.fields_to_vector(g, *(host(a) for a in out))
     du, dp = _errors(g, x, xref)
-    _record(f"grf1024_bfbt_{prec}_m{restart}_tol{tol:g}", {"du": du, "dp": dp, "iters": st.iters,
-                                                           "rel_energy": st.rel_energy_res})
+    _record(f"grf1024_bfbt_{prec}_m{restart}_a{alpha:g}_c{coarsest}_tol{tol:g}",
+            {"du": du, "dp": dp, "iters": st.iters, "rel_energy": st.rel_energy_res})
     assert du <= 1e-8 and dp <= 1e-8, (du, dp)
 
 
