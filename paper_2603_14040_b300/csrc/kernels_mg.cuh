@@ -530,30 +530,90 @@ __global__ void k_coarse_invert(double* __restrict__ A, int n, int* __restrict__
   }
 }
 
-// One Gauss-Jordan step k of the same inversion, spread over the whole GPU (one row per
-// blockIdx.y, columns over blockIdx.x / threads), out of place (B from A) so that no row is read
-// after another CTA has rewritten it; same per-element arithmetic as k_coarse_invert. A single
-// CTA does n^3 FP64 operations at one SM's FP64 rate (about 50 ms at n = 573), n such launches
-// take a few microseconds each.
-__global__ void k_coarse_invert_step(const double* __restrict__ A, double* __restrict__ B, int n, int k,
-                                     int* __restrict__ flag) {
-  const int i = blockIdx.y;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const double piv = A[(size_t)k * n + k];
-  if (!(piv > 0.0)) {  // not SPD or non-finite: report (the host fails the solve)
-    if (i == 0 && j == 0) atomicOr(flag, FLAG_BREAKDOWN);
-    B[(size_t)i * n + j] = A[(size_t)i * n + j];
+// Sixteen Gauss-Jordan pivots of the same inversion at once, spread over the whole GPU, out of
+// place (B from A) so that no element is read after another CTA has rewritten it. With K the pivot
+// set k0 .. k0 + nb - 1 (nb = min(16, n - k0)) and P = A[K, K]:
+//   pivot rows:    B[K, c] = P^-1 A[K, c] for c outside K,          B[K, K] = P^-1
+//   other rows i:  B[i, c] = A[i, c] - A[i, K] B[K, c] for c outside K,   B[i, K] = -A[i, K] P^-1
+// which in exact arithmetic is nb successive single-pivot steps of k_coarse_invert (block
+// Gauss-Jordan). Each CTA owns a 32 x 32 output tile; it inverts P itself (single-pivot steps on
+// 16 x 16 in shared memory) and forms the pivot rows of its own 32 columns. One launch per pivot
+// (n launches, each a few microseconds of launch latency) made the set-up of a 480-unknown
+// coarsest level take about 4 ms; sixteen per launch take n / 16 launches. A pivot <= 0 (the
+// matrix is not SPD, or non-finite) raises FLAG_BREAKDOWN and every CTA copies its tile.
+constexpr int kGJB = 16;   // pivots per launch
+constexpr int kGJT = 32;   // output tile side
+__global__ void __launch_bounds__(256) k_coarse_invert_block(const double* __restrict__ A, double* __restrict__ B,
+                                                             int n, int k0, int* __restrict__ flag) {
+  __shared__ double P0[kGJB][kGJB + 1], P1[kGJB][kGJB + 1];
+  __shared__ double Kr[kGJB][kGJT];       // pivot rows after the step, this CTA's columns
+  __shared__ double Ai[kGJT][kGJB + 1];   // A[i, K] of this CTA's rows
+  const int nb = min(kGJB, n - k0);
+  const int c0 = blockIdx.x * kGJT, r0 = blockIdx.y * kGJT;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kGJB * kGJB; e += blockDim.x) {
+    const int a = e / kGJB, b = e % kGJB;
+    P0[a][b] = (a < nb && b < nb) ? A[(size_t)(k0 + a) * n + k0 + b] : 0.0;
+  }
+  for (int e = tid; e < kGJT * kGJB; e += blockDim.x) {
+    const int r = e / kGJB, t = e % kGJB, i = r0 + r;
+    Ai[r][t] = (i < n && t < nb) ? A[(size_t)i * n + k0 + t] : 0.0;
+  }
+  __syncthreads();
+  // P^-1 by nb single-pivot steps; every thread reads the same pivot, so the exit is uniform
+  double(*S)[kGJB + 1] = P0;
+  double(*D)[kGJB + 1] = P1;
+  bool ok = true;
+  for (int t = 0; t < nb; ++t) {
+    const double piv = S[t][t];
+    if (!(piv > 0.0)) { ok = false; break; }
+    const double ip = 1.0 / piv;
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
+      const int a = e / nb, b = e % nb;
+      const double stb = (b == t) ? ip : S[t][b] * ip;
+      D[a][b] = (a == t) ? stb : ((b == t) ? -S[a][t] * ip : S[a][b] - S[a][t] * stb);
+    }
+    __syncthreads();
+    double(*X)[kGJB + 1] = S;
+    S = D;
+    D = X;
+  }
+  if (!ok) {
+    if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0) atomicOr(flag, FLAG_BREAKDOWN);
+    for (int e = tid; e < kGJT * kGJT; e += blockDim.x) {
+      const int i = r0 + e / kGJT, c = c0 + e % kGJT;
+      if (i < n && c < n) B[(size_t)i * n + c] = A[(size_t)i * n + c];
+    }
     return;
   }
-  const double ip = 1.0 / piv;
-  const double skj = (j == k) ? ip : A[(size_t)k * n + j] * ip;   // row k after scaling
-  if (i == k) {
-    B[(size_t)i * n + j] = skj;
-    return;
+  for (int e = tid; e < kGJB * kGJT; e += blockDim.x) {
+    const int a = e / kGJT, cc = e % kGJT, c = c0 + cc;
+    double v = 0.0;
+    if (a < nb && c < n) {
+      if (c >= k0 && c < k0 + nb) {
+        v = S[a][c - k0];
+      } else {
+        for (int t = 0; t < nb; ++t) v += S[a][t] * A[(size_t)(k0 + t) * n + c];
+      }
+    }
+    Kr[a][cc] = v;
   }
-  const double f = A[(size_t)i * n + k];
-  B[(size_t)i * n + j] = (j == k) ? -f * ip : A[(size_t)i * n + j] - f * skj;
+  __syncthreads();
+  for (int e = tid; e < kGJT * kGJT; e += blockDim.x) {
+    const int r = e / kGJT, cc = e % kGJT, i = r0 + r, c = c0 + cc;
+    if (i >= n || c >= n) continue;
+    double v;
+    if (i >= k0 && i < k0 + nb) {
+      v = Kr[i - k0][cc];
+    } else if (c >= k0 && c < k0 + nb) {
+      v = 0.0;
+      for (int t = 0; t < nb; ++t) v -= Ai[r][t] * S[t][c - k0];
+    } else {
+      v = A[(size_t)i * n + c];
+      for (int t = 0; t < nb; ++t) v -= Ai[r][t] * Kr[t][cc];
+    }
+    B[(size_t)i * n + c] = v;
+  }
 }
 
 // x = L^-1 f = -(-L)^-1 f on the coarsest level (FP64 whatever T is). One warp per row of the

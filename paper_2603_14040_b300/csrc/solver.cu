@@ -27,9 +27,9 @@ using namespace pyro;
 namespace {
 
 constexpr int kMaxCoarse = 1024;
-constexpr int kCoarseInvertMulti = 80;    // larger coarsest systems invert with one launch per pivot
-                                          // (one CTA: about n^3 / 2 clocks of one SM plus a barrier
-                                          // per pivot; one launch per pivot: a few us each)
+constexpr int kCoarseInvertMulti = 80;    // larger coarsest systems invert over the whole GPU, sixteen
+                                          // pivots per launch (one CTA: about n^3 / 2 clocks of one
+                                          // SM plus a barrier per pivot)
 constexpr int kRasTile = 32;        // RAS-type Jacobi tile edge (cells), the paper's 32 x 32
 constexpr long long kSmallTileCells = 65536;  // FP32 levels up to 256^2 smooth with 32 x 16 tiles
 constexpr int kWTileY2 = 48;        // owned rows of the two-sweep warp-per-row tile (2 CTAs per SM)
@@ -47,6 +47,20 @@ struct CudaError {
 inline dim3 grid2(int nx, int ny, dim3 b) { return dim3((nx + 2 + b.x - 1) / b.x, (ny + 2 + b.y - 1) / b.y); }
 inline dim3 grid_rb(int nx, int ny, dim3 b) { return dim3(((nx + 2) / 2 + 1 + b.x - 1) / b.x, (ny + 2 + b.y - 1) / b.y); }
 const dim3 kBlk2(32, 8);
+
+// In-place inverse of the SPD matrix A (n x n, row-major, device) by block Gauss-Jordan steps of
+// sixteen pivots over the whole GPU, through the second buffer tmp; returns the launches made.
+long long invert_spd_blocked(double* A, double* tmp, int n, cudaStream_t s, int* flag) {
+  double *a = A, *b = tmp;
+  const dim3 gg((n + kGJT - 1) / kGJT, (n + kGJT - 1) / kGJT);
+  long long cnt = 0;
+  for (int k0 = 0; k0 < n; k0 += kGJB, ++cnt) {
+    k_coarse_invert_block<<<gg, 256, 0, s>>>(a, b, n, k0, flag);
+    std::swap(a, b);
+  }
+  if (a != A) CK(cudaMemcpyAsync(A, a, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return cnt;
+}
 
 // true for memory the current device reads in place; host pointers are staged. Entry points reject
 // other GPUs' memory up front (places_ok), so everything that is not PTR_HERE here is host memory.
@@ -270,14 +284,7 @@ struct MG {
     else
       k_coarse_assemble<T><<<(nc + 127) / 128, 128, 0, s>>>(C.g, C.en, C.ec, Ainv, nc);
     if (nc > kCoarseInvertMulti) {
-      double *a = Ainv, *b = Atmp;
-      const dim3 gg((nc + 255) / 256, nc);
-      for (int k = 0; k < nc; ++k) {
-        k_coarse_invert_step<<<gg, 256, 0, s>>>(a, b, nc, k, flag);
-        std::swap(a, b);
-      }
-      if (a != Ainv) CK(cudaMemcpyAsync(Ainv, a, (size_t)nc * nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      count((long long)lv.size() - 1 + 1 + nc);
+      count((long long)lv.size() - 1 + 1 + invert_spd_blocked(Ainv, Atmp, nc, s, flag));
     } else {
       k_coarse_invert<<<1, 1024, nc * sizeof(double), s>>>(Ainv, nc, flag);
       count((long long)lv.size() - 1 + 2);
@@ -631,15 +638,8 @@ struct SchurMG {
     }
     k_schur_coarse_assemble<T><<<1, 1024, 0, s>>>(plev((int)lv.size() - 1), Ainv);
     if (nc > kCoarseInvertMulti) {
-      // one launch per Gauss-Jordan pivot over the whole GPU (a single CTA would take milliseconds)
-      double *a = Ainv, *b = Atmp;
-      const dim3 gg((nc + 255) / 256, nc);
-      for (int k = 0; k < nc; ++k) {
-        k_coarse_invert_step<<<gg, 256, 0, s>>>(a, b, nc, k, flag);
-        std::swap(a, b);
-      }
-      if (a != Ainv) CK(cudaMemcpyAsync(Ainv, a, (size_t)nc * nc * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      count(1 + 2 * ((long long)lv.size() - 1) + 1 + nc);
+      // sixteen Gauss-Jordan pivots per launch over the whole GPU (a single CTA would take milliseconds)
+      count(1 + 2 * ((long long)lv.size() - 1) + 1 + invert_spd_blocked(Ainv, Atmp, nc, s, flag));
     } else {
       k_coarse_invert<<<1, 1024, nc * sizeof(double), s>>>(Ainv, nc, flag);
       count(1 + 2 * ((long long)lv.size() - 1) + 2);
