@@ -43,11 +43,12 @@ __device__ inline T negdiag_vy(const GeomT<T>& g, int i, int j, const SE* en, co
 
 // W^-1 = diag(-L)^(-1/2) at the velocity unknowns (padded layout, 0 elsewhere) and, per cell of the
 // finest pressure grid, the conductances of its east face cx and south face cy (0 on walls), the
-// diagonal of K (sum of the four face conductances) and its inverse.
+// diagonal of K (sum of the four face conductances) and omega / diagonal (omega the damping of the
+// pressure cycle's Jacobi sweeps).
 template <typename T, typename SE>
 __global__ void k_schur_weights(GeomT<T> g, const SE* __restrict__ en, const SE* __restrict__ ec, T* __restrict__ wix,
                                 T* __restrict__ wiy, T* __restrict__ cx, T* __restrict__ cy, T* __restrict__ diag,
-                                T* __restrict__ idg) {
+                                T* __restrict__ widg, T omega) {
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (i > g.ny + 1 || j > g.nx + 1) return;
@@ -65,7 +66,7 @@ __global__ void k_schur_weights(GeomT<T> g, const SE* __restrict__ en, const SE*
   cy[k] = cs;
   const T d = ce + cw + cs + cn;
   diag[k] = d;
-  idg[k] = d > T(0) ? one / d : T(0);
+  widg[k] = d > T(0) ? omega / d : T(0);
 }
 
 // One level of the pressure hierarchy as seen by the kernels.
@@ -76,7 +77,7 @@ struct PLev {
   const T* cy;    // finest level: south-face conductances
   const T* box;   // coarse levels: 25 planes of nx*ny coefficients (else null)
   const T* diag;  // diagonal of K
-  const T* idg;   // 1 / diagonal (0 where the diagonal is 0)
+  const T* widg;  // omega / diagonal (0 where the diagonal is 0)
 };
 
 // K(k, k + di nx + dj) for |di|, |dj| <= 2 (0 outside the stencil or the grid)
@@ -130,6 +131,37 @@ __device__ inline T papply(const PLev<T>& L, int i, int j, const T* __restrict__
   return s;
 }
 
+// f_k minus the off-diagonal part of (K x)_k: with it a damped Jacobi update is
+// (1 - omega) x_k + (omega / K_kk) poff, which on the FP64 path (bound by the FP64 rate) takes 6
+// operations per finest-level cell instead of 9. Loads as in papply.
+template <typename T>
+__device__ inline T poff(const PLev<T>& L, int i, int j, T fk, const T* __restrict__ x) {
+  const int n = L.nx * L.ny;
+  const int k = i * L.nx + j;
+  if (!L.box) {
+    const T cE = L.cx[k], cS = L.cy[k];
+    const T cWr = L.cx[max(k - 1, 0)], cNr = L.cy[max(k - L.nx, 0)];
+    const T cW = j >= 1 ? cWr : T(0), cN = i >= 1 ? cNr : T(0);
+    T s = fk;
+    s += cE * x[min(k + 1, n - 1)];
+    s += cW * x[max(k - 1, 0)];
+    s += cS * x[min(k + L.nx, n - 1)];
+    s += cN * x[max(k - L.nx, 0)];
+    return s;
+  }
+  T s = fk;
+#pragma unroll
+  for (int di = -2; di <= 2; ++di) {
+#pragma unroll
+    for (int dj = -2; dj <= 2; ++dj) {
+      if (di == 0 && dj == 0) continue;
+      const int kk = min(max(k + di * L.nx + dj, 0), n - 1);
+      s -= L.box[(size_t)((di + 2) * 5 + (dj + 2)) * n + k] * x[kk];
+    }
+  }
+  return s;
+}
+
 // first coarse row / column of the 2 x 2 window of aggregates that the 3 x 3 neighbourhood of fine
 // index a touches: floor((a - 1) / 2)
 __device__ inline int pwin(int a) { return a >= 1 ? (a - 1) / 2 : -1; }
@@ -170,13 +202,14 @@ __global__ void k_schur_prow(PLev<T> L, int nxc, int nyc, T omega_p, T* __restri
   }
 }
 
-// Galerkin coarse operator K_c = P^T K P into 25 planes (+ the diagonal and its inverse). Sixteen
+// Galerkin coarse operator K_c = P^T K P into 25 planes (+ the diagonal and omega / diagonal). Sixteen
 // threads per coarse cell, one per fine cell of its 4 x 4 window, each summing that fine cell's
 // contributions P(a, K) K(a, b) P(b, J); then a fixed-order shuffle sum over the sixteen (half a
 // warp). One thread per coarse cell left the small levels of the set-up latency-bound on a few SMs.
 template <typename T>
 __global__ void __launch_bounds__(256) k_schur_rap(PLev<T> L, const T* __restrict__ pw, int nxc, int nyc,
-                                                   T* __restrict__ box, T* __restrict__ cdiag, T* __restrict__ cidg) {
+                                                   T* __restrict__ box, T* __restrict__ cdiag, T* __restrict__ cwidg,
+                                                   T omega) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int K0 = gt >> 4, sub = gt & 15;
   const int nc = nxc * nyc;
@@ -216,18 +249,19 @@ __global__ void __launch_bounds__(256) k_schur_rap(PLev<T> L, const T* __restric
 #pragma unroll
   for (int q = 0; q < kSchurBox; ++q) box[(size_t)q * nc + K0] = acc[q];
   cdiag[K0] = acc[12];
-  cidg[K0] = acc[12] > T(0) ? T(1) / acc[12] : T(0);
+  cwidg[K0] = acc[12] > T(0) ? omega / acc[12] : T(0);
 }
 
-// One damped Jacobi sweep x_out = x_in + omega (f - K x_in) / diag (the sweep from zero, omega f /
-// diag, is formed by whoever writes f)
+// One damped Jacobi sweep x_out = x_in + omega (f - K x_in) / diag, formed as
+// (1 - omega) x_in + (omega / diag) poff (the sweep from zero, omega f / diag, is formed by whoever
+// writes f)
 template <typename T>
 __global__ void k_schur_jacobi(PLev<T> L, const T* __restrict__ x_in, T* __restrict__ x_out, const T* __restrict__ f,
-                               T omega) {
+                               T om1) {
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (k0 >= L.nx * L.ny) return;
   const int i = k0 / L.nx, j = k0 - i * L.nx;
-  x_out[k0] = x_in[k0] + omega * (f[k0] - papply<T>(L, i, j, x_in)) * L.idg[k0];
+  x_out[k0] = om1 * x_in[k0] + L.widg[k0] * poff<T>(L, i, j, f[k0], x_in);
 }
 
 // ---- fused steps of the pressure cycle (same arithmetic, fewer dependent launches) ----------
@@ -237,7 +271,7 @@ constexpr int kSchurTS = 16;   // fine cells per tile side of k_schur_prolong_ja
 // CT x CT coarse cells restrict from (a (2 CT + 2)^2 region, kept in shared memory; cells outside
 // the grid hold 0), then f_c = P^T r for each coarse cell exactly as a separate restriction would
 // sum it. With xc given (the coarse level is not the coarsest) the coarse level's first Jacobi
-// sweep from zero is written too: xc = omega f_c / diag_c, as k_schur_jacobi would form it.
+// sweep from zero is written too: xc = (omega / diag_c) f_c.
 // CT is 16, 8 or 4 by level size (schur_tile_ct) so that small levels still spread their residuals
 // over many SMs, one or two per thread: a single block doing a whole small level serially is
 // latency- (and in FP64 arithmetic-) bound.
@@ -250,7 +284,7 @@ template <typename T, int CT>
 __global__ void __launch_bounds__(512) k_schur_resrestrict(PLev<T> L, const T* __restrict__ x,
                                                            const T* __restrict__ f, const T* __restrict__ pw,
                                                            int nxc, int nyc, T* __restrict__ fc,
-                                                           const T* __restrict__ idgc, T omega, T* __restrict__ xc) {
+                                                           const T* __restrict__ widgc, T* __restrict__ xc) {
   constexpr int RW = 2 * CT + 2;
   __shared__ T rs[RW * RW];
   const int I0 = blockIdx.y * CT, J0 = blockIdx.x * CT;
@@ -284,23 +318,22 @@ __global__ void __launch_bounds__(512) k_schur_resrestrict(PLev<T> L, const T* _
       const int sj = b < 2 ? 1 : 0;
       const T w = pw[(size_t)(si * 2 + sj) * n + idx];
       const T rv = rs[(li + a) * RW + (lj + b)];
-      s += ok ? w * rv : T(0);
+      s += (ok ? w : T(0)) * rv;   // the weight masked, so that the product and the sum fuse
     }
   }
   const int K0 = I * nxc + J;
   fc[K0] = s;
-  if (xc) xc[K0] = omega * s * idgc[K0];
+  if (xc) xc[K0] = s * widgc[K0];
 }
 
 // Prolongation and the first post-smoothing Jacobi sweep in one launch: a block forms
 // x + P e_c on its 16 x 16 fine cells and a halo of H (2 for the 5 x 5 boxes, 1 for the finest
 // level's 5-point operator; shared memory, 0 outside the grid), then
-// x_out = x_p + omega (f - K x_p) / diag on its own cells. Same sums, in the same order, as
-// k_schur_prolong followed by k_schur_jacobi.
+// the damped Jacobi sweep on its own cells, in the form k_schur_jacobi uses.
 template <typename T, int H>
 __global__ void __launch_bounds__(256) k_schur_prolong_jacobi(PLev<T> L, const T* __restrict__ x,
                                                               const T* __restrict__ pw, const T* __restrict__ ec,
-                                                              int nxc, int nyc, const T* __restrict__ f, T omega,
+                                                              int nxc, int nyc, const T* __restrict__ f, T om1,
                                                               T* __restrict__ x_out) {
   constexpr int RW = kSchurTS + 2 * H;
   __shared__ T xs[RW * RW];
@@ -329,25 +362,26 @@ __global__ void __launch_bounds__(256) k_schur_prolong_jacobi(PLev<T> L, const T
   if (threadIdx.x >= kSchurTS * kSchurTS || i >= L.ny || j >= L.nx) return;
   const int k = i * L.nx + j;
   const T xc = xs[li * RW + lj];
-  T kx = T(0);
+  T so = f[k];   // f minus the off-diagonal part of K x_p, as poff forms it
   if (!L.box) {
     const T cE = L.cx[k], cS = L.cy[k];
     const T cWr = L.cx[max(k - 1, 0)], cNr = L.cy[max(k - L.nx, 0)];
     const T cW = j >= 1 ? cWr : T(0), cN = i >= 1 ? cNr : T(0);
-    kx = L.diag[k] * xc;
-    kx -= cE * xs[li * RW + lj + 1];
-    kx -= cW * xs[li * RW + lj - 1];
-    kx -= cS * xs[(li + 1) * RW + lj];
-    kx -= cN * xs[(li - 1) * RW + lj];
+    so += cE * xs[li * RW + lj + 1];
+    so += cW * xs[li * RW + lj - 1];
+    so += cS * xs[(li + 1) * RW + lj];
+    so += cN * xs[(li - 1) * RW + lj];
   } else if constexpr (H >= 2) {
 #pragma unroll
     for (int di = -2; di <= 2; ++di) {
 #pragma unroll
-      for (int dj = -2; dj <= 2; ++dj)
-        kx += L.box[(size_t)((di + 2) * 5 + (dj + 2)) * n + k] * xs[(li + di) * RW + (lj + dj)];
+      for (int dj = -2; dj <= 2; ++dj) {
+        if (di == 0 && dj == 0) continue;
+        so -= L.box[(size_t)((di + 2) * 5 + (dj + 2)) * n + k] * xs[(li + di) * RW + (lj + dj)];
+      }
     }
   }
-  x_out[k] = xc + omega * (f[k] - kx) * L.idg[k];
+  x_out[k] = om1 * xc + L.widg[k] * so;
 }
 
 // Dense coarsest matrix K_c + s 1 1^T with s = trace(K_c) / nc^2 (symmetric positive definite for
@@ -447,10 +481,10 @@ __global__ void k_schur_lw(GeomT<T> g, const T* __restrict__ ux, const T* __rest
   wy[c] = oy;
 }
 
-// t = D w (compact), walls 0; x0 = omega t / diag_0, the pressure cycle's first Jacobi sweep from zero
+// t = D w (compact), walls 0; x0 = (omega / diag_0) t, the pressure cycle's first Jacobi sweep from zero
 template <typename T>
 __global__ void k_schur_div(GeomT<T> g, const T* __restrict__ wx, const T* __restrict__ wy, T* __restrict__ t,
-                            const T* __restrict__ idg0, T omega, T* __restrict__ x0) {
+                            const T* __restrict__ widg0, T* __restrict__ x0) {
   const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (k0 >= g.nx * g.ny) return;
   const int i = k0 / g.nx + 1, j = k0 % g.nx + 1;
@@ -461,7 +495,7 @@ __global__ void k_schur_div(GeomT<T> g, const T* __restrict__ wx, const T* __res
   const T nn = (i - 1 >= 1) ? wy[c - g.ld] : T(0);
   const T v = (e - w) * g.idx + (s - nn) * g.idy;
   t[k0] = v;
-  x0[k0] = omega * v * idg0[k0];
+  x0[k0] = v * widg0[k0];
 }
 
 }  // namespace pyro
@@ -470,12 +504,12 @@ namespace pyro {
 
 // As k_precond_out for the velocity planes of Z_j; instead of the diagonal surrogate, y = r_p - D z_v
 // goes to the finest pressure grid (compact) for the Schur surrogate, with the pressure cycle's first
-// Jacobi sweep from zero x0 = omega y / diag_0, and Z_j's pressure plane is left for k_schur_out.
+// Jacobi sweep from zero x0 = (omega / diag_0) y, and Z_j's pressure plane is left for k_schur_out.
 template <typename T, typename TZ>
 __global__ void k_precond_out_schur(GeomT<double> g, const T* __restrict__ vx, const T* __restrict__ vy,
                                     const double* __restrict__ V, size_t vstride, TZ* __restrict__ Z, size_t stride,
                                     const int* __restrict__ d_j, T* __restrict__ y, const double* __restrict__ isw,
-                                    const T* __restrict__ idg0, T omega, T* __restrict__ x0) {
+                                    const T* __restrict__ widg0, T* __restrict__ x0) {
   const size_t P = (size_t)(g.ny + 2) * g.ld;
   const double* v = V + (size_t)(*d_j) * vstride;
   TZ* z = Z + (size_t)(*d_j) * stride;
@@ -496,7 +530,7 @@ __global__ void k_precond_out_schur(GeomT<double> g, const T* __restrict__ vx, c
       const size_t k = (size_t)(i - 1) * g.nx + (j - 1);
       const T yk = (T)(rp - div);
       y[k] = yk;
-      x0[k] = omega * yk * idg0[k];
+      x0[k] = yk * widg0[k];
     }
   }
 }

@@ -561,7 +561,7 @@ struct SchurMG {
   struct Lv {
     int nx = 0, ny = 0;
     size_t n = 0;
-    T *cx = nullptr, *cy = nullptr, *box = nullptr, *diag = nullptr, *idg = nullptr;
+    T *cx = nullptr, *cy = nullptr, *box = nullptr, *diag = nullptr, *widg = nullptr;
     T *x = nullptr, *x2 = nullptr, *f = nullptr, *pw = nullptr;
     int cur = 0;
     T* X() const { return cur ? x2 : x; }
@@ -591,7 +591,7 @@ struct SchurMG {
     size_t b = 2 * P * sizeof(T);
     for (size_t l = 0; l < sz.size(); ++l) {
       const size_t n = (size_t)sz[l].first * sz[l].second;
-      b += (3 + 2) * n * sizeof(T);                                    // x, x2, f, diag, 1/diag
+      b += (3 + 2) * n * sizeof(T);                                    // x, x2, f, diag, omega/diag
       b += (l == 0 ? 2 : kSchurBox) * n * sizeof(T);                   // conductances / box stencil
       if (l + 1 < sz.size()) b += 4 * n * sizeof(T);                   // prolongator rows
       b += 5 * 256;                                                    // allocation rounding
@@ -610,7 +610,7 @@ struct SchurMG {
       if (l == 0) { L.cx = A.get<T>(L.n); L.cy = A.get<T>(L.n); }
       else L.box = A.get<T>((size_t)kSchurBox * L.n);
       L.diag = A.get<T>(L.n);
-      L.idg = A.get<T>(L.n);
+      L.widg = A.get<T>(L.n);
       L.x = A.get<T>(L.n); L.x2 = A.get<T>(L.n); L.f = A.get<T>(L.n);
       if (l + 1 < sz.size()) L.pw = A.get<T>(4 * L.n);
       lv.push_back(L);
@@ -621,7 +621,7 @@ struct SchurMG {
   }
   PLev<T> plev(int l) const {
     const Lv& L = lv[l];
-    return PLev<T>{L.nx, L.ny, L.cx, L.cy, L.box, L.diag, L.idg};
+    return PLev<T>{L.nx, L.ny, L.cx, L.cy, L.box, L.diag, L.widg};
   }
   static unsigned nb(size_t n) { return (unsigned)((n + 255) / 256); }
 
@@ -629,12 +629,12 @@ struct SchurMG {
   // dense coarsest inverse
   void setup(const GeomT<T>& g, const T* en, const T* ec, cudaStream_t s, int* flag) {
     k_schur_weights<T, T><<<grid2(g.nx, g.ny, kBlk2), kBlk2, 0, s>>>(g, en, ec, wix, wiy, lv[0].cx, lv[0].cy,
-                                                                     lv[0].diag, lv[0].idg);
+                                                                     lv[0].diag, lv[0].widg, omega_s);
     for (size_t l = 0; l + 1 < lv.size(); ++l) {
       const Lv& F = lv[l];
       Lv& C = lv[l + 1];
       k_schur_prow<T><<<nb(F.n), 256, 0, s>>>(plev((int)l), C.nx, C.ny, omega_p, F.pw);
-      k_schur_rap<T><<<nb(16 * C.n), 256, 0, s>>>(plev((int)l), F.pw, C.nx, C.ny, C.box, C.diag, C.idg);
+      k_schur_rap<T><<<nb(16 * C.n), 256, 0, s>>>(plev((int)l), F.pw, C.nx, C.ny, C.box, C.diag, C.widg, omega_s);
     }
     k_schur_coarse_assemble<T><<<1, 1024, 0, s>>>(plev((int)lv.size() - 1), Ainv);
     if (nc > kCoarseInvertMulti) {
@@ -653,7 +653,7 @@ struct SchurMG {
     Lv& C = lv[l + 1];
     const dim3 gr((C.nx + CT - 1) / CT, (C.ny + CT - 1) / CT);
     k_schur_resrestrict<T, CT><<<gr, schur_rr_threads<CT>(), 0, s>>>(plev(l), L.X(), L.f, L.pw, C.nx, C.ny, C.f,
-                                                                     C.idg, omega_s, coarse_smoothed ? C.x : nullptr);
+                                                                     C.widg, coarse_smoothed ? C.x : nullptr);
     count(1);
   }
   void resrestrict(int l, bool coarse_smoothed, cudaStream_t s) {
@@ -666,7 +666,7 @@ struct SchurMG {
   // one damped Jacobi sweep X() -> Xo()
   void jacobi(int l, cudaStream_t s) {
     Lv& L = lv[l];
-    k_schur_jacobi<T><<<nb(L.n), 256, 0, s>>>(plev(l), L.X(), L.Xo(), L.f, omega_s);
+    k_schur_jacobi<T><<<nb(L.n), 256, 0, s>>>(plev(l), L.X(), L.Xo(), L.f, T(1) - omega_s);
     L.cur ^= 1;
     count(1);
   }
@@ -693,9 +693,9 @@ struct SchurMG {
     cycle(l + 1, s);
     const dim3 gp((L.nx + kSchurTS - 1) / kSchurTS, (L.ny + kSchurTS - 1) / kSchurTS);
     if (l == 0)
-      k_schur_prolong_jacobi<T, 1><<<gp, 256, 0, s>>>(plev(l), L.X(), L.pw, C.X(), C.nx, C.ny, L.f, omega_s, L.Xo());
+      k_schur_prolong_jacobi<T, 1><<<gp, 256, 0, s>>>(plev(l), L.X(), L.pw, C.X(), C.nx, C.ny, L.f, T(1) - omega_s, L.Xo());
     else
-      k_schur_prolong_jacobi<T, 2><<<gp, 256, 0, s>>>(plev(l), L.X(), L.pw, C.X(), C.nx, C.ny, L.f, omega_s, L.Xo());
+      k_schur_prolong_jacobi<T, 2><<<gp, 256, 0, s>>>(plev(l), L.X(), L.pw, C.X(), C.nx, C.ny, L.f, T(1) - omega_s, L.Xo());
     L.cur ^= 1;
     count(1);
     for (int k = 1; k < nu; ++k) jacobi(l, s);
@@ -849,13 +849,12 @@ void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s, const double* in,
     auto& F0 = sm.lv[0];
     sm.nlaunch = &h->launches;
     k_precond_out_schur<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, zvx, zvy, in, in_stride, out,
-                                                                   out_stride, d_idx, F0.f, isw, F0.idg, sm.omega_s,
-                                                                   F0.x);
+                                                                   out_stride, d_idx, F0.f, isw, F0.widg, F0.x);
     sm.cycle(0, s);
     const dim3 g2 = grid2(h->nx, h->ny, kBlk2);
     k_schur_grad<T><<<g2, kBlk2, 0, s>>>(L0.gt, F0.X(), sm.wix, sm.wiy, L0.rx, L0.ry);
     k_schur_lw<T, T><<<g2, kBlk2, 0, s>>>(L0.gt, L0.rx, L0.ry, L0.en, L0.ec, sm.wix, sm.wiy, L0.fx, L0.fy);
-    k_schur_div<T><<<SchurMG<T>::nb(F0.n), 256, 0, s>>>(L0.gt, L0.fx, L0.fy, F0.f, F0.idg, sm.omega_s, F0.x);
+    k_schur_div<T><<<SchurMG<T>::nb(F0.n), 256, 0, s>>>(L0.gt, L0.fx, L0.fy, F0.f, F0.widg, F0.x);
     sm.cycle(0, s);
     k_schur_out<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, F0.X(), h->o.alpha_p, out, out_stride, d_idx,
                                                            h->part2);
