@@ -465,18 +465,23 @@ __global__ void k_schur_grad(GeomT<T> g, const T* __restrict__ t, const T* __res
   uy[c] = oy;
 }
 
-// w = W^-1 (-L u) at the velocity unknowns (homogeneous boundary rules), 0 elsewhere
+// w = W^-1 (-L u) at the velocity unknowns (homogeneous boundary rules), 0 elsewhere. With the
+// finest velocity level's precomputed coefficient planes (kc, the FP64 path) L u is formed from
+// them: about half the FP64 operations of the form from the viscosity, on a path bound by the FP64
+// rate.
 template <typename T, typename SE>
 __global__ void k_schur_lw(GeomT<T> g, const T* __restrict__ ux, const T* __restrict__ uy, const SE* __restrict__ en,
                            const SE* __restrict__ ec, const T* __restrict__ wix, const T* __restrict__ wiy,
-                           T* __restrict__ wx, T* __restrict__ wy) {
+                           T* __restrict__ wx, T* __restrict__ wy, Coef<T> kc) {
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (i > g.ny + 1 || j > g.nx + 1) return;
   const size_t c = (size_t)i * g.ld + j;
   T ox = T(0), oy = T(0), d;
-  if (is_vx(g.nx, g.ny, i, j)) ox = -lx_point<T>(g, i, j, ux, uy, en, ec, d) * wix[c];
-  if (is_vy(g.nx, g.ny, i, j)) oy = -ly_point<T>(g, i, j, ux, uy, en, ec, d) * wiy[c];
+  if (is_vx(g.nx, g.ny, i, j))
+    ox = -(kc.cxx ? lx_coef<T>(g, i, j, ux, uy, kc) : lx_point<T>(g, i, j, ux, uy, en, ec, d)) * wix[c];
+  if (is_vy(g.nx, g.ny, i, j))
+    oy = -(kc.cxx ? ly_coef<T>(g, i, j, ux, uy, kc) : ly_point<T>(g, i, j, ux, uy, en, ec, d)) * wiy[c];
   wx[c] = ox;
   wy[c] = oy;
 }

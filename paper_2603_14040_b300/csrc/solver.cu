@@ -853,7 +853,7 @@ void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s, const double* in,
     sm.cycle(0, s);
     const dim3 g2 = grid2(h->nx, h->ny, kBlk2);
     k_schur_grad<T><<<g2, kBlk2, 0, s>>>(L0.gt, F0.X(), sm.wix, sm.wiy, L0.rx, L0.ry);
-    k_schur_lw<T, T><<<g2, kBlk2, 0, s>>>(L0.gt, L0.rx, L0.ry, L0.en, L0.ec, sm.wix, sm.wiy, L0.fx, L0.fy);
+    k_schur_lw<T, T><<<g2, kBlk2, 0, s>>>(L0.gt, L0.rx, L0.ry, L0.en, L0.ec, sm.wix, sm.wiy, L0.fx, L0.fy, L0.kc);
     k_schur_div<T><<<SchurMG<T>::nb(F0.n), 256, 0, s>>>(L0.gt, L0.fx, L0.fy, F0.f, F0.widg, F0.x);
     sm.cycle(0, s);
     k_schur_out<T, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, F0.X(), h->o.alpha_p, out, out_stride, d_idx,
