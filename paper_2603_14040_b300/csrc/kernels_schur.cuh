@@ -202,22 +202,27 @@ __global__ void k_schur_prow(PLev<T> L, int nxc, int nyc, T omega_p, T* __restri
   }
 }
 
-// Galerkin coarse operator K_c = P^T K P into 25 planes (+ the diagonal and omega / diagonal). Sixteen
-// threads per coarse cell, one per fine cell of its 4 x 4 window, each summing that fine cell's
-// contributions P(a, K) K(a, b) P(b, J); then a fixed-order shuffle sum over the sixteen (half a
-// warp). One thread per coarse cell left the small levels of the set-up latency-bound on a few SMs.
+// Galerkin coarse operator K_c = P^T K P into 25 planes (+ the diagonal and omega / diagonal).
+// Sixteen threads per coarse cell, one per fine cell of its 4 x 4 window, each summing that fine
+// cell's contributions P(a, K) K(a, b) P(b, J) into its own 25 slots in shared memory (a register
+// array indexed by the coupling would live in local memory); then each of the sixteen sums slots
+// sub and sub + 16 over the sixteen partials, in a fixed order. One thread per coarse cell left the
+// small levels of the set-up latency-bound on a few SMs. Launched with kSchurRapThreads threads and
+// kSchurRapThreads * 25 * sizeof(T) bytes of dynamic shared memory.
+constexpr int kSchurRapThreads = 128;
 template <typename T>
-__global__ void __launch_bounds__(256) k_schur_rap(PLev<T> L, const T* __restrict__ pw, int nxc, int nyc,
-                                                   T* __restrict__ box, T* __restrict__ cdiag, T* __restrict__ cwidg,
-                                                   T omega) {
+__global__ void __launch_bounds__(kSchurRapThreads) k_schur_rap(PLev<T> L, const T* __restrict__ pw, int nxc,
+                                                                int nyc, T* __restrict__ box, T* __restrict__ cdiag,
+                                                                T* __restrict__ cwidg, T omega) {
+  extern __shared__ __align__(16) unsigned char rap_raw[];
+  T* sacc = reinterpret_cast<T*>(rap_raw);
+  T* acc = sacc + (size_t)threadIdx.x * kSchurBox;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int K0 = gt >> 4, sub = gt & 15;
   const int nc = nxc * nyc;
-  const bool active = K0 < nc;   // the sixteen threads of a coarse cell form one half-warp
+  const bool active = K0 < nc;
   const int I = active ? K0 / nxc : 0, J = active ? K0 % nxc : 0;
   const int n = L.nx * L.ny;
-  T acc[kSchurBox];
-#pragma unroll
   for (int q = 0; q < kSchurBox; ++q) acc[q] = T(0);
   const int ai = 2 * I - 1 + (sub >> 2), aj = 2 * J - 1 + (sub & 3);
   if (active && ai >= 0 && ai < L.ny && aj >= 0 && aj < L.nx) {
@@ -242,14 +247,18 @@ __global__ void __launch_bounds__(256) k_schur_rap(PLev<T> L, const T* __restric
         }
     }
   }
-#pragma unroll
-  for (int q = 0; q < kSchurBox; ++q)
-    for (int o = 8; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-  if (!active || sub != 0) return;
-#pragma unroll
-  for (int q = 0; q < kSchurBox; ++q) box[(size_t)q * nc + K0] = acc[q];
-  cdiag[K0] = acc[12];
-  cwidg[K0] = acc[12] > T(0) ? omega / acc[12] : T(0);
+  __syncthreads();
+  if (!active) return;
+  const T* cell = sacc + (size_t)(threadIdx.x - sub) * kSchurBox;   // the cell's first thread's slots
+  for (int q = sub; q < kSchurBox; q += 16) {
+    T t = T(0);
+    for (int u = 0; u < 16; ++u) t += cell[u * kSchurBox + q];
+    box[(size_t)q * nc + K0] = t;
+    if (q == 12) {
+      cdiag[K0] = t;
+      cwidg[K0] = t > T(0) ? omega / t : T(0);
+    }
+  }
 }
 
 // One damped Jacobi sweep x_out = x_in + omega (f - K x_in) / diag, formed as

@@ -634,7 +634,9 @@ struct SchurMG {
       const Lv& F = lv[l];
       Lv& C = lv[l + 1];
       k_schur_prow<T><<<nb(F.n), 256, 0, s>>>(plev((int)l), C.nx, C.ny, omega_p, F.pw);
-      k_schur_rap<T><<<nb(16 * C.n), 256, 0, s>>>(plev((int)l), F.pw, C.nx, C.ny, C.box, C.diag, C.widg, omega_s);
+      k_schur_rap<T><<<(unsigned)((16 * C.n + kSchurRapThreads - 1) / kSchurRapThreads), kSchurRapThreads,
+                       kSchurRapThreads * kSchurBox * sizeof(T), s>>>(plev((int)l), F.pw, C.nx, C.ny, C.box, C.diag,
+                                                                      C.widg, omega_s);
     }
     k_schur_coarse_assemble<T><<<1, 1024, 0, s>>>(plev((int)lv.size() - 1), Ainv);
     if (nc > kCoarseInvertMulti) {
