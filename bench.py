@@ -547,21 +547,24 @@ def serving_sweep(n_req=40, slots=4, sizes=(128, 256, 512, 1024), seed=4, nu=8, 
     return out
 
 
-def adjoint_sample(members=64, n=512, slots=4):
+def adjoint_sample(members=64, n=512, slots=4, opts=None):
     """The adjoint batch: 64 members on 512^2 (log10 eta random fields, seeds 500..563), each a forward
     solve, J = 1/2 |vx(top row) - vx_obs|^2, an adjoint solve and the strain-rate products, chained to
     dJ/dlog(eta) (dJ/dlog eta = eta dJ/deta; the same arithmetic as the torch.autograd.Function, called
     directly so that members on different handles run concurrently instead of queueing behind the
     autograd engine's device thread). Members are spread over `slots` handles, each on its own host
     thread and CUDA stream; the batch is also run on one slot. The observation solves (eta perturbed
-    by 10^(0.1 xi)) are outside the timed region. Mixed precision, tol 1e-10."""
+    by 10^(0.1 xi)) are outside the timed region. Mixed precision, tol 1e-10, with the mixed
+    headline's weighted BFBt options (the adjoint solve uses the forward solve's operator and
+    preconditioner); the batch on `slots` handles with the paper's eta_c block is timed beside it."""
+    opts = dict(MIXED_OPTS if opts is None else opts)
     import threading
     import torch
     import paper_2603_14040_b300 as P
     from synth import adjoint_member
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     data = []
-    hobs = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=3000)
+    hobs = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=3000, **opts)
     for b in range(members):
         base, pert = adjoint_member(b, n, n)
         obs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
@@ -588,8 +591,8 @@ def adjoint_sample(members=64, n=512, slots=4):
             rec[b] = {"ms": (time.perf_counter() - t0) * 1e3, "fwd_iters": sf.iters, "adj_iters": sa.iters,
                       "grad_norm": gnorm, "grad_n_norm": float(torch.linalg.norm(glog_n))}
 
-    def run(nslots):
-        hs = [P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=3000) for _ in range(nslots)]
+    def run(nslots, o=opts):
+        hs = [P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=3000, **o) for _ in range(nslots)]
         ss = [torch.cuda.Stream() for _ in range(nslots)]
         rec = {}
         for k in range(nslots):       # warm-up: capture each handle's iteration graph
@@ -612,10 +615,15 @@ def adjoint_sample(members=64, n=512, slots=4):
 
     wall1, rec1 = run(1)
     wallk, reck = run(slots)
+    wallp, recp = run(slots, {})
     ms = np.array([reck[b]["ms"] for b in range(members)])
     its = np.array([reck[b]["fwd_iters"] + reck[b]["adj_iters"] for b in range(members)])
     slow = int(np.argmax([rec1[b]["ms"] for b in range(members)]))
-    return {"members": members, "grid": n, "slots": slots, "batch_s": wallk, "batch_s_one_slot": wall1,
+    itp = np.array([recp[b]["fwd_iters"] + recp[b]["adj_iters"] for b in range(members)])
+    return {"members": members, "grid": n, "slots": slots, "solver_opts": opts, "batch_s": wallk,
+            "batch_s_one_slot": wall1,
+            "paper_block": {"batch_s": wallp, "members_per_s": members / wallp,
+                            "iters_fwd_plus_adj_p50": float(np.median(itp))},
             "overlap_speedup": wall1 / wallk, "members_per_s": members / wallk,
             "ms_per_member_one_slot": {"p50": float(np.percentile([rec1[b]["ms"] for b in range(members)], 50)),
                                        "max": float(max(rec1[b]["ms"] for b in range(members)))},

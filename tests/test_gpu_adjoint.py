@@ -21,9 +21,13 @@ def _case(n, seed, corr=0.2):
     return f, vx_obs
 
 
+@pytest.mark.parametrize("block", ["paper", "bfbt"])
 @pytest.mark.parametrize("bc", ["free", "noslip"])
 @pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
-def test_adjoint_matches_oracle_linearity(bc, prec):
+def test_adjoint_matches_oracle_linearity(bc, prec, block):
+    """The adjoint solve (the same symmetric operator and preconditioner as the forward solve) and
+    the strain-rate products against the oracle's gradient by assembly linearity, with the paper's
+    eta_c pressure block and with the weighted BFBt block."""
     n = 16
     kind = (S.FREE_SLIP,) * 4 if bc == "free" else (S.NO_SLIP,) * 4
     f, vx_obs = _case(n, 11)
@@ -38,7 +42,8 @@ def test_adjoint_matches_oracle_linearity(bc, prec):
     gn_o, gc_o = S.eta_gradient_by_linearity(g, f.eta_n, f.eta_c, x, lam)
     gr_o = S.rho_gradient_by_linearity(g, (0.0, 1.0), lam)
 
-    h = P.Stokes(n, n, bc=P.make_bc(kind), prec=prec)
+    opts = {} if block == "paper" else {"schur": 1, "alpha_p": 0.8}
+    h = P.Stokes(n, n, bc=P.make_bc(kind), prec=prec, **opts)
     out = [zeros(n, n) for _ in range(3)]
     h.solve(dev(f.eta_n), dev(f.eta_c), dev(f.rho), (0.0, 1.0), 1e-13, *out)
     dvx = np.zeros((n + 2, n + 2))

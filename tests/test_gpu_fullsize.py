@@ -43,6 +43,9 @@ import paper_2603_14040_b300 as P
 from paper_2603_14040_b300.autograd import stokes_solve, surface_misfit, node_from_cell
 
 G = (0.0, 1.0)
+# the adjoint workload's solver options: the paper's eta_c pressure block, or the weighted BFBt block
+# of the mixed headline (FGMRES(60), block scaled by 0.8, 16 x 16 coarsest velocity level)
+ADJ_OPTS = {"paper": {}, "bfbt": {"schur": 1, "restart_m": 60, "alpha_p": 0.8, "coarsest_min": 16}}
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
@@ -136,10 +139,11 @@ def test_layered_4096_mixed_operator_rows_only_match_oracle_windows():
     assert checked > 2000
 
 
-def test_adjoint_512_directional_derivatives_match_central_differences():
+@pytest.mark.parametrize("block", ["paper", "bfbt"])
+def test_adjoint_512_directional_derivatives_match_central_differences(block):
     n = 512
     base, pert = adjoint_member(0, n, n)
-    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=3000)
+    h = P.Stokes(n, n, prec=P.PREC_MIXED, max_iter=3000, **ADJ_OPTS[block])
     rho = dev(base.rho)
     obs_out = [zeros(n, n) for _ in range(3)]
     st = h.solve(dev(pert.eta_n), dev(pert.eta_c), rho, G, 1e-12, *obs_out)
@@ -213,18 +217,20 @@ def test_random_viscosity_1024_bfbt_matches_iterative_reference_elementwise(prec
     assert du <= 1e-8 and dp <= 1e-8, (du, dp)
 
 
+@pytest.mark.parametrize("block", ["paper", "bfbt"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_adjoint_member_512_forward_matches_iterative_reference_elementwise(prec):
+def test_adjoint_member_512_forward_matches_iterative_reference_elementwise(prec, block):
     n = 512
     base, _ = adjoint_member(0, n, n)
     g = S.Grid(n, n)
     xref, eref = _reference("adjoint512")
     assert eref <= 1e-13
-    out, st = _solve(base, n, 1e-12, prec=P.PREC_FP64 if prec == "fp64" else P.PREC_MIXED, max_iter=3000)
+    out, st = _solve(base, n, 1e-12, prec=P.PREC_FP64 if prec == "fp64" else P.PREC_MIXED, max_iter=3000,
+                     **ADJ_OPTS[block])
     assert st.status == P.PYRO_OK, st.as_dict()
     x = S.fields_to_vector(g, *(host(a) for a in out))
     du, dp = _errors(g, x, xref)
-    _record(f"adjoint512_{prec}_tol1e-12", {"du": du, "dp": dp, "iters": st.iters})
+    _record(f"adjoint512_{prec}_{block}_tol1e-12", {"du": du, "dp": dp, "iters": st.iters})
     assert du <= 1e-8 and dp <= 1e-8, (du, dp)
 
 
