@@ -547,6 +547,48 @@ def serving_sweep(n_req=40, slots=4, sizes=(128, 256, 512, 1024), seed=4, nu=8, 
     return out
 
 
+def serving_large_sample(seed=4, per_aspect=1, slots=4, nu=8, max_iter=3000):
+    """The n = 2048 rows of the serving distribution (ny = 2048, nx = a 2048, a in {1, 2, 4}: up to
+    16.8 M cells, 16 inclusions of contrast 10^U[2,6], tol 1e-8), served through the same server with
+    the whole memory budget open to one handle, so every request gets FGMRES(200) (up to 170 GB) and
+    the footprint admission runs one such request at a time. Reports per request: size, contrast,
+    restart, footprint, iterations, status (0: converged to tol) and the latency of the first solve of
+    its shape (handle creation and graph capture included) and of a second solve on the warm handle."""
+    import torch
+    from synth import serving_request
+    from paper_2603_14040_b300.serving import SolveServer, Request, PyroBackend
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    be = PyroBackend(opts_kw={"max_iter": max_iter, "prec": 1, "nu1": nu, "nu2": nu},
+                     restart_choices=(200, 100, 50, 30), per_handle_bytes=None)
+    be.per_handle_bytes = be.default_budget()
+    rows = []
+    k = 0
+    for a in (1, 2, 4):
+        for r in range(per_aspect):
+            f, C = serving_request(10_000 + k, base_seed=seed, force_n=2048, force_a=a)
+            k += 1
+            shape = (f.nx, f.ny, f.Lx, f.Ly)
+            rec = {"nx": f.nx, "ny": f.ny, "contrast": float(C), "restart_m": be.opts_for(shape)["restart_m"],
+                   "footprint_GB": be.footprint(shape) / 1e9}
+            srv = SolveServer(be, max_slots=slots)
+            for label in ("first", "warm"):
+                req = Request(rid=k, nx=f.nx, ny=f.ny, Lx=f.Lx, Ly=f.Ly, eta_n=dev(f.eta_n), eta_c=dev(f.eta_c),
+                              rho=dev(f.rho), g=(0.0, 1.0), tol=1e-8)
+                srv.submit(req)
+                srv.drain(timeout=3600)
+                rec[f"latency_ms_{label}"] = req.latency * 1e3
+                rec[f"iters_{label}"] = req.iters
+                rec[f"status_{label}"] = req.status
+                req.result = None
+            srv.close()
+            rows.append(rec)
+            print(json.dumps({"serving_large_row": rec}), flush=True)
+            del f
+            torch.cuda.empty_cache()
+    return {"requests": rows, "cycle": f"V({nu},{nu})", "tol": 1e-8,
+            "note": "n = 2048 rows of the serving distribution; one handle may take the whole budget"}
+
+
 def adjoint_sample(members=64, n=512, slots=4, opts=None):
     """The adjoint batch: 64 members on 512^2 (log10 eta random fields, seeds 500..563), each a forward
     solve, J = 1/2 |vx(top row) - vx_obs|^2, an adjoint solve and the strain-rate products, chained to
@@ -765,6 +807,8 @@ def main():
     ap.add_argument("--serving-sweep", action="store_true",
                     help="only the serving measurement on the config-4 request distribution (n <= 1024): capacity, "
                          "1-slot vs 4-slot saturation, arrival-rate sweep")
+    ap.add_argument("--serving-large", action="store_true",
+                    help="serve the n = 2048 rows of the serving distribution (one request per aspect) and exit")
     ap.add_argument("--config3", action="store_true",
                     help="only config 3 (4096^2 layered, mixed, weighted BFBt + inner CG): one solve, about 170 GB")
     ap.add_argument("--markers", action="store_true",
@@ -784,6 +828,9 @@ def main():
         return
     if args.serving_sweep:
         print(json.dumps({"serving_sweep": serving_sweep()}))
+        return
+    if args.serving_large:
+        print(json.dumps({"serving_large": serving_large_sample()}))
         return
     if args.impl == "reference":
         # the oracle runs on rank 0's host cores; the other ranks exit without work
