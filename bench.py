@@ -198,9 +198,9 @@ def vcycle_rooflines(peaks):
     # sweeps: smoothing sweeps (RBGS) or local Jacobi iterations (RAS) one launch performs for its
     # one HBM pass; effective = sweeps x algorithmic bytes of one sweep / launch time
     for key, label, launches, sweeps, opts in [
-            ("rbgs_tiles_2_sweeps_default", "k_rbgs_tile_w<2,32> (2 RBGS sweeps per launch, the default)", 1, 2,
+            ("rbgs_tiles_2_sweeps_default", "k_rbgs_tile_w<2,48> (2 RBGS sweeps per launch, the default)", 1, 2,
              dict(tile_sweeps=2)),
-            ("rbgs_tiles_1_sweep", "k_rbgs_tile_w<1,32> (1 RBGS sweep per launch)", 2, 1, dict(tile_sweeps=1)),
+            ("rbgs_tiles_1_sweep", "k_rbgs_tile_w<1,48> (1 RBGS sweep per launch)", 2, 1, dict(tile_sweeps=1)),
             ("ras_inner_2", "k_ras_tile<float,32,32> (RAS pass of 2 local Jacobi iterations)", 1, 2,
              dict(smoother=2, ras_inner=2, omega_v=0.6)),
             ("ras_inner_4", "k_ras_tile<float,32,32> (RAS pass of 4 local Jacobi iterations, the paper's T_inner)",
