@@ -289,7 +289,7 @@ def layered_sample(n=1024, steps=3):
     return res
 
 
-def config3_sample(n=4096, max_iter=6000, restart_m=256, prec="mixed", **extra):
+def config3_sample(n=4096, max_iter=6000, restart_m=256, prec="mixed", schur=1, **extra):
     """Config 3 itself: the 4096^2 layered workload (lid 1e6 over a mantle with 64 inclusions of
     10^U[-3,3]) to relative energy residual 1e-10 with the weighted BFBt pressure block, 5 inner
     flexible-CG steps and FGMRES(restart_m), V(4,4). In FP64 it converges (2746-3328 iterations and
@@ -305,7 +305,7 @@ def config3_sample(n=4096, max_iter=6000, restart_m=256, prec="mixed", **extra):
     en, ec, rho = dev(f.eta_n), dev(f.eta_c), dev(f.rho)
     del f
     outs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
-    h = P.Stokes(n, n, prec=P.PREC_MIXED if prec == "mixed" else P.PREC_FP64, schur=1, inner_cg=5,
+    h = P.Stokes(n, n, prec=P.PREC_MIXED if prec == "mixed" else P.PREC_FP64, schur=schur, inner_cg=5,
                  restart_m=restart_m, nu1=4, nu2=4, max_iter=max_iter, **extra)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -313,7 +313,7 @@ def config3_sample(n=4096, max_iter=6000, restart_m=256, prec="mixed", **extra):
     st = h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
     e1.record()
     torch.cuda.synchronize()
-    res = {"grid": [n, n], "options": f"{prec}, schur=1, inner_cg=5, restart_m={restart_m}, V(4,4), tol 1e-10, {extra}",
+    res = {"grid": [n, n], "options": f"{prec}, schur={schur}, inner_cg=5, restart_m={restart_m}, V(4,4), tol 1e-10, {extra}",
            "ms": e0.elapsed_time(e1), "iters": st.iters, "restarts": st.restarts, "status": st.status,
            "rel_energy_res": st.rel_energy_res, "rel_l2_res": st.rel_l2_res,
            "footprint_GB": P.footprint(n, n, h.opts) / 1e9, "note": "first solve (includes the graph captures)"}

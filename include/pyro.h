@@ -171,7 +171,9 @@ typedef struct {
                             W^-1 G) K^-1 (r_p - D z_v) with K = D W^-1 G, W = diag(-L)^(1/2), each K^-1
                             one V-cycle of a smoothed-aggregation multigrid on the cell grid (2 x 2
                             aggregates, Galerkin coarse operators in a 5 x 5-box stencil, damped Jacobi
-                            smoothing, dense coarsest inverse); 0 or 1 [0] */
+                            smoothing, dense coarsest inverse); 2 the same block computed in FP64 also
+                            when the V-cycle is FP32 (mixed precision; in FP64 mode the same as 1);
+                            0..2 [0] */
   int galerkin;          /* 1: every coarse level reached by halving takes the Galerkin operator R L P of
                             the level above it (the V-cycle's own restriction and prolongation; a
                             31-point stencil per velocity unknown) instead of the re-discretised

@@ -519,11 +519,11 @@ namespace pyro {
 // As k_precond_out for the velocity planes of Z_j; instead of the diagonal surrogate, y = r_p - D z_v
 // goes to the finest pressure grid (compact) for the Schur surrogate, with the pressure cycle's first
 // Jacobi sweep from zero x0 = (omega / diag_0) y, and Z_j's pressure plane is left for k_schur_out.
-template <typename T, typename TZ>
+template <typename T, typename TZ, typename TS = T>
 __global__ void k_precond_out_schur(GeomT<double> g, const T* __restrict__ vx, const T* __restrict__ vy,
                                     const double* __restrict__ V, size_t vstride, TZ* __restrict__ Z, size_t stride,
-                                    const int* __restrict__ d_j, T* __restrict__ y, const double* __restrict__ isw,
-                                    const T* __restrict__ widg0, T* __restrict__ x0) {
+                                    const int* __restrict__ d_j, TS* __restrict__ y, const double* __restrict__ isw,
+                                    const TS* __restrict__ widg0, TS* __restrict__ x0) {
   const size_t P = (size_t)(g.ny + 2) * g.ld;
   const double* v = V + (size_t)(*d_j) * vstride;
   TZ* z = Z + (size_t)(*d_j) * stride;
@@ -542,7 +542,7 @@ __global__ void k_precond_out_schur(GeomT<double> g, const T* __restrict__ vx, c
       const double div = (ux - uxw) * g.idx + (uy - uyn) * g.idy;
       const double rp = isw ? v[2 * P + e] * isw[2 * P + e] : v[2 * P + e];
       const size_t k = (size_t)(i - 1) * g.nx + (j - 1);
-      const T yk = (T)(rp - div);
+      const TS yk = (TS)(rp - div);
       y[k] = yk;
       x0[k] = yk * widg0[k];
     }

@@ -752,8 +752,9 @@ struct pyro_stokes_s {
   int* hflag = nullptr;
   MG<float> mgf;
   MG<double> mgd;
-  SchurMG<float> smf;                        // weighted BFBt pressure block (option schur = 1)
-  SchurMG<double> smd;
+  SchurMG<float> smf;                        // weighted BFBt pressure block (option schur = 1, mixed)
+  SchurMG<double> smd;                       // the same block in FP64 (FP64 mode, or schur = 2)
+  double* sc64 = nullptr;                    // schur = 2 in mixed mode: FP64 middle-product planes (4 P)
   InnerCG ic;                                 // inner flexible CG on the finest velocity level
   std::vector<cudaGraphExec_t> graphs;       // captured iteration graphs (per Krylov column with MGS)
   std::vector<long long> graph_kernel_counts;
@@ -845,7 +846,35 @@ void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s, const double* in,
   }
   mg.hooks = nullptr;
   h->launches += 3;
-  if (h->o.schur) {
+  bool schur_done = false;
+  if constexpr (sizeof(T) == 4) {
+    if (h->o.schur == 2) {
+      // the weighted BFBt block in FP64 after the FP32 V-cycle: the same steps as below on the FP64
+      // pressure hierarchy, the middle product on the FP64 viscosity and outer coefficient planes
+      SchurMG<double>& sm = h->smd;
+      auto& F0 = sm.lv[0];
+      sm.nlaunch = &h->launches;
+      double* ux = h->sc64;
+      double* uy = ux + h->P;
+      double* wx = uy + h->P;
+      double* wy = wx + h->P;
+      k_precond_out_schur<T, TZ, double><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, zvx, zvy, in, in_stride, out,
+                                                                            out_stride, d_idx, F0.f, isw, F0.widg,
+                                                                            F0.x);
+      sm.cycle(0, s);
+      const dim3 g2 = grid2(h->nx, h->ny, kBlk2);
+      k_schur_grad<double><<<g2, kBlk2, 0, s>>>(h->g64, F0.X(), sm.wix, sm.wiy, ux, uy);
+      k_schur_lw<double, double><<<g2, kBlk2, 0, s>>>(h->g64, ux, uy, h->en, h->ec, sm.wix, sm.wiy, wx, wy, h->okc);
+      k_schur_div<double><<<SchurMG<double>::nb(F0.n), 256, 0, s>>>(h->g64, wx, wy, F0.f, F0.widg, F0.x);
+      sm.cycle(0, s);
+      k_schur_out<double, TZ><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, F0.X(), h->o.alpha_p, out, out_stride,
+                                                                  d_idx, h->part2);
+      h->launches += 4;
+      schur_done = true;
+    }
+  }
+  if (schur_done) {
+  } else if (h->o.schur) {
     // weighted BFBt pressure block: z_p = alpha K^-1 (D W^-1 (-L) W^-1 G) K^-1 (r_p - D z_v)
     SchurMG<T>& sm = schur_of<T>(h);
     auto& F0 = sm.lv[0];
@@ -1114,9 +1143,12 @@ void setup_eta(pyro_stokes_s* h, cudaStream_t s) {
     h->launches += 2;
     h->mgf.nlaunch = &h->launches;
     h->mgf.setup(s, h->flag);
-    if (h->o.schur) {
+    if (h->o.schur == 1) {
       h->smf.nlaunch = &h->launches;
       h->smf.setup(L0.gt, L0.en, L0.ec, s, h->flag);
+    } else if (h->o.schur == 2) {
+      h->smd.nlaunch = &h->launches;
+      h->smd.setup(h->g64, h->en, h->ec, s, h->flag);
     }
   } else {
     h->mgd.nlaunch = &h->launches;
@@ -1475,7 +1507,7 @@ bool opts_valid(const pyro_opts& o) {
          o.accel <= PYRO_ACCEL_ANDERSON && o.aa_beta > 0.0 && o.aa_beta <= 1.0 && o.smoother >= PYRO_SMOOTH_RBGS &&
          o.smoother <= PYRO_SMOOTH_MIXED && o.ras_inner >= 1 && o.cont_stages >= 0 && o.cont_iters >= 1 &&
          o.coarse_sweeps >= 1 && o.coarsen_ratio >= 1.5 && o.coarsen_ratio <= 8.0 &&
-         o.gram_schmidt >= 0 && o.gram_schmidt <= 2 && (o.schur == 0 || o.schur == 1) &&
+         o.gram_schmidt >= 0 && o.gram_schmidt <= 2 && o.schur >= 0 && o.schur <= 2 &&
          (o.galerkin == 0 || (o.galerkin == 1 && o.kcycle == 0 && o.cluster_cells <= 0)) && o.inner_cg >= 0 &&
          o.inner_cg <= 16;
 }
@@ -1508,7 +1540,8 @@ size_t footprint_bytes(int nx, int ny, const pyro_opts& o, int L) {
   (void)L;
   const auto sz = sizes_of(nx, ny, o);
   b += mixed ? MG<float>::bytes(sz, o.kcycle, o.galerkin) : MG<double>::bytes(sz, o.kcycle, o.galerkin) - 2 * P * 8;
-  if (o.schur) b += mixed ? SchurMG<float>::bytes(nx, ny, P) : SchurMG<double>::bytes(nx, ny, P);
+  if (o.schur) b += (mixed && o.schur == 1) ? SchurMG<float>::bytes(nx, ny, P) : SchurMG<double>::bytes(nx, ny, P);
+  if (mixed && o.schur == 2) b += 4 * P * 8;   // FP64 middle-product planes
   if (o.inner_cg) b += InnerCG::bytes(P);
   b += 2 * (kMaxRestart + 2) * 8 + 2 * (size_t)kReduceBlocks * (kMaxRestart + 1) * 8 + 4 * kReduceBlocks * 8 +
        (size_t)kMaxRestart * kHcolStride * 8 + 64;
@@ -1654,7 +1687,11 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       if (h->mgf.tiles) MG<float>::enable_tiles();
       CK(cudaDeviceSynchronize());
       h->mgf.alloc(A, h->g, Lx, Ly, sizes_of(nx, ny, o), false);
-      if (o.schur) h->smf.alloc(A, nx, ny, h->P);
+      if (o.schur == 1) h->smf.alloc(A, nx, ny, h->P);
+      if (o.schur == 2) {
+        h->smd.alloc(A, nx, ny, h->P);
+        h->sc64 = A.get<double>(4 * h->P);
+      }
       if (o.inner_cg) h->ic.alloc(A, h->P);
     } else {
       h->mgd.nu1 = o.nu1; h->mgd.nu2 = o.nu2; h->mgd.omega = o.omega_v; h->mgd.eta_mode = o.eta_coarsen;

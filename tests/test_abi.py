@@ -53,7 +53,7 @@ def test_host_logic_without_gpu():
                                 dict(ras_inner=0), dict(max_iter=0), dict(coarsen_ratio=1.2), dict(coarse_sweeps=0),
                                 dict(cont_iters=0), dict(coarsest_min=0),
                                 dict(gram_schmidt=3), dict(tile_fusion=2), dict(tile_fusion=3),
-                                dict(cluster_cells=4096), dict(schur=2), dict(galerkin=2),
+                                dict(cluster_cells=4096), dict(schur=3), dict(galerkin=2),
                                 dict(galerkin=1, kcycle=2), dict(inner_cg=-1), dict(inner_cg=17)])
 def test_options_outside_their_range_are_rejected_not_clamped(kw):
     """pyro_stokes_footprint (host logic, no GPU) answers 0 for an option outside its documented

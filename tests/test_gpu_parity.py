@@ -400,30 +400,31 @@ def test_memory_of_another_gpu_is_rejected():
 @pytest.mark.parametrize("nx,ny,Lx,Ly", [(2, 2, 1, 1), (16, 16, 1, 1), (37, 23, 1.2, 0.8), (48, 80, 0.6, 1.0),
                                          (64, 16, 4, 1), (256, 128, 2, 1)])
 @pytest.mark.parametrize("bc", list(BCS))
-@pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
-def test_preconditioner_weighted_bfbt_matches_oracle(nx, ny, Lx, Ly, bc, prec):
+@pytest.mark.parametrize("prec,schur", [(P.PREC_FP64, 1), (P.PREC_MIXED, 1), (P.PREC_MIXED, 2)])
+def test_preconditioner_weighted_bfbt_matches_oracle(nx, ny, Lx, Ly, bc, prec, schur):
     """The weighted BFBt pressure block (face weights diag(-L)^(-1/2), the smoothed-aggregation
     pressure cycle with its Galerkin 5 x 5-box coarse operators and dense coarsest inverse, the
     middle product D W^-1 (-L) W^-1 G), step by step against the oracle, on even, odd and
-    elongated grids (one to five pressure levels) and every boundary combination."""
-    gpu, ora, nlev = _precond_case(nx, ny, Lx, Ly, bc, prec, 31, schur=1, coarsen_general=1)
+    elongated grids (one to five pressure levels) and every boundary combination; in mixed
+    precision computed in FP32 (schur 1) or in FP64 after the FP32 V-cycle (schur 2)."""
+    gpu, ora, nlev = _precond_case(nx, ny, Lx, Ly, bc, prec, 31, schur=schur, coarsen_general=1)
     for a, b in zip(gpu, ora):
         assert rel(a, b) <= (1e-10 if prec == P.PREC_FP64 else 2e-4), (rel(a, b), nlev)
 
 
-@pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
-def test_preconditioner_weighted_bfbt_on_the_layered_field_matches_oracle(prec):
+@pytest.mark.parametrize("prec,schur", [(P.PREC_FP64, 1), (P.PREC_MIXED, 1), (P.PREC_MIXED, 2)])
+def test_preconditioner_weighted_bfbt_on_the_layered_field_matches_oracle(prec, schur):
     nx, ny = 64, 48
     f = layered_config(nx, ny, seed=3, Lx=1.0, Ly=0.75)
     gpu, ora, nlev = _precond_case(nx, ny, 1.0, 0.75, "free", prec, 37, eta=(f.eta_n, f.eta_c), eta_coarsen=1,
-                                   schur=1)
+                                   schur=schur)
     for a, b in zip(gpu, ora):
         # FP32: the cycle's rounding is amplified by the field's contrast (1e9)
         assert rel(a, b) <= (1e-10 if prec == P.PREC_FP64 else 5e-3), (rel(a, b), nlev)
 
 
-@pytest.mark.parametrize("prec", [P.PREC_FP64, P.PREC_MIXED])
-def test_weighted_bfbt_solve_of_the_layered_field_matches_direct_oracle(prec):
+@pytest.mark.parametrize("prec,schur", [(P.PREC_FP64, 1), (P.PREC_MIXED, 1), (P.PREC_MIXED, 2)])
+def test_weighted_bfbt_solve_of_the_layered_field_matches_direct_oracle(prec, schur):
     """FGMRES with the weighted BFBt pressure block on the lid + inclusions field (viscosity 1e-3 ..
     1e6) converges to 1e-10 and matches the direct solve."""
     n = 64
@@ -431,7 +432,7 @@ def test_weighted_bfbt_solve_of_the_layered_field_matches_direct_oracle(prec):
     g = S.Grid(n, n)
     sysm = S.assemble(g, f.eta_n, f.eta_c, f.rho, (0.0, 1.0))
     xd = S.remove_pressure_mean(g, S.solve_direct(sysm))
-    h = P.Stokes(n, n, prec=prec, schur=1, restart_m=256, max_iter=2000, eta_coarsen=1, nu1=4, nu2=4)
+    h = P.Stokes(n, n, prec=prec, schur=schur, restart_m=256, max_iter=2000, eta_coarsen=1, nu1=4, nu2=4)
     out = [zeros(n, n) for _ in range(3)]
     st = h.solve(dev(f.eta_n), dev(f.eta_c), dev(f.rho), (0.0, 1.0), 1e-10, *out)
     torch.cuda.synchronize()
