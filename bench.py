@@ -255,7 +255,8 @@ def accelerator_sample(f, n, steps=3):
 def layered_sample(n=1024, steps=3):
     """The layered workload's recipe (stiff lid 1e6, mantle 1 +- 50 %, 64 inclusions 10^U[-3,3]) at
     n x n, solved to 1e-10 with the options that converge on it: weighted BFBt pressure block, 5
-    inner flexible-CG steps per preconditioner application, FGMRES(200), V(4,4); mixed and FP64."""
+    inner flexible-CG steps per preconditioner application, FGMRES(200), V(4,4); mixed (the block in
+    FP32, and in FP64 after the FP32 V-cycle: schur 2, the form that converges at 4096^2) and FP64."""
     import torch
     import paper_2603_14040_b300 as P
     from synth import layered_config
@@ -265,11 +266,11 @@ def layered_sample(n=1024, steps=3):
     outs = [torch.zeros((n + 2, n + 2), dtype=torch.float64, device="cuda") for _ in range(3)]
     res = {"grid": [n, n], "options": "schur=1 (weighted BFBt), inner_cg=5, restart_m=200, V(4,4), tol 1e-10"}
     sols = {}
-    for prec, name in ((P.PREC_MIXED, "mixed"), (P.PREC_FP64, "fp64")):
-        h = P.Stokes(n, n, prec=prec, schur=1, inner_cg=5, restart_m=200, nu1=4, nu2=4, max_iter=3000)
+    for prec, name, sc in ((P.PREC_MIXED, "mixed", 1), (P.PREC_MIXED, "mixed_schur2", 2), (P.PREC_FP64, "fp64", 1)):
+        h = P.Stokes(n, n, prec=prec, schur=sc, inner_cg=5, restart_m=200, nu1=4, nu2=4, max_iter=3000)
         h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
         ts = []
-        for _ in range(steps if name == "mixed" else 1):
+        for _ in range(steps if name != "fp64" else 1):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record()
@@ -281,6 +282,11 @@ def layered_sample(n=1024, steps=3):
         res[name] = {"ms": float(np.median(ts)), "solves_per_s": 1e3 / float(np.median(ts)), "iters": st.iters,
                      "status": st.status, "rel_energy_res": st.rel_energy_res}
         h.close()
+    c = sols["mixed_schur2"]
+    res["rel_diff_mixed_schur2_vs_fp64_v"] = float(
+        torch.linalg.norm(torch.cat([c[0].flatten(), c[1].flatten()]) - torch.cat([sols["fp64"][0].flatten(),
+                                                                                   sols["fp64"][1].flatten()])) /
+        torch.linalg.norm(torch.cat([sols["fp64"][0].flatten(), sols["fp64"][1].flatten()])))
     a, b = sols["mixed"], sols["fp64"]
     res["rel_diff_mixed_vs_fp64_v"] = float(torch.linalg.norm(torch.cat([a[0].flatten(), a[1].flatten()]) -
                                                               torch.cat([b[0].flatten(), b[1].flatten()])) /
@@ -799,7 +805,8 @@ def main():
     ap.add_argument("--omega", type=float, default=1.0, help="pyro_opts.omega_v of the --profile solve")
     ap.add_argument("--accel", type=int, default=0, help="pyro_opts.accel of the --profile solve")
     ap.add_argument("--workload", default="grf", choices=["grf", "layered"], help="field of the --profile solve")
-    ap.add_argument("--schur", type=int, default=0, help="pyro_opts.schur of the --profile solve")
+    ap.add_argument("--schur", type=int, default=0,
+                    help="pyro_opts.schur of the --profile solve; of the --config3 solve when non-zero")
     ap.add_argument("--inner-cg", type=int, default=0, help="pyro_opts.inner_cg of the --profile solve")
     ap.add_argument("--nu", type=int, default=2, help="pre/post smoothing sweeps of the --profile solve")
     ap.add_argument("--alpha-p", type=float, default=1.0, help="pyro_opts.alpha_p of the --profile solve")
@@ -824,7 +831,9 @@ def main():
         print(json.dumps({"markers": marker_sample(reps=1)}))
         return
     if args.config3:
-        print(json.dumps({"config3": config3_sample(prec=args.prec)}))
+        # mixed precision keeps the pressure block in FP64 (schur 2) unless --schur says otherwise
+        sc = args.schur if args.schur else (2 if args.prec == "mixed" else 1)
+        print(json.dumps({"config3": config3_sample(prec=args.prec, schur=sc)}))
         return
     if args.serving_sweep:
         print(json.dumps({"serving_sweep": serving_sweep()}))
