@@ -256,7 +256,8 @@ def layered_sample(n=1024, steps=3):
     """The layered workload's recipe (stiff lid 1e6, mantle 1 +- 50 %, 64 inclusions 10^U[-3,3]) at
     n x n, solved to 1e-10 with the options that converge on it: weighted BFBt pressure block, 5
     inner flexible-CG steps per preconditioner application, FGMRES(200), V(4,4); mixed (the block in
-    FP32, and in FP64 after the FP32 V-cycle: schur 2, the form that converges at 4096^2) and FP64."""
+    FP32; and the block in FP64 after the FP32 V-cycle with the finest residual in FP64: schur 2,
+    res64, the form that converges at 4096^2) and FP64."""
     import torch
     import paper_2603_14040_b300 as P
     from synth import layered_config
@@ -267,7 +268,8 @@ def layered_sample(n=1024, steps=3):
     res = {"grid": [n, n], "options": "schur=1 (weighted BFBt), inner_cg=5, restart_m=200, V(4,4), tol 1e-10"}
     sols = {}
     for prec, name, sc in ((P.PREC_MIXED, "mixed", 1), (P.PREC_MIXED, "mixed_schur2", 2), (P.PREC_FP64, "fp64", 1)):
-        h = P.Stokes(n, n, prec=prec, schur=sc, inner_cg=5, restart_m=200, nu1=4, nu2=4, max_iter=3000)
+        h = P.Stokes(n, n, prec=prec, schur=sc, inner_cg=5, restart_m=200, nu1=4, nu2=4, max_iter=3000,
+                     res64=1 if sc == 2 else 0)
         h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
         ts = []
         for _ in range(steps if name != "fp64" else 1):
@@ -831,9 +833,11 @@ def main():
         print(json.dumps({"markers": marker_sample(reps=1)}))
         return
     if args.config3:
-        # mixed precision keeps the pressure block in FP64 (schur 2) unless --schur says otherwise
+        # mixed precision keeps the pressure block in FP64 (schur 2) unless --schur says otherwise,
+        # and forms its finest V-cycle residual in FP64 (res64)
         sc = args.schur if args.schur else (2 if args.prec == "mixed" else 1)
-        print(json.dumps({"config3": config3_sample(prec=args.prec, schur=sc)}))
+        extra = {"res64": 1} if args.prec == "mixed" else {}
+        print(json.dumps({"config3": config3_sample(prec=args.prec, schur=sc, **extra)}))
         return
     if args.serving_sweep:
         print(json.dumps({"serving_sweep": serving_sweep()}))

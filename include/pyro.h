@@ -190,6 +190,12 @@ typedef struct {
                             viscosity that jumps by orders
                             of magnitude a single cycle leaves most of the velocity error, and each
                             outer Krylov iteration saved also saves its orthogonalisation; 0..16 [0] */
+  int res64;             /* mixed precision: 1 forms the finest level's V-cycle residual (the one the
+                            restriction passes down) in FP64, from the FP32 iterate and right-hand side
+                            with the FP64 outer operator, and rounds it to FP32 once; smoothing stays
+                            FP32. Not in the paper: where viscosity jumps by many orders of magnitude
+                            the FP32 residual cancels terms of eta / h^2. Ignored in FP64 mode; 0 or 1
+                            [0] */
 } pyro_opts;
 
 typedef struct {

@@ -156,6 +156,26 @@ __global__ void k_vresidual(GeomT<T> g, const T* __restrict__ vx, const T* __res
   else vresid_point<T>(g, i, j, vx, vy, fx, fy, en, ec, rx, ry, Coef<T>{});
 }
 
+// r = f - L x on the finest level of an FP32 cycle with the products and sums formed in FP64: x
+// and f are read in their storage type, L is the FP64 outer operator (its precomputed coefficient
+// planes), and r is rounded to the storage type once. Where viscosity jumps by many orders of
+// magnitude the FP32 form cancels terms of eta / h^2 against each other; this form keeps the
+// residual of the stored iterate exact to FP64 before the restriction.
+template <typename T>
+__global__ void k_vresidual64(GeomT<double> g, const T* __restrict__ vx, const T* __restrict__ vy,
+                              const T* __restrict__ fx, const T* __restrict__ fy, Coef<double> kc,
+                              T* __restrict__ rx, T* __restrict__ ry) {
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > g.ny + 1 || j > g.nx + 1) return;
+  const size_t c = (size_t)i * g.ld + j;
+  double ox = 0.0, oy = 0.0;
+  if (is_vx(g.nx, g.ny, i, j)) ox = (double)fx[c] - lx_coef<double>(g, i, j, vx, vy, kc);
+  if (is_vy(g.nx, g.ny, i, j)) oy = (double)fy[c] - ly_coef<double>(g, i, j, vx, vy, kc);
+  rx[c] = (T)ox;
+  ry[c] = (T)oy;
+}
+
 template <typename T>
 __device__ inline void restrict_point(const GeomT<T>& gf, const GeomT<T>& gc, int I, int J, const T* rx,
                                       const T* ry, T* fxc, T* fyc) {

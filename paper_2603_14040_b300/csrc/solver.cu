@@ -161,6 +161,9 @@ struct MG {
   int kcycle = 0;  // levels l < kcycle get their coarse correction from two flexible-CG steps
   bool tiles = true;                        // tile-fused smoothing / residual+restriction
   int tile_form = 0;                        // FP32 large levels: 0 warp-per-row tiles, 1 64 x 32 colour-split
+  bool res64 = false;                       // FP32 cycles: finest residual formed in FP64 (option res64)
+  GeomT<double> r64_g{};                    // ... with the FP64 outer operator's geometry and coefficients
+  Coef<double> r64_kc{};
   int smoother = PYRO_SMOOTH_RBGS;          // velocity smoother (MIXED: Jacobi on level 0, RAS below)
   int ras_inner = 4;                        // RAS-type Jacobi: local iterations per tile pass
   int tile_sweeps = 2;                      // FP32: sweeps fused per tile launch
@@ -493,7 +496,21 @@ struct MG {
     const bool fz = fused(l);
     smooth(l, nu1, nullptr, 0, s);
     if (l == 0 && hooks) CK(cudaEventRecordWithFlags(hooks[2], s, cudaEventRecordExternal));
-    if (fz && f2[l]) {
+    bool restricted = false;
+    if constexpr (sizeof(T) == 4) {
+      if (l == 0 && res64 && f2[0] && !L.gal) {
+        // finest residual of the FP32 cycle formed in FP64 (option res64), then the restriction
+        k_vresidual64<T><<<grid2(L.g.nx, L.g.ny, blk(L)), blk(L), 0, s>>>(r64_g, L.X(), L.Y(), L.fx, L.fy, r64_kc,
+                                                                           L.rx, L.ry);
+        k_restrict<T><<<grid2(C.g.nx, C.g.ny, blk(C)), blk(C), 0, s>>>(L.gt, C.gt, L.rx, L.ry, C.fx, C.fy, C.vx,
+                                                                         C.vy);   // also zeroes the coarse iterate
+        count(2);
+        C.cur = 0;
+        restricted = true;
+      }
+    }
+    if (restricted) {
+    } else if (fz && f2[l]) {
       resrestrict_tiles(l, s);  // also zeroes the coarse iterate
     } else if (!f2[l]) {
       if (L.gal)
@@ -1509,7 +1526,7 @@ bool opts_valid(const pyro_opts& o) {
          o.coarse_sweeps >= 1 && o.coarsen_ratio >= 1.5 && o.coarsen_ratio <= 8.0 &&
          o.gram_schmidt >= 0 && o.gram_schmidt <= 2 && o.schur >= 0 && o.schur <= 2 &&
          (o.galerkin == 0 || (o.galerkin == 1 && o.kcycle == 0 && o.cluster_cells <= 0)) && o.inner_cg >= 0 &&
-         o.inner_cg <= 16;
+         o.inner_cg <= 16 && (o.res64 == 0 || o.res64 == 1);
 }
 
 std::vector<std::pair<int, int>> sizes_of(int nx, int ny, const pyro_opts& o) {
@@ -1585,6 +1602,7 @@ void pyro_default_opts(pyro_opts* o) {
   o->schur = 0;
   o->galerkin = 0;
   o->inner_cg = 0;
+  o->res64 = 0;
 }
 
 const char* pyro_version(void) { return "pyro-b300 0.1 (sm_103a)"; }
@@ -1687,6 +1705,9 @@ int pyro_stokes_create(int nx, int ny, double Lx, double Ly, const pyro_bc* bc, 
       if (h->mgf.tiles) MG<float>::enable_tiles();
       CK(cudaDeviceSynchronize());
       h->mgf.alloc(A, h->g, Lx, Ly, sizes_of(nx, ny, o), false);
+      h->mgf.res64 = o.res64 != 0;
+      h->mgf.r64_g = h->g64;
+      h->mgf.r64_kc = h->okc;
       if (o.schur == 1) h->smf.alloc(A, nx, ny, h->P);
       if (o.schur == 2) {
         h->smd.alloc(A, nx, ny, h->P);

@@ -37,7 +37,7 @@ class PyroOpts(ctypes.Structure):
                 ("litho_guess", ctypes.c_int), ("cont_stages", ctypes.c_int), ("cont_iters", ctypes.c_int),
                 ("coarse_sweeps", ctypes.c_int), ("coarsen_ratio", ctypes.c_double),
                 ("coarsen_general", ctypes.c_int), ("gram_schmidt", ctypes.c_int), ("schur", ctypes.c_int),
-                ("galerkin", ctypes.c_int), ("inner_cg", ctypes.c_int)]
+                ("galerkin", ctypes.c_int), ("inner_cg", ctypes.c_int), ("res64", ctypes.c_int)]
 
 
 class PyroStats(ctypes.Structure):

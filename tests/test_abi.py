@@ -54,7 +54,7 @@ def test_host_logic_without_gpu():
                                 dict(cont_iters=0), dict(coarsest_min=0),
                                 dict(gram_schmidt=3), dict(tile_fusion=2), dict(tile_fusion=3),
                                 dict(cluster_cells=4096), dict(schur=3), dict(galerkin=2),
-                                dict(galerkin=1, kcycle=2), dict(inner_cg=-1), dict(inner_cg=17)])
+                                dict(galerkin=1, kcycle=2), dict(inner_cg=-1), dict(inner_cg=17), dict(res64=2)])
 def test_options_outside_their_range_are_rejected_not_clamped(kw):
     """pyro_stokes_footprint (host logic, no GPU) answers 0 for an option outside its documented
     range, as pyro_stokes_create answers PYRO_E_INVALID; the same options in range are served."""

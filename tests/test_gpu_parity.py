@@ -43,7 +43,7 @@ def test_apply_matches_oracle(nx, ny, Lx, Ly, bc):
 
 def _precond_case(nx, ny, Lx, Ly, bc, prec, seed, kcycle=0, cluster_cells=0, tile_fusion=1, eta_coarsen=0,
                   eta=None, smoother=0, ras_inner=4, omega=1.0, coarsen_general=1, coarsen_ratio=2.0, schur=0,
-                  galerkin=0, inner_cg=0):
+                  galerkin=0, inner_cg=0, res64=0):
     kind, vt = BCS[bc]
     g = S.Grid(nx, ny, Lx, Ly, S.BC(kind, vt))
     en, ec = rand_eta(nx, ny, seed, -1, 1) if eta is None else eta
@@ -60,7 +60,7 @@ def _precond_case(nx, ny, Lx, Ly, bc, prec, seed, kcycle=0, cluster_cells=0, til
     h = P.Stokes(nx, ny, Lx, Ly, bc=P.make_bc(kind, vt), prec=prec, kcycle=kcycle, cluster_cells=cluster_cells,
                  tile_fusion=tile_fusion, tile_fusion64=1 if tile_fusion else 0, eta_coarsen=eta_coarsen, coarsest_min=2,
                  smoother=smoother, ras_inner=ras_inner, omega_v=omega, coarsen_general=coarsen_general,
-                 coarsen_ratio=coarsen_ratio, schur=schur, galerkin=galerkin, inner_cg=inner_cg)
+                 coarsen_ratio=coarsen_ratio, schur=schur, galerkin=galerkin, inner_cg=inner_cg, res64=res64)
     Zx, Zy, Zp = zeros(ny, nx), zeros(ny, nx), zeros(ny, nx)
     h.precond(dev(en), dev(ec), dev(rx), dev(ry), dev(rp), Zx, Zy, Zp)
     torch.cuda.synchronize()
@@ -187,6 +187,18 @@ def test_preconditioner_kcycle_fp64_matches_oracle(nx, ny, Lx, Ly, kc, cc, tf):
 @pytest.mark.parametrize("tf", [0, 1, 4])
 def test_preconditioner_fp32_close_to_oracle(nx, ny, tf):
     gpu, ora, _ = _precond_case(nx, ny, 1.0, 1.0, "free", P.PREC_MIXED, 5, tile_fusion=tf)
+    for a, b in zip(gpu, ora):
+        assert rel(a, b) <= 2e-4
+
+
+@pytest.mark.parametrize("nx,ny,bc", [(16, 16, "free"), (48, 80, "noslip"), (37, 23, "mixed"), (320, 192, "free"),
+                                      (512, 386, "noslip")])
+@pytest.mark.parametrize("tf", [0, 1])
+def test_preconditioner_fp32_with_fp64_finest_residual_close_to_oracle(nx, ny, bc, tf):
+    """Mixed precision with the finest V-cycle residual formed in FP64 (option res64): the same
+    preconditioner as the oracle's to FP32 rounding, on even, odd and ragged grids and every
+    boundary kind, with the tile kernels and with one kernel per colour."""
+    gpu, ora, _ = _precond_case(nx, ny, 1.0, ny / nx, bc, P.PREC_MIXED, 7, tile_fusion=tf, res64=1)
     for a, b in zip(gpu, ora):
         assert rel(a, b) <= 2e-4
 
@@ -412,12 +424,13 @@ def test_preconditioner_weighted_bfbt_matches_oracle(nx, ny, Lx, Ly, bc, prec, s
         assert rel(a, b) <= (1e-10 if prec == P.PREC_FP64 else 2e-4), (rel(a, b), nlev)
 
 
-@pytest.mark.parametrize("prec,schur", [(P.PREC_FP64, 1), (P.PREC_MIXED, 1), (P.PREC_MIXED, 2)])
-def test_preconditioner_weighted_bfbt_on_the_layered_field_matches_oracle(prec, schur):
+@pytest.mark.parametrize("prec,schur,res64", [(P.PREC_FP64, 1, 0), (P.PREC_MIXED, 1, 0), (P.PREC_MIXED, 2, 0),
+                                              (P.PREC_MIXED, 2, 1)])
+def test_preconditioner_weighted_bfbt_on_the_layered_field_matches_oracle(prec, schur, res64):
     nx, ny = 64, 48
     f = layered_config(nx, ny, seed=3, Lx=1.0, Ly=0.75)
     gpu, ora, nlev = _precond_case(nx, ny, 1.0, 0.75, "free", prec, 37, eta=(f.eta_n, f.eta_c), eta_coarsen=1,
-                                   schur=schur)
+                                   schur=schur, res64=res64)
     for a, b in zip(gpu, ora):
         # FP32: the cycle's rounding is amplified by the field's contrast (1e9)
         assert rel(a, b) <= (1e-10 if prec == P.PREC_FP64 else 5e-3), (rel(a, b), nlev)
