@@ -300,11 +300,11 @@ def layered_sample(n=1024, steps=3):
 def config3_sample(n=4096, max_iter=6000, restart_m=256, prec="mixed", schur=1, **extra):
     """Config 3 itself: the 4096^2 layered workload (lid 1e6 over a mantle with 64 inclusions of
     10^U[-3,3]) to relative energy residual 1e-10 with the weighted BFBt pressure block, 5 inner
-    flexible-CG steps and FGMRES(restart_m), V(4,4). In FP64 it converges (2746-3328 iterations and
-    318-379 s on a B300 across builds whose pressure-cycle rounding differs); with the FP32 V-cycle
-    of the mixed mode it does not, nor in FP64 with the random-field tuning (pressure scaling 0.8,
-    16 x 16 coarsest level: 1.4e-8 after 4000 iterations). `extra` passes further solver options.
-    One timed solve (it includes the graph captures); about 220 GB on the device at restart 256."""
+    flexible-CG steps and FGMRES(restart_m), V(4,4). FP64 converges in 2527 iterations (284 s on a
+    B300); mixed precision converges with the block in FP64 (schur 2) and the finest V-cycle residual
+    in FP64 (res64) in 3072 iterations (253 s), the V-cycle otherwise FP32; with the block in FP32 it
+    stalls near 6e-6. `extra` passes further solver options. One timed solve (it includes the graph
+    captures); about 220 GB on the device at restart 256."""
     import torch
     import paper_2603_14040_b300 as P
     from synth import layered_config
