@@ -194,8 +194,9 @@ typedef struct {
                             restriction passes down) in FP64, from the FP32 iterate and right-hand side
                             with the FP64 outer operator, and rounds it to FP32 once; smoothing stays
                             FP32. Not in the paper: where viscosity jumps by many orders of magnitude
-                            the FP32 residual cancels terms of eta / h^2. Ignored in FP64 mode; 0 or 1
-                            [0] */
+                            the FP32 residual cancels terms of eta / h^2. Takes effect when the first
+                            coarsening halves the grid (otherwise the FP32 residual is kept); ignored
+                            in FP64 mode; 0 or 1 [0] */
 } pyro_opts;
 
 typedef struct {
