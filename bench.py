@@ -171,8 +171,9 @@ def vcycle_roofline_4096(peaks, iters=6, label="", launches=1, **opts):
     h.close()
     del outs, en, ec, rho
     torch.cuda.empty_cache()
-    # the whole V-cycle against SURVEY 8(d)'s algorithmic bytes: 208 B per fine cell for V(2,2) over all
-    # levels when fused (FP32), scaled by the sweeps per level
+    # the whole V-cycle against its algorithmic bytes: 208 B per fine cell for V(2,2) over all levels
+    # when fused (FP32: 32 B per smoothing pass of a level, the residual-restriction and the
+    # prolongation, summed over the levels' 4/3 geometric series), scaled by the sweeps per level
     vcycle_ms = (ph["l0_pre_smooth"] + ph["coarse_levels"] + ph["l0_post_smooth"]) / it
     nu = opts.get("nu1", 2)
     vbytes = (208.0 + (nu - 2) * 2 * 32 * 4.0 / 3.0) * cells
@@ -925,7 +926,7 @@ def main():
 
     # roofline of the FP64 smoother (the largest share after the Gram-Schmidt step): finest-level RBGS sweep (4 launches vx-red, vx-black, vy-red,
     # vy-black), FP64. Algorithmic per cell and sweep: read eta_n, eta_c, fx, fy, vx, vy + write vx,
-    # vy = 64 B; arithmetic: per velocity point the off-diagonal sum on precomputed
+    # vy = 64 B in FP64; arithmetic: per velocity point the off-diagonal sum on precomputed
     # coefficients (6 products, 2 differences, 5 sums) and the update (2) = 15 flop, 30 per cell.
     # B300's FP64 rate binds it, so the bound is the FP64 rate measured in this run.
     peaks = load_peaks()
