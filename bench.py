@@ -172,8 +172,9 @@ def vcycle_roofline_4096(peaks, iters=6, label="", launches=1, **opts):
     del outs, en, ec, rho
     torch.cuda.empty_cache()
     # the whole V-cycle against its algorithmic bytes: 208 B per fine cell for V(2,2) over all levels
-    # when fused (FP32: 32 B per smoothing pass of a level, the residual-restriction and the
-    # prolongation, summed over the levels' 4/3 geometric series), scaled by the sweeps per level
+    # when fused (FP32, per level: 32 B per RBGS sweep x 4 sweeps, 26 B for the residual-restriction,
+    # about 2 B for the prolongation fused into the post-sweep, about 156 B, times 4/3 for the
+    # coarser levels), scaled by the sweeps per level
     vcycle_ms = (ph["l0_pre_smooth"] + ph["coarse_levels"] + ph["l0_post_smooth"]) / it
     nu = opts.get("nu1", 2)
     vbytes = (208.0 + (nu - 2) * 2 * 32 * 4.0 / 3.0) * cells
