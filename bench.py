@@ -728,8 +728,8 @@ def profile_solve(args):
     prec = P.PREC_MIXED if args.prec == "mixed" else P.PREC_FP64
     h = P.Stokes(n, n, prec=prec, max_iter=args.max_iter, restart_m=args.restart, tile_fusion=args.tile_fusion,
                  tile_sweeps=args.tile_sweeps, smoother=args.smoother, omega_v=args.omega, accel=args.accel,
-                 schur=args.schur, inner_cg=args.inner_cg, nu1=args.nu, nu2=args.nu, alpha_p=args.alpha_p,
-                 coarsest_min=args.coarsest_min)
+                 schur=args.schur, inner_cg=args.inner_cg, res64=args.res64, nu1=args.nu, nu2=args.nu,
+                 alpha_p=args.alpha_p, coarsest_min=args.coarsest_min)
     st = h.solve(en, ec, rho, (0.0, 1.0), 1e-10, *outs)
     torch.cuda.synchronize()
     print(json.dumps({"profile_solve": n, "workload": args.workload, "prec": args.prec, "iters": st.iters,
@@ -812,6 +812,7 @@ def main():
     ap.add_argument("--schur", type=int, default=0,
                     help="pyro_opts.schur of the --profile solve; of the --config3 solve when non-zero")
     ap.add_argument("--inner-cg", type=int, default=0, help="pyro_opts.inner_cg of the --profile solve")
+    ap.add_argument("--res64", type=int, default=0, help="pyro_opts.res64 of the --profile solve")
     ap.add_argument("--nu", type=int, default=2, help="pre/post smoothing sweeps of the --profile solve")
     ap.add_argument("--alpha-p", type=float, default=1.0, help="pyro_opts.alpha_p of the --profile solve")
     ap.add_argument("--coarsest-min", type=int, default=4, help="pyro_opts.coarsest_min of the --profile solve")
