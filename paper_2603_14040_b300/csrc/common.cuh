@@ -81,6 +81,19 @@ __host__ __device__ inline bool is_vx(int nx, int ny, int i, int j) { return i >
 __host__ __device__ inline bool is_vy(int nx, int ny, int i, int j) { return i >= 1 && i <= ny - 1 && j >= 1 && j <= nx; }
 __host__ __device__ inline bool is_p(int nx, int ny, int i, int j) { return i >= 1 && i <= ny && j >= 1 && j <= nx; }
 
+// Row and column of entry e of a row-major array with `cols` columns. A 32-bit division when e fits
+// in 32 bits (every grid a device can hold), instead of the much longer 64-bit division sequence.
+__device__ __forceinline__ void row_col(size_t e, int cols, int& i, int& j) {
+  if (e <= 0xffffffffull) {
+    const unsigned u = (unsigned)e, c = (unsigned)cols, q = u / c;
+    i = (int)q;
+    j = (int)(u - q * c);
+  } else {
+    i = (int)(e / (size_t)cols);
+    j = (int)(e % (size_t)cols);
+  }
+}
+
 // vx value with walls masked (used where a reference may land on a wall column)
 template <typename T, typename S>
 __device__ inline T ldvx(const S* vx, int ld, int nx, int i, int j) {

@@ -27,26 +27,28 @@ __device__ inline void fcg_block_sum(double v, double* sh, double* part) {
   }
 }
 
-// w = L z at the velocity unknowns (0 elsewhere; FP64 operator and viscosity) and block partials of
-// z . q (previous q)
+// w = L z at the velocity unknowns (0 elsewhere; the FP64 operator, from the outer operator's
+// precomputed coefficient planes when given: about a third fewer FP64 operations than from the
+// viscosity, on a pass bound by the FP64 rate) and block partials of z . q (previous q)
 template <typename TZ>
 __global__ void k_fcg_apply(GeomT<double> g, const TZ* __restrict__ zx, const TZ* __restrict__ zy,
-                            const double* __restrict__ en, const double* __restrict__ ec, const double* __restrict__ qx,
-                            const double* __restrict__ qy, double* __restrict__ wx, double* __restrict__ wy, int first,
-                            double* __restrict__ part) {
+                            const double* __restrict__ en, const double* __restrict__ ec, Coef<double> kc,
+                            const double* __restrict__ qx, const double* __restrict__ qy, double* __restrict__ wx,
+                            double* __restrict__ wy, int first, double* __restrict__ part) {
   __shared__ double sh[32];
   const size_t P = (size_t)(g.ny + 2) * g.ld;
   const int cols = g.nx + 2;
   double acc = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / cols), j = (int)(e % cols);
+    int i, j;
+    row_col(e, cols, i, j);
     double ox = 0.0, oy = 0.0, d;
     if (is_vx(g.nx, g.ny, i, j)) {
-      ox = lx_point<double>(g, i, j, zx, zy, en, ec, d);
+      ox = kc.cxx ? lx_coef<double>(g, i, j, zx, zy, kc) : lx_point<double>(g, i, j, zx, zy, en, ec, d);
       if (!first) acc += (double)zx[e] * qx[e];
     }
     if (is_vy(g.nx, g.ny, i, j)) {
-      oy = ly_point<double>(g, i, j, zx, zy, en, ec, d);
+      oy = kc.cxx ? ly_coef<double>(g, i, j, zx, zy, kc) : ly_point<double>(g, i, j, zx, zy, en, ec, d);
       if (!first) acc += (double)zy[e] * qy[e];
     }
     wx[e] = ox;
@@ -84,7 +86,8 @@ __global__ void k_fcg_orth(GeomT<double> g, const TZ* __restrict__ zx, const TZ*
   const double beta = first ? 0.0 : scal[0];
   double a1 = 0.0, a2 = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / cols), j = (int)(e % cols);
+    int i, j;
+    row_col(e, cols, i, j);
     double nx_ = 0.0, ny_ = 0.0, mx = 0.0, my = 0.0;
     if (is_vx(g.nx, g.ny, i, j)) {
       nx_ = first ? (double)zx[e] : (double)zx[e] - beta * dx[e];

@@ -102,7 +102,8 @@ __global__ void k_residual(GeomT<double> g, const double* __restrict__ en, const
   const int rows = g.ny + 2, cols = g.nx + 2;
   double sw = 0.0, s2 = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / cols), j = (int)(e % cols);
+    int i, j;
+    row_col(e, cols, i, j);
     if (i >= rows) break;
     double ox, oy, op;
     stokes_point<double>(g, i, j, en, ec, x, x + P, x + 2 * P, ox, oy, op, kc);
@@ -488,7 +489,8 @@ __global__ void k_precond_out(GeomT<double> g, const T* __restrict__ vx, const T
   const int cols = g.nx + 2;
   double acc = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / cols), j = (int)(e % cols);
+    int i, j;
+    row_col(e, cols, i, j);
     const TZ zx = is_vx(g.nx, g.ny, i, j) ? (TZ)vx[e] : TZ(0);
     const TZ zy = is_vy(g.nx, g.ny, i, j) ? (TZ)vy[e] : TZ(0);
     z[e] = zx;
@@ -529,7 +531,8 @@ __global__ void k_sub_mean(GeomT<double> g, TZ* __restrict__ Zp0, size_t stride,
   const size_t P = (size_t)(g.ny + 2) * g.ld;
   const int cols = g.nx + 2;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / cols), j = (int)(e % cols);
+    int i, j;
+    row_col(e, cols, i, j);
     if (is_p(g.nx, g.ny, i, j)) zp[e] = (TZ)((double)zp[e] - mean);
   }
 }
@@ -541,7 +544,8 @@ __global__ void k_psum(GeomT<double> g, const double* __restrict__ p, double* __
   const int cols = g.nx + 2;
   double acc = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / cols), j = (int)(e % cols);
+    int i, j;
+    row_col(e, cols, i, j);
     if (is_p(g.nx, g.ny, i, j)) acc += p[e];
   }
   const double s = block_sum(acc, sh);
@@ -644,7 +648,8 @@ __global__ void k_eta_min(GeomT<double> g, const double* __restrict__ en, const 
   const int cols = g.nx + 2;
   double m = INFINITY;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / cols), j = (int)(e % cols);
+    int i, j;
+    row_col(e, cols, i, j);
     if (i <= g.ny && j <= g.nx) m = fmin(m, en[e]);
     if (is_p(g.nx, g.ny, i, j)) m = fmin(m, ec[e]);
   }
@@ -664,7 +669,8 @@ __global__ void k_eta_blend(GeomT<double> g, const double* __restrict__ en_full,
   const size_t P = (size_t)(g.ny + 2) * g.ld;
   const int cols = g.nx + 2;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / cols), j = (int)(e % cols);
+    int i, j;
+    row_col(e, cols, i, j);
     en[e] = (i <= g.ny && j <= g.nx) ? (1.0 - theta) * emin + theta * en_full[e] : en_full[e];
     ec[e] = is_p(g.nx, g.ny, i, j) ? (1.0 - theta) * emin + theta * ec_full[e] : ec_full[e];
   }

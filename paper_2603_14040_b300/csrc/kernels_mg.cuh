@@ -387,7 +387,8 @@ __global__ void k_kc_step1(GeomT<T> g, const T* __restrict__ xx, const T* __rest
   const int cols = g.nx + 2;
   double a = 0.0, b = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / cols), j = (int)(e % cols);
+    int i, j;
+    row_col(e, cols, i, j);
     T d, qx = T(0), qy = T(0), zx = T(0), zy = T(0);
     if (is_vx(g.nx, g.ny, i, j)) { zx = xx[e]; qx = lx_point<T>(g, i, j, xx, xy, en, ec, d); }
     if (is_vy(g.nx, g.ny, i, j)) { zy = xy[e]; qy = ly_point<T>(g, i, j, xx, xy, en, ec, d); }
@@ -440,7 +441,8 @@ __global__ void k_kc_step2(GeomT<T> g, const T* __restrict__ xx, const T* __rest
   const int cols = g.nx + 2;
   double a = 0.0, b = 0.0, c = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / cols), j = (int)(e % cols);
+    int i, j;
+    row_col(e, cols, i, j);
     T d;
     if (is_vx(g.nx, g.ny, i, j)) {
       const T z = xx[e], Lz = lx_point<T>(g, i, j, xx, xy, en, ec, d);

@@ -529,7 +529,8 @@ __global__ void k_precond_out_schur(GeomT<double> g, const T* __restrict__ vx, c
   TZ* z = Z + (size_t)(*d_j) * stride;
   const int cols = g.nx + 2;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / cols), j = (int)(e % cols);
+    int i, j;
+    row_col(e, cols, i, j);
     const TZ zx = is_vx(g.nx, g.ny, i, j) ? (TZ)vx[e] : TZ(0);
     const TZ zy = is_vy(g.nx, g.ny, i, j) ? (TZ)vy[e] : TZ(0);
     z[e] = zx;
@@ -560,7 +561,8 @@ __global__ void k_schur_out(GeomT<double> g, const T* __restrict__ t, double alp
   const int cols = g.nx + 2;
   double acc = 0.0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / cols), j = (int)(e % cols);
+    int i, j;
+    row_col(e, cols, i, j);
     double v = 0.0;
     if (is_p(g.nx, g.ny, i, j)) {
       v = (double)(TZ)(alpha * (double)t[(size_t)(i - 1) * g.nx + (j - 1)]);
