@@ -27,14 +27,13 @@ __device__ inline void fcg_block_sum(double v, double* sh, double* part) {
   }
 }
 
-// w = L z at the velocity unknowns (0 elsewhere; the FP64 operator, from the outer operator's
-// precomputed coefficient planes when given: about a third fewer FP64 operations than from the
-// viscosity, on a pass bound by the FP64 rate) and block partials of z . q (previous q)
+// w = L z at the velocity unknowns (0 elsewhere; FP64 operator and viscosity) and block partials of
+// z . q (previous q)
 template <typename TZ>
 __global__ void k_fcg_apply(GeomT<double> g, const TZ* __restrict__ zx, const TZ* __restrict__ zy,
-                            const double* __restrict__ en, const double* __restrict__ ec, Coef<double> kc,
-                            const double* __restrict__ qx, const double* __restrict__ qy, double* __restrict__ wx,
-                            double* __restrict__ wy, int first, double* __restrict__ part) {
+                            const double* __restrict__ en, const double* __restrict__ ec, const double* __restrict__ qx,
+                            const double* __restrict__ qy, double* __restrict__ wx, double* __restrict__ wy, int first,
+                            double* __restrict__ part) {
   __shared__ double sh[32];
   const size_t P = (size_t)(g.ny + 2) * g.ld;
   const int cols = g.nx + 2;
@@ -44,11 +43,11 @@ __global__ void k_fcg_apply(GeomT<double> g, const TZ* __restrict__ zx, const TZ
     row_col(e, cols, i, j);
     double ox = 0.0, oy = 0.0, d;
     if (is_vx(g.nx, g.ny, i, j)) {
-      ox = kc.cxx ? lx_coef<double>(g, i, j, zx, zy, kc) : lx_point<double>(g, i, j, zx, zy, en, ec, d);
+      ox = lx_point<double>(g, i, j, zx, zy, en, ec, d);
       if (!first) acc += (double)zx[e] * qx[e];
     }
     if (is_vy(g.nx, g.ny, i, j)) {
-      oy = kc.cxx ? ly_coef<double>(g, i, j, zx, zy, kc) : ly_point<double>(g, i, j, zx, zy, en, ec, d);
+      oy = ly_point<double>(g, i, j, zx, zy, en, ec, d);
       if (!first) acc += (double)zy[e] * qy[e];
     }
     wx[e] = ox;

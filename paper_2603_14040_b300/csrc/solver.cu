@@ -841,8 +841,8 @@ void precond_body(pyro_stokes_s* h, MG<T>& mg, cudaStream_t s, const double* in,
       if (!first) k_fcg_load<T><<<kReduceBlocks, kThreads, 0, s>>>(L0.P, ic.rx, ic.ry, L0.fx, L0.fy, L0.vx, L0.vy);
       mg.cycle(0, s);
       mg.hooks = nullptr;
-      k_fcg_apply<T><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->en, h->ec, h->okc, ic.qx, ic.qy,
-                                                        ic.wx, ic.wy, first, ic.part);
+      k_fcg_apply<T><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), h->en, h->ec, ic.qx, ic.qy, ic.wx,
+                                                        ic.wy, first, ic.part);
       k_fcg_beta<<<1, kThreads, 0, s>>>(ic.part, kReduceBlocks, first, ic.scal);
       k_fcg_orth<T><<<kReduceBlocks, kThreads, 0, s>>>(h->g64, L0.X(), L0.Y(), ic.wx, ic.wy, ic.rx, ic.ry, ic.dx,
                                                        ic.dy, ic.qx, ic.qy, ic.scal, first, ic.part);
